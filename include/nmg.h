@@ -1,0 +1,203 @@
+/*
+ * nmg.h -- C ABI of the GB300 neural multigrid solver.
+ *
+ * The library solves A u = f for many right-hand sides f with the neural
+ * multigrid cycle of the paper "A level-wise training scheme for learning
+ * neural multigrid smoothers with application to integral equations":
+ * NMGF1d (Algorithm 3) in 1D and NMGF2d (Algorithm 4) in 2D, iterated as
+ * x^tau = NMGF(x^{tau-1}, f) from x^0 = 0 (Section 3.2) until the relative
+ * residual ||f - A u|| / ||f|| reaches a tolerance.  As in the paper's
+ * statement of the problem (Section 5: the matrix is fixed, only the
+ * right-hand sides vary), a hierarchy is set up once from the kernel, grid,
+ * regularisation weight, level count and frozen smoother weights, and then
+ * solves any number of batches.
+ *
+ * Conventions for every entry point:
+ *  - All functions return an nmg_status; no C++ exception crosses the ABI.
+ *    Argument errors are detected before any kernel launch and leave device
+ *    buffers untouched.  The text of the last error of a context is kept
+ *    in nmg_last_error().
+ *  - "device" pointers are CUDA device pointers on the context's device;
+ *    work is ordered on the context's stream.  Functions that report values
+ *    to the host (nmg_solve's info, norms) synchronise that stream before
+ *    they return; the others are asynchronous.
+ *  - The caller owns every pointer it passes.  The library owns contexts,
+ *    hierarchies and their workspaces until the matching destroy call.
+ *  - Layouts are row-major: a batch of 2D grids is [batch][n][n], a batch
+ *    of 1D grids is [batch][n], contiguous.  In 2D the operator is
+ *    symmetric in both axes, so row-major storage of X is the paper's
+ *    column-major Vec(X) of Section 3.3 read transposed, with the same
+ *    operator.
+ *  - Element types follow the hierarchy's precision:
+ *      NMG_FP64          f, u, every level vector: double
+ *      NMG_FP32          f, u, every level vector: float
+ *      NMG_BF16_REFINE   f: float, u: double; level vectors of the inner
+ *                        cycle (step entry points): float.  The smoother
+ *                        runs on bf16 tensor cores with fp32 accumulation.
+ */
+#ifndef NMG_H
+#define NMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nmg_ctx nmg_ctx;   /* opaque: device, stream, error text */
+typedef struct nmg_hier nmg_hier; /* opaque: one operator's level hierarchy */
+
+typedef enum {
+  NMG_OK = 0,
+  NMG_ERR_ARG = -1,        /* invalid argument (null pointer, size, level) */
+  NMG_ERR_OOM = -2,        /* device allocation failed */
+  NMG_ERR_NOT_SPD = -3,    /* coarsest operator not positive definite */
+  NMG_ERR_CUDA = -4,       /* a CUDA call failed; see nmg_last_error */
+  NMG_ERR_TIMEOUT = -5,    /* a bounded device wait gave up */
+  NMG_ERR_WEIGHTS = -6,    /* smoother weights inconsistent with the desc */
+  NMG_ERR_UNSUPPORTED = -7 /* valid request this build does not implement */
+} nmg_status;
+
+/* per right-hand-side outcome, in nmg_solve_info.status */
+enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };
+
+typedef enum { NMG_FP64 = 0, NMG_FP32 = 1, NMG_BF16_REFINE = 2 } nmg_precision;
+
+/*
+ * Operator description (Section 2.1, Eq. (1); Eq. (10) in 1D; the
+ * Kronecker form alpha I(x)I + K(x)K of Section 4.2 in 2D).
+ *   dim      1 or 2
+ *   n        fine grid side; n % 2^(levels-1) == 0 (Section 2.3).  The
+ *            coarsest grid must have at most 4096 unknowns.
+ *   levels   L, counting the coarsest level; smoothers run on levels
+ *            1..L-1, the exact solve on level L.  levels >= 1.
+ *   alpha    regularisation weight (> 0 is not required, but the coarsest
+ *            Galerkin operator must be SPD or setup fails NMG_ERR_NOT_SPD)
+ *   taps     host array, copied at setup:
+ *              dim 1: ntaps == n, the first column t_0..t_{n-1} of the
+ *                     symmetric Toeplitz matrix (the discretised h*K);
+ *                     A_1 = Toeplitz(t) + alpha I
+ *              dim 2: ntaps == w+1, symmetric PSF taps g_0..g_w with
+ *                     K[i][j] = g_|i-j| for |i-j| <= w;
+ *                     A_1 = alpha I(x)I + K(x)K, zero boundary
+ *   precision  nmg_precision
+ *   filter   1: NMGF with the output filter F'_l (Algorithms 3/4);
+ *            0: no filter (Algorithm 2, x = x* + h)
+ * Coarse operators are Galerkin products A_{l+1} = R A_l P with linear
+ * interpolation P (coarse node J at fine 2J) and full weighting R = P^T/2
+ * per axis.
+ */
+typedef struct {
+  int dim;
+  int n;
+  int levels;
+  double alpha;
+  int ntaps;
+  const double* taps;
+  int precision;
+  int filter;
+} nmg_operator_desc;
+
+/*
+ * Smoother description: a CNN per smoother level (the paper's smoothers
+ * are neural operators, Section 3.1; here conv -> ReLU -> ... -> conv with
+ * zero 'same' padding and a bias on every layer).
+ *   layers   number of conv layers (>= 2); channels 1 -> width ->...-> 1
+ *   width    hidden channels (2D: 32; 1D: 16 in this build)
+ *   ksize    kernel size (2D: 3; 1D: 5 in this build)
+ *   nlevels  smoother levels present in `weights`; must be >= levels-1.
+ *            Only the first levels-1 are used (a coarsest level chosen
+ *            below the trained one, as in Section 4.3).
+ *   weights  host doubles, copied at setup.  For each level, for each
+ *            layer: W in PyTorch Conv layout [Cout][Cin][k] (1D) or
+ *            [Cout][Cin][k][k] (2D), then bias [Cout].
+ *   nweights total number of doubles in `weights` (checked).
+ */
+typedef struct {
+  int layers;
+  int width;
+  int ksize;
+  int nlevels;
+  const double* weights;
+  size_t nweights;
+} nmg_smoother_desc;
+
+typedef struct {
+  int cycles;     /* cycles applied before the tolerance was met */
+  int status;     /* NMG_CONVERGED / NMG_NOT_CONVERGED / NMG_DIVERGED */
+  double relres;  /* final ||f - A u|| / ||f|| (fp64 norm) */
+} nmg_solve_info;
+
+/* Create a context on CUDA device `device`.  stream: a cudaStream_t to
+ * order work on, or NULL for a library-owned non-blocking stream. */
+nmg_status nmg_create(nmg_ctx** ctx, int device, void* stream);
+void nmg_destroy(nmg_ctx* ctx);
+
+/* Build the hierarchy (host fp64 Galerkin products, device fp64 Cholesky
+ * of the coarsest operator, filter twiddles, packed weights).  Errors:
+ * NMG_ERR_ARG, NMG_ERR_WEIGHTS, NMG_ERR_NOT_SPD, NMG_ERR_OOM, NMG_ERR_CUDA. */
+nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op,
+                     const nmg_smoother_desc* sm, nmg_hier** out);
+void nmg_destroy_hier(nmg_hier* h);
+
+/* Solve A u = f for `batch` right-hand sides on the device.  u holds the
+ * initial guess on entry (zeros for the paper's x^0 = 0) and the solution on
+ * return.  A right-hand side stops receiving cycles once its relative
+ * residual is <= rtol.  info: host array [batch] or NULL.  Synchronous. */
+nmg_status nmg_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u,
+                     double rtol, int max_cycles, nmg_solve_info* info);
+
+/* Same as nmg_solve with HOST f and u: the library copies f (and u) to its
+ * own device buffers, solves, and copies u back.  Host buffers may be
+ * pageable or pinned.  Synchronous. */
+nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host,
+                          void* u_host, double rtol, int max_cycles,
+                          nmg_solve_info* info);
+
+/* Exactly one cycle u <- NMGF(u, f) at the finest level for every
+ * right-hand side (no convergence test).  Asynchronous. */
+nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u);
+
+/* ---- single steps of the cycle (level is 0-based: 0 is the paper's l=1) --
+ * Vectors are the hierarchy's level type (see above).  Asynchronous unless
+ * a host output is requested. */
+
+/* r = y - A_l x.  norms: host double[batch] receiving ||r||_2, or NULL. */
+nmg_status nmg_residual(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                        const void* x, const void* y, void* r, double* norms);
+/* yc = I_l^{l+1} (y - A_l x), yc on level l+1 (Algorithm 4, restriction). */
+nmg_status nmg_residual_restrict(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                                 const void* x, const void* y, void* yc);
+/* h = N_l(b / ||b||) ||b||, h = 0 where ||b|| = 0 (level < levels-1). */
+nmg_status nmg_smooth(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                      const void* b, void* hout);
+/* x = x* + F'_l(h) (filter on) or x* + h (filter off); xstar may be NULL
+ * (zero) and may alias x. */
+nmg_status nmg_filter_update(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                             const void* xstar, const void* hin, void* x);
+/* x = (A^(L))^{-1} y on the coarsest level (fp64 Cholesky solve). */
+nmg_status nmg_coarse_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* y, void* x);
+/* x += I_{l+1}^l e, e on level l+1, x on level l. */
+nmg_status nmg_prolong_correct(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                               const void* e, void* x);
+
+/* ---- inspection ------------------------------------------------------- */
+/* Level side length, band half-widths and precision. */
+nmg_status nmg_hier_info(const nmg_hier* h, int level, int* n, int* wK, int* wM,
+                         int* precision);
+/* Copy the level operator's 1D factors to host in dense form:
+ * 2D: K_l and M_l, each n_l x n_l row-major (M may be NULL);
+ * 1D: A_l (n_l x n_l) into K (M unused). */
+nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double* M);
+
+/* Number of kernels the library launched on this context so far. */
+long long nmg_launch_count(const nmg_ctx* ctx);
+/* Wait for the context's stream. */
+nmg_status nmg_sync(nmg_ctx* ctx);
+const char* nmg_status_str(nmg_status s);
+const char* nmg_last_error(const nmg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NMG_H */

@@ -1,0 +1,272 @@
+"""GB300 neural multigrid solver for convolution-type integral equations.
+
+A thin ctypes binding over the C ABI in ``include/nmg.h`` (library
+``_build/libnmg.so``, built by ``build.py``).  Every step of the solve runs in
+the library's CUDA kernels; this module only marshals arguments (torch
+tensors' device pointers, numpy host arrays) and raises on error codes.
+There is no CPU fallback: importing works without the library, but creating
+a ``Context`` fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+__all__ = [
+    "FP64", "FP32", "BF16_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
+    "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo",
+]
+
+FP64, FP32, BF16_REFINE = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE}
+CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libnmg.so")
+_lib = None
+
+
+class NMGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nmg error {code}: {msg}")
+        self.code = code
+
+
+class _OpDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("ntaps", ctypes.c_int),
+                ("taps", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int),
+                ("filter", ctypes.c_int)]
+
+
+class _SmDesc(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int), ("width", ctypes.c_int), ("ksize", ctypes.c_int),
+                ("nlevels", ctypes.c_int), ("weights", ctypes.POINTER(ctypes.c_double)),
+                ("nweights", ctypes.c_size_t)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libnmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2603_01064_gb300/build.py "
+                           "(or __graft_entry__.build()); there is no fallback path")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    sig = {
+        "nmg_create": (I, [ctypes.POINTER(P), I, P]),
+        "nmg_destroy": (V, [P]),
+        "nmg_setup": (I, [P, ctypes.POINTER(_OpDesc), ctypes.POINTER(_SmDesc), ctypes.POINTER(P)]),
+        "nmg_destroy_hier": (V, [P]),
+        "nmg_solve": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
+        "nmg_solve_host": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
+        "nmg_cycle": (I, [P, P, I, P, P]),
+        "nmg_residual": (I, [P, P, I, I, P, P, P, ctypes.POINTER(D)]),
+        "nmg_residual_restrict": (I, [P, P, I, I, P, P, P]),
+        "nmg_smooth": (I, [P, P, I, I, P, P]),
+        "nmg_filter_update": (I, [P, P, I, I, P, P, P]),
+        "nmg_coarse_solve": (I, [P, P, I, P, P]),
+        "nmg_prolong_correct": (I, [P, P, I, I, P, P]),
+        "nmg_hier_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                              ctypes.POINTER(I)]),
+        "nmg_hier_level_dense": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "nmg_launch_count": (ctypes.c_longlong, [P]),
+        "nmg_sync": (I, [P]),
+        "nmg_status_str": (ctypes.c_char_p, [I]),
+        "nmg_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pack_weights(levels: Sequence[Sequence[tuple]]) -> np.ndarray:
+    """Flatten [[(W, b), ...] per level] into the ABI order (per level, per
+    layer: W in PyTorch Conv layout, then b)."""
+    parts = []
+    for lv in levels:
+        for W, b in lv:
+            parts.append(np.asarray(W, np.float64).ravel())
+            parts.append(np.asarray(b, np.float64).ravel())
+    return np.ascontiguousarray(np.concatenate(parts)) if parts else np.zeros(0)
+
+
+def load_weights(path: str):
+    """Read a trained smoother file (npz: l{level}_w{layer}, l{level}_b{layer})."""
+    z = np.load(path)
+    nl = int(z["meta_smoother_levels"])
+    nlayers = len([k for k in z.files if k.startswith("l0_w")])
+    return [[(z[f"l{l}_w{i}"], z[f"l{l}_b{i}"]) for i in range(nlayers)] for l in range(nl)]
+
+
+class Context:
+    """A CUDA device + stream for the library."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = L.nmg_create(ctypes.byref(self._h), int(device), s)
+        if rc != 0:
+            raise NMGError(rc, L.nmg_status_str(rc).decode())
+        self.device = device
+
+    def check(self, rc):
+        if rc != 0:
+            L = lib()
+            raise NMGError(rc, f"{L.nmg_status_str(rc).decode()}: {L.nmg_last_error(self._h).decode()}")
+
+    def sync(self):
+        self.check(lib().nmg_sync(self._h))
+
+    def launches(self) -> int:
+        return int(lib().nmg_launch_count(self._h))
+
+    def close(self):
+        if self._h:
+            lib().nmg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """One operator's level hierarchy (nmg_setup)."""
+
+    def __init__(self, ctx: Context, *, dim: int, n: int, levels: int, alpha: float,
+                 taps, precision="fp32", filter: bool = True, weights=None,
+                 layers=None, width=None, ksize=None):
+        L = lib()
+        self.ctx = ctx
+        self.dim, self.n, self.levels, self.alpha = dim, n, levels, alpha
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._taps = np.ascontiguousarray(taps, dtype=np.float64)
+        op = _OpDesc(dim, n, levels, alpha, len(self._taps),
+                     self._taps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     self.precision, 1 if filter else 0)
+        smp = None
+        if weights is not None:
+            if layers is None:
+                W0 = np.asarray(weights[0][0][0])  # first layer: [width, 1, k(, k)]
+                layers, width, ksize = len(weights[0]), W0.shape[0], W0.shape[-1]
+            self._w = pack_weights(weights)
+            sm = _SmDesc(layers, width, ksize, len(weights),
+                         self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._w.size)
+            smp = ctypes.byref(sm)
+        self._h = ctypes.c_void_p()
+        ctx.check(L.nmg_setup(ctx._h, ctypes.byref(op), smp, ctypes.byref(self._h)))
+
+    # ---- shapes / dtypes
+    def size(self, level: int = 0) -> int:
+        return self.n >> level
+
+    def shape(self, batch: int, level: int = 0):
+        m = self.size(level)
+        return (batch, m) if self.dim == 1 else (batch, m, m)
+
+    # ---- solves
+    def solve(self, f, u, rtol=1e-6, max_cycles=100):
+        """Device solve; f, u torch CUDA tensors of the hierarchy's types.
+        Returns (cycles, status, relres) numpy arrays."""
+        B = f.shape[0]
+        info = (SolveInfo * max(B, 1))()
+        self.ctx.check(lib().nmg_solve(self.ctx._h, self._h, B, _ptr(f), _ptr(u), float(rtol),
+                                       int(max_cycles), info))
+        return _unpack(info, B)
+
+    def solve_host(self, f: np.ndarray, u: np.ndarray, rtol=1e-6, max_cycles=100):
+        """Solve from host (numpy) buffers; u is updated in place."""
+        assert f.flags.c_contiguous and u.flags.c_contiguous
+        B = f.shape[0]
+        info = (SolveInfo * max(B, 1))()
+        self.ctx.check(lib().nmg_solve_host(self.ctx._h, self._h, B,
+                                            ctypes.c_void_p(f.ctypes.data),
+                                            ctypes.c_void_p(u.ctypes.data), float(rtol),
+                                            int(max_cycles), info))
+        return _unpack(info, B)
+
+    def cycle(self, f, u):
+        self.ctx.check(lib().nmg_cycle(self.ctx._h, self._h, f.shape[0], _ptr(f), _ptr(u)))
+
+    # ---- single steps
+    def residual(self, level, x, y, r, norms=False):
+        B = x.shape[0]
+        out = (ctypes.c_double * max(B, 1))() if norms else None
+        self.ctx.check(lib().nmg_residual(self.ctx._h, self._h, level, B, _ptr(x), _ptr(y),
+                                          _ptr(r), out))
+        return np.array(out[:B]) if norms else None
+
+    def residual_restrict(self, level, x, y, yc):
+        self.ctx.check(lib().nmg_residual_restrict(self.ctx._h, self._h, level, x.shape[0],
+                                                   _ptr(x), _ptr(y), _ptr(yc)))
+
+    def smooth(self, level, b, h):
+        self.ctx.check(lib().nmg_smooth(self.ctx._h, self._h, level, b.shape[0], _ptr(b), _ptr(h)))
+
+    def filter_update(self, level, xstar, h, x):
+        self.ctx.check(lib().nmg_filter_update(self.ctx._h, self._h, level, h.shape[0],
+                                               _ptr(xstar), _ptr(h), _ptr(x)))
+
+    def coarse_solve(self, y, x):
+        self.ctx.check(lib().nmg_coarse_solve(self.ctx._h, self._h, y.shape[0], _ptr(y), _ptr(x)))
+
+    def prolong_correct(self, level, e, x):
+        self.ctx.check(lib().nmg_prolong_correct(self.ctx._h, self._h, level, x.shape[0],
+                                                 _ptr(e), _ptr(x)))
+
+    # ---- inspection
+    def level_dense(self, level):
+        m = self.size(level)
+        K = np.zeros((m, m))
+        M = np.zeros((m, m))
+        dp = ctypes.POINTER(ctypes.c_double)
+        rc = lib().nmg_hier_level_dense(self._h, level, K.ctypes.data_as(dp), M.ctypes.data_as(dp))
+        self.ctx.check(rc)
+        return (K, M) if self.dim == 2 else K
+
+    def close(self):
+        if self._h:
+            lib().nmg_destroy_hier(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _unpack(info, B):
+    cyc = np.array([info[i].cycles for i in range(B)], dtype=np.int64)
+    st = np.array([info[i].status for i in range(B)], dtype=np.int64)
+    rr = np.array([info[i].relres for i in range(B)], dtype=np.float64)
+    return cyc, st, rr

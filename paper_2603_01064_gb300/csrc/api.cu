@@ -1,0 +1,953 @@
+// C ABI of the solver: contexts, hierarchy setup, the cycle and the solve
+// loops.  The cycle is NMGF1d (Algorithm 3) / NMGF2d (Algorithm 4):
+//
+//   level l < L:  b = y - A x*;  h = N(b/||b||)||b||;  x = x* + F'(h);
+//                 y_{l+1} = R (y - A x);  x += P NMGF(0, y_{l+1})
+//   level L:      x = (A^(L))^{-1} y
+//
+// and the outer iteration x^tau = NMGF(x^{tau-1}, f) stops per right-hand
+// side once ||f - A x|| / ||f|| <= rtol (Section 3.2; Section 4 uses 1e-6).
+// The residual computed at the start of a cycle is both the convergence test
+// and the cycle's b_1, so a converged right-hand side costs no extra apply.
+//
+// The bf16 form runs the same cycle as an inner solve on the outer
+// residual: r = f - A u with u in fp64 and r computed in compensated fp32,
+// d = NMGF(0, r), u += d in fp64.  Because NMGF(x*, y) = x* + NMGF(0, y - A x*)
+// (the cycle's first steps only see y - A x*), this is the same iteration.
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "nmg_internal.h"
+
+namespace nmg {
+void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b, const double* s,
+                     float* act0, float* act1, float* h, const int* active, cudaStream_t st,
+                     LaunchLog& log);
+void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::vector<const double*>& bias);
+void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
+                       double alpha, int B, const double* u, const float* f, float* r,
+                       double* partials, int* ntiles, const int* active, cudaStream_t st,
+                       LaunchLog& log);
+}  // namespace nmg
+
+using namespace nmg;
+
+struct nmg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  LaunchLog log;
+};
+
+namespace {
+
+struct DevLevel {
+  int n = 0, wK = 0, wM = 0;
+  double *Kd_d = nullptr, *Md_d = nullptr;
+  float *Kd_f = nullptr, *Md_f = nullptr;
+  float *Kd_lo = nullptr, *Md_lo = nullptr;  // fp32 residual of the fp64 coefficients
+  double* A_d = nullptr;
+  float* A_f = nullptr;
+  double* tw_d = nullptr;
+  float* tw_f = nullptr;
+  double* mtab = nullptr;
+  double* circ = nullptr;
+  // smoother (levels < L-1)
+  std::vector<double*> Wd, bd;
+  std::vector<float*> Wf, bf;
+  double* wp_d = nullptr;  // 1D packed
+  float* wp_f = nullptr;
+  void* bf16_pack = nullptr;  // bf16 tensor-core weight pack (2D)
+};
+
+struct Work {
+  int cap = 0;
+  std::vector<void*> x, y, h, t;       // per level, cap * n_l^dim elements of T
+  std::vector<double*> part;           // per level partial sums
+  std::vector<double*> s;              // per level norms [cap]
+  double* fn = nullptr;
+  double* relres = nullptr;
+  int* status = nullptr;
+  int* cycles = nullptr;
+  int* active = nullptr;
+  int* ones = nullptr;
+  int* nactive = nullptr;
+  int* h_nactive = nullptr;  // pinned
+  void* act0 = nullptr;
+  void* act1 = nullptr;
+  void* cbuf = nullptr;
+  float* r32 = nullptr;   // refinement residual (inner rhs)
+  float* d32 = nullptr;   // refinement correction
+  void* fdev = nullptr;   // nmg_solve_host staging
+  void* udev = nullptr;
+  size_t part_per_level = 0;
+  std::vector<void*> all;
+};
+
+}  // namespace
+
+struct nmg_hier {
+  nmg_ctx* ctx = nullptr;
+  int dim = 0, n = 0, L = 0, precision = 0, filter = 1;
+  double alpha = 0;
+  int nc = 0;
+  int layers = 0, width = 0, ksize = 0;
+  HostHierarchy host;
+  std::vector<DevLevel> lv;
+  double* chol = nullptr;
+  std::vector<void*> allocs;
+  Work w;
+};
+
+namespace {
+
+const char* kStatusText[] = {"ok",
+                             "invalid argument",
+                             "device allocation failed",
+                             "coarsest operator is not positive definite",
+                             "CUDA error",
+                             "device wait timed out",
+                             "smoother weights inconsistent with the description",
+                             "unsupported by this build"};
+
+nmg_status fail(nmg_ctx* c, nmg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+nmg_status cuda_fail(nmg_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? NMG_ERR_OOM : NMG_ERR_CUDA, m);
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+size_t elem_size(int precision) { return precision == NMG_FP64 ? 8 : 4; }
+
+size_t plane(const nmg_hier* h, int l) {
+  size_t n = (size_t)(h->n >> l);
+  return h->dim == 1 ? n : n * n;
+}
+
+template <typename T>
+T* upload(nmg_ctx* ctx, std::vector<void*>& allocs, const std::vector<T>& v, nmg_status* st) {
+  T* p = nullptr;
+  if (v.empty()) return nullptr;
+  cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    *st = cuda_fail(ctx, e, "cudaMalloc");
+    return nullptr;
+  }
+  allocs.push_back(p);
+  e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) *st = cuda_fail(ctx, e, "cudaMemcpy");
+  return p;
+}
+
+std::vector<float> to_f(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+std::vector<float> lo_f(const std::vector<double>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)(v[i] - (double)(float)v[i]);
+  return o;
+}
+
+void free_work(Work& w) {
+  for (void* p : w.all) cudaFree(p);
+  if (w.h_nactive) cudaFreeHost(w.h_nactive);
+  w = Work();
+}
+
+nmg_status ensure_work(nmg_hier* h, int B) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  if (B <= w.cap) return NMG_OK;
+  free_work(w);
+  const size_t es = elem_size(h->precision);
+  auto alloc = [&](size_t bytes, void** out) -> nmg_status {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+    w.all.push_back(*out);
+    return NMG_OK;
+  };
+#define AL(bytes, ptr)                                                 \
+  do {                                                                 \
+    void* p_ = nullptr;                                                \
+    nmg_status s_ = alloc((bytes), &p_);                               \
+    if (s_ != NMG_OK) { free_work(w); return s_; }                     \
+    ptr = reinterpret_cast<decltype(ptr)>(p_);                         \
+  } while (0)
+  const int L = h->L;
+  w.x.assign(L, nullptr);
+  w.y.assign(L, nullptr);
+  w.h.assign(L, nullptr);
+  w.t.assign(L, nullptr);
+  w.part.assign(L, nullptr);
+  w.s.assign(L, nullptr);
+  // partial-sum slots per level: generous upper bound on tiles per item
+  size_t maxparts = 4096;
+  w.part_per_level = maxparts;
+  for (int l = 0; l < L; ++l) {
+    size_t pl = plane(h, l) * (size_t)B * es;
+    AL(pl, w.x[l]);
+    AL(pl, w.y[l]);
+    AL(pl, w.h[l]);
+    AL(pl, w.t[l]);
+    AL(maxparts * B * sizeof(double), w.part[l]);
+    AL(B * sizeof(double), w.s[l]);
+  }
+  AL(B * sizeof(double), w.fn);
+  AL(B * sizeof(double), w.relres);
+  AL(B * sizeof(int), w.status);
+  AL(B * sizeof(int), w.cycles);
+  AL(B * sizeof(int), w.active);
+  AL(B * sizeof(int), w.ones);
+  AL(sizeof(int), w.nactive);
+  if (h->dim == 2 && h->L > 1) {
+    size_t n0 = plane(h, 0);
+    size_t actb = (size_t)h->width * n0 * B * (h->precision == NMG_FP64 ? 8 : 4);
+    AL(actb, w.act0);
+    AL(actb, w.act1);
+    AL(n0 * B * 2 * es, w.cbuf);
+  }
+  if (h->precision == NMG_BF16_REFINE) {
+    AL(plane(h, 0) * B * sizeof(float), w.r32);
+    AL(plane(h, 0) * B * sizeof(float), w.d32);
+  }
+  {
+    cudaError_t e = cudaMallocHost(&w.h_nactive, sizeof(int));
+    if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "cudaMallocHost"); }
+  }
+  std::vector<int> ones(B, 1);
+  cudaError_t e = cudaMemcpy(w.ones, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "cudaMemcpy(ones)"); }
+  w.cap = B;
+#undef AL
+  return NMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// level operations (typed)
+// ---------------------------------------------------------------------------
+
+template <typename T> const T* Kd(const DevLevel& d);
+template <> const double* Kd<double>(const DevLevel& d) { return d.Kd_d; }
+template <> const float* Kd<float>(const DevLevel& d) { return d.Kd_f; }
+template <typename T> const T* Md(const DevLevel& d);
+template <> const double* Md<double>(const DevLevel& d) { return d.Md_d; }
+template <> const float* Md<float>(const DevLevel& d) { return d.Md_f; }
+template <typename T> const T* Ad(const DevLevel& d);
+template <> const double* Ad<double>(const DevLevel& d) { return d.A_d; }
+template <> const float* Ad<float>(const DevLevel& d) { return d.A_f; }
+template <typename T> const T* Tw(const DevLevel& d);
+template <> const double* Tw<double>(const DevLevel& d) { return d.tw_d; }
+template <> const float* Tw<float>(const DevLevel& d) { return d.tw_f; }
+
+template <typename T>
+Band2D<T> band(const nmg_hier* h, int l) {
+  const DevLevel& d = h->lv[l];
+  return Band2D<T>{d.n, d.wK, d.wM, Kd<T>(d), Md<T>(d), (T)h->alpha};
+}
+
+template <typename T>
+int op_residual(nmg_hier* h, int l, int B, const T* x, const T* y, T* r, double* part,
+                const int* active) {
+  int nt = 0;
+  nmg_ctx* c = h->ctx;
+  if (h->dim == 2)
+    launch_residual2d<T>(band<T>(h, l), B, x, y, r, part, &nt, active, c->stream, c->log);
+  else
+    launch_residual1d<T>(h->lv[l].n, Ad<T>(h->lv[l]), B, x, y, r, part, &nt, active, c->stream,
+                         c->log);
+  return nt;
+}
+
+template <typename T>
+int op_residual_restrict(nmg_hier* h, int l, int B, const T* x, const T* y, T* yc, double* part,
+                         const int* active) {
+  int nt = 0;
+  nmg_ctx* c = h->ctx;
+  if (h->dim == 2) {
+    launch_residual_restrict2d<T>(band<T>(h, l), B, x, y, yc, part, &nt, active, c->stream,
+                                  c->log);
+  } else {
+    T* tmp = reinterpret_cast<T*>(h->w.t[l]);
+    launch_residual1d<T>(h->lv[l].n, Ad<T>(h->lv[l]), B, x, y, tmp, nullptr, nullptr, active,
+                         c->stream, c->log);
+    launch_restrict1d<T>(h->lv[l].n, B, tmp, yc, part, &nt, active, c->stream, c->log);
+  }
+  return nt;
+}
+
+void launch_cnn2d_bf16_dispatch(nmg_hier* h, int l, int B, const float* b, const double* s,
+                                float* out, const int* active);
+
+template <typename T>
+void op_smooth(nmg_hier* h, int l, int B, const T* b, const double* s, T* out, const int* active);
+
+template <>
+void op_smooth<double>(nmg_hier* h, int l, int B, const double* b, const double* s, double* out,
+                       const int* active) {
+  nmg_ctx* c = h->ctx;
+  const DevLevel& d = h->lv[l];
+  if (h->dim == 2) {
+    std::vector<ConvW<double>> cw(h->layers);
+    for (int i = 0; i < h->layers; ++i) cw[i] = ConvW<double>{d.Wd[i], d.bd[i]};
+    launch_cnn2d_simt<double>(d.n, B, h->layers, h->width, cw.data(), b, s,
+                              reinterpret_cast<double*>(h->w.act0),
+                              reinterpret_cast<double*>(h->w.act1), out, active, c->stream, c->log);
+  } else {
+    launch_cnn1d<double>(d.n, B, h->layers, h->width, h->ksize, d.wp_d, b, s, out, active,
+                         c->stream, c->log);
+  }
+}
+
+template <>
+void op_smooth<float>(nmg_hier* h, int l, int B, const float* b, const double* s, float* out,
+                      const int* active) {
+  nmg_ctx* c = h->ctx;
+  const DevLevel& d = h->lv[l];
+  if (h->dim == 2) {
+    if (h->precision == NMG_BF16_REFINE) {
+      launch_cnn2d_bf16_dispatch(h, l, B, b, s, out, active);
+      return;
+    }
+    std::vector<ConvW<float>> cw(h->layers);
+    for (int i = 0; i < h->layers; ++i) cw[i] = ConvW<float>{d.Wf[i], d.bf[i]};
+    launch_cnn2d_simt<float>(d.n, B, h->layers, h->width, cw.data(), b, s,
+                             reinterpret_cast<float*>(h->w.act0),
+                             reinterpret_cast<float*>(h->w.act1), out, active, c->stream, c->log);
+  } else {
+    launch_cnn1d<float>(d.n, B, h->layers, h->width, h->ksize, d.wp_f, b, s, out, active,
+                        c->stream, c->log);
+  }
+}
+
+template <typename T>
+void op_filter(nmg_hier* h, int l, int B, const T* xstar, const T* hv, T* x, const int* active) {
+  nmg_ctx* c = h->ctx;
+  const DevLevel& d = h->lv[l];
+  if (!h->filter) {
+    launch_axpy_update<T>((long long)plane(h, l), B, xstar, hv, x, active, c->stream, c->log);
+  } else if (h->dim == 2) {
+    launch_filter2d<T>(d.n, B, xstar, hv, x, h->w.cbuf, Tw<T>(d), d.mtab, active, c->stream,
+                       c->log);
+  } else {
+    launch_filter1d<T>(d.n, B, xstar, hv, x, d.circ, active, c->stream, c->log);
+  }
+}
+
+template <typename T>
+void op_coarse(nmg_hier* h, int B, const T* y, T* x, const int* active) {
+  launch_coarse_solve<T>(h->nc, h->chol, B, y, x, active, h->ctx->stream, h->ctx->log);
+}
+
+template <typename T>
+void op_prolong(nmg_hier* h, int l, int B, const T* e, T* x, const int* active) {
+  nmg_ctx* c = h->ctx;
+  if (h->dim == 2)
+    launch_prolong2d<T>(h->lv[l].n, B, e, x, active, c->stream, c->log);
+  else
+    launch_prolong1d<T>(h->lv[l].n, B, e, x, active, c->stream, c->log);
+}
+
+// The cycle body after the level-1 residual b0 and its norm s0 exist:
+// h = s0 N(b0/s0); x0 = x0* + F'(h); y_2 = R(f - A x0); recursion with
+// x* = 0 below; coarsest solve; prolongation back up.
+template <typename T>
+void cycle_body(nmg_hier* h, int B, const T* f, T* x0, const T* xstar0, const T* b0,
+                const double* s0, const int* active) {
+  Work& w = h->w;
+  nmg_ctx* c = h->ctx;
+  const int L = h->L;
+  if (L == 1) {
+    op_coarse<T>(h, B, f, x0, active);
+    return;
+  }
+  auto X = [&](int l) { return l == 0 ? x0 : reinterpret_cast<T*>(w.x[l]); };
+  auto Y = [&](int l) { return l == 0 ? f : reinterpret_cast<const T*>(w.y[l]); };
+  // level 0
+  T* h0 = reinterpret_cast<T*>(w.h[0]);
+  op_smooth<T>(h, 0, B, b0, s0, h0, active);
+  op_filter<T>(h, 0, B, xstar0, h0, x0, active);
+  int nt = op_residual_restrict<T>(h, 0, B, x0, f, reinterpret_cast<T*>(w.y[1]), w.part[1], active);
+  for (int l = 1; l < L - 1; ++l) {
+    launch_norms(w.part[l], nt, B, w.s[l], active, c->stream, c->log);
+    T* hl = reinterpret_cast<T*>(w.h[l]);
+    op_smooth<T>(h, l, B, Y(l), w.s[l], hl, active);
+    op_filter<T>(h, l, B, (const T*)nullptr, hl, X(l), active);
+    nt = op_residual_restrict<T>(h, l, B, X(l), Y(l), reinterpret_cast<T*>(w.y[l + 1]),
+                                 w.part[l + 1], active);
+  }
+  op_coarse<T>(h, B, Y(L - 1), X(L - 1), active);
+  for (int l = L - 2; l >= 0; --l) op_prolong<T>(h, l, B, X(l + 1), X(l), active);
+}
+
+void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const float* f,
+                                     float* r, double* part, int* nt, const int* active);
+
+template <typename T>
+nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int max_cycles,
+                       nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(w.active, w.ones, B * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(w.cycles, 0, B * sizeof(int), st));
+  {
+    std::vector<int> nc(B, NMG_NOT_CONVERGED);
+    CK(cudaMemcpyAsync(w.status, nc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  int nt = 0;
+  launch_sumsq<T>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, st, ctx->log);
+  launch_norms(w.part[0], nt, B, w.fn, w.ones, st, ctx->log);
+  T* b0 = reinterpret_cast<T*>(w.t[0]);
+  int tau = 0;
+  for (;; ++tau) {
+    nt = op_residual<T>(h, 0, B, u, f, b0, w.part[0], w.active);
+    launch_norms(w.part[0], nt, B, w.s[0], w.active, st, ctx->log);
+    CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), st));
+    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, st, ctx->log);
+    CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*w.h_nactive == 0 || tau >= max_cycles) break;
+    cycle_body<T>(h, B, f, u, u, b0, w.s[0], w.active);
+    launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
+  }
+  CK(cudaGetLastError());
+  if (info) {
+    std::vector<int> cyc(B), stt(B);
+    std::vector<double> rr(B);
+    CK(cudaMemcpyAsync(cyc.data(), w.cycles, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(stt.data(), w.status, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rr.data(), w.relres, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < B; ++b) info[b] = nmg_solve_info{cyc[b], stt[b], rr[b]};
+  }
+  return NMG_OK;
+}
+
+nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rtol,
+                        int max_cycles, nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(w.active, w.ones, B * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(w.cycles, 0, B * sizeof(int), st));
+  {
+    std::vector<int> nc(B, NMG_NOT_CONVERGED);
+    CK(cudaMemcpyAsync(w.status, nc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  int nt = 0;
+  launch_sumsq<float>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, st, ctx->log);
+  launch_norms(w.part[0], nt, B, w.fn, w.ones, st, ctx->log);
+  for (int tau = 0;; ++tau) {
+    launch_refine_residual_dispatch(h, B, u, f, w.r32, w.part[0], &nt, w.active);
+    launch_norms(w.part[0], nt, B, w.s[0], w.active, st, ctx->log);
+    CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), st));
+    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, st, ctx->log);
+    CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*w.h_nactive == 0 || tau >= max_cycles) break;
+    // inner bf16 cycle on (0, r): d = NMGF(0, r)
+    cycle_body<float>(h, B, w.r32, w.d32, nullptr, w.r32, w.s[0], w.active);
+    launch_update_f64((long long)plane(h, 0), B, w.d32, u, w.active, st, ctx->log);
+    launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
+  }
+  CK(cudaGetLastError());
+  if (info) {
+    std::vector<int> cyc(B), stt(B);
+    std::vector<double> rr(B);
+    CK(cudaMemcpyAsync(cyc.data(), w.cycles, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(stt.data(), w.status, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rr.data(), w.relres, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < B; ++b) info[b] = nmg_solve_info{cyc[b], stt[b], rr[b]};
+  }
+  return NMG_OK;
+}
+
+nmg_status check_common(nmg_ctx* ctx, const nmg_hier* h, int batch) {
+  if (!ctx || !h) return fail(ctx, NMG_ERR_ARG, "null context or hierarchy");
+  if (h->ctx != ctx) return fail(ctx, NMG_ERR_ARG, "hierarchy belongs to another context");
+  if (batch < 0) return fail(ctx, NMG_ERR_ARG, "batch < 0");
+  return NMG_OK;
+}
+
+nmg_status set_device(nmg_ctx* ctx) {
+  CK(cudaSetDevice(ctx->device));
+  return NMG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+nmg_status nmg_create(nmg_ctx** out, int device, void* stream) {
+  if (!out) return NMG_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) return NMG_ERR_ARG;
+  std::unique_ptr<nmg_ctx> ctx(new nmg_ctx());
+  ctx->device = device;
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return NMG_ERR_CUDA;
+  if (stream) {
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return NMG_ERR_CUDA;
+    ctx->own_stream = true;
+  }
+  *out = ctx.release();
+  return NMG_OK;
+}
+
+void nmg_destroy(nmg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->own_stream && ctx->stream) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smoother_desc* sm,
+                     nmg_hier** out) {
+  if (!ctx || !op || !out) return fail(ctx, NMG_ERR_ARG, "null argument to nmg_setup");
+  *out = nullptr;
+  if (op->precision < NMG_FP64 || op->precision > NMG_BF16_REFINE)
+    return fail(ctx, NMG_ERR_ARG, "unknown precision");
+  if (op->precision == NMG_BF16_REFINE && op->dim != 2)
+    return fail(ctx, NMG_ERR_UNSUPPORTED, "the bf16 refinement form is 2D only");
+  std::unique_ptr<nmg_hier> h(new nmg_hier());
+  h->ctx = ctx;
+  std::string err;
+  if (!build_host_hierarchy(*op, h->host, err)) return fail(ctx, NMG_ERR_ARG, err);
+  h->dim = op->dim;
+  h->n = op->n;
+  h->L = op->levels;
+  h->alpha = op->alpha;
+  h->precision = op->precision;
+  h->filter = op->filter ? 1 : 0;
+  h->nc = h->host.nc;
+  const int L = h->L;
+  // ---- smoother description checks
+  if (L > 1) {
+    if (!sm || !sm->weights) return fail(ctx, NMG_ERR_WEIGHTS, "smoother weights required for levels > 1");
+    if (sm->nlevels < L - 1) return fail(ctx, NMG_ERR_WEIGHTS, "fewer smoother levels than levels-1");
+    if (sm->layers < 2) return fail(ctx, NMG_ERR_WEIGHTS, "smoother needs at least 2 layers");
+    if (op->dim == 2 && (sm->width != 32 || sm->ksize != 3))
+      return fail(ctx, NMG_ERR_UNSUPPORTED, "2D smoother must be width 32, 3x3");
+    if (op->dim == 1 && (sm->width < 1 || sm->width > 64 || sm->ksize < 1 || sm->ksize > 15 ||
+                         (sm->ksize % 2) == 0))
+      return fail(ctx, NMG_ERR_UNSUPPORTED, "1D smoother: width <= 64, odd ksize <= 15");
+    h->layers = sm->layers;
+    h->width = sm->width;
+    h->ksize = sm->ksize;
+    size_t kk = op->dim == 1 ? (size_t)sm->ksize : (size_t)sm->ksize * sm->ksize;
+    size_t per_level = 0;
+    for (int i = 0; i < sm->layers; ++i) {
+      size_t cin = i == 0 ? 1 : sm->width, cout = i == sm->layers - 1 ? 1 : sm->width;
+      per_level += cout * cin * kk + cout;
+    }
+    if (sm->nweights != per_level * (size_t)sm->nlevels)
+      return fail(ctx, NMG_ERR_WEIGHTS, "nweights does not match layers/width/ksize/nlevels");
+    for (size_t i = 0; i < sm->nweights; ++i)
+      if (!std::isfinite(sm->weights[i])) return fail(ctx, NMG_ERR_WEIGHTS, "non-finite weight");
+  }
+  nmg_status rc = set_device(ctx);
+  if (rc != NMG_OK) return rc;
+  nmg_status st = NMG_OK;
+  h->lv.assign(L, DevLevel());
+  for (int l = 0; l < L; ++l) {
+    const HostLevel& hl = h->host.lv[l];
+    DevLevel& d = h->lv[l];
+    d.n = hl.n;
+    d.wK = hl.wK;
+    d.wM = hl.wM;
+    if (op->dim == 2) {
+      d.Kd_d = upload(ctx, h->allocs, hl.Kd, &st);
+      d.Md_d = upload(ctx, h->allocs, hl.Md, &st);
+      d.Kd_f = upload(ctx, h->allocs, to_f(hl.Kd), &st);
+      d.Md_f = upload(ctx, h->allocs, to_f(hl.Md), &st);
+      d.Kd_lo = upload(ctx, h->allocs, lo_f(hl.Kd), &st);
+      d.Md_lo = upload(ctx, h->allocs, lo_f(hl.Md), &st);
+    } else {
+      d.A_d = upload(ctx, h->allocs, hl.A, &st);
+      d.A_f = upload(ctx, h->allocs, to_f(hl.A), &st);
+    }
+    if (l < L - 1) {
+      std::vector<double> tw = fft_twiddles(hl.n);
+      d.tw_d = upload(ctx, h->allocs, tw, &st);
+      d.tw_f = upload(ctx, h->allocs, to_f(tw), &st);
+      d.mtab = upload(ctx, h->allocs, filter_mask_table(hl.n), &st);
+      if (op->dim == 1) d.circ = upload(ctx, h->allocs, filter_circulant_1d(hl.n), &st);
+    }
+    if (st != NMG_OK) {
+      for (void* p : h->allocs) cudaFree(p);
+      return st;
+    }
+  }
+  // ---- weights
+  if (L > 1) {
+    size_t off = 0;
+    const size_t kk = op->dim == 1 ? (size_t)h->ksize : (size_t)h->ksize * h->ksize;
+    size_t per_level = 0;
+    for (int i = 0; i < h->layers; ++i) {
+      size_t cin = i == 0 ? 1 : h->width, cout = i == h->layers - 1 ? 1 : h->width;
+      per_level += cout * cin * kk + cout;
+    }
+    for (int l = 0; l < L - 1; ++l) {
+      DevLevel& d = h->lv[l];
+      const double* base = sm->weights + per_level * l;
+      if (op->dim == 1) {
+        std::vector<double> v(base, base + per_level);
+        d.wp_d = upload(ctx, h->allocs, v, &st);
+        d.wp_f = upload(ctx, h->allocs, to_f(v), &st);
+      } else {
+        off = 0;
+        for (int i = 0; i < h->layers; ++i) {
+          int cin = i == 0 ? 1 : h->width, cout = i == h->layers - 1 ? 1 : h->width;
+          std::vector<double> W((size_t)cin * 9 * cout), bb(cout);
+          for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+              for (int t = 0; t < 9; ++t)
+                W[((size_t)ci * 9 + t) * cout + co] = base[off + ((size_t)co * cin + ci) * 9 + t];
+          off += (size_t)cout * cin * 9;
+          for (int co = 0; co < cout; ++co) bb[co] = base[off + co];
+          off += cout;
+          d.Wd.push_back(upload(ctx, h->allocs, W, &st));
+          d.bd.push_back(upload(ctx, h->allocs, bb, &st));
+          d.Wf.push_back(upload(ctx, h->allocs, to_f(W), &st));
+          d.bf.push_back(upload(ctx, h->allocs, to_f(bb), &st));
+        }
+      }
+      if (st == NMG_OK && h->precision == NMG_BF16_REFINE) {
+        std::vector<const double*> Wp, bp;
+        size_t o = 0;
+        for (int i = 0; i < h->layers; ++i) {
+          int cin = i == 0 ? 1 : h->width, cout = i == h->layers - 1 ? 1 : h->width;
+          Wp.push_back(base + o);
+          o += (size_t)cout * cin * 9;
+          bp.push_back(base + o);
+          o += cout;
+        }
+        d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp);
+        if (!d.bf16_pack) st = fail(ctx, NMG_ERR_UNSUPPORTED, "bf16 tensor-core smoother unavailable");
+        else h->allocs.push_back(d.bf16_pack);
+      }
+      if (st != NMG_OK) {
+        for (void* p : h->allocs) cudaFree(p);
+        return st;
+      }
+    }
+  }
+  // ---- coarsest Cholesky on the device (fp64)
+  {
+    double* A = upload(ctx, h->allocs, h->host.coarse, &st);
+    int* flag = nullptr;
+    if (st == NMG_OK) {
+      cudaError_t e = cudaMalloc(&flag, sizeof(int));
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaMalloc(flag)");
+    }
+    if (st == NMG_OK) {
+      launch_cholesky(h->nc, A, flag, ctx->stream, ctx->log);
+      int hflag = 0;
+      cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "cholesky");
+      else if (hflag) st = fail(ctx, NMG_ERR_NOT_SPD, "coarsest Galerkin operator is not SPD");
+      cudaFree(flag);
+    }
+    if (st != NMG_OK) {
+      for (void* p : h->allocs) cudaFree(p);
+      return st;
+    }
+    h->chol = A;
+  }
+  *out = h.release();
+  return NMG_OK;
+}
+
+void nmg_destroy_hier(nmg_hier* h) {
+  if (!h) return;
+  cudaSetDevice(h->ctx->device);
+  cudaStreamSynchronize(h->ctx->stream);
+  free_work(h->w);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+nmg_status nmg_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u, double rtol,
+                     int max_cycles, nmg_solve_info* info) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!f || !u) return fail(ctx, NMG_ERR_ARG, "null f or u");
+  if (!(rtol >= 0.0) || max_cycles < 0) return fail(ctx, NMG_ERR_ARG, "bad rtol or max_cycles");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  switch (h->precision) {
+    case NMG_FP64:
+      return solve_plain<double>(h, batch, (const double*)f, (double*)u, rtol, max_cycles, info);
+    case NMG_FP32:
+      return solve_plain<float>(h, batch, (const float*)f, (float*)u, rtol, max_cycles, info);
+    default:
+      return solve_refine(h, batch, (const float*)f, (double*)u, rtol, max_cycles, info);
+  }
+}
+
+nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host, void* u_host,
+                          double rtol, int max_cycles, nmg_solve_info* info) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!f_host || !u_host) return fail(ctx, NMG_ERR_ARG, "null f or u");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  const size_t fes = h->precision == NMG_FP64 ? 8 : 4;
+  const size_t ues = h->precision == NMG_FP32 ? 4 : 8;
+  const size_t n = plane(h, 0) * (size_t)batch;
+  Work& w = h->w;
+  if (!w.fdev) {
+    // staging sized for the workspace capacity
+    size_t cap = plane(h, 0) * (size_t)w.cap;
+    cudaError_t e = cudaMalloc(&w.fdev, cap * fes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(staging f)");
+    w.all.push_back(w.fdev);
+    e = cudaMalloc(&w.udev, cap * ues);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(staging u)");
+    w.all.push_back(w.udev);
+  }
+  CK(cudaMemcpyAsync(w.fdev, f_host, n * fes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(w.udev, u_host, n * ues, cudaMemcpyHostToDevice, ctx->stream));
+  s = nmg_solve(ctx, h, batch, w.fdev, w.udev, rtol, max_cycles, info);
+  if (s != NMG_OK) return s;
+  CK(cudaMemcpyAsync(u_host, w.udev, n * ues, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return NMG_OK;
+}
+
+nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!f || !u) return fail(ctx, NMG_ERR_ARG, "null f or u");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  Work& w = h->w;
+  if (h->precision == NMG_BF16_REFINE) {
+    int nt = 0;
+    launch_refine_residual_dispatch(h, batch, (const double*)u, (const float*)f, w.r32, w.part[0],
+                                    &nt, w.ones);
+    launch_norms(w.part[0], nt, batch, w.s[0], w.ones, ctx->stream, ctx->log);
+    cycle_body<float>(h, batch, w.r32, w.d32, nullptr, w.r32, w.s[0], w.ones);
+    launch_update_f64((long long)plane(h, 0), batch, w.d32, (double*)u, w.ones, ctx->stream,
+                      ctx->log);
+  } else if (h->precision == NMG_FP64) {
+    double* b0 = reinterpret_cast<double*>(w.t[0]);
+    int nt = op_residual<double>(h, 0, batch, (const double*)u, (const double*)f, b0, w.part[0], w.ones);
+    launch_norms(w.part[0], nt, batch, w.s[0], w.ones, ctx->stream, ctx->log);
+    cycle_body<double>(h, batch, (const double*)f, (double*)u, (const double*)u, b0, w.s[0], w.ones);
+  } else {
+    float* b0 = reinterpret_cast<float*>(w.t[0]);
+    int nt = op_residual<float>(h, 0, batch, (const float*)u, (const float*)f, b0, w.part[0], w.ones);
+    launch_norms(w.part[0], nt, batch, w.s[0], w.ones, ctx->stream, ctx->log);
+    cycle_body<float>(h, batch, (const float*)f, (float*)u, (const float*)u, b0, w.s[0], w.ones);
+  }
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+// ---- step entry points -----------------------------------------------------
+
+static nmg_status step_check(nmg_ctx* ctx, nmg_hier* h, int level, int batch, int maxlevel) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (level < 0 || level > maxlevel) return fail(ctx, NMG_ERR_ARG, "level out of range");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  return ensure_work(h, batch > 0 ? batch : 1);
+}
+
+nmg_status nmg_residual(nmg_ctx* ctx, nmg_hier* h, int level, int batch, const void* x,
+                        const void* y, void* r, double* norms) {
+  nmg_status s = step_check(ctx, h, level, batch, h ? h->L - 1 : 0);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!x || !r) return fail(ctx, NMG_ERR_ARG, "null x or r");
+  Work& w = h->w;
+  int nt;
+  if (h->precision == NMG_FP64)
+    nt = op_residual<double>(h, level, batch, (const double*)x, (const double*)y, (double*)r, w.part[level], w.ones);
+  else
+    nt = op_residual<float>(h, level, batch, (const float*)x, (const float*)y, (float*)r, w.part[level], w.ones);
+  if (norms) {
+    launch_norms(w.part[level], nt, batch, w.s[level], w.ones, ctx->stream, ctx->log);
+    CK(cudaMemcpyAsync(norms, w.s[level], batch * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+nmg_status nmg_residual_restrict(nmg_ctx* ctx, nmg_hier* h, int level, int batch, const void* x,
+                                 const void* y, void* yc) {
+  nmg_status s = step_check(ctx, h, level, batch, h ? h->L - 2 : 0);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!x || !yc) return fail(ctx, NMG_ERR_ARG, "null x or yc");
+  if (h->precision == NMG_FP64)
+    op_residual_restrict<double>(h, level, batch, (const double*)x, (const double*)y, (double*)yc, h->w.part[level + 1], h->w.ones);
+  else
+    op_residual_restrict<float>(h, level, batch, (const float*)x, (const float*)y, (float*)yc, h->w.part[level + 1], h->w.ones);
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+nmg_status nmg_smooth(nmg_ctx* ctx, nmg_hier* h, int level, int batch, const void* b, void* hout) {
+  nmg_status s = step_check(ctx, h, level, batch, h ? h->L - 2 : 0);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!b || !hout) return fail(ctx, NMG_ERR_ARG, "null b or h");
+  Work& w = h->w;
+  int nt = 0;
+  if (h->precision == NMG_FP64) {
+    launch_sumsq<double>((const double*)b, (long long)plane(h, level), batch, w.part[level], &nt, w.ones, ctx->stream, ctx->log);
+    launch_norms(w.part[level], nt, batch, w.s[level], w.ones, ctx->stream, ctx->log);
+    op_smooth<double>(h, level, batch, (const double*)b, w.s[level], (double*)hout, w.ones);
+  } else {
+    launch_sumsq<float>((const float*)b, (long long)plane(h, level), batch, w.part[level], &nt, w.ones, ctx->stream, ctx->log);
+    launch_norms(w.part[level], nt, batch, w.s[level], w.ones, ctx->stream, ctx->log);
+    op_smooth<float>(h, level, batch, (const float*)b, w.s[level], (float*)hout, w.ones);
+  }
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+nmg_status nmg_filter_update(nmg_ctx* ctx, nmg_hier* h, int level, int batch, const void* xstar,
+                             const void* hin, void* x) {
+  nmg_status s = step_check(ctx, h, level, batch, h ? h->L - 2 : 0);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!hin || !x) return fail(ctx, NMG_ERR_ARG, "null h or x");
+  if (h->precision == NMG_FP64)
+    op_filter<double>(h, level, batch, (const double*)xstar, (const double*)hin, (double*)x, h->w.ones);
+  else
+    op_filter<float>(h, level, batch, (const float*)xstar, (const float*)hin, (float*)x, h->w.ones);
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+nmg_status nmg_coarse_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* y, void* x) {
+  nmg_status s = step_check(ctx, h, 0, batch, 0);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!y || !x) return fail(ctx, NMG_ERR_ARG, "null y or x");
+  if (h->precision == NMG_FP64)
+    op_coarse<double>(h, batch, (const double*)y, (double*)x, h->w.ones);
+  else
+    op_coarse<float>(h, batch, (const float*)y, (float*)x, h->w.ones);
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+nmg_status nmg_prolong_correct(nmg_ctx* ctx, nmg_hier* h, int level, int batch, const void* e,
+                               void* x) {
+  nmg_status s = step_check(ctx, h, level, batch, h ? h->L - 2 : 0);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!e || !x) return fail(ctx, NMG_ERR_ARG, "null e or x");
+  if (h->precision == NMG_FP64)
+    op_prolong<double>(h, level, batch, (const double*)e, (double*)x, h->w.ones);
+  else
+    op_prolong<float>(h, level, batch, (const float*)e, (float*)x, h->w.ones);
+  CK(cudaGetLastError());
+  return NMG_OK;
+}
+
+nmg_status nmg_hier_info(const nmg_hier* h, int level, int* n, int* wK, int* wM, int* precision) {
+  if (!h || level < 0 || level >= h->L) return NMG_ERR_ARG;
+  if (n) *n = h->lv[level].n;
+  if (wK) *wK = h->lv[level].wK;
+  if (wM) *wM = h->lv[level].wM;
+  if (precision) *precision = h->precision;
+  return NMG_OK;
+}
+
+nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double* M) {
+  if (!h || level < 0 || level >= h->L || !K) return NMG_ERR_ARG;
+  const HostLevel& hl = h->host.lv[level];
+  const int n = hl.n;
+  if (h->dim == 1) {
+    std::memcpy(K, hl.A.data(), (size_t)n * n * sizeof(double));
+    return NMG_OK;
+  }
+  auto dense = [n](const std::vector<double>& dia, int w, double* out) {
+    std::memset(out, 0, (size_t)n * n * sizeof(double));
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k <= 2 * w; ++k) {
+        int j = i + k - w;
+        if (j >= 0 && j < n) out[(size_t)i * n + j] = dia[(size_t)i * (2 * w + 1) + k];
+      }
+  };
+  dense(hl.Kd, hl.wK, K);
+  if (M) dense(hl.Md, hl.wM, M);
+  return NMG_OK;
+}
+
+long long nmg_launch_count(const nmg_ctx* ctx) { return ctx ? ctx->log.launches : 0; }
+
+nmg_status nmg_sync(nmg_ctx* ctx) {
+  if (!ctx) return NMG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return NMG_OK;
+}
+
+const char* nmg_status_str(nmg_status s) {
+  int i = -(int)s;
+  if (i < 0 || i > 7) return "unknown status";
+  return kStatusText[i];
+}
+
+const char* nmg_last_error(const nmg_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hooks implemented with the bf16 / refinement kernels
+// ---------------------------------------------------------------------------
+
+namespace {
+void launch_cnn2d_bf16_dispatch(nmg_hier* h, int l, int B, const float* b, const double* s,
+                                float* out, const int* active) {
+  DevLevel& d = h->lv[l];
+  // fp32 SIMT fallback is not used: the bf16 pack is built at setup
+  bf16_cnn_launch(d.n, B, h->layers, d.bf16_pack, b, s, reinterpret_cast<float*>(h->w.act0),
+                  reinterpret_cast<float*>(h->w.act1), out, active, h->ctx->stream, h->ctx->log);
+}
+
+void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const float* f,
+                                     float* r, double* part, int* nt, const int* active) {
+  const DevLevel& d = h->lv[0];
+  Band2D<float> hi{d.n, d.wK, d.wM, d.Kd_f, d.Md_f, (float)h->alpha};
+  refine_residual2d(hi, d.Kd_lo, d.Md_lo, h->alpha, B, u, f, r, part, nt, active, h->ctx->stream,
+                    h->ctx->log);
+}
+}  // namespace

@@ -1,0 +1,496 @@
+// Operator kernels of the cycle:
+//  * residual r = y - A_l x for A_l = alpha M(x)M + K(x)K with banded 1D
+//    factors (Algorithm 4: B_l = Y_l - Mat(A Vec(X*)) and the residual
+//    before restriction), as two separable passes over a shared-memory tile;
+//  * the same residual followed by full-weighting restriction
+//    R = (P(x)P)^T / 4, writing only the coarse vector;
+//  * prolongation + correction X_l += Mat(I_{l+1}^l Vec(E_{l+1}));
+//  * per-tile partial sums of squares for the residual norms ||B_l||.
+// The 1D variants use a dense level matrix (Algorithm 3).
+#include <cmath>
+
+#include "nmg_internal.h"
+
+namespace nmg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  // warp shuffle then one value per warp in shared memory
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];  // fixed order: deterministic
+  }
+  return s;
+}
+
+// Fine region handled by one block: rows [r0, r0+RH), cols [c0, c0+RW).
+// Shared memory: xs (RH+2W) x (RW+2W), tk (RH+2wK) x RW, tm (RH+2wM) x RW,
+// rs RH x RW (restrict only).  W = max(wK, wM).
+template <typename T, bool RESTRICT>
+__global__ void __launch_bounds__(kThreads)
+k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
+             T* __restrict__ out, double* __restrict__ partials, const int* __restrict__ active,
+             int tile, int tiles_x) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const int n = op.n, wK = op.wK, wM = op.wM;
+  const int W = wK > wM ? wK : wM;
+  const int ty = blockIdx.x / tiles_x, tx = blockIdx.x % tiles_x;
+  int r0, c0, RH, RW, nc = n / 2, CH = 0, CW = 0;
+  if (RESTRICT) {
+    int I0 = ty * tile, J0 = tx * tile;
+    CH = min(tile, nc - I0);
+    CW = min(tile, nc - J0);
+    r0 = 2 * I0 - 1;
+    c0 = 2 * J0 - 1;
+    RH = 2 * CH + 1;
+    RW = 2 * CW + 1;
+  } else {
+    r0 = ty * tile;
+    c0 = tx * tile;
+    RH = min(tile, n - r0);
+    RW = min(tile, n - c0);
+  }
+  const int XH = RH + 2 * W, XW = RW + 2 * W;
+  T* xs = sm;
+  T* tk = xs + XH * XW;
+  T* tm = tk + (RH + 2 * wK) * RW;
+  T* rs = tm + (RH + 2 * wM) * RW;
+  const size_t plane = (size_t)n * n;
+  const T* xb = x + (size_t)b * plane;
+  const T* yb = y ? y + (size_t)b * plane : nullptr;
+
+  for (int idx = threadIdx.x; idx < XH * XW; idx += blockDim.x) {
+    int a = idx / XW, c = idx % XW;
+    int gr = r0 - W + a, gc = c0 - W + c;
+    xs[idx] = (gr >= 0 && gr < n && gc >= 0 && gc < n) ? xb[(size_t)gr * n + gc] : T(0);
+  }
+  __syncthreads();
+  // row pass: tk[a][j] = sum_d K[gj][gj+d-wK] x[row][gj+d-wK]
+  {
+    const int nk = 2 * wK + 1, nm = 2 * wM + 1;
+    const int HK = RH + 2 * wK, HM = RH + 2 * wM;
+    for (int idx = threadIdx.x; idx < HK * RW; idx += blockDim.x) {
+      int a = idx / RW, j = idx % RW;
+      int gj = c0 + j;
+      T acc = T(0);
+      if (gj >= 0 && gj < n) {
+        const T* kr = op.Kd + (size_t)gj * nk;
+        const T* xr = xs + (a + W - wK) * XW + (j + W - wK);
+        for (int d = 0; d < nk; ++d) acc += kr[d] * xr[d];
+      }
+      tk[idx] = acc;
+    }
+    for (int idx = threadIdx.x; idx < HM * RW; idx += blockDim.x) {
+      int a = idx / RW, j = idx % RW;
+      int gj = c0 + j;
+      T acc = T(0);
+      if (gj >= 0 && gj < n) {
+        const T* mr = op.Md + (size_t)gj * nm;
+        const T* xr = xs + (a + W - wM) * XW + (j + W - wM);
+        for (int d = 0; d < nm; ++d) acc += mr[d] * xr[d];
+      }
+      tm[idx] = acc;
+    }
+  }
+  __syncthreads();
+  // column pass and residual
+  double ss = 0.0;
+  {
+    const int nk = 2 * wK + 1, nm = 2 * wM + 1;
+    for (int idx = threadIdx.x; idx < RH * RW; idx += blockDim.x) {
+      int i = idx / RW, j = idx % RW;
+      int gi = r0 + i, gj = c0 + j;
+      T r = T(0);
+      if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
+        const T* kr = op.Kd + (size_t)gi * nk;
+        const T* mr = op.Md + (size_t)gi * nm;
+        T zk = T(0), zm = T(0);
+        for (int d = 0; d < nk; ++d) zk += kr[d] * tk[(i + d) * RW + j];
+        for (int d = 0; d < nm; ++d) zm += mr[d] * tm[(i + d) * RW + j];
+        T yv = yb ? yb[(size_t)gi * n + gj] : T(0);
+        r = yv - (op.alpha * zm + zk);
+        if (!RESTRICT) {
+          out[(size_t)b * plane + (size_t)gi * n + gj] = r;
+          ss += (double)r * (double)r;
+        }
+      }
+      if (RESTRICT) rs[idx] = r;
+    }
+  }
+  if (RESTRICT) {
+    __syncthreads();
+    const size_t cplane = (size_t)nc * nc;
+    const int I0 = ty * tile, J0 = tx * tile;
+    for (int idx = threadIdx.x; idx < CH * CW; idx += blockDim.x) {
+      int ci = idx / CW, cj = idx % CW;
+      int li = 2 * ci + 1, lj = 2 * cj + 1;  // local fine center
+      const T* c = rs + li * RW + lj;
+      T v = T(0.25) * (T(0.25) * c[-RW - 1] + T(0.5) * c[-RW] + T(0.25) * c[-RW + 1]) +
+            T(0.5) * (T(0.25) * c[-1] + T(0.5) * c[0] + T(0.25) * c[1]) +
+            T(0.25) * (T(0.25) * c[RW - 1] + T(0.5) * c[RW] + T(0.25) * c[RW + 1]);
+      out[(size_t)b * cplane + (size_t)(I0 + ci) * nc + (J0 + cj)] = v;
+      ss += (double)v * (double)v;
+    }
+  }
+  if (partials) {
+    double s = block_sum<T>(ss, red);
+    if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_prolong2d(int n, int B, const T* __restrict__ e, T* __restrict__ x,
+                            const int* __restrict__ active) {
+  const int nc = n / 2;
+  const size_t plane = (size_t)n * n;
+  const size_t total = plane * B;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int b = (int)(idx / plane);
+    if (!active[b]) continue;
+    int rem = (int)(idx % plane);
+    int i = rem / n, j = rem % n;
+    const T* eb = e + (size_t)b * nc * nc;
+    int I = i >> 1, J = j >> 1;
+    T v;
+    if (!(i & 1) && !(j & 1)) {
+      v = eb[I * nc + J];
+    } else if (!(i & 1)) {
+      T a = eb[I * nc + J];
+      T c = (J + 1 < nc) ? eb[I * nc + J + 1] : T(0);
+      v = T(0.5) * (a + c);
+    } else if (!(j & 1)) {
+      T a = eb[I * nc + J];
+      T c = (I + 1 < nc) ? eb[(I + 1) * nc + J] : T(0);
+      v = T(0.5) * (a + c);
+    } else {
+      T a = eb[I * nc + J];
+      T c1 = (J + 1 < nc) ? eb[I * nc + J + 1] : T(0);
+      T c2 = (I + 1 < nc) ? eb[(I + 1) * nc + J] : T(0);
+      T c3 = (I + 1 < nc && J + 1 < nc) ? eb[(I + 1) * nc + J + 1] : T(0);
+      v = T(0.25) * ((a + c1) + (c2 + c3));
+    }
+    x[idx] += v;
+  }
+}
+
+// ---- 1D dense ---------------------------------------------------------------
+
+// r[b][i] = y[b][i] - sum_j A[i][j] x[b][j]; one warp per output row
+template <typename T>
+__global__ void k_residual1d(int n, const T* __restrict__ A, const T* __restrict__ x,
+                             const T* __restrict__ y, T* __restrict__ r,
+                             double* __restrict__ partials, const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rows_per_block = nw;
+  double ss = 0.0;
+  int i = blockIdx.x * rows_per_block + wid;
+  if (i < n) {
+    const T* ar = A + (size_t)i * n;
+    const T* xb = x + (size_t)b * n;
+    T acc = T(0);
+    for (int j = lane; j < n; j += 32) acc += ar[j] * xb[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      T v = (y ? y[(size_t)b * n + i] : T(0)) - acc;
+      r[(size_t)b * n + i] = v;
+      ss = (double)v * (double)v;
+    }
+  }
+  if (partials) {
+    double s = block_sum<T>(ss, red);
+    if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_restrict1d(int n, const T* __restrict__ r, T* __restrict__ yc,
+                             double* __restrict__ partials, const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ double red[32];
+  const int nc = n / 2;
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  double ss = 0.0;
+  if (I < nc) {
+    const T* rb = r + (size_t)b * n;
+    T lo = (2 * I - 1 >= 0) ? rb[2 * I - 1] : T(0);
+    T v = T(0.25) * lo + T(0.5) * rb[2 * I] + T(0.25) * rb[2 * I + 1];
+    yc[(size_t)b * nc + I] = v;
+    ss = (double)v * (double)v;
+  }
+  if (partials) {
+    double s = block_sum<T>(ss, red);
+    if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_prolong1d(int n, int B, const T* __restrict__ e, T* __restrict__ x,
+                            const int* __restrict__ active) {
+  const int nc = n / 2;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * B; idx += gridDim.x * blockDim.x) {
+    int b = idx / n, i = idx % n;
+    if (!active[b]) continue;
+    const T* eb = e + (size_t)b * nc;
+    int I = i >> 1;
+    T v = (i & 1) ? T(0.5) * (eb[I] + ((I + 1 < nc) ? eb[I + 1] : T(0))) : eb[I];
+    x[idx] += v;
+  }
+}
+
+// ---- norms, convergence -------------------------------------------------------
+
+__global__ void k_norms(const double* __restrict__ partials, int ntiles, int B,
+                        double* __restrict__ s, const int* __restrict__ active) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  double acc = 0.0;
+  for (int t = 0; t < ntiles; ++t) acc += partials[(size_t)b * ntiles + t];
+  s[b] = sqrt(acc);
+}
+
+template <typename T>
+__global__ void k_sumsq(const T* __restrict__ v, long long len, double* __restrict__ partials,
+                        const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ double red[32];
+  double ss = 0.0;
+  const T* vb = v + (size_t)b * len;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    double t = (double)vb[i];
+    ss += t * t;
+  }
+  double s = block_sum<T>(ss, red);
+  if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_converge(const double* __restrict__ s, const double* __restrict__ fn,
+                           double rtol, int B, int* __restrict__ active,
+                           double* __restrict__ relres, int* __restrict__ status,
+                           int* __restrict__ nactive) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  double f = fn[b];
+  double rr = f > 0.0 ? s[b] / f : 0.0;
+  relres[b] = rr;
+  if (!(rr == rr) || rr > 1e30) {
+    status[b] = NMG_DIVERGED;
+    active[b] = 0;
+  } else if (rr <= rtol) {
+    status[b] = NMG_CONVERGED;
+    active[b] = 0;
+  } else {
+    atomicAdd(nactive, 1);
+  }
+}
+
+template <typename T>
+__global__ void k_axpy_update(long long len, int B, const T* xs, const T* __restrict__ h, T* x,
+                              const int* __restrict__ active) {
+  const long long total = len * B;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(i / len);
+    if (!active[b]) continue;
+    x[i] = (xs ? xs[i] : T(0)) + h[i];
+  }
+}
+
+__global__ void k_update_f64(long long len, int B, const float* __restrict__ d,
+                             double* __restrict__ u, const int* __restrict__ active) {
+  const long long total = len * B;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(i / len);
+    if (!active[b]) continue;
+    u[i] += (double)d[i];
+  }
+}
+
+__global__ void k_count_cycles(int B, const int* __restrict__ active, int* __restrict__ cycles) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B && active[b]) cycles[b] += 1;
+}
+
+int grid_for(long long total, int threads) {
+  long long g = (total + threads - 1) / threads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename T>
+size_t residual_smem(int RH, int RW, int wK, int wM, bool restrict_) {
+  int W = wK > wM ? wK : wM;
+  size_t e = (size_t)(RH + 2 * W) * (RW + 2 * W) + (size_t)(RH + 2 * wK) * RW +
+             (size_t)(RH + 2 * wM) * RW + (restrict_ ? (size_t)RH * RW : 0);
+  return e * sizeof(T);
+}
+
+// tile sizes: fine tile for the residual, coarse tile for residual+restrict;
+// shrunk until the shared-memory footprint fits in 200 KB
+template <typename T>
+int pick_tile(int n, int wK, int wM, bool restrict_) {
+  int t = restrict_ ? 32 : 64;
+  int lim = restrict_ ? n / 2 : n;
+  if (t > lim) t = lim;
+  while (t > 4) {
+    int R = restrict_ ? 2 * t + 1 : t;
+    if (residual_smem<T>(R, R, wK, wM, restrict_) <= 200 * 1024) break;
+    t /= 2;
+  }
+  return t;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
+                       double* partials, int* ntiles, const int* active, cudaStream_t st,
+                       LaunchLog& log) {
+  int tile = pick_tile<T>(op.n, op.wK, op.wM, false);
+  int tx = ceil_div(op.n, tile);
+  size_t sm = residual_smem<T>(tile, tile, op.wK, op.wM, false);
+  auto kern = k_residual2d<T, false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid(tx * tx, B);
+  kern<<<grid, kThreads, sm, st>>>(op, x, y, r, partials, active, tile, tx);
+  if (ntiles) *ntiles = tx * tx;
+  log.launches++;
+}
+
+template <typename T>
+void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T* y, T* yc,
+                                double* partials, int* ntiles, const int* active,
+                                cudaStream_t st, LaunchLog& log) {
+  int tile = pick_tile<T>(op.n, op.wK, op.wM, true);
+  int nc = op.n / 2;
+  int tx = ceil_div(nc, tile);
+  size_t sm = residual_smem<T>(2 * tile + 1, 2 * tile + 1, op.wK, op.wM, true);
+  auto kern = k_residual2d<T, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid(tx * tx, B);
+  kern<<<grid, kThreads, sm, st>>>(op, x, y, yc, partials, active, tile, tx);
+  if (ntiles) *ntiles = tx * tx;
+  log.launches++;
+}
+
+template <typename T>
+void launch_prolong2d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
+                      LaunchLog& log) {
+  long long total = (long long)n * n * B;
+  k_prolong2d<T><<<grid_for(total, 256), 256, 0, st>>>(n, B, e, x, active);
+  log.launches++;
+}
+
+template <typename T>
+void launch_residual1d(int n, const T* A, int B, const T* x, const T* y, T* r,
+                       double* partials, int* ntiles, const int* active, cudaStream_t st,
+                       LaunchLog& log) {
+  int rows = 8;  // warps per block
+  dim3 grid(ceil_div(n, rows), B);
+  k_residual1d<T><<<grid, rows * 32, 0, st>>>(n, A, x, y, r, partials, active);
+  if (ntiles) *ntiles = grid.x;
+  log.launches++;
+}
+
+template <typename T>
+void launch_restrict1d(int n, int B, const T* r, T* yc, double* partials, int* ntiles,
+                       const int* active, cudaStream_t st, LaunchLog& log) {
+  dim3 grid(ceil_div(n / 2, 128), B);
+  k_restrict1d<T><<<grid, 128, 0, st>>>(n, r, yc, partials, active);
+  if (ntiles) *ntiles = grid.x;
+  log.launches++;
+}
+
+template <typename T>
+void launch_prolong1d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
+                      LaunchLog& log) {
+  k_prolong1d<T><<<grid_for((long long)n * B, 256), 256, 0, st>>>(n, B, e, x, active);
+  log.launches++;
+}
+
+void launch_norms(const double* partials, int ntiles, int B, double* s, const int* active,
+                  cudaStream_t st, LaunchLog& log) {
+  k_norms<<<ceil_div(B, 128), 128, 0, st>>>(partials, ntiles, B, s, active);
+  log.launches++;
+}
+
+template <typename T>
+void launch_sumsq(const T* v, long long len, int B, double* partials, int* ntiles,
+                  const int* active, cudaStream_t st, LaunchLog& log) {
+  int g = (int)std::min<long long>(64, (len + 255) / 256);
+  if (g < 1) g = 1;
+  dim3 grid(g, B);
+  k_sumsq<T><<<grid, 256, 0, st>>>(v, len, partials, active);
+  if (ntiles) *ntiles = g;
+  log.launches++;
+}
+
+void launch_converge(const double* s, const double* fn, double rtol, int B, int* active,
+                     double* relres, int* status, int* nactive, cudaStream_t st,
+                     LaunchLog& log) {
+  k_converge<<<ceil_div(B, 128), 128, 0, st>>>(s, fn, rtol, B, active, relres, status, nactive);
+  log.launches++;
+}
+
+template <typename T>
+void launch_axpy_update(long long len, int B, const T* xstar, const T* h, T* x,
+                        const int* active, cudaStream_t st, LaunchLog& log) {
+  k_axpy_update<T><<<grid_for(len * B, 256), 256, 0, st>>>(len, B, xstar, h, x, active);
+  log.launches++;
+}
+
+void launch_count_cycles(int B, const int* active, int* cycles, cudaStream_t st, LaunchLog& log) {
+  k_count_cycles<<<ceil_div(B, 128), 128, 0, st>>>(B, active, cycles);
+  log.launches++;
+}
+
+void launch_update_f64(long long len, int B, const float* d, double* u, const int* active,
+                       cudaStream_t st, LaunchLog& log) {
+  k_update_f64<<<grid_for(len * B, 256), 256, 0, st>>>(len, B, d, u, active);
+  log.launches++;
+}
+
+#define NMG_INST(T)                                                                          \
+  template void launch_residual2d<T>(const Band2D<T>&, int, const T*, const T*, T*, double*, \
+                                     int*, const int*, cudaStream_t, LaunchLog&);            \
+  template void launch_residual_restrict2d<T>(const Band2D<T>&, int, const T*, const T*,     \
+                                              T*, double*, int*, const int*, cudaStream_t,   \
+                                              LaunchLog&);                                   \
+  template void launch_prolong2d<T>(int, int, const T*, T*, const int*, cudaStream_t,        \
+                                    LaunchLog&);                                             \
+  template void launch_residual1d<T>(int, const T*, int, const T*, const T*, T*, double*,    \
+                                     int*, const int*, cudaStream_t, LaunchLog&);            \
+  template void launch_restrict1d<T>(int, int, const T*, T*, double*, int*, const int*,      \
+                                     cudaStream_t, LaunchLog&);                              \
+  template void launch_prolong1d<T>(int, int, const T*, T*, const int*, cudaStream_t,        \
+                                    LaunchLog&);                                             \
+  template void launch_sumsq<T>(const T*, long long, int, double*, int*, const int*,         \
+                                cudaStream_t, LaunchLog&);                                   \
+  template void launch_axpy_update<T>(long long, int, const T*, const T*, T*, const int*,    \
+                                      cudaStream_t, LaunchLog&);
+NMG_INST(float)
+NMG_INST(double)
+#undef NMG_INST
+
+}  // namespace nmg

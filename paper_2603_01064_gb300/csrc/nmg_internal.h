@@ -1,0 +1,163 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nmg.h"
+
+namespace nmg {
+
+// ---------------------------------------------------------------------------
+// host-side hierarchy (fp64), built once per operator
+// ---------------------------------------------------------------------------
+
+// One level's operator.  2D: A_l = alpha M_l (x) M_l + K_l (x) K_l with K_l,
+// M_l banded and stored as DIA rows: Kd[i*(2wK+1) + d] = K_l[i][i+d-wK]
+// (zero where the column is outside [0, n)).  1D: dense A_l (n x n).
+struct HostLevel {
+  int n = 0;
+  int wK = 0;
+  int wM = 0;
+  std::vector<double> Kd, Md;  // 2D
+  std::vector<double> A;       // 1D dense
+};
+
+struct HostHierarchy {
+  int dim = 0, n = 0, levels = 0;
+  double alpha = 0;
+  std::vector<HostLevel> lv;
+  std::vector<double> coarse;  // dense nc x nc coarsest operator
+  int nc = 0;
+};
+
+// Builds the Galerkin hierarchy; returns false with a message on bad input.
+bool build_host_hierarchy(const nmg_operator_desc& op, HostHierarchy& H, std::string& err);
+
+// Filter helpers (fp64, host): sqrt(2k/n) for folded bin k = 0..n/2 and the
+// first column of the 1D circulant filter Re(IDFT(m' . DFT(.))).
+std::vector<double> filter_mask_table(int n);
+std::vector<double> filter_circulant_1d(int n);
+// twiddles exp(-2 pi i k / n), k = 0..n/2-1, interleaved (re, im)
+std::vector<double> fft_twiddles(int n);
+
+// ---------------------------------------------------------------------------
+// device-side views passed to kernels by value
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct Band2D {
+  int n, wK, wM;
+  const T* Kd;
+  const T* Md;
+  T alpha;
+};
+
+// weights of one 2D conv layer: w[(ci*9 + tap)*cout + co], bias[co]
+template <typename T>
+struct ConvW {
+  const T* w;
+  const T* b;
+};
+
+// counters / error state shared by launch helpers
+struct LaunchLog {
+  long long launches = 0;
+};
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+// ---------------------------------------------------------------------------
+// kernel launchers (implemented in k_*.cu); every launcher enqueues on `st`
+// and adds the number of kernels it launched to `log`.
+// `active` is a device int[B]: right-hand sides with active[b] == 0 are
+// skipped (their outputs are left untouched).
+// ---------------------------------------------------------------------------
+
+// r = y - A x on a 2D level (+ per-tile partial sums of r^2 if partials)
+template <typename T>
+void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
+                       double* partials, int* ntiles, const int* active, cudaStream_t st,
+                       LaunchLog& log);
+// yc = R (y - A x) on a 2D level (+ partial sums of yc^2)
+template <typename T>
+void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T* y, T* yc,
+                                double* partials, int* ntiles, const int* active,
+                                cudaStream_t st, LaunchLog& log);
+// x += P e (2D)
+template <typename T>
+void launch_prolong2d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
+                      LaunchLog& log);
+
+// 1D dense variants
+template <typename T>
+void launch_residual1d(int n, const T* A, int B, const T* x, const T* y, T* r,
+                       double* partials, int* ntiles, const int* active, cudaStream_t st,
+                       LaunchLog& log);
+template <typename T>
+void launch_restrict1d(int n, int B, const T* r, T* yc, double* partials, int* ntiles,
+                       const int* active, cudaStream_t st, LaunchLog& log);
+template <typename T>
+void launch_prolong1d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
+                      LaunchLog& log);
+
+// s[b] = sqrt(sum_t partials[b*ntiles + t])
+void launch_norms(const double* partials, int ntiles, int B, double* s, const int* active,
+                  cudaStream_t st, LaunchLog& log);
+// partial sums of v^2 for a plain vector batch of `len` elements per item
+template <typename T>
+void launch_sumsq(const T* v, long long len, int B, double* partials, int* ntiles,
+                  const int* active, cudaStream_t st, LaunchLog& log);
+// relres = s / fn; deactivate converged (<= rtol) or diverged items;
+// cycles[b] += 1 for items still active after the test if count_cycle.
+void launch_converge(const double* s, const double* fn, double rtol, int B, int* active,
+                     double* relres, int* status, int* nactive, cudaStream_t st,
+                     LaunchLog& log);
+
+// CNN smoother (SIMT), 2D: h = s * N(b / s)
+template <typename T>
+void launch_cnn2d_simt(int n, int B, int layers, int width, const ConvW<T>* layers_w,
+                       const T* b, const double* s, T* act0, T* act1, T* h, const int* active,
+                       cudaStream_t st, LaunchLog& log);
+// CNN smoother, 1D, all layers fused: weights packed per layer as
+// w[(co*cin + ci)*k + t] then bias
+template <typename T>
+void launch_cnn1d(int n, int B, int layers, int width, int ksize, const T* wpacked,
+                  const T* b, const double* s, T* h, const int* active, cudaStream_t st,
+                  LaunchLog& log);
+
+// filter: x = xstar + F'(h) (2D FFT passes); xstar may be null; x may alias xstar
+template <typename T>
+void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
+                     const T* twiddles, const double* mask_tab, const int* active,
+                     cudaStream_t st, LaunchLog& log);
+template <typename T>
+void launch_filter1d(int n, int B, const T* xstar, const T* h, T* x, const double* circ,
+                     const int* active, cudaStream_t st, LaunchLog& log);
+// x = xstar + h (filter off)
+template <typename T>
+void launch_axpy_update(long long len, int B, const T* xstar, const T* h, T* x,
+                        const int* active, cudaStream_t st, LaunchLog& log);
+
+// coarse: in-place Cholesky of an nc x nc fp64 matrix (device); flag set to
+// 1 if a pivot is not positive
+void launch_cholesky(int nc, double* A, int* flag, cudaStream_t st, LaunchLog& log);
+template <typename T>
+void launch_coarse_solve(int nc, const double* L, int B, const T* y, T* x, const int* active,
+                         cudaStream_t st, LaunchLog& log);
+
+// cycles[b] += 1 for active items
+void launch_count_cycles(int B, const int* active, int* cycles, cudaStream_t st, LaunchLog& log);
+
+// fp64 helpers for the refinement form
+// u += d (u fp64, d float)
+void launch_update_f64(long long len, int B, const float* d, double* u, const int* active,
+                       cudaStream_t st, LaunchLog& log);
+
+}  // namespace nmg

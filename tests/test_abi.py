@@ -1,0 +1,65 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/nmg.h declares; host-side argument handling of the binding."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nmg_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_2603_01064_gb300 as nmg
+    from paper_2603_01064_gb300 import build
+    if not os.path.exists(nmg.lib_path()):
+        build.build()
+    return nmg.lib_path()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["nmg_create", "nmg_setup", "nmg_solve", "nmg_solve_host", "nmg_cycle",
+                 "nmg_destroy", "nmg_destroy_hier", "nmg_status_str", "nmg_residual",
+                 "nmg_residual_restrict", "nmg_smooth", "nmg_filter_update", "nmg_coarse_solve",
+                 "nmg_prolong_correct"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(libpath):
+    import paper_2603_01064_gb300 as nmg
+    L = nmg.lib()
+    assert L.nmg_status_str(0) == b"ok"
+    assert L.nmg_status_str(-3).startswith(b"coarsest")
+    assert L.nmg_status_str(-99) == b"unknown status"
+
+
+def test_create_rejects_bad_device_without_gpu(libpath):
+    import paper_2603_01064_gb300 as nmg
+    h = ctypes.c_void_p()
+    assert nmg.lib().nmg_create(ctypes.byref(h), 12345, None) == -1
+
+
+def test_pack_weights_order():
+    import nmg_inputs as I
+    import paper_2603_01064_gb300 as nmg
+    W = I.random_cnn_weights(2, 2, seed=1)
+    p = nmg.pack_weights(W)
+    assert p.size == 2 * 19105
+    assert p[0] == W[0][0][0].ravel()[0]
+    assert p[288] == W[0][0][1][0]          # bias after the first conv weights
+    assert p[19105] == W[1][0][0].ravel()[0]

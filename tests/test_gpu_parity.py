@@ -1,0 +1,270 @@
+"""GPU parity: every step and whole cycles of the CUDA path against the FP64
+oracle on the same seeded inputs, through the C ABI.
+
+Tolerances (norm-wise relative error unless stated):
+  fp64: single steps 1e-12, one cycle 1e-10 (per-cycle iterate bound);
+  fp32: single steps 2e-5, one cycle 1e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import nmg_inputs as I  # noqa: E402
+import oracle as O  # noqa: E402
+import paper_2603_01064_gb300 as nmg  # noqa: E402
+
+TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5}
+TOL_CYCLE = {"fp64": 1e-10, "fp32": 1e-5}
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+def relerr(a, b):
+    a = np.asarray(a, np.float64).reshape(a.shape[0], -1)
+    b = np.asarray(b, np.float64).reshape(b.shape[0], -1)
+    return np.max(np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return nmg.Context(0)
+
+
+def dev(a, prec):
+    return torch.tensor(np.ascontiguousarray(a), dtype=DT[prec], device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def make2d(ctx, prec, n=64, levels=4, sigma=2.0, alpha=1e-2, seed=3, filt=True):
+    taps = I.gaussian_taps(sigma)
+    W = I.random_cnn_weights(2, levels - 1, seed=seed)
+    H = O.build_hierarchy_2d(taps, n, alpha, levels)
+    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=levels, alpha=alpha, taps=taps, precision=prec,
+                      filter=filt, weights=W)
+    return H, G, W
+
+
+def make1d(ctx, n=256, levels=3, alpha=1e-3, seed=4, weights=None, filt=True):
+    col = I.kernel_column_1d(n)
+    W = weights if weights is not None else I.random_cnn_weights(1, levels - 1, seed=seed)
+    H = O.build_hierarchy_1d(col, alpha, levels)
+    G = nmg.Hierarchy(ctx, dim=1, n=n, levels=levels, alpha=alpha, taps=col, precision="fp64",
+                      filter=filt, weights=W)
+    return H, G, W
+
+
+# ---------------------------------------------------------------------------
+# setup (a1): the library's Galerkin factors equal the oracle's dense RAP
+# ---------------------------------------------------------------------------
+
+def test_hierarchy_factors_match_oracle(ctx):
+    H, G, _ = make2d(ctx, "fp64", n=128, levels=5)
+    for l in range(5):
+        K, M = G.level_dense(l)
+        Mo, Ko = H.ops[l]
+        assert np.max(np.abs(K - Ko)) < 1e-15
+        assert np.max(np.abs(M - Mo)) < 1e-15
+    H1, G1, _ = make1d(ctx)
+    for l in range(3):
+        assert np.max(np.abs(G1.level_dense(l) - H1.ops[l])) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# single steps (2D)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_residual_and_norms(ctx, prec):
+    H, G, _ = make2d(ctx, prec)
+    rng = np.random.default_rng(1)
+    for l in range(H.levels):
+        m = H.size(l)
+        x = rng.standard_normal((3, m, m))
+        y = rng.standard_normal((3, m, m))
+        xd, yd = dev(x, prec), dev(y, prec)
+        rd = torch.empty_like(xd)
+        norms = G.residual(l, xd, yd, rd, norms=True)
+        ref = y - O.apply_level(H, l, x)
+        assert relerr(host(rd), ref) < TOL_STEP[prec]
+        assert np.max(np.abs(norms - np.linalg.norm(ref.reshape(3, -1), axis=1)) /
+                      np.linalg.norm(ref.reshape(3, -1), axis=1)) < TOL_STEP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_residual_restrict(ctx, prec):
+    H, G, _ = make2d(ctx, prec)
+    rng = np.random.default_rng(2)
+    for l in range(H.levels - 1):
+        m = H.size(l)
+        x = rng.standard_normal((2, m, m))
+        y = rng.standard_normal((2, m, m))
+        yc = torch.empty((2, m // 2, m // 2), dtype=DT[prec], device="cuda")
+        G.residual_restrict(l, dev(x, prec), dev(y, prec), yc)
+        ref = O.restrict(H, l, y - O.apply_level(H, l, x))
+        assert relerr(host(yc), ref) < TOL_STEP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_smoother(ctx, prec):
+    H, G, W = make2d(ctx, prec)
+    rng = np.random.default_rng(3)
+    for l in range(H.levels - 1):
+        m = H.size(l)
+        b = rng.standard_normal((3, m, m)) * np.array([1.0, 1e-3, 50.0])[:, None, None]
+        hd = torch.empty((3, m, m), dtype=DT[prec], device="cuda")
+        G.smooth(l, dev(b, prec), hd)
+        ref = O.smoother(W[l], b)
+        assert relerr(host(hd), ref) < 10 * TOL_STEP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_smoother_zero_input(ctx, prec):
+    H, G, W = make2d(ctx, prec)
+    b = torch.zeros((2, 64, 64), dtype=DT[prec], device="cuda")
+    hd = torch.full((2, 64, 64), 7.0, dtype=DT[prec], device="cuda")
+    G.smooth(0, b, hd)
+    assert torch.count_nonzero(hd).item() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_filter_update(ctx, prec):
+    H, G, _ = make2d(ctx, prec)
+    rng = np.random.default_rng(4)
+    for l in range(H.levels - 1):
+        m = H.size(l)
+        h = rng.standard_normal((2, m, m))
+        xs = rng.standard_normal((2, m, m))
+        xd = dev(xs, prec)
+        G.filter_update(l, xd, dev(h, prec), xd)  # in place: x = x* + F'(h)
+        ref = xs + O.spectral_filter(h, 2)
+        assert relerr(host(xd), ref) < TOL_STEP[prec]
+        out = torch.empty_like(xd)
+        G.filter_update(l, None, dev(h, prec), out)
+        assert relerr(host(out), O.spectral_filter(h, 2)) < TOL_STEP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coarse_and_prolong(ctx, prec):
+    H, G, _ = make2d(ctx, prec)
+    rng = np.random.default_rng(5)
+    nc = H.size(H.levels - 1)
+    y = rng.standard_normal((3, nc, nc))
+    xd = torch.empty((3, nc, nc), dtype=DT[prec], device="cuda")
+    G.coarse_solve(dev(y, prec), xd)
+    ref = O.cholesky_solve(H.chol, y.reshape(3, -1).T).T.reshape(3, nc, nc)
+    assert relerr(host(xd), ref) < 10 * TOL_STEP[prec]
+    for l in range(H.levels - 1):
+        m = H.size(l)
+        e = rng.standard_normal((2, m // 2, m // 2))
+        x = rng.standard_normal((2, m, m))
+        xd = dev(x, prec)
+        G.prolong_correct(l, dev(e, prec), xd)
+        assert relerr(host(xd), x + O.prolong(H, l, e)) < TOL_STEP[prec]
+
+
+# ---------------------------------------------------------------------------
+# one cycle from the same state (per-cycle iterate parity)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("filt", [True, False])
+def test_one_cycle_2d(ctx, prec, filt):
+    H, G, W = make2d(ctx, prec, filt=filt)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal((4, 64, 64))
+    u0 = rng.standard_normal((4, 64, 64)) * 0.1
+    u0[0] = 0.0  # the paper's x^0 = 0
+    ud = dev(u0, prec)
+    G.cycle(dev(f, prec), ud)
+    ref = O.nmgf(H, W, 0, u0, f, filt=filt)
+    assert relerr(host(ud), ref) < TOL_CYCLE[prec]
+
+
+def test_one_cycle_ragged_small_levels(ctx):
+    """n = 64 with 5 levels: smoother on an 8x8 grid (smaller than a tile) and a
+    4x4 coarsest grid."""
+    H, G, W = make2d(ctx, "fp64", n=64, levels=5, sigma=1.0)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((3, 64, 64))
+    ud = torch.zeros((3, 64, 64), dtype=torch.float64, device="cuda")
+    G.cycle(dev(f, "fp64"), ud)
+    ref = O.nmgf(H, W, 0, None, f)
+    assert relerr(host(ud), ref) < TOL_CYCLE["fp64"]
+
+
+def test_one_cycle_single_level_is_exact(ctx):
+    taps = I.gaussian_taps(1.0)
+    G = nmg.Hierarchy(ctx, dim=2, n=8, levels=1, alpha=1e-2, taps=taps, precision="fp64")
+    H = O.build_hierarchy_2d(taps, 8, 1e-2, 1)
+    f = np.random.default_rng(8).standard_normal((2, 8, 8))
+    ud = torch.zeros((2, 8, 8), dtype=torch.float64, device="cuda")
+    G.cycle(dev(f, "fp64"), ud)
+    assert relerr(host(ud), O.nmgf(H, [], 0, None, f)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# 1D (Algorithm 3), fp64
+# ---------------------------------------------------------------------------
+
+def test_1d_steps(ctx):
+    H, G, W = make1d(ctx)
+    rng = np.random.default_rng(9)
+    for l in range(2):
+        m = H.size(l)
+        x, y = rng.standard_normal((2, m)), rng.standard_normal((2, m))
+        rd = torch.empty((2, m), dtype=torch.float64, device="cuda")
+        G.residual(l, dev(x, "fp64"), dev(y, "fp64"), rd)
+        assert relerr(host(rd), y - O.apply_level(H, l, x)) < 1e-13
+        yc = torch.empty((2, m // 2), dtype=torch.float64, device="cuda")
+        G.residual_restrict(l, dev(x, "fp64"), dev(y, "fp64"), yc)
+        assert relerr(host(yc), O.restrict(H, l, y - O.apply_level(H, l, x))) < 1e-13
+        hd = torch.empty((2, m), dtype=torch.float64, device="cuda")
+        G.smooth(l, dev(y, "fp64"), hd)
+        assert relerr(host(hd), O.smoother(W[l], y)) < 1e-12
+        xd = dev(x, "fp64")
+        G.filter_update(l, xd, dev(y, "fp64"), xd)
+        assert relerr(host(xd), x + O.spectral_filter(y, 1)) < 1e-12
+
+
+def test_1d_one_cycle(ctx):
+    H, G, W = make1d(ctx)
+    rng = np.random.default_rng(10)
+    f = rng.standard_normal((5, 256))
+    u0 = 0.01 * rng.standard_normal((5, 256))
+    ud = dev(u0, "fp64")
+    G.cycle(dev(f, "fp64"), ud)
+    assert relerr(host(ud), O.nmgf(H, W, 0, u0, f)) < TOL_CYCLE["fp64"]
+
+
+# ---------------------------------------------------------------------------
+# argument checking (no launch happens for any of these)
+# ---------------------------------------------------------------------------
+
+def test_setup_argument_errors(ctx):
+    taps = I.gaussian_taps(2.0)
+    with pytest.raises(nmg.NMGError) as e:
+        nmg.Hierarchy(ctx, dim=2, n=96, levels=4, alpha=1e-2, taps=taps, precision="fp32",
+                      weights=I.random_cnn_weights(2, 3, 0))
+    assert e.value.code == -1
+    with pytest.raises(nmg.NMGError) as e:
+        nmg.Hierarchy(ctx, dim=2, n=64, levels=4, alpha=1e-2, taps=taps, precision="fp32",
+                      weights=I.random_cnn_weights(2, 2, 0))
+    assert e.value.code == -6
+    with pytest.raises(nmg.NMGError) as e:
+        nmg.Hierarchy(ctx, dim=2, n=64, levels=4, alpha=-1.0, taps=taps, precision="fp32",
+                      weights=I.random_cnn_weights(2, 3, 0))
+    assert e.value.code == -3
+
+
+def test_batch_zero_is_noop(ctx):
+    H, G, W = make2d(ctx, "fp32")
+    f = torch.zeros((0, 64, 64), dtype=torch.float32, device="cuda")
+    cyc, st, rr = G.solve(f, f.clone())
+    assert len(cyc) == 0
