@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the neural multigrid solve: right-hand sides solved per
+second to relative residual 1e-6.
+
+One step = one full solve of a batch of right-hand sides (every row of the
+cycle: residual, norms, smoother, output filter, fused residual+restriction,
+coarsest Cholesky solve, prolongation; the refinement form adds the
+compensated outer residual and the fp64 update) from x^0 = 0 until every
+right-hand side meets the tolerance.  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (a 256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c3]
+
+Under torchrun each rank solves its own batch (different seeds, the same
+sizes): weak scaling with no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import nmg_inputs as I  # noqa: E402
+
+WEIGHTS = os.path.join(ROOT, "paper_2603_01064_gb300", "weights")
+METRIC = "RHS solved/s to 1e-6 rel. residual"
+
+WORKLOADS = {
+    # 2D BTTB deblurring, 128x128, PSF sigma 2 px (truncated at 4 sigma), alpha 1e-2,
+    # 5 levels, 256 right-hand sides (ellipses + Gaussian random field, blurred, 1% noise)
+    "c2": dict(name="2d_bttb_128x128_sigma2_alpha1e-2_L5_batch256", n=128, levels=5, alpha=1e-2,
+               sigma=2.0, batch=256, precision="fp32", rhs="ellipses_grf", rhs_seed=1002,
+               weights="c2_2d_n128_s2_a1e-2.npz"),
+}
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x fp32 lanes x FMA x max clock
+FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_last": 2 * 9 * 32}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_rhs(wl, batch, seed):
+    if wl["rhs"] == "ellipses_grf":
+        f, _ = I.rhs_2d_ellipses_grf(wl["n"], batch, seed, wl["sigma"])
+    else:
+        f, _ = I.rhs_2d_waves_rects(wl["n"], batch, seed, wl["sigma"])
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_solve_rate(wl, nrhs, seed, reps=1):
+    """Time the FP64 oracle on `nrhs` right-hand sides of the workload."""
+    import oracle as O
+    import paper_2603_01064_gb300 as nmg_pkg  # weights loader only (no library call)
+    W = nmg_pkg.load_weights(os.path.join(WEIGHTS, wl["weights"]))
+    H = O.build_hierarchy_2d(I.gaussian_taps(wl["sigma"]), wl["n"], wl["alpha"], wl["levels"])
+    f = make_rhs(wl, nrhs, seed)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        u, cyc, rr = O.solve(H, W, f, rtol=1e-6, max_cycles=100)
+    dt = time.perf_counter() - t0
+    return nrhs * reps / dt, dt, cyc, rr
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return
+    nrhs = 1
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_solve_rate(wl, nrhs, wl["rhs_seed"])
+    times = []
+    for k in range(args.steps):
+        _, dt, cyc, rr = oracle_solve_rate(wl, nrhs, wl["rhs_seed"] + k)
+        times.append(dt)
+    value = nrhs * args.steps / sum(times)
+    sample = f"{nrhs} right-hand sides of the workload per step (FP64 numpy oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "n": wl["n"], "levels": wl["levels"],
+                       "batch": nrhs, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl, world, rank, local):
+    import torch
+    import paper_2603_01064_gb300 as nmg
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = nmg.Context(local, stream=stream.cuda_stream)
+    W = nmg.load_weights(os.path.join(WEIGHTS, wl["weights"]))
+    taps = I.gaussian_taps(wl["sigma"])
+    G = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"], taps=taps,
+                      precision=wl["precision"], weights=W)
+    B = args.batch or wl["batch"]
+    f_np = make_rhs(wl, B, wl["rhs_seed"] + 7919 * rank)
+    fdt = torch.float32
+    udt = torch.float64 if wl["precision"] == "bf16_refine" else torch.float32
+    f = torch.tensor(f_np, dtype=fdt, device="cuda")
+    u = torch.zeros(f.shape, dtype=udt, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        u.zero_()
+        return G.solve(f, u, rtol=1e-6, max_cycles=100)
+
+    if args.ncu:
+        # one solve only: the command profiled by ncu
+        cyc, st, rr = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_run": wl["name"], "batch": B, "cycles": float(cyc.mean()),
+                          "max_relres": float(rr.max()), "launches": ctx.launches()}))
+        return
+    for _ in range(max(args.warmup, 0)):
+        cyc, st, rr = step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = ctx.launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    times = []
+    cycles, relres, statuses = [], [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cyc, st, rr = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        cycles.append(cyc)
+        relres.append(rr)
+        statuses.append(st)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = ctx.launches() - l0
+    clk = clocks.stop()
+    total_ms = reduce_max(sum(times), world)
+    value = B * world * args.steps / (total_ms / 1e3)
+    converged = bool(all((s == 0).all() for s in statuses))
+    max_relres = float(max(r.max() for r in relres))
+    mean_cycles = float(np.mean([c.mean() for c in cycles]))
+
+    # ---- per-kernel timing with CUDA events on the library's stream
+    ctx.profile(True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        step()
+    ctx.profile(False)
+    kern = {}
+    for kind, name in enumerate(nmg.KERNEL_CLASSES):
+        c, ms, units = ctx.profile_read(kind)
+        if c:
+            kern[name] = {"launches": c, "ms": ms, "units": units}
+    prof_total = sum(v["ms"] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    peaks, peak_src = load_peaks()
+    d = kern[dom]
+    if dom in FLOPS_PER_PX:
+        achieved = FLOPS_PER_PX[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
+        roof = {"kernel": f"{dom} (fp32 SIMT 3x3 conv)", "bound": "alu", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None,
+                "peak_source": "152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz (derived)",
+                "flop_per_unit": FLOPS_PER_PX[dom], "launch_ms": d["ms"] / d["launches"]}
+    else:
+        bpu = {"residual": 12, "restrict": 9, "prolong": 9, "filter": 8}.get(dom, 8)
+        achieved = bpu * d["units"] / (d["ms"] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peak_src, "bytes_per_unit": bpu,
+                "launch_ms": d["ms"] / d["launches"]}
+    breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                     "share": v["ms"] / prof_total} for k, v in kern.items()}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    fh = torch.tensor(f_np, dtype=fdt).pin_memory().numpy()
+    uh = torch.zeros(f.shape, dtype=udt).pin_memory().numpy()
+    G.solve_host(fh, uh)  # warm the staging buffers
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        uh[...] = 0.0
+        G.solve_host(fh, uh)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e = {"value": B * world * args.steps / e2e_s, "unit": "RHS/s",
+           "h2d_bytes_per_step": int(fh.nbytes + uh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, _, _ = oracle_solve_rate(wl, 2, wl["rhs_seed"])
+        cpu = {"value": rate, "unit": "RHS/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"2 of the {B} right-hand sides, full solve to 1e-6 ({dt:.1f} s, "
+                         "numpy FP64, BLAS threads = all host cores)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "bf16_refine": "bf16+f32+f64"}[wl["precision"]],
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "n": wl["n"], "levels": wl["levels"],
+                           "batch_per_gpu": B, "precision": wl["precision"],
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "parallelism": f"replicas x{world}"},
+                "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
+                "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling runs)")
+    ap.add_argument("--ncu", action="store_true", help="a single solve, nothing else (profiling)")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+    else:
+        run_ours(args, wl, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -67,8 +67,9 @@ typedef enum { NMG_FP64 = 0, NMG_FP32 = 1, NMG_BF16_REFINE = 2 } nmg_precision;
  * Operator description (Section 2.1, Eq. (1); Eq. (10) in 1D; the
  * Kronecker form alpha I(x)I + K(x)K of Section 4.2 in 2D).
  *   dim      1 or 2
- *   n        fine grid side; n % 2^(levels-1) == 0 (Section 2.3).  The
- *            coarsest grid must have at most 4096 unknowns.
+ *   n        fine grid side: a power of two (the output filter uses radix-2
+ *            FFTs), so n % 2^(levels-1) == 0 as Section 2.3 requires.  The
+ *            coarsest grid must have at most 1024 unknowns.
  *   levels   L, counting the coarsest level; smoothers run on levels
  *            1..L-1, the exact solve on level L.  levels >= 1.
  *   alpha    regularisation weight (> 0 is not required, but the coarsest
@@ -192,6 +193,30 @@ nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double*
 
 /* Number of kernels the library launched on this context so far. */
 long long nmg_launch_count(const nmg_ctx* ctx);
+
+/* Per-kernel-class timing.  nmg_profile_enable(ctx, 1) clears previous
+ * records and starts recording a pair of CUDA events on the context's stream
+ * around every launch; 0 stops recording (records are kept).
+ * nmg_profile_read synchronises the stream and reports, for one class, the
+ * number of recorded launches, their summed device time in milliseconds and
+ * the summed work units (grid points x active right-hand sides; 0 for
+ * bookkeeping kernels).  Classes: */
+enum {
+  NMG_K_RESIDUAL = 0,         /* r = y - A x (banded 2D / dense 1D) */
+  NMG_K_RESTRICT = 1,         /* R (y - A x) fused */
+  NMG_K_CNN_FIRST = 2,        /* first conv layer (2D SIMT) */
+  NMG_K_CNN_HIDDEN = 3,       /* hidden conv layers (2D SIMT) */
+  NMG_K_CNN_LAST = 4,         /* last conv layer (2D SIMT) */
+  NMG_K_FILTER = 5,           /* output filter passes */
+  NMG_K_COARSE = 6,           /* coarsest triangular solves */
+  NMG_K_PROLONG = 7,          /* prolongation + correction */
+  NMG_K_REFINE_RESIDUAL = 8,  /* compensated outer residual */
+  NMG_K_OTHER = 9,            /* norms, convergence flags, updates */
+  NMG_K_CNN_FUSED = 10        /* fused smoother (bf16 tensor cores, 1D) */
+};
+nmg_status nmg_profile_enable(nmg_ctx* ctx, int enable);
+nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double* ms,
+                            double* units);
 /* Wait for the context's stream. */
 nmg_status nmg_sync(nmg_ctx* ctx);
 const char* nmg_status_str(nmg_status s);

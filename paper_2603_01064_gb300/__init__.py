@@ -21,6 +21,9 @@ __all__ = [
 ]
 
 FP64, FP32, BF16_REFINE = 0, 1, 2
+# kernel classes of Context.profile_read (NMG_K_* in nmg.h)
+KERNEL_CLASSES = ["residual", "restrict", "cnn_first", "cnn_hidden", "cnn_last", "filter",
+                  "coarse", "prolong", "refine_residual", "other", "cnn_fused"]
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE}
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
 
@@ -84,6 +87,9 @@ def lib():
                               ctypes.POINTER(I)]),
         "nmg_hier_level_dense": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "nmg_launch_count": (ctypes.c_longlong, [P]),
+        "nmg_profile_enable": (I, [P, I]),
+        "nmg_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
+                                 ctypes.POINTER(D)]),
         "nmg_sync": (I, [P]),
         "nmg_status_str": (ctypes.c_char_p, [I]),
         "nmg_last_error": (ctypes.c_char_p, [P]),
@@ -146,6 +152,18 @@ class Context:
 
     def launches(self) -> int:
         return int(lib().nmg_launch_count(self._h))
+
+    def profile(self, enable: bool):
+        self.check(lib().nmg_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self, kind: int):
+        """(launches, total device ms, work units) recorded for a kernel class."""
+        c = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        u = ctypes.c_double()
+        self.check(lib().nmg_profile_read(self._h, kind, ctypes.byref(c), ctypes.byref(ms),
+                                          ctypes.byref(u)))
+        return c.value, ms.value, u.value
 
     def close(self):
         if self._h:

@@ -408,6 +408,7 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     CK(cudaStreamSynchronize(st));
   }
   int nt = 0;
+  ctx->log.active_hint = B;
   launch_sumsq<T>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, st, ctx->log);
   launch_norms(w.part[0], nt, B, w.fn, w.ones, st, ctx->log);
   T* b0 = reinterpret_cast<T*>(w.t[0]);
@@ -419,6 +420,7 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, st, ctx->log);
     CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    ctx->log.active_hint = *w.h_nactive;
     if (*w.h_nactive == 0 || tau >= max_cycles) break;
     cycle_body<T>(h, B, f, u, u, b0, w.s[0], w.active);
     launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
@@ -449,6 +451,7 @@ nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rt
     CK(cudaStreamSynchronize(st));
   }
   int nt = 0;
+  ctx->log.active_hint = B;
   launch_sumsq<float>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, st, ctx->log);
   launch_norms(w.part[0], nt, B, w.fn, w.ones, st, ctx->log);
   for (int tau = 0;; ++tau) {
@@ -458,6 +461,7 @@ nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rt
     launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, st, ctx->log);
     CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    ctx->log.active_hint = *w.h_nactive;
     if (*w.h_nactive == 0 || tau >= max_cycles) break;
     // inner bf16 cycle on (0, r): d = NMGF(0, r)
     cycle_body<float>(h, B, w.r32, w.d32, nullptr, w.r32, w.s[0], w.active);
@@ -521,6 +525,7 @@ nmg_status nmg_create(nmg_ctx** out, int device, void* stream) {
 void nmg_destroy(nmg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  for (cudaEvent_t e : ctx->log.pool) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) {
     cudaStreamSynchronize(ctx->stream);
     cudaStreamDestroy(ctx->stream);
@@ -752,6 +757,7 @@ nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* 
   if (!f || !u) return fail(ctx, NMG_ERR_ARG, "null f or u");
   if ((s = set_device(ctx)) != NMG_OK) return s;
   if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  ctx->log.active_hint = batch;
   Work& w = h->w;
   if (h->precision == NMG_BF16_REFINE) {
     int nt = 0;
@@ -783,6 +789,7 @@ static nmg_status step_check(nmg_ctx* ctx, nmg_hier* h, int level, int batch, in
   if (s != NMG_OK) return s;
   if (level < 0 || level > maxlevel) return fail(ctx, NMG_ERR_ARG, "level out of range");
   if ((s = set_device(ctx)) != NMG_OK) return s;
+  ctx->log.active_hint = batch;
   return ensure_work(h, batch > 0 ? batch : 1);
 }
 
@@ -913,6 +920,37 @@ nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double*
 }
 
 long long nmg_launch_count(const nmg_ctx* ctx) { return ctx ? ctx->log.launches : 0; }
+
+nmg_status nmg_profile_enable(nmg_ctx* ctx, int enable) {
+  if (!ctx) return NMG_ERR_ARG;
+  if (enable) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->log.recs.clear();
+    ctx->log.pool_used = 0;
+  }
+  ctx->log.prof = enable != 0;
+  return NMG_OK;
+}
+
+nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double* ms,
+                            double* units) {
+  if (!ctx || kind < 0 || kind >= K_NKINDS) return NMG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  long long c = 0;
+  double t = 0.0, u = 0.0;
+  for (const ProfRec& r : ctx->log.recs) {
+    if (r.kind != kind) continue;
+    float e = 0.f;
+    CK(cudaEventElapsedTime(&e, r.a, r.b));
+    ++c;
+    t += e;
+    u += r.units;
+  }
+  if (launches) *launches = c;
+  if (ms) *ms = t;
+  if (units) *units = u;
+  return NMG_OK;
+}
 
 nmg_status nmg_sync(nmg_ctx* ctx) {
   if (!ctx) return NMG_ERR_ARG;

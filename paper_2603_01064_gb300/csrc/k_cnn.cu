@@ -135,8 +135,9 @@ void launch_layer(int n, int B, const T* in, T* out, const ConvW<T>& cw, const d
   auto kern = k_conv3x3<T, CIN, COUT, MODE>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(tx * tx, B);
+  int pi_ = log.begin(MODE == 0 ? K_CNN_FIRST : (MODE == 1 ? K_CNN_HIDDEN : K_CNN_LAST), st);
   kern<<<grid, 256, sm, st>>>(n, in, out, cw.w, cw.b, s, active, tx);
-  log.launches++;
+  log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
 // ---- 1D fused ---------------------------------------------------------------
@@ -237,8 +238,9 @@ void launch_cnn1d(int n, int B, int layers, int width, int ksize, const T* wpack
   size_t sm = 2 * (size_t)width * (SEG + 2 * H) * sizeof(T);
   cudaFuncSetAttribute(k_cnn1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(ceil_div(n, SEG), B);
+  int pi_ = log.begin(K_CNN_FUSED, st);
   k_cnn1d<T><<<grid, 256, sm, st>>>(n, layers, width, ksize, wpacked, b, s, h, active);
-  log.launches++;
+  log.end(pi_, st, (double)n * log.active_hint);
 }
 
 template void launch_cnn2d_simt<float>(int, int, int, int, const ConvW<float>*, const float*,

@@ -67,16 +67,18 @@ __global__ void k_coarse_solve(int nc, const double* __restrict__ L, const T* __
 }  // namespace
 
 void launch_cholesky(int nc, double* A, int* flag, cudaStream_t st, LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
   k_cholesky<<<1, 256, 0, st>>>(nc, A, flag);
-  log.launches++;
+  log.end(pi_, st, 0.0);
 }
 
 template <typename T>
 void launch_coarse_solve(int nc, const double* L, int B, const T* y, T* x, const int* active,
                          cudaStream_t st, LaunchLog& log) {
   int threads = nc < 64 ? 32 : (nc < 256 ? 64 : 256);
+  int pi_ = log.begin(K_COARSE, st);
   k_coarse_solve<T><<<B, threads, nc * sizeof(double), st>>>(nc, L, y, x, active);
-  log.launches++;
+  log.end(pi_, st, (double)nc * log.active_hint);
 }
 
 template void launch_coarse_solve<float>(int, const double*, int, const float*, float*,

@@ -197,18 +197,25 @@ void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
   cudaFuncSetAttribute(k_fft_cols_mask<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_fft_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(n / per, B);
+  const double units = (double)n * n * log.active_hint;
+  int pi_ = log.begin(K_FILTER, st);
   k_fft_rows_fwd<T><<<grid, 256, sm, st>>>(n, logn, per, h, C, tw, active);
+  log.end(pi_, st, units);
+  pi_ = log.begin(K_FILTER, st);
   k_fft_cols_mask<T><<<grid, 256, sm, st>>>(n, logn, per, C, tw, mask_tab, active);
+  log.end(pi_, st, units);
+  pi_ = log.begin(K_FILTER, st);
   k_fft_rows_inv<T><<<grid, 256, sm, st>>>(n, logn, per, C, xstar, x, tw, active);
-  log.launches += 3;
+  log.end(pi_, st, units);
 }
 
 template <typename T>
 void launch_filter1d(int n, int B, const T* xstar, const T* h, T* x, const double* circ,
                      const int* active, cudaStream_t st, LaunchLog& log) {
   dim3 grid(ceil_div(n, 8), B);
+  int pi_ = log.begin(K_FILTER, st);
   k_filter1d<T><<<grid, 256, 0, st>>>(n, xstar, h, x, circ, active);
-  log.launches++;
+  log.end(pi_, st, (double)n * log.active_hint);
 }
 
 template void launch_filter2d<float>(int, int, const float*, const float*, float*, void*,

@@ -373,9 +373,10 @@ void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
   auto kern = k_residual2d<T, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(tx * tx, B);
+  int pi_ = log.begin(K_RESIDUAL, st);
   kern<<<grid, kThreads, sm, st>>>(op, x, y, r, partials, active, tile, tx);
   if (ntiles) *ntiles = tx * tx;
-  log.launches++;
+  log.end(pi_, st, (double)op.n * op.n * log.active_hint);
 }
 
 template <typename T>
@@ -389,17 +390,19 @@ void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T*
   auto kern = k_residual2d<T, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(tx * tx, B);
+  int pi_ = log.begin(K_RESTRICT, st);
   kern<<<grid, kThreads, sm, st>>>(op, x, y, yc, partials, active, tile, tx);
   if (ntiles) *ntiles = tx * tx;
-  log.launches++;
+  log.end(pi_, st, (double)op.n * op.n * log.active_hint);
 }
 
 template <typename T>
 void launch_prolong2d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
                       LaunchLog& log) {
   long long total = (long long)n * n * B;
+  int pi_ = log.begin(K_PROLONG, st);
   k_prolong2d<T><<<grid_for(total, 256), 256, 0, st>>>(n, B, e, x, active);
-  log.launches++;
+  log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
 template <typename T>
@@ -408,31 +411,35 @@ void launch_residual1d(int n, const T* A, int B, const T* x, const T* y, T* r,
                        LaunchLog& log) {
   int rows = 8;  // warps per block
   dim3 grid(ceil_div(n, rows), B);
+  int pi_ = log.begin(K_RESIDUAL, st);
   k_residual1d<T><<<grid, rows * 32, 0, st>>>(n, A, x, y, r, partials, active);
   if (ntiles) *ntiles = grid.x;
-  log.launches++;
+  log.end(pi_, st, (double)n * log.active_hint);
 }
 
 template <typename T>
 void launch_restrict1d(int n, int B, const T* r, T* yc, double* partials, int* ntiles,
                        const int* active, cudaStream_t st, LaunchLog& log) {
   dim3 grid(ceil_div(n / 2, 128), B);
+  int pi_ = log.begin(K_RESTRICT, st);
   k_restrict1d<T><<<grid, 128, 0, st>>>(n, r, yc, partials, active);
   if (ntiles) *ntiles = grid.x;
-  log.launches++;
+  log.end(pi_, st, (double)n * log.active_hint);
 }
 
 template <typename T>
 void launch_prolong1d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
                       LaunchLog& log) {
+  int pi_ = log.begin(K_PROLONG, st);
   k_prolong1d<T><<<grid_for((long long)n * B, 256), 256, 0, st>>>(n, B, e, x, active);
-  log.launches++;
+  log.end(pi_, st, (double)n * log.active_hint);
 }
 
 void launch_norms(const double* partials, int ntiles, int B, double* s, const int* active,
                   cudaStream_t st, LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
   k_norms<<<ceil_div(B, 128), 128, 0, st>>>(partials, ntiles, B, s, active);
-  log.launches++;
+  log.end(pi_, st, 0.0);
 }
 
 template <typename T>
@@ -441,34 +448,39 @@ void launch_sumsq(const T* v, long long len, int B, double* partials, int* ntile
   int g = (int)std::min<long long>(64, (len + 255) / 256);
   if (g < 1) g = 1;
   dim3 grid(g, B);
+  int pi_ = log.begin(K_OTHER, st);
   k_sumsq<T><<<grid, 256, 0, st>>>(v, len, partials, active);
   if (ntiles) *ntiles = g;
-  log.launches++;
+  log.end(pi_, st, 0.0);
 }
 
 void launch_converge(const double* s, const double* fn, double rtol, int B, int* active,
                      double* relres, int* status, int* nactive, cudaStream_t st,
                      LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
   k_converge<<<ceil_div(B, 128), 128, 0, st>>>(s, fn, rtol, B, active, relres, status, nactive);
-  log.launches++;
+  log.end(pi_, st, 0.0);
 }
 
 template <typename T>
 void launch_axpy_update(long long len, int B, const T* xstar, const T* h, T* x,
                         const int* active, cudaStream_t st, LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
   k_axpy_update<T><<<grid_for(len * B, 256), 256, 0, st>>>(len, B, xstar, h, x, active);
-  log.launches++;
+  log.end(pi_, st, 0.0);
 }
 
 void launch_count_cycles(int B, const int* active, int* cycles, cudaStream_t st, LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
   k_count_cycles<<<ceil_div(B, 128), 128, 0, st>>>(B, active, cycles);
-  log.launches++;
+  log.end(pi_, st, 0.0);
 }
 
 void launch_update_f64(long long len, int B, const float* d, double* u, const int* active,
                        cudaStream_t st, LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
   k_update_f64<<<grid_for(len * B, 256), 256, 0, st>>>(len, B, d, u, active);
-  log.launches++;
+  log.end(pi_, st, (double)len * log.active_hint);
 }
 
 #define NMG_INST(T)                                                                          \

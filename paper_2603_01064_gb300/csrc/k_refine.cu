@@ -143,10 +143,11 @@ void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float*
   size_t sm = smem(tile);
   cudaFuncSetAttribute(k_refine_residual2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(tx * tx, B);
+  int pi_ = log.begin(K_REFINE_RESIDUAL, st);
   k_refine_residual2d<0><<<grid, 256, sm, st>>>(hi, Kd_lo, Md_lo, alpha, u, f, r, partials, active,
                                                 tile, tx);
   if (ntiles) *ntiles = tx * tx;
-  log.launches++;
+  log.end(pi_, st, (double)hi.n * hi.n * log.active_hint);
 }
 
 }  // namespace nmg

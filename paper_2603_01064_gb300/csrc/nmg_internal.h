@@ -65,9 +65,48 @@ struct ConvW {
   const T* b;
 };
 
-// counters / error state shared by launch helpers
+// kernel classes for the optional per-class event timing (nmg_profile_*)
+enum KernelKind {
+  K_RESIDUAL = 0, K_RESTRICT = 1, K_CNN_FIRST = 2, K_CNN_HIDDEN = 3, K_CNN_LAST = 4,
+  K_FILTER = 5, K_COARSE = 6, K_PROLONG = 7, K_REFINE_RESIDUAL = 8, K_OTHER = 9,
+  K_CNN_FUSED = 10, K_NKINDS = 11
+};
+
+// launch counter and, when profiling is on, CUDA-event records around each
+// launch on the launching stream (events come from a reusable pool)
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double units;
+};
 struct LaunchLog {
   long long launches = 0;
+  bool prof = false;
+  double active_hint = 0;  // right-hand sides currently active (host view)
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  cudaEvent_t get_event() {
+    if (pool_used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[pool_used++];
+  }
+  int begin(int kind, cudaStream_t st) {
+    ++launches;
+    if (!prof) return -1;
+    ProfRec r{kind, get_event(), get_event(), 0.0};
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+  }
+  void end(int idx, cudaStream_t st, double units) {
+    if (idx < 0) return;
+    cudaEventRecord(recs[idx].b, st);
+    recs[idx].units = units;
+  }
 };
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
