@@ -24,8 +24,9 @@
 
 namespace nmg {
 void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b, const double* s,
-                     float* act0, float* act1, float* h, const int* active, cudaStream_t st,
-                     LaunchLog& log);
+                     float* act0, float* act1, float* h, const int* active, int* err,
+                     cudaStream_t st, LaunchLog& log);
+void bf16_cnn_forget(const void* pack);
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::vector<const double*>& bias);
 void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
                        double alpha, int B, const double* u, const float* f, float* r,
@@ -77,6 +78,7 @@ struct Work {
   int* ones = nullptr;
   int* nactive = nullptr;
   int* h_nactive = nullptr;  // pinned
+  int* err = nullptr;        // device error word of bounded waits (0 = ok)
   void* act0 = nullptr;
   void* act1 = nullptr;
   void* cbuf = nullptr;
@@ -211,6 +213,7 @@ nmg_status ensure_work(nmg_hier* h, int B) {
   AL(B * sizeof(int), w.active);
   AL(B * sizeof(int), w.ones);
   AL(sizeof(int), w.nactive);
+  AL(sizeof(int), w.err);
   if (h->dim == 2 && h->L > 1) {
     size_t n0 = plane(h, 0);
     size_t actb = (size_t)h->width * n0 * B * (h->precision == NMG_FP64 ? 8 : 4);
@@ -225,6 +228,10 @@ nmg_status ensure_work(nmg_hier* h, int B) {
   {
     cudaError_t e = cudaMallocHost(&w.h_nactive, sizeof(int));
     if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "cudaMallocHost"); }
+  }
+  {
+    cudaError_t e0 = cudaMemset(w.err, 0, sizeof(int));
+    if (e0 != cudaSuccess) { free_work(w); return cuda_fail(ctx, e0, "cudaMemset(err)"); }
   }
   std::vector<int> ones(B, 1);
   cudaError_t e = cudaMemcpy(w.ones, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice);
@@ -426,6 +433,15 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
   }
   CK(cudaGetLastError());
+  {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) {
+      cudaMemsetAsync(w.err, 0, sizeof(int), st);
+      return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its iteration limit");
+    }
+  }
   if (info) {
     std::vector<int> cyc(B), stt(B);
     std::vector<double> rr(B);
@@ -469,6 +485,15 @@ nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rt
     launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
   }
   CK(cudaGetLastError());
+  {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) {
+      cudaMemsetAsync(w.err, 0, sizeof(int), st);
+      return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its iteration limit");
+    }
+  }
   if (info) {
     std::vector<int> cyc(B), stt(B);
     std::vector<double> rr(B);
@@ -695,6 +720,8 @@ void nmg_destroy_hier(nmg_hier* h) {
   if (!h) return;
   cudaSetDevice(h->ctx->device);
   cudaStreamSynchronize(h->ctx->stream);
+  for (DevLevel& d : h->lv)
+    if (d.bf16_pack) bf16_cnn_forget(d.bf16_pack);
   free_work(h->w);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
@@ -978,7 +1005,8 @@ void launch_cnn2d_bf16_dispatch(nmg_hier* h, int l, int B, const float* b, const
   DevLevel& d = h->lv[l];
   // fp32 SIMT fallback is not used: the bf16 pack is built at setup
   bf16_cnn_launch(d.n, B, h->layers, d.bf16_pack, b, s, reinterpret_cast<float*>(h->w.act0),
-                  reinterpret_cast<float*>(h->w.act1), out, active, h->ctx->stream, h->ctx->log);
+                  reinterpret_cast<float*>(h->w.act1), out, active, h->w.err, h->ctx->stream,
+                  h->ctx->log);
 }
 
 void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const float* f,

@@ -1,20 +1,436 @@
-// bf16 tensor-core CNN smoother (placeholder until the tensor-core kernel
-// lands): the pack builder reports "unsupported".
+// bf16 tensor-core CNN smoother h = N(b / ||b||) ||b|| (Algorithms 3/4)
+// with tcgen05.mma (accumulators in tensor memory), one kernel per layer.
+//
+// Each 3x3 conv layer is an implicit GEMM  D[pixel][cout] = sum over taps
+// and input channels of A[pixel + shift(tap)][cin] * W[tap][cin][cout].
+// One MMA tile is M = 128 output pixels arranged as 16 image rows x 8
+// columns, so its eight-row groups of the K-major no-swizzle operand layout
+// are image rows: with the input tile staged in shared memory as
+// [channel chunk of 8][tile row][tile column][8 channels], the operand for
+// tap (dy, dx) is the same layout started dy rows and dx pixels further on,
+// and the group stride (SBO) is one tile row.  A block covers 16 x 16
+// output pixels (two M tiles side by side), the 9 taps x 2 K halves give 18
+// MMAs of 128 x N x 16 per M tile, accumulated in fp32 in tensor memory.
+//
+//   first layer  1 -> 32: A is the 3x3 neighbourhood (9 values, padded to
+//                K = 16) of b / ||b|| built in shared memory; one MMA.
+//   hidden       32 -> 32: 18 MMAs, ReLU, bf16 activations NHWC.
+//   last         32 -> 1: N padded to 16 with zero weights; output
+//                ||b|| * (acc + bias) in fp32.
+//
+// Blocks are persistent: a block stages its layer's weights once and loops
+// over tiles.  Every wait on the MMA-completion mbarrier is bounded; on
+// timeout the block records an error code and stops.
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
 #include "nmg_internal.h"
 
 namespace nmg {
 
-void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
-                    const std::vector<const double*>& bias) {
-  (void)layers; (void)W; (void)bias;
-  return nullptr;
+namespace {
+
+constexpr int TILE = 16;           // output tile side (pixels)
+constexpr int NT = 2;              // M tiles per block (columns 0-7, 8-15)
+constexpr int RW = TILE + 2;       // staged input row pitch in pixels
+constexpr int RH = TILE + 2;       // staged input rows
+constexpr int CH_BYTES = RH * RW * 16;  // one 8-channel chunk of the staged tile
+constexpr int WIDTH = 32;
+constexpr int THREADS = 128;
+constexpr long long kSpinLimit = 1LL << 26;
+
+enum Mode { FIRST = 0, HIDDEN = 1, LAST = 2 };
+
+// weights per layer in the MMA B layout, bf16:
+//   FIRST : [kchunk 2][cout 32][8]  (k = tap, zero for k >= 9)
+//   HIDDEN: [tap 9][kchunk 4][cout 32][8 cin]
+//   LAST  : [tap 9][kchunk 4][cout 16][8 cin] (cout >= 1 zero)
+struct LayerPack {
+  const __nv_bfloat16* w;
+  const float* bias;
+  int wcount;  // bf16 elements
+};
+struct Bf16Pack {
+  int layers;
+  LayerPack l[8];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// SM100 shared-memory matrix descriptor, no swizzle (K-major canonical
+// layout ((8, m), 2) : ((16 B, SBO), LBO)).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;
+}
+
+// instruction descriptor, kind::f16: bf16 A and B, fp32 D, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// 32 lanes x 32 columns of fp32 from tensor memory (this warp's lane quarter)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(THREADS)
+k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level vector
+          const __nv_bfloat16* __restrict__ ain,                // HIDDEN/LAST: NHWC input
+          __nv_bfloat16* __restrict__ aout,                     // FIRST/HIDDEN: NHWC output
+          float* __restrict__ hout,                             // LAST: level vector
+          LayerPack lp, const double* __restrict__ snorm, const int* __restrict__ active,
+          int* __restrict__ err) {
+  constexpr int NOUT = MODE == LAST ? 16 : 32;
+  constexpr int A_BYTES = MODE == FIRST ? NT * 2 * 128 * 16 : 4 * CH_BYTES;
+  constexpr int B_BYTES = MODE == FIRST ? 2 * 32 * 16 : 9 * 4 * NOUT * 16;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* As = smem;
+  unsigned char* Bs = smem + A_BYTES;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // weights once per block
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(lp.w);
+    uint4* dst = reinterpret_cast<uint4*>(Bs);
+    for (int i = tid; i < B_BYTES / 16; i += THREADS) dst[i] = src[i];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs), mb = smem_u32(&mbar);
+  const uint32_t idesc = make_idesc(128, NOUT);
+  const int tiles_x = (n + TILE - 1) / TILE;
+  const int per_img = tiles_x * tiles_x;
+  const long long total = (long long)nimg * per_img;
+  const size_t plane = (size_t)n * n;
+  uint32_t phase = 0;
+
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int b = (int)(t / per_img);
+    const int tt = (int)(t % per_img);
+    const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
+    if (!active[b]) continue;  // uniform across the block
+    const double s = snorm[b];
+    if (s == 0.0) {
+      if (MODE == LAST) {
+        for (int p = tid; p < TILE * TILE; p += THREADS) {
+          int y = y0 + p / TILE, x = x0 + p % TILE;
+          if (y < n && x < n) hout[(size_t)b * plane + (size_t)y * n + x] = 0.f;
+        }
+      }
+      continue;
+    }
+    // ---- stage the A operand
+    if (MODE == FIRST) {
+      const float inv = (float)(1.0 / s);
+      const float* bb = bsrc + (size_t)b * plane;
+      for (int i = tid; i < TILE * TILE * 16; i += THREADS) {
+        int k = i & 15, p = i >> 4;
+        int ry = p / TILE, rx = p % TILE;
+        float v = 0.f;
+        if (k < 9) {
+          int y = y0 + ry + k / 3 - 1, x = x0 + rx + k % 3 - 1;
+          if (y >= 0 && y < n && x >= 0 && x < n) v = bb[(size_t)y * n + x] * inv;
+        }
+        int mt = rx >> 3, m = ry * 8 + (rx & 7);
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(
+            As + mt * (2 * 128 * 16) + (k >> 3) * (128 * 16) + m * 16 + (k & 7) * 2);
+        *dst = __float2bfloat16_rn(v);
+      }
+    } else {
+      const __nv_bfloat16* ab = ain + (size_t)b * plane * WIDTH;
+      for (int i = tid; i < RH * RW * 4; i += THREADS) {
+        int c = i & 3, p = i >> 2;
+        int ry = p / RW, rx = p % RW;
+        int y = y0 + ry - 1, x = x0 + rx - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (y >= 0 && y < n && x >= 0 && x < n)
+          v = *reinterpret_cast<const uint4*>(ab + ((size_t)y * n + x) * WIDTH + c * 8);
+        *reinterpret_cast<uint4*>(As + c * CH_BYTES + (ry * RW + rx) * 16) = v;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- MMAs (one thread)
+    if (tid == 0) {
+      for (int mt = 0; mt < NT; ++mt) {
+        const uint32_t d = tmem + mt * 32;
+        if (MODE == FIRST) {
+          uint64_t ad = make_desc(a_base + mt * (2 * 128 * 16), 128 * 16, 128);
+          uint64_t bd = make_desc(b_base, 32 * 16, 128);
+          mma_bf16(d, ad, bd, idesc, 0u);
+        } else {
+          uint32_t acc = 0;
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+            for (int kh = 0; kh < 2; ++kh) {
+              uint64_t ad = make_desc(a_base + 2 * kh * CH_BYTES + (dy * RW + 8 * mt + dx) * 16,
+                                      CH_BYTES, RW * 16);
+              uint64_t bd = make_desc(b_base + (tap * 4 + 2 * kh) * NOUT * 16, NOUT * 16, 128);
+              mma_bf16(d, ad, bd, idesc, acc);
+              acc = 1u;
+            }
+          }
+        }
+      }
+      mma_commit(mb);
+    }
+    // ---- wait for the accumulators (bounded)
+    {
+      long long it = 0;
+      while (!mbar_try_wait(mb, phase)) {
+        if (++it > kSpinLimit) {
+          if (tid == 0) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+          }
+          break;
+        }
+      }
+      phase ^= 1u;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- epilogue: warp w reads TMEM lanes 32w..32w+31 = pixels m of each M tile
+    for (int mt = 0; mt < NT; ++mt) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + mt * 32, v);
+      const int m = warp * 32 + lane;
+      const int y = y0 + (m >> 3), x = x0 + mt * 8 + (m & 7);
+      if (y < n && x < n) {
+        if (MODE == LAST) {
+          hout[(size_t)b * plane + (size_t)y * n + x] = (float)s * (v[0] + lp.bias[0]);
+        } else {
+          uint32_t pk[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(v[2 * c] + lp.bias[2 * c], 0.f),
+                                                      fmaxf(v[2 * c + 1] + lp.bias[2 * c + 1], 0.f));
+            pk[c] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(aout + ((size_t)b * plane + (size_t)y * n + x) * WIDTH);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+}
+
+// host bf16 round-to-nearest-even of a finite float
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+int g_num_sms = 0;
+
+template <int MODE>
+void launch_mode(int n, int nimg, const float* b, const __nv_bfloat16* ain, __nv_bfloat16* aout,
+                 float* h, const LayerPack& lp, const double* s, const int* active, int* err,
+                 cudaStream_t st, LaunchLog& log) {
+  constexpr int NOUT = MODE == LAST ? 16 : 32;
+  constexpr int A_BYTES = MODE == FIRST ? NT * 2 * 128 * 16 : 4 * CH_BYTES;
+  constexpr int B_BYTES = MODE == FIRST ? 2 * 32 * 16 : 9 * 4 * NOUT * 16;
+  const size_t sm = A_BYTES + B_BYTES;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  const int tiles_x = (n + TILE - 1) / TILE;
+  long long total = (long long)nimg * tiles_x * tiles_x;
+  long long grid = (long long)g_num_sms * 4;
+  if (grid > total) grid = total;
+  if (grid < 1) grid = 1;
+  cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int pi_ = log.begin(MODE == FIRST ? K_CNN_FIRST : (MODE == HIDDEN ? K_CNN_HIDDEN : K_CNN_LAST), st);
+  k_conv_tc<MODE><<<(int)grid, THREADS, sm, st>>>(n, nimg, b, ain, aout, h, lp, s, active, err);
+  log.end(pi_, st, (double)n * n * log.active_hint);
+}
+
+}  // namespace
+
+// Build the device weight pack of one smoother level from PyTorch-layout
+// fp64 weights (width 32, 3x3).  Returns a single device allocation that
+// holds the Bf16Pack header followed by the packed weights and biases.
+void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
+                    const std::vector<const double*>& bias) {
+  if (layers < 2 || layers > 8) return nullptr;
+  std::vector<std::vector<uint16_t>> wl(layers);
+  std::vector<std::vector<float>> bl(layers);
+  for (int li = 0; li < layers; ++li) {
+    const int mode = li == 0 ? FIRST : (li == layers - 1 ? LAST : HIDDEN);
+    const int cin = li == 0 ? 1 : WIDTH, cout = li == layers - 1 ? 1 : WIDTH;
+    const double* w = W[li];
+    if (mode == FIRST) {
+      std::vector<uint16_t> p(2 * 32 * 8, 0);
+      for (int co = 0; co < 32; ++co)
+        for (int k = 0; k < 9; ++k) p[((k >> 3) * 32 + co) * 8 + (k & 7)] = bf16_bits((float)w[co * 9 + k]);
+      wl[li] = p;
+    } else {
+      const int NOUT = mode == LAST ? 16 : 32;
+      std::vector<uint16_t> p((size_t)9 * 4 * NOUT * 8, 0);
+      for (int co = 0; co < cout; ++co)
+        for (int ci = 0; ci < cin; ++ci)
+          for (int tap = 0; tap < 9; ++tap)
+            p[(((size_t)tap * 4 + ci / 8) * NOUT + co) * 8 + ci % 8] =
+                bf16_bits((float)w[((size_t)co * cin + ci) * 9 + tap]);
+      wl[li] = p;
+    }
+    bl[li].assign(32, 0.f);
+    for (int co = 0; co < cout; ++co) bl[li][co] = (float)bias[li][co];
+  }
+  size_t bytes = 256;
+  std::vector<size_t> woff(layers), boff(layers);
+  for (int li = 0; li < layers; ++li) {
+    woff[li] = bytes;
+    bytes += (wl[li].size() * 2 + 255) / 256 * 256;
+    boff[li] = bytes;
+    bytes += 256;
+  }
+  unsigned char* dptr = nullptr;
+  if (cudaMalloc(&dptr, bytes) != cudaSuccess) return nullptr;
+  std::vector<unsigned char> host(bytes, 0);
+  Bf16Pack hdr{};
+  hdr.layers = layers;
+  for (int li = 0; li < layers; ++li) {
+    std::memcpy(host.data() + woff[li], wl[li].data(), wl[li].size() * 2);
+    std::memcpy(host.data() + boff[li], bl[li].data(), 32 * sizeof(float));
+    hdr.l[li].w = reinterpret_cast<const __nv_bfloat16*>(dptr + woff[li]);
+    hdr.l[li].bias = reinterpret_cast<const float*>(dptr + boff[li]);
+    hdr.l[li].wcount = (int)wl[li].size();
+  }
+  std::memcpy(host.data(), &hdr, sizeof(hdr));
+  if (cudaMemcpy(dptr, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dptr);
+    return nullptr;
+  }
+  return dptr;
+}
+
+// The pack's header lives at the start of the device allocation; launches
+// need it on the host, so it is read back once per pack and cached.
+namespace {
+struct PackCache {
+  const void* key = nullptr;
+  Bf16Pack hdr{};
+};
+PackCache g_cache[64];
+const Bf16Pack* host_header(const void* pack) {
+  for (auto& c : g_cache)
+    if (c.key == pack) return &c.hdr;
+  for (auto& c : g_cache)
+    if (c.key == nullptr) {
+      cudaMemcpy(&c.hdr, pack, sizeof(Bf16Pack), cudaMemcpyDeviceToHost);
+      c.key = pack;
+      return &c.hdr;
+    }
+  static Bf16Pack tmp;
+  cudaMemcpy(&tmp, pack, sizeof(Bf16Pack), cudaMemcpyDeviceToHost);
+  return &tmp;
+}
+}  // namespace
+
+void bf16_cnn_forget(const void* pack) {
+  for (auto& c : g_cache)
+    if (c.key == pack) c.key = nullptr;
+}
+
+// h = s N(b / s) for `B` images of side n; act0/act1 hold NHWC bf16
+// activations (B * n * n * 32 elements each); err: device error word.
 void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b, const double* s,
-                     float* act0, float* act1, float* h, const int* active, cudaStream_t st,
-                     LaunchLog& log) {
-  (void)n; (void)B; (void)layers; (void)pack; (void)b; (void)s; (void)act0; (void)act1;
-  (void)h; (void)active; (void)st; (void)log;
+                     float* act0, float* act1, float* h, const int* active, int* err,
+                     cudaStream_t st, LaunchLog& log) {
+  const Bf16Pack* P = host_header(pack);
+  __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(act0);
+  __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(act1);
+  launch_mode<FIRST>(n, B, b, nullptr, a0, nullptr, P->l[0], s, active, err, st, log);
+  __nv_bfloat16* cur = a0;
+  __nv_bfloat16* nxt = a1;
+  for (int li = 1; li < layers - 1; ++li) {
+    launch_mode<HIDDEN>(n, B, nullptr, cur, nxt, nullptr, P->l[li], s, active, err, st, log);
+    __nv_bfloat16* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  launch_mode<LAST>(n, B, nullptr, cur, nullptr, h, P->l[layers - 1], s, active, err, st, log);
 }
 
 }  // namespace nmg
