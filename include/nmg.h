@@ -31,7 +31,9 @@
  *  - Element types follow the hierarchy's precision:
  *      NMG_FP64          f, u, every level vector: double
  *      NMG_FP32          f, u, every level vector: float
- *      NMG_BF16_REFINE   f: float, u: double; level vectors of the inner
+ *      NMG_BF16_REFINE,
+ *      NMG_BF16FAST_REFINE
+ *                        f: float, u: double; level vectors of the inner
  *                        cycle (step entry points): float.  The smoother
  *                        runs on bf16 tensor cores with fp32 accumulation.
  */
@@ -61,7 +63,23 @@ typedef enum {
 /* per right-hand-side outcome, in nmg_solve_info.status */
 enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };
 
-typedef enum { NMG_FP64 = 0, NMG_FP32 = 1, NMG_BF16_REFINE = 2 } nmg_precision;
+/* Precision forms.  The two bf16 forms run the cycle as an inner solve of
+ * an outer iterative refinement (residual in compensated fp32, update in
+ * fp64) with the smoother on bf16 tensor cores and fp32 accumulation:
+ *   NMG_BF16_REFINE      every smoother operand is a pair of bf16 values
+ *                        (hi + lo), 2-3 MMAs per product; per-cycle
+ *                        iterates agree with fp64 to about 1e-4.
+ *   NMG_BF16FAST_REFINE  one bf16 value per operand, 1 MMA per product;
+ *                        the cycle converges at the same rate but single
+ *                        cycles differ from fp64 by up to ~20%, because the
+ *                        smoother's output carries a large near-constant
+ *                        part that the output filter removes. */
+typedef enum {
+  NMG_FP64 = 0,
+  NMG_FP32 = 1,
+  NMG_BF16_REFINE = 2,
+  NMG_BF16FAST_REFINE = 3
+} nmg_precision;
 
 /*
  * Operator description (Section 2.1, Eq. (1); Eq. (10) in 1D; the

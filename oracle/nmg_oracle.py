@@ -40,7 +40,7 @@ __all__ = [
     "prolongation", "restriction", "toeplitz_from_column", "banded_toeplitz",
     "Hierarchy", "build_hierarchy_1d", "build_hierarchy_2d",
     "cholesky", "cholesky_solve", "apply_level", "cnn_forward", "smoother",
-    "filter_mask", "spectral_filter", "restrict", "prolong", "nmgf", "solve",
+    "filter_mask", "spectral_filter", "restrict", "prolong", "nmgf", "relres", "solve",
 ]
 
 

@@ -16,15 +16,16 @@ from typing import Sequence
 import numpy as np
 
 __all__ = [
-    "FP64", "FP32", "BF16_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
+    "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
     "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo",
 ]
 
-FP64, FP32, BF16_REFINE = 0, 1, 2
+FP64, FP32, BF16_REFINE, BF16FAST_REFINE = 0, 1, 2, 3
 # kernel classes of Context.profile_read (NMG_K_* in nmg.h)
 KERNEL_CLASSES = ["residual", "restrict", "cnn_first", "cnn_hidden", "cnn_last", "filter",
                   "coarse", "prolong", "refine_residual", "other", "cnn_fused"]
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE,
+              "bf16fast_refine": BF16FAST_REFINE}
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

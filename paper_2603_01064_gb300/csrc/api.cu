@@ -27,7 +27,8 @@ void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b,
                      float* act0, float* act1, float* h, const int* active, int* err,
                      cudaStream_t st, LaunchLog& log);
 void bf16_cnn_forget(const void* pack);
-void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::vector<const double*>& bias);
+void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::vector<const double*>& bias,
+                    int split);
 void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
                        double alpha, int B, const double* u, const float* f, float* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
@@ -133,6 +134,9 @@ nmg_status cuda_fail(nmg_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 size_t elem_size(int precision) { return precision == NMG_FP64 ? 8 : 4; }
+bool is_refine(int precision) {
+  return precision == NMG_BF16_REFINE || precision == NMG_BF16FAST_REFINE;
+}
 
 size_t plane(const nmg_hier* h, int l) {
   size_t n = (size_t)(h->n >> l);
@@ -221,7 +225,7 @@ nmg_status ensure_work(nmg_hier* h, int B) {
     AL(actb, w.act1);
     AL(n0 * B * 2 * es, w.cbuf);
   }
-  if (h->precision == NMG_BF16_REFINE) {
+  if (is_refine(h->precision)) {
     AL(plane(h, 0) * B * sizeof(float), w.r32);
     AL(plane(h, 0) * B * sizeof(float), w.d32);
   }
@@ -323,7 +327,7 @@ void op_smooth<float>(nmg_hier* h, int l, int B, const float* b, const double* s
   nmg_ctx* c = h->ctx;
   const DevLevel& d = h->lv[l];
   if (h->dim == 2) {
-    if (h->precision == NMG_BF16_REFINE) {
+    if (is_refine(h->precision)) {
       launch_cnn2d_bf16_dispatch(h, l, B, b, s, out, active);
       return;
     }
@@ -562,9 +566,9 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
                      nmg_hier** out) {
   if (!ctx || !op || !out) return fail(ctx, NMG_ERR_ARG, "null argument to nmg_setup");
   *out = nullptr;
-  if (op->precision < NMG_FP64 || op->precision > NMG_BF16_REFINE)
+  if (op->precision < NMG_FP64 || op->precision > NMG_BF16FAST_REFINE)
     return fail(ctx, NMG_ERR_ARG, "unknown precision");
-  if (op->precision == NMG_BF16_REFINE && op->dim != 2)
+  if (is_refine(op->precision) && op->dim != 2)
     return fail(ctx, NMG_ERR_UNSUPPORTED, "the bf16 refinement form is 2D only");
   std::unique_ptr<nmg_hier> h(new nmg_hier());
   h->ctx = ctx;
@@ -669,7 +673,7 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
           d.bf.push_back(upload(ctx, h->allocs, to_f(bb), &st));
         }
       }
-      if (st == NMG_OK && h->precision == NMG_BF16_REFINE) {
+      if (st == NMG_OK && is_refine(h->precision)) {
         std::vector<const double*> Wp, bp;
         size_t o = 0;
         for (int i = 0; i < h->layers; ++i) {
@@ -679,7 +683,7 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
           bp.push_back(base + o);
           o += cout;
         }
-        d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp);
+        d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp, h->precision == NMG_BF16_REFINE ? 1 : 0);
         if (!d.bf16_pack) st = fail(ctx, NMG_ERR_UNSUPPORTED, "bf16 tensor-core smoother unavailable");
         else h->allocs.push_back(d.bf16_pack);
       }
@@ -786,7 +790,7 @@ nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* 
   if ((s = ensure_work(h, batch)) != NMG_OK) return s;
   ctx->log.active_hint = batch;
   Work& w = h->w;
-  if (h->precision == NMG_BF16_REFINE) {
+  if (is_refine(h->precision)) {
     int nt = 0;
     launch_refine_residual_dispatch(h, batch, (const double*)u, (const float*)f, w.r32, w.part[0],
                                     &nt, w.ones);

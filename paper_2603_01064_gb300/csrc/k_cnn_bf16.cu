@@ -21,6 +21,15 @@
 // Blocks are persistent: a block stages its layer's weights once and loops
 // over tiles.  Every wait on the MMA-completion mbarrier is bounded; on
 // timeout the block records an error code and stops.
+//
+// Split form (SPLIT = 1, the default bf16 form): the smoother's output is
+// dominated by near-constant content that the output filter removes, so a
+// single bf16 rounding of the input and the activations (2^-9 relative) is
+// amplified far beyond the useful filtered part.  Every operand is therefore
+// carried as a pair of bf16 values v = hi + lo (|lo| <= 2^-9 |v|) and each
+// product is formed from bf16 tensor-core MMAs a_hi*w_hi + a_lo*w_hi
+// (+ a_hi*w_lo when the fp32 weights are not bf16-exact), accumulated in
+// fp32 in tensor memory.  Activations are stored as [hi 32 | lo 32] bf16.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -47,12 +56,14 @@ enum Mode { FIRST = 0, HIDDEN = 1, LAST = 2 };
 //   HIDDEN: [tap 9][kchunk 4][cout 32][8 cin]
 //   LAST  : [tap 9][kchunk 4][cout 16][8 cin] (cout >= 1 zero)
 struct LayerPack {
-  const __nv_bfloat16* w;
+  const __nv_bfloat16* w;  // SPLIT: hi block then lo block
   const float* bias;
-  int wcount;  // bf16 elements
+  int wcount;  // bf16 elements of one block
+  int has_lo;  // lo block not all zero
 };
 struct Bf16Pack {
   int layers;
+  int split;
   LayerPack l[8];
 };
 
@@ -119,7 +130,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int MODE>
+template <int MODE, int SPLIT>
 __global__ void __launch_bounds__(THREADS)
 k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level vector
           const __nv_bfloat16* __restrict__ ain,                // HIDDEN/LAST: NHWC input
@@ -128,8 +139,11 @@ k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level 
           LayerPack lp, const double* __restrict__ snorm, const int* __restrict__ active,
           int* __restrict__ err) {
   constexpr int NOUT = MODE == LAST ? 16 : 32;
-  constexpr int A_BYTES = MODE == FIRST ? NT * 2 * 128 * 16 : 4 * CH_BYTES;
-  constexpr int B_BYTES = MODE == FIRST ? 2 * 32 * 16 : 9 * 4 * NOUT * 16;
+  constexpr int ACH = MODE == FIRST ? (SPLIT ? 6 : 2) : (SPLIT ? 8 : 4);  // A chunks
+  constexpr int A_BYTES = MODE == FIRST ? NT * ACH * 128 * 16 : ACH * CH_BYTES;
+  constexpr int B_HALF = MODE == FIRST ? (SPLIT ? 6 : 2) * 32 * 16 : 9 * 4 * NOUT * 16;
+  constexpr int B_BYTES = (SPLIT && MODE != FIRST) ? 2 * B_HALF : B_HALF;
+  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;  // stored channels per pixel
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* As = smem;
   unsigned char* Bs = smem + A_BYTES;
@@ -196,19 +210,25 @@ k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level 
           if (y >= 0 && y < n && x >= 0 && x < n) v = bb[(size_t)y * n + x] * inv;
         }
         int mt = rx >> 3, m = ry * 8 + (rx & 7);
-        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(
-            As + mt * (2 * 128 * 16) + (k >> 3) * (128 * 16) + m * 16 + (k & 7) * 2);
-        *dst = __float2bfloat16_rn(v);
+        unsigned char* base = As + mt * (ACH * 128 * 16) + m * 16 + (k & 7) * 2;
+        __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(base + (k >> 3) * (128 * 16)) = hi;
+        if (SPLIT) {
+          // chunks 2,3: lo taps (times W_hi); chunks 4,5: hi taps again (times W_lo)
+          __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+          *reinterpret_cast<__nv_bfloat16*>(base + (2 + (k >> 3)) * (128 * 16)) = lo;
+          *reinterpret_cast<__nv_bfloat16*>(base + (4 + (k >> 3)) * (128 * 16)) = hi;
+        }
       }
     } else {
-      const __nv_bfloat16* ab = ain + (size_t)b * plane * WIDTH;
-      for (int i = tid; i < RH * RW * 4; i += THREADS) {
-        int c = i & 3, p = i >> 2;
+      const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
+      for (int i = tid; i < RH * RW * ACH; i += THREADS) {
+        int c = i % ACH, p = i / ACH;
         int ry = p / RW, rx = p % RW;
         int y = y0 + ry - 1, x = x0 + rx - 1;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (y >= 0 && y < n && x >= 0 && x < n)
-          v = *reinterpret_cast<const uint4*>(ab + ((size_t)y * n + x) * WIDTH + c * 8);
+          v = *reinterpret_cast<const uint4*>(ab + ((size_t)y * n + x) * CW + c * 8);
         *reinterpret_cast<uint4*>(As + c * CH_BYTES + (ry * RW + rx) * 16) = v;
       }
     }
@@ -221,19 +241,31 @@ k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level 
       for (int mt = 0; mt < NT; ++mt) {
         const uint32_t d = tmem + mt * 32;
         if (MODE == FIRST) {
-          uint64_t ad = make_desc(a_base + mt * (2 * 128 * 16), 128 * 16, 128);
-          uint64_t bd = make_desc(b_base, 32 * 16, 128);
-          mma_bf16(d, ad, bd, idesc, 0u);
+          const int nk = SPLIT ? (lp.has_lo ? 3 : 2) : 1;
+          for (int q = 0; q < nk; ++q) {
+            uint64_t ad = make_desc(a_base + mt * (ACH * 128 * 16) + 2 * q * (128 * 16), 128 * 16, 128);
+            uint64_t bd = make_desc(b_base + 2 * q * (32 * 16), 32 * 16, 128);
+            mma_bf16(d, ad, bd, idesc, q > 0 ? 1u : 0u);
+          }
         } else {
           uint32_t acc = 0;
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3;
             for (int kh = 0; kh < 2; ++kh) {
-              uint64_t ad = make_desc(a_base + 2 * kh * CH_BYTES + (dy * RW + 8 * mt + dx) * 16,
-                                      CH_BYTES, RW * 16);
-              uint64_t bd = make_desc(b_base + (tap * 4 + 2 * kh) * NOUT * 16, NOUT * 16, 128);
+              const uint32_t shift = (dy * RW + 8 * mt + dx) * 16;
+              const uint32_t boff = (tap * 4 + 2 * kh) * NOUT * 16;
+              uint64_t ad = make_desc(a_base + 2 * kh * CH_BYTES + shift, CH_BYTES, RW * 16);
+              uint64_t bd = make_desc(b_base + boff, NOUT * 16, 128);
               mma_bf16(d, ad, bd, idesc, acc);
               acc = 1u;
+              if (SPLIT) {
+                uint64_t adl = make_desc(a_base + (4 + 2 * kh) * CH_BYTES + shift, CH_BYTES, RW * 16);
+                mma_bf16(d, adl, bd, idesc, 1u);
+                if (lp.has_lo) {
+                  uint64_t bdl = make_desc(b_base + B_HALF + boff, NOUT * 16, 128);
+                  mma_bf16(d, ad, bdl, idesc, 1u);
+                }
+              }
             }
           }
         }
@@ -267,16 +299,26 @@ k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level 
         if (MODE == LAST) {
           hout[(size_t)b * plane + (size_t)y * n + x] = (float)s * (v[0] + lp.bias[0]);
         } else {
-          uint32_t pk[16];
+          uint32_t pk[16], pl[16];
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(v[2 * c] + lp.bias[2 * c], 0.f),
-                                                      fmaxf(v[2 * c + 1] + lp.bias[2 * c + 1], 0.f));
+            const float a0 = fmaxf(v[2 * c] + lp.bias[2 * c], 0.f);
+            const float a1 = fmaxf(v[2 * c + 1] + lp.bias[2 * c + 1], 0.f);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
             pk[c] = *reinterpret_cast<uint32_t*>(&h2);
+            if (SPLIT) {
+              __nv_bfloat162 l2 = __floats2bfloat162_rn(a0 - __low2float(h2), a1 - __high2float(h2));
+              pl[c] = *reinterpret_cast<uint32_t*>(&l2);
+            }
           }
-          uint4* dst = reinterpret_cast<uint4*>(aout + ((size_t)b * plane + (size_t)y * n + x) * WIDTH);
+          uint4* dst = reinterpret_cast<uint4*>(aout + ((size_t)b * plane + (size_t)y * n + x) * CW);
 #pragma unroll
           for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+          if (SPLIT) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[4 + q] = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
+          }
         }
       }
     }
@@ -300,13 +342,15 @@ uint16_t bf16_bits(float f) {
 
 int g_num_sms = 0;
 
-template <int MODE>
+template <int MODE, int SPLIT>
 void launch_mode(int n, int nimg, const float* b, const __nv_bfloat16* ain, __nv_bfloat16* aout,
                  float* h, const LayerPack& lp, const double* s, const int* active, int* err,
                  cudaStream_t st, LaunchLog& log) {
   constexpr int NOUT = MODE == LAST ? 16 : 32;
-  constexpr int A_BYTES = MODE == FIRST ? NT * 2 * 128 * 16 : 4 * CH_BYTES;
-  constexpr int B_BYTES = MODE == FIRST ? 2 * 32 * 16 : 9 * 4 * NOUT * 16;
+  constexpr int ACH = MODE == FIRST ? (SPLIT ? 6 : 2) : (SPLIT ? 8 : 4);
+  constexpr int A_BYTES = MODE == FIRST ? NT * ACH * 128 * 16 : ACH * CH_BYTES;
+  constexpr int B_HALF = MODE == FIRST ? (SPLIT ? 6 : 2) * 32 * 16 : 9 * 4 * NOUT * 16;
+  constexpr int B_BYTES = (SPLIT && MODE != FIRST) ? 2 * B_HALF : B_HALF;
   const size_t sm = A_BYTES + B_BYTES;
   if (g_num_sms == 0) {
     int dev = 0;
@@ -319,45 +363,76 @@ void launch_mode(int n, int nimg, const float* b, const __nv_bfloat16* ain, __nv
   long long grid = (long long)g_num_sms * 4;
   if (grid > total) grid = total;
   if (grid < 1) grid = 1;
-  cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_conv_tc<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int pi_ = log.begin(MODE == FIRST ? K_CNN_FIRST : (MODE == HIDDEN ? K_CNN_HIDDEN : K_CNN_LAST), st);
-  k_conv_tc<MODE><<<(int)grid, THREADS, sm, st>>>(n, nimg, b, ain, aout, h, lp, s, active, err);
+  k_conv_tc<MODE, SPLIT><<<(int)grid, THREADS, sm, st>>>(n, nimg, b, ain, aout, h, lp, s, active, err);
   log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
 }  // namespace
 
+// Host copies of the pack headers, keyed by device allocation (launches read
+// the per-layer pointers on the host).
+namespace {
+std::vector<std::pair<const void*, Bf16Pack>> g_headers;
+}
+
 // Build the device weight pack of one smoother level from PyTorch-layout
-// fp64 weights (width 32, 3x3).  Returns a single device allocation that
-// holds the Bf16Pack header followed by the packed weights and biases.
+// fp64 weights (width 32, 3x3).  split = 1: the split bf16 form (each weight
+// stored as bf16 hi and lo blocks, operands hi + lo); 0: plain bf16.
+// Returns one device allocation with the packed weights and fp32 biases.
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
-                    const std::vector<const double*>& bias) {
+                    const std::vector<const double*>& bias, int split) {
   if (layers < 2 || layers > 8) return nullptr;
   std::vector<std::vector<uint16_t>> wl(layers);
   std::vector<std::vector<float>> bl(layers);
+  std::vector<int> has_lo(layers, 0);
   for (int li = 0; li < layers; ++li) {
     const int mode = li == 0 ? FIRST : (li == layers - 1 ? LAST : HIDDEN);
     const int cin = li == 0 ? 1 : WIDTH, cout = li == layers - 1 ? 1 : WIDTH;
     const double* w = W[li];
+    auto hi_lo = [&](double v, uint16_t& hb, uint16_t& lb) {
+      hb = bf16_bits((float)v);
+      uint32_t u = (uint32_t)hb << 16;
+      float hf;
+      std::memcpy(&hf, &u, 4);
+      lb = bf16_bits((float)(v - (double)hf));
+      if (lb != 0 && lb != 0x8000) has_lo[li] = 1;
+    };
     if (mode == FIRST) {
-      std::vector<uint16_t> p(2 * 32 * 8, 0);
+      // chunks: [0,1] W_hi (x hi taps), [2,3] W_hi (x lo taps), [4,5] W_lo (x hi taps)
+      const int nch = split ? 6 : 2;
+      std::vector<uint16_t> p((size_t)nch * 32 * 8, 0);
       for (int co = 0; co < 32; ++co)
-        for (int k = 0; k < 9; ++k) p[((k >> 3) * 32 + co) * 8 + (k & 7)] = bf16_bits((float)w[co * 9 + k]);
+        for (int k = 0; k < 9; ++k) {
+          uint16_t hb, lb;
+          hi_lo(w[co * 9 + k], hb, lb);
+          p[((k >> 3) * 32 + co) * 8 + (k & 7)] = hb;
+          if (split) {
+            p[((2 + (k >> 3)) * 32 + co) * 8 + (k & 7)] = hb;
+            p[((4 + (k >> 3)) * 32 + co) * 8 + (k & 7)] = lb;
+          }
+        }
       wl[li] = p;
     } else {
       const int NOUT = mode == LAST ? 16 : 32;
-      std::vector<uint16_t> p((size_t)9 * 4 * NOUT * 8, 0);
+      const size_t half = (size_t)9 * 4 * NOUT * 8;
+      std::vector<uint16_t> p(split ? 2 * half : half, 0);
       for (int co = 0; co < cout; ++co)
         for (int ci = 0; ci < cin; ++ci)
-          for (int tap = 0; tap < 9; ++tap)
-            p[(((size_t)tap * 4 + ci / 8) * NOUT + co) * 8 + ci % 8] =
-                bf16_bits((float)w[((size_t)co * cin + ci) * 9 + tap]);
+          for (int tap = 0; tap < 9; ++tap) {
+            uint16_t hb, lb;
+            hi_lo(w[((size_t)co * cin + ci) * 9 + tap], hb, lb);
+            size_t idx = (((size_t)tap * 4 + ci / 8) * NOUT + co) * 8 + ci % 8;
+            p[idx] = hb;
+            if (split) p[half + idx] = lb;
+          }
       wl[li] = p;
     }
     bl[li].assign(32, 0.f);
     for (int co = 0; co < cout; ++co) bl[li][co] = (float)bias[li][co];
   }
-  size_t bytes = 256;
+  size_t bytes = 0;
   std::vector<size_t> woff(layers), boff(layers);
   for (int li = 0; li < layers; ++li) {
     woff[li] = bytes;
@@ -370,67 +445,65 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
   std::vector<unsigned char> host(bytes, 0);
   Bf16Pack hdr{};
   hdr.layers = layers;
+  hdr.split = split;
   for (int li = 0; li < layers; ++li) {
     std::memcpy(host.data() + woff[li], wl[li].data(), wl[li].size() * 2);
     std::memcpy(host.data() + boff[li], bl[li].data(), 32 * sizeof(float));
     hdr.l[li].w = reinterpret_cast<const __nv_bfloat16*>(dptr + woff[li]);
     hdr.l[li].bias = reinterpret_cast<const float*>(dptr + boff[li]);
     hdr.l[li].wcount = (int)wl[li].size();
+    hdr.l[li].has_lo = split ? has_lo[li] : 0;
   }
-  std::memcpy(host.data(), &hdr, sizeof(hdr));
   if (cudaMemcpy(dptr, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(dptr);
     return nullptr;
   }
+  g_headers.emplace_back(dptr, hdr);
   return dptr;
 }
 
-// The pack's header lives at the start of the device allocation; launches
-// need it on the host, so it is read back once per pack and cached.
-namespace {
-struct PackCache {
-  const void* key = nullptr;
-  Bf16Pack hdr{};
-};
-PackCache g_cache[64];
-const Bf16Pack* host_header(const void* pack) {
-  for (auto& c : g_cache)
-    if (c.key == pack) return &c.hdr;
-  for (auto& c : g_cache)
-    if (c.key == nullptr) {
-      cudaMemcpy(&c.hdr, pack, sizeof(Bf16Pack), cudaMemcpyDeviceToHost);
-      c.key = pack;
-      return &c.hdr;
-    }
-  static Bf16Pack tmp;
-  cudaMemcpy(&tmp, pack, sizeof(Bf16Pack), cudaMemcpyDeviceToHost);
-  return &tmp;
-}
-}  // namespace
-
 void bf16_cnn_forget(const void* pack) {
-  for (auto& c : g_cache)
-    if (c.key == pack) c.key = nullptr;
+  for (size_t i = 0; i < g_headers.size(); ++i)
+    if (g_headers[i].first == pack) {
+      g_headers.erase(g_headers.begin() + i);
+      return;
+    }
 }
 
-// h = s N(b / s) for `B` images of side n; act0/act1 hold NHWC bf16
-// activations (B * n * n * 32 elements each); err: device error word.
-void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b, const double* s,
-                     float* act0, float* act1, float* h, const int* active, int* err,
-                     cudaStream_t st, LaunchLog& log) {
-  const Bf16Pack* P = host_header(pack);
-  __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(act0);
-  __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(act1);
-  launch_mode<FIRST>(n, B, b, nullptr, a0, nullptr, P->l[0], s, active, err, st, log);
+namespace {
+template <int SPLIT>
+void run_layers(int n, int B, int layers, const Bf16Pack& P, const float* b, const double* s,
+                __nv_bfloat16* a0, __nv_bfloat16* a1, float* h, const int* active, int* err,
+                cudaStream_t st, LaunchLog& log) {
+  launch_mode<FIRST, SPLIT>(n, B, b, nullptr, a0, nullptr, P.l[0], s, active, err, st, log);
   __nv_bfloat16* cur = a0;
   __nv_bfloat16* nxt = a1;
   for (int li = 1; li < layers - 1; ++li) {
-    launch_mode<HIDDEN>(n, B, nullptr, cur, nxt, nullptr, P->l[li], s, active, err, st, log);
+    launch_mode<HIDDEN, SPLIT>(n, B, nullptr, cur, nxt, nullptr, P.l[li], s, active, err, st, log);
     __nv_bfloat16* t = cur;
     cur = nxt;
     nxt = t;
   }
-  launch_mode<LAST>(n, B, nullptr, cur, nullptr, h, P->l[layers - 1], s, active, err, st, log);
+  launch_mode<LAST, SPLIT>(n, B, nullptr, cur, nullptr, h, P.l[layers - 1], s, active, err, st, log);
+}
+}  // namespace
+
+// h = s N(b / s) for `B` images of side n; act0/act1 hold NHWC bf16
+// activations (B * n * n * 32 elements, x2 in the split form); err: device
+// error word of the bounded waits.
+void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b, const double* s,
+                     float* act0, float* act1, float* h, const int* active, int* err,
+                     cudaStream_t st, LaunchLog& log) {
+  const Bf16Pack* P = nullptr;
+  for (auto& e : g_headers)
+    if (e.first == pack) P = &e.second;
+  if (!P) return;
+  __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(act0);
+  __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(act1);
+  if (P->split)
+    run_layers<1>(n, B, layers, *P, b, s, a0, a1, h, active, err, st, log);
+  else
+    run_layers<0>(n, B, layers, *P, b, s, a0, a1, h, active, err, st, log);
 }
 
 }  // namespace nmg

@@ -1,14 +1,18 @@
-"""GPU parity of the bf16 refinement form (tensor-core smoother, compensated
+"""GPU parity of the bf16 refinement forms (tensor-core smoother, compensated
 fp32 outer residual, fp64 update) against the FP64 oracle.
 
-* The tensor-core smoother is compared with a CPU evaluation of the same
-  network that rounds to bf16 exactly where the kernel stores bf16 (input
-  b/||b||, weights, hidden activations) and accumulates in fp64: the two may
-  differ only by fp32 accumulation order (tolerance 1e-4), which pins the
-  MMA operand layout.
-* Against the plain FP64 oracle (no rounding anywhere) one refinement step
-  must match the oracle's cycle to 1e-3 and a full solve must reach
-  ||f - A u|| / ||f|| <= 1e-6 measured by the oracle's own fp64 apply.
+* bf16_refine (split operands hi + lo): the smoother and one refinement
+  step are compared directly with the un-rounded FP64 oracle; the per-cycle
+  iterate bar is 1e-3 (norm-wise relative), also for trained smoothers on
+  the first cycle from zero, where the smoother's large filtered-out
+  near-constant output makes single-rounding bf16 fail.
+* bf16fast_refine (one bf16 per operand): compared with a CPU evaluation of
+  the same network that rounds to bf16 exactly where the kernel stores bf16
+  (input b/||b||, weights, hidden activations) and accumulates in fp64: the
+  two may differ only by fp32 accumulation order (1e-4), which pins the MMA
+  operand layout; its solve must still reach the tolerance.
+* Full solves reach ||f - A u|| / ||f|| <= 1e-6 as measured by the oracle's
+  own fp64 apply.
 """
 import os
 
@@ -25,23 +29,24 @@ import paper_2603_01064_gb300 as nmg  # noqa: E402
 
 WDIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                     "paper_2603_01064_gb300", "weights")
+C2W = os.path.join(WDIR, "c2_2d_n128_s2_a1e-2.npz")
 
 
 def bf16(a):
-    """Round float64 values to bf16 (round to nearest even), returned as float64."""
+    """Round to bf16 (round to nearest even), returned as float64."""
     f = np.asarray(a, np.float32)
     u = f.view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def emulated_forward(W, b):
+def emulated_fast(W, b):
+    """s N(b/s) with single bf16 rounding at the fast kernel's storage points."""
     s = np.sqrt(np.sum(b.reshape(b.shape[0], -1) ** 2, axis=1))[:, None, None]
     x = bf16(b / s)[:, None]
-    nl = len(W)
     for i, (w, bias) in enumerate(W):
         x = ON._conv_same(x, bf16(w), np.asarray(bias, np.float32).astype(np.float64))
-        if i < nl - 1:
+        if i < len(W) - 1:
             x = bf16(np.maximum(x, 0.0))
     return x[:, 0] * s
 
@@ -53,11 +58,11 @@ def ctx():
     return nmg.Context(0)
 
 
-def make(ctx, n=64, levels=4, sigma=2.0, alpha=1e-2, seed=21, weights=None):
+def make(ctx, prec="bf16_refine", n=64, levels=4, sigma=2.0, alpha=1e-2, seed=21, weights=None):
     taps = I.gaussian_taps(sigma)
     W = weights if weights is not None else I.random_cnn_weights(2, levels - 1, seed=seed)
-    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=levels, alpha=alpha, taps=taps,
-                      precision="bf16_refine", weights=W)
+    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=levels, alpha=alpha, taps=taps, precision=prec,
+                      weights=W)
     H = O.build_hierarchy_2d(taps, n, alpha, levels)
     return H, G, W
 
@@ -68,40 +73,51 @@ def rel(a, b):
     return np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1))
 
 
-def test_tc_smoother_matches_bf16_emulation(ctx):
-    H, G, W = make(ctx)
+def smooth_gpu(G, l, b):
+    bd = torch.tensor(b, dtype=torch.float32, device="cuda")
+    hd = torch.full_like(bd, 5.0)
+    G.smooth(l, bd, hd)
+    torch.cuda.synchronize()
+    return bd.double().cpu().numpy(), hd.double().cpu().numpy()
+
+
+def test_fast_smoother_matches_bf16_emulation(ctx):
+    H, G, W = make(ctx, "bf16fast_refine")
     rng = np.random.default_rng(1)
     for l in range(H.levels - 1):
         m = H.size(l)
         b = rng.standard_normal((3, m, m)) * np.array([1.0, 1e-4, 30.0])[:, None, None]
-        bd = torch.tensor(b, dtype=torch.float32, device="cuda")
-        hd = torch.empty_like(bd)
-        G.smooth(l, bd, hd)
-        torch.cuda.synchronize()
-        ref = emulated_forward(W[l], bd.double().cpu().numpy())
-        assert rel(hd.double().cpu().numpy(), ref) < 1e-4, l
+        b32, h = smooth_gpu(G, l, b)
+        assert rel(h, emulated_fast(W[l], b32)) < 1e-4, l
 
 
-def test_tc_smoother_ragged_and_zero(ctx):
-    """A 24x24-equivalent ragged case is not possible (powers of two), so use
-    an 8x8 level (smaller than the 16x16 tile) and a zero right-hand side."""
-    H, G, W = make(ctx, n=64, levels=5, sigma=1.0)
-    rng = np.random.default_rng(2)
-    b = rng.standard_normal((2, 8, 8))
+@pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine"])
+def test_smoother_small_level_and_zero_rhs(ctx, prec):
+    """An 8x8 level (smaller than the 16x16 tile) and a zero right-hand side."""
+    H, G, W = make(ctx, prec, n=64, levels=5, sigma=1.0)
+    b = np.random.default_rng(2).standard_normal((2, 8, 8))
     b[1] = 0.0
-    bd = torch.tensor(b, dtype=torch.float32, device="cuda")
-    hd = torch.full_like(bd, 3.0)
-    G.smooth(3, bd, hd)
-    torch.cuda.synchronize()
-    h = hd.double().cpu().numpy()
+    b32, h = smooth_gpu(G, 3, b)
     assert np.all(h[1] == 0.0)
-    ref = emulated_forward(W[3], b[:1])
-    assert rel(h[:1], ref) < 1e-4
+    if prec == "bf16fast_refine":
+        assert rel(h[:1], emulated_fast(W[3], b32[:1])) < 1e-4
+    else:
+        assert rel(h[:1], O.smoother(W[3], b32[:1])) < 1e-4
+
+
+def test_split_smoother_matches_fp64(ctx):
+    H, G, W = make(ctx, "bf16_refine")
+    rng = np.random.default_rng(3)
+    for l in range(H.levels - 1):
+        m = H.size(l)
+        b = rng.standard_normal((3, m, m)) * np.array([1.0, 1e-4, 30.0])[:, None, None]
+        b32, h = smooth_gpu(G, l, b)
+        assert rel(h, O.smoother(W[l], b32)) < 1e-4, l
 
 
 def test_refine_step_matches_fp64_cycle(ctx):
-    H, G, W = make(ctx)
-    rng = np.random.default_rng(3)
+    H, G, W = make(ctx, "bf16_refine")
+    rng = np.random.default_rng(4)
     f = rng.standard_normal((4, 64, 64))
     u0 = 0.05 * rng.standard_normal((4, 64, 64))
     u0[0] = 0.0
@@ -110,16 +126,35 @@ def test_refine_step_matches_fp64_cycle(ctx):
     ud = torch.tensor(u0, dtype=torch.float64, device="cuda")
     G.cycle(fd, ud)
     torch.cuda.synchronize()
-    ref = O.nmgf(H, W, 0, u0, f32)
-    assert rel(ud.cpu().numpy(), ref) < 1e-3
+    assert rel(ud.cpu().numpy(), O.nmgf(H, W, 0, u0, f32)) < 1e-3
 
 
-def test_refine_solve_trained_c2_reaches_tolerance(ctx):
-    path = os.path.join(WDIR, "c2_2d_n128_s2_a1e-2.npz")
-    if not os.path.exists(path):
+@pytest.fixture(scope="module")
+def c2w():
+    if not os.path.exists(C2W):
         pytest.skip("trained weights missing")
-    W = nmg.load_weights(path)
-    H, G, _ = make(ctx, n=128, levels=5, sigma=2.0, alpha=1e-2, weights=W)
+    return nmg.load_weights(C2W)
+
+
+def test_trained_first_cycles_match_fp64(ctx, c2w):
+    """Per-cycle iterate parity with trained smoothers on the 128x128 operator:
+    cycles 1..4 from the GPU's own previous iterate, each against one oracle
+    cycle from the same state."""
+    H, G, _ = make(ctx, "bf16_refine", n=128, levels=5, weights=c2w)
+    f, _ = I.rhs_2d_ellipses_grf(128, 3, seed=5, sigma=2.0)
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    f32 = fd.double().cpu().numpy()
+    ud = torch.zeros((3, 128, 128), dtype=torch.float64, device="cuda")
+    for _ in range(4):
+        up = ud.cpu().numpy().copy()
+        G.cycle(fd, ud)
+        torch.cuda.synchronize()
+        assert rel(ud.cpu().numpy(), O.nmgf(H, c2w, 0, up, f32)) < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine"])
+def test_refine_solve_trained_c2_reaches_tolerance(ctx, c2w, prec):
+    H, G, _ = make(ctx, prec, n=128, levels=5, sigma=2.0, alpha=1e-2, weights=c2w)
     f, _ = I.rhs_2d_ellipses_grf(128, 8, seed=77, sigma=2.0)
     fd = torch.tensor(f, dtype=torch.float32, device="cuda")
     ud = torch.zeros((8, 128, 128), dtype=torch.float64, device="cuda")
