@@ -10,7 +10,12 @@ right-hand side meets the tolerance.  Inputs are resident in HBM when the
 timed region starts; L2 is flushed (a 256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c3]
+                  [--precision bf16_refine|bf16fast_refine|fp32]
+
+The headline is the bf16 refinement form solving the whole batch at once;
+the same run also times, on the same GPU and right-hand sides, the fp32
+form batched, the fp32 form one right-hand side per call (the plain fp32
+single-RHS cycle) and the other bf16 form ("compare").
 
 Under torchrun each rank solves its own batch (different seeds, the same
 sizes): weak scaling with no data-path collective.
@@ -40,12 +45,28 @@ WORKLOADS = {
     # 2D BTTB deblurring, 128x128, PSF sigma 2 px (truncated at 4 sigma), alpha 1e-2,
     # 5 levels, 256 right-hand sides (ellipses + Gaussian random field, blurred, 1% noise)
     "c2": dict(name="2d_bttb_128x128_sigma2_alpha1e-2_L5_batch256", n=128, levels=5, alpha=1e-2,
-               sigma=2.0, batch=256, precision="fp32", rhs="ellipses_grf", rhs_seed=1002,
+               sigma=2.0, batch=256, rhs="ellipses_grf", rhs_seed=1002,
                weights="c2_2d_n128_s2_a1e-2.npz"),
 }
+PRECISION_TEXT = {
+    "bf16_refine": "bf16 tensor-core smoother with split hi+lo bf16 operands and fp32 accumulation, "
+                   "fp32 cycle vectors, compensated-fp32 outer residual, fp64 update and coarse solve",
+    "bf16fast_refine": "bf16 tensor-core smoother (one bf16 per operand, fp32 accumulation), fp32 "
+                       "cycle vectors, compensated-fp32 outer residual, fp64 update and coarse solve",
+    "fp32": "fp32 throughout (SIMT smoother), fp64 coarse solve",
+}
+DTYPE = {"bf16_refine": "bf16x2+f32+f64", "bf16fast_refine": "bf16+f32+f64", "fp32": "f32"}
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x fp32 lanes x FMA x max clock
 FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_last": 2 * 9 * 32}
+# tensor-core MMA flops per pixel actually issued, per bf16 form (split: a_hi*w + a_lo*w;
+# the first layer pads K to 16, the last pads N to 16)
+MMA_FLOPS_PER_PX = {
+    "bf16_refine": {"cnn_hidden": 2 * 2 * 9 * 32 * 32, "cnn_first": 2 * 2 * 16 * 32,
+                    "cnn_last": 2 * 2 * 9 * 32 * 16},
+    "bf16fast_refine": {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 16 * 32,
+                        "cnn_last": 2 * 9 * 32 * 16},
+}
 
 
 def load_peaks():
@@ -201,30 +222,49 @@ def run_ours(args, wl, world, rank, local):
     ctx = nmg.Context(local, stream=stream.cuda_stream)
     W = nmg.load_weights(os.path.join(WEIGHTS, wl["weights"]))
     taps = I.gaussian_taps(wl["sigma"])
-    G = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"], taps=taps,
-                      precision=wl["precision"], weights=W)
+    prec = args.precision
+
+    def hier(p):
+        return nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"],
+                             taps=taps, precision=p, weights=W)
+
+    G = hier(prec)
     B = args.batch or wl["batch"]
     f_np = make_rhs(wl, B, wl["rhs_seed"] + 7919 * rank)
-    fdt = torch.float32
-    udt = torch.float64 if wl["precision"] == "bf16_refine" else torch.float32
-    f = torch.tensor(f_np, dtype=fdt, device="cuda")
+    refine = prec != "fp32"
+    udt = torch.float64 if refine else torch.float32
+    f = torch.tensor(f_np, dtype=torch.float32, device="cuda")
     u = torch.zeros(f.shape, dtype=udt, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def step():
-        u.zero_()
-        return G.solve(f, u, rtol=1e-6, max_cycles=100)
+    def step(Gx=G, fx=f, ux=u):
+        ux.zero_()
+        return Gx.solve(fx, ux, rtol=1e-6, max_cycles=100)
 
     if args.ncu:
         # one solve only: the command profiled by ncu
         cyc, st, rr = step()
         torch.cuda.synchronize()
-        print(json.dumps({"ncu_run": wl["name"], "batch": B, "cycles": float(cyc.mean()),
-                          "max_relres": float(rr.max()), "launches": ctx.launches()}))
+        print(json.dumps({"ncu_run": wl["name"], "precision": prec, "batch": B,
+                          "cycles": float(cyc.mean()), "max_relres": float(rr.max()),
+                          "launches": ctx.launches()}))
         return
     for _ in range(max(args.warmup, 0)):
         cyc, st, rr = step()
     torch.cuda.synchronize()
+
+    def timed(stepfn, K):
+        times, res = [], []
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res.append(stepfn())
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, res
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -232,35 +272,20 @@ def run_ours(args, wl, world, rank, local):
     l0 = ctx.launches()
     barrier(world)
     torch.cuda.synchronize()
-    times = []
-    cycles, relres, statuses = [], [], []
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        cyc, st, rr = step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        cycles.append(cyc)
-        relres.append(rr)
-        statuses.append(st)
+    times, res = timed(step, args.steps)
     torch.cuda.synchronize()
     barrier(world)
     launches = ctx.launches() - l0
     clk = clocks.stop()
     total_ms = reduce_max(sum(times), world)
     value = B * world * args.steps / (total_ms / 1e3)
-    converged = bool(all((s == 0).all() for s in statuses))
-    max_relres = float(max(r.max() for r in relres))
-    mean_cycles = float(np.mean([c.mean() for c in cycles]))
+    converged = bool(all((r[1] == 0).all() for r in res))
+    max_relres = float(max(r[2].max() for r in res))
+    mean_cycles = float(np.mean([r[0].mean() for r in res]))
 
-    # ---- per-kernel timing with CUDA events on the library's stream
+    # ---- per-kernel timing with CUDA events on the library's stream (same steps again)
     ctx.profile(True)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        step()
+    timed(step, args.steps)
     ctx.profile(False)
     kern = {}
     for kind, name in enumerate(nmg.KERNEL_CLASSES):
@@ -271,7 +296,16 @@ def run_ours(args, wl, world, rank, local):
     dom = max(kern, key=lambda k: kern[k]["ms"])
     peaks, peak_src = load_peaks()
     d = kern[dom]
-    if dom in FLOPS_PER_PX:
+    if dom in FLOPS_PER_PX and refine:
+        fl = MMA_FLOPS_PER_PX[prec][dom]
+        achieved = fl * d["units"] / (d["ms"] / 1e3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"kernel": f"{dom} (tcgen05 bf16 3x3 conv)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "flop_per_unit": fl, "unit_def": "output pixel x active right-hand side",
+                "launch_ms": d["ms"] / d["launches"]}
+    elif dom in FLOPS_PER_PX:
         achieved = FLOPS_PER_PX[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
         roof = {"kernel": f"{dom} (fp32 SIMT 3x3 conv)", "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
@@ -279,7 +313,8 @@ def run_ours(args, wl, world, rank, local):
                 "peak_source": "152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz (derived)",
                 "flop_per_unit": FLOPS_PER_PX[dom], "launch_ms": d["ms"] / d["launches"]}
     else:
-        bpu = {"residual": 12, "restrict": 9, "prolong": 9, "filter": 8}.get(dom, 8)
+        bpu = {"residual": 12, "restrict": 9, "prolong": 9, "filter": 8,
+               "refine_residual": 16}.get(dom, 8)
         achieved = bpu * d["units"] / (d["ms"] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
@@ -288,8 +323,46 @@ def run_ours(args, wl, world, rank, local):
     breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "share": v["ms"] / prof_total} for k, v in kern.items()}
 
+    # ---- the comparison forms on the same GPU and right-hand sides
+    compare = {}
+    if not args.no_compare:
+        f32 = torch.zeros(f.shape, dtype=torch.float32, device="cuda")
+        for p in ["fp32", "bf16fast_refine", "bf16_refine"]:
+            if p == prec:
+                continue
+            Gp = hier(p)
+            up = torch.zeros(f.shape, dtype=torch.float32 if p == "fp32" else torch.float64,
+                             device="cuda")
+            step_p = (lambda Gp=Gp, up=up: step(Gp, f, up))
+            step_p()
+            tp, rp = timed(step_p, max(1, min(args.steps, 2)))
+            compare[p + "_batched"] = {
+                "value": B * len(tp) / (sum(tp) / 1e3), "unit": "RHS/s", "batch": B,
+                "mean_cycles": float(np.mean([r[0].mean() for r in rp])),
+                "max_relres": float(max(r[2].max() for r in rp))}
+            Gp.close()
+        # plain fp32 single-RHS cycle: one right-hand side per solve call
+        Gs = hier("fp32")
+        nsingle = min(16, B)
+        us = torch.zeros((1, wl["n"], wl["n"]), dtype=torch.float32, device="cuda")
+        step(Gs, f[0:1], us)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rr1 = []
+        for i in range(nsingle):
+            rr1.append(step(Gs, f[i:i + 1], us)[2][0])
+        e1.record(stream)
+        e1.synchronize()
+        compare["fp32_single_rhs"] = {
+            "value": nsingle / (e0.elapsed_time(e1) / 1e3), "unit": "RHS/s", "batch": 1,
+            "rhs_timed": nsingle, "max_relres": float(max(rr1))}
+        Gs.close()
+        del f32
+
     # ---- end to end through the C ABI with host buffers (pinned)
-    fh = torch.tensor(f_np, dtype=fdt).pin_memory().numpy()
+    fh = torch.tensor(f_np, dtype=torch.float32).pin_memory().numpy()
     uh = torch.zeros(f.shape, dtype=udt).pin_memory().numpy()
     G.solve_host(fh, uh)  # warm the staging buffers
     barrier(world)
@@ -312,16 +385,16 @@ def run_ours(args, wl, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp32": "f32", "fp64": "f64", "bf16_refine": "bf16+f32+f64"}[wl["precision"]],
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
                 "data": "synthetic",
                 "config": {"workload": wl["name"], "n": wl["n"], "levels": wl["levels"],
-                           "batch_per_gpu": B, "precision": wl["precision"],
+                           "batch_per_gpu": B, "precision": prec,
+                           "precision_detail": PRECISION_TEXT[prec],
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
-                "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk}
+                "compare": compare, "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)
 
 
@@ -335,6 +408,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling runs)")
     ap.add_argument("--ncu", action="store_true", help="a single solve, nothing else (profiling)")
+    ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
+    ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
     args = ap.parse_args()
     world, rank, local = dist_init()
     wl = WORKLOADS[args.workload]
