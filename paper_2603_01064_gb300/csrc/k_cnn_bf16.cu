@@ -1,35 +1,42 @@
-// bf16 tensor-core CNN smoother h = N(b / ||b||) ||b|| (Algorithms 3/4)
-// with tcgen05.mma (accumulators in tensor memory), one kernel per layer.
+// CNN smoother h = N(b / ||b||) ||b|| (Algorithms 3/4) of the bf16
+// refinement forms: hidden 32 -> 32 layers on the tensor cores with
+// tcgen05.mma (fp32 accumulators in tensor memory), first (1 -> 32) and
+// last (32 -> 1) layers in fp32 SIMT (2% of the flops; they are bound by
+// their activation traffic).
 //
-// Each 3x3 conv layer is an implicit GEMM  D[pixel][cout] = sum over taps
-// and input channels of A[pixel + shift(tap)][cin] * W[tap][cin][cout].
-// One MMA tile is M = 128 output pixels arranged as 16 image rows x 8
-// columns, so its eight-row groups of the K-major no-swizzle operand layout
-// are image rows: with the input tile staged in shared memory as
-// [channel chunk of 8][tile row][tile column][8 channels], the operand for
-// tap (dy, dx) is the same layout started dy rows and dx pixels further on,
-// and the group stride (SBO) is one tile row.  A block covers 16 x 16
-// output pixels (two M tiles side by side), the 9 taps x 2 K halves give 18
-// MMAs of 128 x N x 16 per M tile, accumulated in fp32 in tensor memory.
+// Hidden layer = implicit GEMM  D[pixel][cout] = sum over the 9 taps and 32
+// input channels of A[pixel + shift(tap)][cin] * W[tap][cin][cout].  One MMA
+// tile is M = 128 output pixels arranged as 16 image rows x 8 columns, so the
+// eight-row groups of the K-major no-swizzle operand layout are image rows:
+// with the input tile staged in shared memory as [channel chunk of 8][tile
+// row][tile column][8 channels], the operand of tap (dy, dx) is the same
+// layout started dy rows and dx pixels further on, and the group stride
+// (SBO) is one staged row.  A block tile is 16 x 16 output pixels (two M
+// tiles side by side): 9 taps x 2 K halves = 18 MMAs of 128 x 32 x 16 per M
+// tile and operand pair.
 //
-//   first layer  1 -> 32: A is the 3x3 neighbourhood (9 values, padded to
-//                K = 16) of b / ||b|| built in shared memory; one MMA.
-//   hidden       32 -> 32: 18 MMAs, ReLU, bf16 activations NHWC.
-//   last         32 -> 1: N padded to 16 with zero weights; output
-//                ||b|| * (acc + bias) in fp32.
-//
-// Blocks are persistent: a block stages its layer's weights once and loops
-// over tiles.  Every wait on the MMA-completion mbarrier is bounded; on
-// timeout the block records an error code and stops.
+// Levels with n >= 32 use a warp-specialised persistent kernel: one warp
+// issues TMA tensor copies of the input tiles (the halo outside the image is
+// zero-filled by the copy engine) into a ring of shared-memory stages, one
+// warp issues the MMAs of a tile into one of two tensor-memory accumulators
+// as soon as its stage is full, and four warps drain the other accumulator
+// (tensor memory -> registers -> bias, ReLU -> bf16 -> global).  Stages and
+// accumulators are handed over with mbarriers (full/empty, acc_full/
+// acc_empty).  Smaller levels use a single-role version that stages with
+// cp.async and overlaps one tile ahead.  Every mbarrier wait is bounded; on
+// timeout the block records an error code, stops and releases its tensor
+// memory.
 //
 // Split form (SPLIT = 1, the default bf16 form): the smoother's output is
 // dominated by near-constant content that the output filter removes, so a
-// single bf16 rounding of the input and the activations (2^-9 relative) is
-// amplified far beyond the useful filtered part.  Every operand is therefore
-// carried as a pair of bf16 values v = hi + lo (|lo| <= 2^-9 |v|) and each
-// product is formed from bf16 tensor-core MMAs a_hi*w_hi + a_lo*w_hi
-// (+ a_hi*w_lo when the fp32 weights are not bf16-exact), accumulated in
-// fp32 in tensor memory.  Activations are stored as [hi 32 | lo 32] bf16.
+// single bf16 rounding of the activations (2^-9 relative) is amplified far
+// beyond the useful filtered part.  Activations are stored as [hi 32 | lo 32]
+// bf16 (v = hi + lo, |lo| <= 2^-9 |v|) and each product is formed from bf16
+// MMAs a_hi*w_hi + a_lo*w_hi (+ a_hi*w_lo when the weights are not
+// bf16-exact), accumulated in fp32.  The SIMT layers read and write the
+// pairs and compute in fp32.
+#include <cuda.h>
+
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -40,26 +47,25 @@ namespace nmg {
 
 namespace {
 
-constexpr int TILE = 16;           // output tile side (pixels)
-constexpr int NT = 2;              // M tiles per block (columns 0-7, 8-15)
-constexpr int RW = TILE + 2;       // staged input row pitch in pixels
-constexpr int RH = TILE + 2;       // staged input rows
+constexpr int TILE = 16;                // output tile side (pixels)
+constexpr int NT = 2;                   // M tiles per block tile (columns 0-7, 8-15)
+constexpr int RW = TILE + 2;            // staged input row pitch in pixels
+constexpr int RH = TILE + 2;            // staged input rows
 constexpr int CH_BYTES = RH * RW * 16;  // one 8-channel chunk of the staged tile
 constexpr int WIDTH = 32;
 constexpr int THREADS = 128;
-constexpr long long kSpinLimit = 1LL << 26;
+constexpr int TMEM_COLS = 128;          // 2 accumulators x 2 M tiles x 32 columns
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bound of every mbarrier wait
+constexpr int B_HALF = 9 * 4 * WIDTH * 16;  // one bf16 weight block of a hidden layer
 
-enum Mode { FIRST = 0, HIDDEN = 1, LAST = 2 };
-
-// weights per layer in the MMA B layout, bf16:
-//   FIRST : [kchunk 2][cout 32][8]  (k = tap, zero for k >= 9)
-//   HIDDEN: [tap 9][kchunk 4][cout 32][8 cin]
-//   LAST  : [tap 9][kchunk 4][cout 16][8 cin] (cout >= 1 zero)
+// per layer: hidden layers use bf16 weights in the MMA B layout
+// [tap 9][kchunk 4][cout 32][8 cin] (SPLIT: hi block then lo block);
+// first/last layers use fp32 weights [c][tap] and fp32 biases.
 struct LayerPack {
-  const __nv_bfloat16* w;  // SPLIT: hi block then lo block
+  const __nv_bfloat16* w;
+  const float* wf;
   const float* bias;
-  int wcount;  // bf16 elements of one block
-  int has_lo;  // lo block not all zero
+  int has_lo;
 };
 struct Bf16Pack {
   int layers;
@@ -112,6 +118,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for a phase of an mbarrier, giving up after kWaitLimitNs
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
 // 32 lanes x 32 columns of fp32 from tensor memory (this warp's lane quarter)
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -130,29 +157,158 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int MODE, int SPLIT>
+// write 32 channel values of one pixel as bf16 (SPLIT: hi block then lo block)
+template <int SPLIT>
+__device__ __forceinline__ void store_channels(__nv_bfloat16* dst_px, const float* a) {
+  uint32_t pk[16], pl[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
+    pk[c] = *reinterpret_cast<uint32_t*>(&h2);
+    if (SPLIT) {
+      __nv_bfloat162 l2 = __floats2bfloat162_rn(a[2 * c] - __low2float(h2),
+                                                a[2 * c + 1] - __high2float(h2));
+      pl[c] = *reinterpret_cast<uint32_t*>(&l2);
+    }
+  }
+  uint4* d = reinterpret_cast<uint4*>(dst_px);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  if (SPLIT) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      d[4 + q] = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// first layer 1 -> 32 (fp32 SIMT): a = ReLU(b1 + W1 * (b / s)), stored bf16
+// ---------------------------------------------------------------------------
+template <int SPLIT>
+__global__ void __launch_bounds__(256)
+k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ aout,
+             LayerPack lp, const double* __restrict__ snorm, const int* __restrict__ active,
+             int tiles_x) {
+  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const double s = snorm[b];
+  if (s == 0.0) return;  // h = 0 is written by the last layer
+  __shared__ float xs[RH][RW + 1];
+  __shared__ float ws[WIDTH * 9];
+  __shared__ float bs[WIDTH];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < WIDTH * 9; i += 256) ws[i] = lp.wf[i];
+  if (tid < WIDTH) bs[tid] = lp.bias[tid];
+  const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
+  const size_t plane = (size_t)n * n;
+  const float inv = (float)(1.0 / s);
+  const float* bb = bsrc + (size_t)b * plane;
+  for (int i = tid; i < RH * RW; i += 256) {
+    int ry = i / RW, rx = i % RW;
+    int y = y0 + ry - 1, x = x0 + rx - 1;
+    xs[ry][rx] = (y >= 0 && y < n && x >= 0 && x < n) ? bb[(size_t)y * n + x] * inv : 0.f;
+  }
+  __syncthreads();
+  const int ry = tid / TILE, rx = tid % TILE;
+  const int y = y0 + ry, x = x0 + rx;
+  if (y >= n || x >= n) return;
+  float v[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) v[t] = xs[ry + t / 3][rx + t % 3];
+  float a[WIDTH];
+#pragma unroll
+  for (int c = 0; c < WIDTH; ++c) {
+    float acc = bs[c];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc = fmaf(ws[c * 9 + t], v[t], acc);
+    a[c] = fmaxf(acc, 0.f);
+  }
+  store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + x) * CW, a);
+}
+
+// ---------------------------------------------------------------------------
+// last layer 32 -> 1 (fp32 SIMT): h = s * (b4 + W4 * a)
+// ---------------------------------------------------------------------------
+template <int SPLIT>
+__global__ void __launch_bounds__(256)
+k_last_simt(int n, const __nv_bfloat16* __restrict__ ain, float* __restrict__ hout, LayerPack lp,
+            const double* __restrict__ snorm, const int* __restrict__ active, int tiles_x) {
+  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  constexpr int PXB = CW * 2 + 16;  // padded bytes per staged pixel (bank-conflict free)
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const double s = snorm[b];
+  const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
+  const size_t plane = (size_t)n * n;
+  const int tid = threadIdx.x;
+  if (s == 0.0) {
+    const int y = y0 + tid / TILE, x = x0 + tid % TILE;
+    if (y < n && x < n) hout[(size_t)b * plane + (size_t)y * n + x] = 0.f;
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* ws = reinterpret_cast<float*>(smem);            // [c][tap]
+  unsigned char* ts = smem + WIDTH * 9 * sizeof(float);  // [ry][rx] x PXB bytes
+  for (int i = tid; i < WIDTH * 9; i += 256) ws[i] = lp.wf[i];
+  const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
+  constexpr int Q = CW / 8;  // 16-byte pieces per pixel
+  for (int i = tid; i < RH * RW * Q; i += 256) {
+    int q = i % Q, p = i / Q;
+    int ry = p / RW, rx = p % RW;
+    int y = y0 + ry - 1, x = x0 + rx - 1;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (y >= 0 && y < n && x >= 0 && x < n)
+      v = *reinterpret_cast<const uint4*>(ab + ((size_t)y * n + x) * CW + q * 8);
+    *reinterpret_cast<uint4*>(ts + p * PXB + q * 16) = v;
+  }
+  __syncthreads();
+  const int ry = tid / TILE, rx = tid % TILE;
+  const int y = y0 + ry, x = x0 + rx;
+  if (y >= n || x >= n) return;
+  float acc = lp.bias[0];
+#pragma unroll 1
+  for (int t = 0; t < 9; ++t) {
+    const unsigned char* px = ts + ((ry + t / 3) * RW + (rx + t % 3)) * PXB;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 hv = *reinterpret_cast<const uint4*>(px + q * 16);
+      const __nv_bfloat16* hh = reinterpret_cast<const __nv_bfloat16*>(&hv);
+      float a[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a[e] = __bfloat162float(hh[e]);
+      if (SPLIT) {
+        uint4 lv = *reinterpret_cast<const uint4*>(px + 64 + q * 16);
+        const __nv_bfloat16* ll = reinterpret_cast<const __nv_bfloat16*>(&lv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] += __bfloat162float(ll[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc = fmaf(ws[(q * 8 + e) * 9 + t], a[e], acc);
+    }
+  }
+  hout[(size_t)b * plane + (size_t)y * n + x] = (float)s * acc;
+}
+
+// ---------------------------------------------------------------------------
+// hidden layer 32 -> 32 on the tensor cores (pipelined, persistent)
+// ---------------------------------------------------------------------------
+template <int SPLIT>
 __global__ void __launch_bounds__(THREADS)
-k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level vector
-          const __nv_bfloat16* __restrict__ ain,                // HIDDEN/LAST: NHWC input
-          __nv_bfloat16* __restrict__ aout,                     // FIRST/HIDDEN: NHWC output
-          float* __restrict__ hout,                             // LAST: level vector
-          LayerPack lp, const double* __restrict__ snorm, const int* __restrict__ active,
-          int* __restrict__ err) {
-  constexpr int NOUT = MODE == LAST ? 16 : 32;
-  constexpr int ACH = MODE == FIRST ? (SPLIT ? 6 : 2) : (SPLIT ? 8 : 4);  // A chunks
-  constexpr int A_BYTES = MODE == FIRST ? NT * ACH * 128 * 16 : ACH * CH_BYTES;
-  constexpr int B_HALF = MODE == FIRST ? (SPLIT ? 6 : 2) * 32 * 16 : 9 * 4 * NOUT * 16;
-  constexpr int B_BYTES = (SPLIT && MODE != FIRST) ? 2 * B_HALF : B_HALF;
-  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;  // stored channels per pixel
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* As = smem;
-  unsigned char* Bs = smem + A_BYTES;
-  __shared__ __align__(8) uint64_t mbar;
+k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
+            __nv_bfloat16* __restrict__ aout, LayerPack lp, const double* __restrict__ snorm,
+            const int* __restrict__ active, int* __restrict__ err) {
+  constexpr int ACH = SPLIT ? 8 : 4;  // 8-channel chunks per staged pixel
+  constexpr int ABUF = ACH * CH_BYTES;
+  constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* Bs = smem + 2 * ABUF;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // weights once per block
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
@@ -161,11 +317,12 @@ k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(64));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
   }
@@ -174,162 +331,366 @@ k_conv_tc(int n, int nimg, const float* __restrict__ bsrc,      // FIRST: level 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs), mb = smem_u32(&mbar);
-  const uint32_t idesc = make_idesc(128, NOUT);
+  const uint32_t a_base0 = smem_u32(smem), b_base = smem_u32(Bs);
+  const uint32_t idesc = make_idesc(128, WIDTH);
   const int tiles_x = (n + TILE - 1) / TILE;
   const int per_img = tiles_x * tiles_x;
   const long long total = (long long)nimg * per_img;
   const size_t plane = (size_t)n * n;
-  uint32_t phase = 0;
 
-  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+  auto valid = [&](long long t) {
     const int b = (int)(t / per_img);
-    const int tt = (int)(t % per_img);
+    return active[b] != 0 && snorm[b] != 0.0;
+  };
+  auto advance = [&](long long t) {
+    t += gridDim.x;
+    while (t < total && !valid(t)) t += gridDim.x;
+    return t;
+  };
+  auto stage = [&](long long t, int buf) {
+    const int b = (int)(t / per_img), tt = (int)(t % per_img);
     const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
-    if (!active[b]) continue;  // uniform across the block
-    const double s = snorm[b];
-    if (s == 0.0) {
-      if (MODE == LAST) {
-        for (int p = tid; p < TILE * TILE; p += THREADS) {
-          int y = y0 + p / TILE, x = x0 + p % TILE;
-          if (y < n && x < n) hout[(size_t)b * plane + (size_t)y * n + x] = 0.f;
-        }
-      }
-      continue;
+    const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
+    const uint32_t base = a_base0 + buf * ABUF;
+    for (int i = tid; i < RH * RW * ACH; i += THREADS) {
+      const int c = i % ACH, p = i / ACH;
+      const int ry = p / RW, rx = p % RW;
+      const int y = y0 + ry - 1, x = x0 + rx - 1;
+      const bool in = y >= 0 && y < n && x >= 0 && x < n;
+      const __nv_bfloat16* src = in ? ab + ((size_t)y * n + x) * CW + c * 8 : ain;
+      cp_async16(base + c * CH_BYTES + (ry * RW + rx) * 16, src, in ? 16u : 0u);
     }
-    // ---- stage the A operand
-    if (MODE == FIRST) {
-      const float inv = (float)(1.0 / s);
-      const float* bb = bsrc + (size_t)b * plane;
-      for (int i = tid; i < TILE * TILE * 16; i += THREADS) {
-        int k = i & 15, p = i >> 4;
-        int ry = p / TILE, rx = p % TILE;
-        float v = 0.f;
-        if (k < 9) {
-          int y = y0 + ry + k / 3 - 1, x = x0 + rx + k % 3 - 1;
-          if (y >= 0 && y < n && x >= 0 && x < n) v = bb[(size_t)y * n + x] * inv;
-        }
-        int mt = rx >> 3, m = ry * 8 + (rx & 7);
-        unsigned char* base = As + mt * (ACH * 128 * 16) + m * 16 + (k & 7) * 2;
-        __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        *reinterpret_cast<__nv_bfloat16*>(base + (k >> 3) * (128 * 16)) = hi;
-        if (SPLIT) {
-          // chunks 2,3: lo taps (times W_hi); chunks 4,5: hi taps again (times W_lo)
-          __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-          *reinterpret_cast<__nv_bfloat16*>(base + (2 + (k >> 3)) * (128 * 16)) = lo;
-          *reinterpret_cast<__nv_bfloat16*>(base + (4 + (k >> 3)) * (128 * 16)) = hi;
-        }
-      }
-    } else {
-      const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
-      for (int i = tid; i < RH * RW * ACH; i += THREADS) {
-        int c = i % ACH, p = i / ACH;
-        int ry = p / RW, rx = p % RW;
-        int y = y0 + ry - 1, x = x0 + rx - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (y >= 0 && y < n && x >= 0 && x < n)
-          v = *reinterpret_cast<const uint4*>(ab + ((size_t)y * n + x) * CW + c * 8);
-        *reinterpret_cast<uint4*>(As + c * CH_BYTES + (ry * RW + rx) * 16) = v;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto wait_mma = [&](int buf, uint32_t parity) {
+    if (!mbar_wait_bounded(smem_u32(&mbar[buf]), parity)) {
+      atomicExch(err, 1);
+      abort_flag = 1;
+    }
+  };
+  auto epilogue = [&](long long t, int acc) {
+    const int b = (int)(t / per_img), tt = (int)(t % per_img);
+    const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
+    for (int mt = 0; mt < NT; ++mt) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + acc * (NT * 32) + mt * 32, v);
+      const int m = warp * 32 + lane;
+      const int y = y0 + (m >> 3), x = x0 + mt * 8 + (m & 7);
+      if (y < n && x < n) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + lp.bias[c], 0.f);
+        store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + x) * CW, v);
       }
     }
+  };
+
+  long long cur = blockIdx.x;
+  while (cur < total && !valid(cur)) cur += gridDim.x;
+  long long prev = -1;
+  uint32_t parity[2] = {0u, 0u};
+  int k = 0;
+  if (cur < total) stage(cur, 0);
+  while (cur < total) {
+    const int sb = k & 1;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- MMAs (one thread)
     if (tid == 0) {
+      const uint32_t a_base = a_base0 + sb * ABUF;
       for (int mt = 0; mt < NT; ++mt) {
-        const uint32_t d = tmem + mt * 32;
-        if (MODE == FIRST) {
-          const int nk = SPLIT ? (lp.has_lo ? 3 : 2) : 1;
-          for (int q = 0; q < nk; ++q) {
-            uint64_t ad = make_desc(a_base + mt * (ACH * 128 * 16) + 2 * q * (128 * 16), 128 * 16, 128);
-            uint64_t bd = make_desc(b_base + 2 * q * (32 * 16), 32 * 16, 128);
-            mma_bf16(d, ad, bd, idesc, q > 0 ? 1u : 0u);
+        const uint32_t d = tmem + sb * (NT * 32) + mt * 32;
+        uint32_t accf = 0;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+          const uint32_t shift = (dy * RW + 8 * mt + dx) * 16;
+#pragma unroll
+          for (int kh = 0; kh < 2; ++kh) {
+            const uint32_t boff = (tap * 4 + 2 * kh) * WIDTH * 16;
+            const uint64_t ad = make_desc(a_base + 2 * kh * CH_BYTES + shift, CH_BYTES, RW * 16);
+            const uint64_t bd = make_desc(b_base + boff, WIDTH * 16, 128);
+            mma_bf16(d, ad, bd, idesc, accf);
+            accf = 1u;
+            if (SPLIT) {
+              const uint64_t adl = make_desc(a_base + (4 + 2 * kh) * CH_BYTES + shift, CH_BYTES, RW * 16);
+              mma_bf16(d, adl, bd, idesc, 1u);
+              if (lp.has_lo) mma_bf16(d, ad, make_desc(b_base + B_HALF + boff, WIDTH * 16, 128), idesc, 1u);
+            }
           }
-        } else {
-          uint32_t acc = 0;
+        }
+      }
+      mma_commit(smem_u32(&mbar[sb]));
+    }
+    const long long nxt = advance(cur);
+    if (prev >= 0) {
+      // MMAs of the previous tile are done: its operand buffer is free and its
+      // accumulator can be read
+      wait_mma(sb ^ 1, parity[sb ^ 1]);
+      parity[sb ^ 1] ^= 1u;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    if (nxt < total) stage(nxt, sb ^ 1);
+    if (prev >= 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      epilogue(prev, sb ^ 1);
+    }
+    prev = cur;
+    cur = nxt;
+    ++k;
+  }
+  if (!abort_flag && prev >= 0) {
+    const int lb = (k - 1) & 1;
+    wait_mma(lb, parity[lb]);
+    __syncthreads();
+    if (!abort_flag) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      epilogue(prev, lb);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
+// hidden layer, warp-specialised: TMA producer / MMA issuer / 4 epilogue warps
+// ---------------------------------------------------------------------------
+constexpr int CH_PITCH = 5248;       // chunk stride in shared memory (128-byte multiple)
+constexpr int WS_THREADS = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
+}
+
+template <int SPLIT, int STAGES>
+__global__ void __launch_bounds__(WS_THREADS)
+k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
+            __nv_bfloat16* __restrict__ aout, LayerPack lp, const double* __restrict__ snorm,
+            const int* __restrict__ active, int* __restrict__ err) {
+  constexpr int ACH = SPLIT ? 8 : 4;
+  constexpr int SBYTES = ACH * CH_PITCH;           // one stage
+  constexpr uint32_t TX = ACH * RH * RW * 16;      // bytes the copies of one stage write
+  constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  extern __shared__ __align__(16) unsigned char smem_raw_ws[];
+  // stage buffers start on a 1024-byte boundary (TMA destinations need 128)
+  unsigned char* smem = smem_raw_ws + ((1024u - (smem_u32(smem_raw_ws) & 1023u)) & 1023u);
+  unsigned char* Bs = smem + STAGES * SBYTES;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(lp.w);
+    uint4* dst = reinterpret_cast<uint4*>(Bs);
+    for (int i = tid; i < B_BYTES / 16; i += WS_THREADS) dst[i] = src[i];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 32) {
+    for (int i = 0; i < STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])), "r"(4));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int tiles_x = (n + TILE - 1) / TILE;
+  const int per_img = tiles_x * tiles_x;
+  const long long total = (long long)nimg * per_img;
+  const size_t plane = (size_t)n * n;
+  auto valid = [&](long long t) {
+    const int b = (int)(t / per_img);
+    return active[b] != 0 && snorm[b] != 0.0;
+  };
+  auto first = [&]() {
+    long long t = blockIdx.x;
+    while (t < total && !valid(t)) t += gridDim.x;
+    return t;
+  };
+  auto advance = [&](long long t) {
+    t += gridDim.x;
+    while (t < total && !valid(t)) t += gridDim.x;
+    return t;
+  };
+  // bounded wait; returns false (and flags the error) on timeout
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(smem_u32(bar), parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+      if (mbar_try_wait(smem_u32(bar), parity)) return true;
+      if ((it & 63u) == 0 && (*(volatile int*)&abort_flag || global_ns() - t0 > kWaitLimitNs)) {
+        atomicExch(err, 1);
+        abort_flag = 1;
+        return false;
+      }
+    }
+  };
+
+  if (warp == 0) {
+    // ---- TMA producer
+    if (lane == 0) {
+      int i = 0;
+      for (long long t = first(); t < total; t = advance(t), ++i) {
+        const int s = i % STAGES;
+        if (i >= STAGES && !wait(&empty[s], (uint32_t)((i / STAGES - 1) & 1))) break;
+        const int b = (int)(t / per_img), tt = (int)(t % per_img);
+        const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, TX);
+        const uint32_t dst = smem_u32(smem + s * SBYTES);
+        for (int c = 0; c < ACH; ++c) tma_load_4d(dst + c * CH_PITCH, &amap, c * 8, x0 - 1, y0 - 1, b, fb);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(128, WIDTH);
+      const uint32_t b_base = smem_u32(Bs);
+      int i = 0;
+      for (long long t = first(); t < total; t = advance(t), ++i) {
+        const int s = i % STAGES, a = i & 1;
+        if (!wait(&full[s], (uint32_t)((i / STAGES) & 1))) break;
+        if (i >= 2 && !wait(&acc_empty[a], (uint32_t)((i / 2 - 1) & 1))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_base = smem_u32(smem + s * SBYTES);
+        for (int mt = 0; mt < NT; ++mt) {
+          const uint32_t d = tmem + a * (NT * 32) + mt * 32;
+          uint32_t accf = 0;
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3;
+            const uint32_t shift = (dy * RW + 8 * mt + dx) * 16;
+#pragma unroll
             for (int kh = 0; kh < 2; ++kh) {
-              const uint32_t shift = (dy * RW + 8 * mt + dx) * 16;
-              const uint32_t boff = (tap * 4 + 2 * kh) * NOUT * 16;
-              uint64_t ad = make_desc(a_base + 2 * kh * CH_BYTES + shift, CH_BYTES, RW * 16);
-              uint64_t bd = make_desc(b_base + boff, NOUT * 16, 128);
-              mma_bf16(d, ad, bd, idesc, acc);
-              acc = 1u;
+              const uint32_t boff = (tap * 4 + 2 * kh) * WIDTH * 16;
+              const uint64_t ad = make_desc(a_base + 2 * kh * CH_PITCH + shift, CH_PITCH, RW * 16);
+              const uint64_t bd = make_desc(b_base + boff, WIDTH * 16, 128);
+              mma_bf16(d, ad, bd, idesc, accf);
+              accf = 1u;
               if (SPLIT) {
-                uint64_t adl = make_desc(a_base + (4 + 2 * kh) * CH_BYTES + shift, CH_BYTES, RW * 16);
+                const uint64_t adl = make_desc(a_base + (4 + 2 * kh) * CH_PITCH + shift, CH_PITCH, RW * 16);
                 mma_bf16(d, adl, bd, idesc, 1u);
-                if (lp.has_lo) {
-                  uint64_t bdl = make_desc(b_base + B_HALF + boff, NOUT * 16, 128);
-                  mma_bf16(d, ad, bdl, idesc, 1u);
-                }
+                if (lp.has_lo) mma_bf16(d, ad, make_desc(b_base + B_HALF + boff, WIDTH * 16, 128), idesc, 1u);
               }
             }
           }
         }
+        mma_commit(smem_u32(&empty[s]));
+        mma_commit(smem_u32(&acc_full[a]));
       }
-      mma_commit(mb);
     }
-    // ---- wait for the accumulators (bounded)
-    {
-      long long it = 0;
-      while (!mbar_try_wait(mb, phase)) {
-        if (++it > kSpinLimit) {
-          if (tid == 0) {
-            atomicExch(err, 1);
-            abort_flag = 1;
-          }
-          break;
+  } else {
+    // ---- epilogue warps 2..5: lane quarter q = warp % 4 of tensor memory
+    const int q = warp & 3;
+    int i = 0;
+    for (long long t = first(); t < total; t = advance(t), ++i) {
+      const int a = i & 1;
+      if (!wait(&acc_full[a], (uint32_t)((i / 2) & 1))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float v0[32], v1[32];
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * (NT * 32), v0);
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * (NT * 32) + 32, v1);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[a]));
+      const int b = (int)(t / per_img), tt = (int)(t % per_img);
+      const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
+      const int m = q * 32 + lane;
+      const int y = y0 + (m >> 3);
+      if (y < n) {
+        const int xa = x0 + (m & 7), xb = x0 + 8 + (m & 7);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          v0[c] = fmaxf(v0[c] + lp.bias[c], 0.f);
+          v1[c] = fmaxf(v1[c] + lp.bias[c], 0.f);
         }
-      }
-      phase ^= 1u;
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- epilogue: warp w reads TMEM lanes 32w..32w+31 = pixels m of each M tile
-    for (int mt = 0; mt < NT; ++mt) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + mt * 32, v);
-      const int m = warp * 32 + lane;
-      const int y = y0 + (m >> 3), x = x0 + mt * 8 + (m & 7);
-      if (y < n && x < n) {
-        if (MODE == LAST) {
-          hout[(size_t)b * plane + (size_t)y * n + x] = (float)s * (v[0] + lp.bias[0]);
-        } else {
-          uint32_t pk[16], pl[16];
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const float a0 = fmaxf(v[2 * c] + lp.bias[2 * c], 0.f);
-            const float a1 = fmaxf(v[2 * c + 1] + lp.bias[2 * c + 1], 0.f);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
-            pk[c] = *reinterpret_cast<uint32_t*>(&h2);
-            if (SPLIT) {
-              __nv_bfloat162 l2 = __floats2bfloat162_rn(a0 - __low2float(h2), a1 - __high2float(h2));
-              pl[c] = *reinterpret_cast<uint32_t*>(&l2);
-            }
-          }
-          uint4* dst = reinterpret_cast<uint4*>(aout + ((size_t)b * plane + (size_t)y * n + x) * CW);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-          if (SPLIT) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              dst[4 + q] = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
-          }
-        }
+        if (xa < n) store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + xa) * CW, v0);
+        if (xb < n) store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + xb) * CW, v1);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// tensor maps over the NHWC activation buffers, created on first use
+struct MapEntry {
+  const void* ptr;
+  int n, nimg, cw;
+  CUtensorMap map;
+};
+std::vector<MapEntry>& map_cache() {
+  static std::vector<MapEntry> v;
+  return v;
+}
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+const CUtensorMap* act_map(const void* ptr, int n, int nimg, int cw) {
+  for (auto& e : map_cache())
+    if (e.ptr == ptr && e.n == n && e.nimg == nimg && e.cw == cw) return &e.map;
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return nullptr;
+  MapEntry e{ptr, n, nimg, cw, {}};
+  cuuint64_t dims[4] = {(cuuint64_t)cw, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nimg};
+  cuuint64_t strides[3] = {(cuuint64_t)cw * 2, (cuuint64_t)n * cw * 2, (cuuint64_t)n * n * cw * 2};
+  cuuint32_t box[4] = {8, (cuuint32_t)RW, (cuuint32_t)RH, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return nullptr;
+  map_cache().push_back(e);
+  return &map_cache().back().map;
 }
 
 // host bf16 round-to-nearest-even of a finite float
@@ -341,102 +702,134 @@ uint16_t bf16_bits(float f) {
 }
 
 int g_num_sms = 0;
-
-template <int MODE, int SPLIT>
-void launch_mode(int n, int nimg, const float* b, const __nv_bfloat16* ain, __nv_bfloat16* aout,
-                 float* h, const LayerPack& lp, const double* s, const int* active, int* err,
-                 cudaStream_t st, LaunchLog& log) {
-  constexpr int NOUT = MODE == LAST ? 16 : 32;
-  constexpr int ACH = MODE == FIRST ? (SPLIT ? 6 : 2) : (SPLIT ? 8 : 4);
-  constexpr int A_BYTES = MODE == FIRST ? NT * ACH * 128 * 16 : ACH * CH_BYTES;
-  constexpr int B_HALF = MODE == FIRST ? (SPLIT ? 6 : 2) * 32 * 16 : 9 * 4 * NOUT * 16;
-  constexpr int B_BYTES = (SPLIT && MODE != FIRST) ? 2 * B_HALF : B_HALF;
-  const size_t sm = A_BYTES + B_BYTES;
+int num_sms() {
   if (g_num_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 148;
   }
+  return g_num_sms;
+}
+
+template <int SPLIT>
+void launch_hidden(int n, int nimg, const __nv_bfloat16* ain, __nv_bfloat16* aout,
+                   const LayerPack& lp, const double* s, const int* active, int* err,
+                   cudaStream_t st, LaunchLog& log) {
+  constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
+  const CUtensorMap* map = n >= 32 ? act_map(ain, n, nimg, CWs) : nullptr;
+  if (map) {
+    constexpr int STAGES = SPLIT ? 3 : 4;
+    constexpr int ACHs = SPLIT ? 8 : 4;
+    constexpr int B_BYTESs = SPLIT ? 2 * B_HALF : B_HALF;
+    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + 1024;
+    const int tiles_x = (n + TILE - 1) / TILE;
+    long long total = (long long)nimg * tiles_x * tiles_x;
+    long long grid = (long long)num_sms() * (SPLIT ? 1 : 2);
+    if (grid > total) grid = total;
+    if (grid < 1) grid = 1;
+    cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int pi_ = log.begin(K_CNN_HIDDEN, st);
+    k_hidden_ws<SPLIT, STAGES><<<(int)grid, WS_THREADS, sm, st>>>(*map, n, nimg, aout, lp, s, active, err);
+    log.end(pi_, st, (double)n * n * log.active_hint);
+    return;
+  }
+  constexpr int ACH = SPLIT ? 8 : 4;
+  constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  const size_t sm = 2 * ACH * CH_BYTES + B_BYTES;
   const int tiles_x = (n + TILE - 1) / TILE;
   long long total = (long long)nimg * tiles_x * tiles_x;
-  long long grid = (long long)g_num_sms * 4;
+  long long grid = (long long)num_sms() * (SPLIT ? 1 : 3);
   if (grid > total) grid = total;
   if (grid < 1) grid = 1;
-  cudaFuncSetAttribute(k_conv_tc<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int pi_ = log.begin(MODE == FIRST ? K_CNN_FIRST : (MODE == HIDDEN ? K_CNN_HIDDEN : K_CNN_LAST), st);
-  k_conv_tc<MODE, SPLIT><<<(int)grid, THREADS, sm, st>>>(n, nimg, b, ain, aout, h, lp, s, active, err);
+  cudaFuncSetAttribute(k_hidden_tc<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int pi_ = log.begin(K_CNN_HIDDEN, st);
+  k_hidden_tc<SPLIT><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, lp, s, active, err);
   log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
-}  // namespace
-
-// Host copies of the pack headers, keyed by device allocation (launches read
-// the per-layer pointers on the host).
-namespace {
-std::vector<std::pair<const void*, Bf16Pack>> g_headers;
+template <int SPLIT>
+void run_layers(int n, int B, int layers, const Bf16Pack& P, const float* b, const double* s,
+                __nv_bfloat16* a0, __nv_bfloat16* a1, float* h, const int* active, int* err,
+                cudaStream_t st, LaunchLog& log) {
+  const int tiles_x = (n + TILE - 1) / TILE;
+  dim3 grid(tiles_x * tiles_x, B);
+  const double units = (double)n * n * log.active_hint;
+  int pi_ = log.begin(K_CNN_FIRST, st);
+  k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.l[0], s, active, tiles_x);
+  log.end(pi_, st, units);
+  __nv_bfloat16* cur = a0;
+  __nv_bfloat16* nxt = a1;
+  for (int li = 1; li < layers - 1; ++li) {
+    launch_hidden<SPLIT>(n, B, cur, nxt, P.l[li], s, active, err, st, log);
+    __nv_bfloat16* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  const size_t sm = WIDTH * 9 * sizeof(float) + (size_t)RH * RW * (CW * 2 + 16);
+  cudaFuncSetAttribute(k_last_simt<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  pi_ = log.begin(K_CNN_LAST, st);
+  k_last_simt<SPLIT><<<grid, 256, sm, st>>>(n, cur, h, P.l[layers - 1], s, active, tiles_x);
+  log.end(pi_, st, units);
 }
 
+std::vector<std::pair<const void*, Bf16Pack>> g_headers;
+
+}  // namespace
+
 // Build the device weight pack of one smoother level from PyTorch-layout
-// fp64 weights (width 32, 3x3).  split = 1: the split bf16 form (each weight
-// stored as bf16 hi and lo blocks, operands hi + lo); 0: plain bf16.
-// Returns one device allocation with the packed weights and fp32 biases.
+// fp64 weights (width 32, 3x3, at least 3 layers).  split = 1: the split
+// bf16 form; 0: plain bf16.  Returns one device allocation holding packed
+// weights and biases; the per-layer device pointers are kept in a host
+// table keyed by it.
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
                     const std::vector<const double*>& bias, int split) {
-  if (layers < 2 || layers > 8) return nullptr;
-  std::vector<std::vector<uint16_t>> wl(layers);
-  std::vector<std::vector<float>> bl(layers);
+  if (layers < 3 || layers > 8) return nullptr;
+  std::vector<std::vector<unsigned char>> wl(layers), bl(layers);
   std::vector<int> has_lo(layers, 0);
   for (int li = 0; li < layers; ++li) {
-    const int mode = li == 0 ? FIRST : (li == layers - 1 ? LAST : HIDDEN);
     const int cin = li == 0 ? 1 : WIDTH, cout = li == layers - 1 ? 1 : WIDTH;
     const double* w = W[li];
-    auto hi_lo = [&](double v, uint16_t& hb, uint16_t& lb) {
-      hb = bf16_bits((float)v);
-      uint32_t u = (uint32_t)hb << 16;
-      float hf;
-      std::memcpy(&hf, &u, 4);
-      lb = bf16_bits((float)(v - (double)hf));
-      if (lb != 0 && lb != 0x8000) has_lo[li] = 1;
-    };
-    if (mode == FIRST) {
-      // chunks: [0,1] W_hi (x hi taps), [2,3] W_hi (x lo taps), [4,5] W_lo (x hi taps)
-      const int nch = split ? 6 : 2;
-      std::vector<uint16_t> p((size_t)nch * 32 * 8, 0);
-      for (int co = 0; co < 32; ++co)
-        for (int k = 0; k < 9; ++k) {
-          uint16_t hb, lb;
-          hi_lo(w[co * 9 + k], hb, lb);
-          p[((k >> 3) * 32 + co) * 8 + (k & 7)] = hb;
+    std::vector<float> bb(WIDTH, 0.f);
+    for (int co = 0; co < cout; ++co) bb[co] = (float)bias[li][co];
+    bl[li].resize(WIDTH * sizeof(float));
+    std::memcpy(bl[li].data(), bb.data(), WIDTH * sizeof(float));
+    if (li == 0 || li == layers - 1) {
+      // fp32 [c][tap]: first layer c = cout, last layer c = cin
+      std::vector<float> f(WIDTH * 9, 0.f);
+      for (int c = 0; c < WIDTH; ++c)
+        for (int t = 0; t < 9; ++t) f[c * 9 + t] = (float)w[c * 9 + t];
+      wl[li].resize(f.size() * sizeof(float));
+      std::memcpy(wl[li].data(), f.data(), wl[li].size());
+      continue;
+    }
+    const size_t half = (size_t)9 * 4 * WIDTH * 8;
+    std::vector<uint16_t> p(split ? 2 * half : half, 0);
+    for (int co = 0; co < cout; ++co)
+      for (int ci = 0; ci < cin; ++ci)
+        for (int tap = 0; tap < 9; ++tap) {
+          const double v = w[((size_t)co * cin + ci) * 9 + tap];
+          const uint16_t hb = bf16_bits((float)v);
+          uint32_t u = (uint32_t)hb << 16;
+          float hf;
+          std::memcpy(&hf, &u, 4);
+          const size_t idx = (((size_t)tap * 4 + ci / 8) * WIDTH + co) * 8 + ci % 8;
+          p[idx] = hb;
           if (split) {
-            p[((2 + (k >> 3)) * 32 + co) * 8 + (k & 7)] = hb;
-            p[((4 + (k >> 3)) * 32 + co) * 8 + (k & 7)] = lb;
+            const uint16_t lb = bf16_bits((float)(v - (double)hf));
+            p[half + idx] = lb;
+            if (lb != 0 && lb != 0x8000) has_lo[li] = 1;
           }
         }
-      wl[li] = p;
-    } else {
-      const int NOUT = mode == LAST ? 16 : 32;
-      const size_t half = (size_t)9 * 4 * NOUT * 8;
-      std::vector<uint16_t> p(split ? 2 * half : half, 0);
-      for (int co = 0; co < cout; ++co)
-        for (int ci = 0; ci < cin; ++ci)
-          for (int tap = 0; tap < 9; ++tap) {
-            uint16_t hb, lb;
-            hi_lo(w[((size_t)co * cin + ci) * 9 + tap], hb, lb);
-            size_t idx = (((size_t)tap * 4 + ci / 8) * NOUT + co) * 8 + ci % 8;
-            p[idx] = hb;
-            if (split) p[half + idx] = lb;
-          }
-      wl[li] = p;
-    }
-    bl[li].assign(32, 0.f);
-    for (int co = 0; co < cout; ++co) bl[li][co] = (float)bias[li][co];
+    wl[li].resize(p.size() * 2);
+    std::memcpy(wl[li].data(), p.data(), wl[li].size());
   }
   size_t bytes = 0;
   std::vector<size_t> woff(layers), boff(layers);
   for (int li = 0; li < layers; ++li) {
     woff[li] = bytes;
-    bytes += (wl[li].size() * 2 + 255) / 256 * 256;
+    bytes += (wl[li].size() + 255) / 256 * 256;
     boff[li] = bytes;
     bytes += 256;
   }
@@ -447,11 +840,12 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
   hdr.layers = layers;
   hdr.split = split;
   for (int li = 0; li < layers; ++li) {
-    std::memcpy(host.data() + woff[li], wl[li].data(), wl[li].size() * 2);
-    std::memcpy(host.data() + boff[li], bl[li].data(), 32 * sizeof(float));
-    hdr.l[li].w = reinterpret_cast<const __nv_bfloat16*>(dptr + woff[li]);
+    std::memcpy(host.data() + woff[li], wl[li].data(), wl[li].size());
+    std::memcpy(host.data() + boff[li], bl[li].data(), bl[li].size());
+    const bool simt = li == 0 || li == layers - 1;
+    hdr.l[li].w = simt ? nullptr : reinterpret_cast<const __nv_bfloat16*>(dptr + woff[li]);
+    hdr.l[li].wf = simt ? reinterpret_cast<const float*>(dptr + woff[li]) : nullptr;
     hdr.l[li].bias = reinterpret_cast<const float*>(dptr + boff[li]);
-    hdr.l[li].wcount = (int)wl[li].size();
     hdr.l[li].has_lo = split ? has_lo[li] : 0;
   }
   if (cudaMemcpy(dptr, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -469,24 +863,6 @@ void bf16_cnn_forget(const void* pack) {
       return;
     }
 }
-
-namespace {
-template <int SPLIT>
-void run_layers(int n, int B, int layers, const Bf16Pack& P, const float* b, const double* s,
-                __nv_bfloat16* a0, __nv_bfloat16* a1, float* h, const int* active, int* err,
-                cudaStream_t st, LaunchLog& log) {
-  launch_mode<FIRST, SPLIT>(n, B, b, nullptr, a0, nullptr, P.l[0], s, active, err, st, log);
-  __nv_bfloat16* cur = a0;
-  __nv_bfloat16* nxt = a1;
-  for (int li = 1; li < layers - 1; ++li) {
-    launch_mode<HIDDEN, SPLIT>(n, B, nullptr, cur, nxt, nullptr, P.l[li], s, active, err, st, log);
-    __nv_bfloat16* t = cur;
-    cur = nxt;
-    nxt = t;
-  }
-  launch_mode<LAST, SPLIT>(n, B, nullptr, cur, nullptr, h, P.l[layers - 1], s, active, err, st, log);
-}
-}  // namespace
 
 // h = s N(b / s) for `B` images of side n; act0/act1 hold NHWC bf16
 // activations (B * n * n * 32 elements, x2 in the split form); err: device

@@ -7,10 +7,11 @@ fp32 outer residual, fp64 update) against the FP64 oracle.
   the first cycle from zero, where the smoother's large filtered-out
   near-constant output makes single-rounding bf16 fail.
 * bf16fast_refine (one bf16 per operand): compared with a CPU evaluation of
-  the same network that rounds to bf16 exactly where the kernel stores bf16
-  (input b/||b||, weights, hidden activations) and accumulates in fp64: the
-  two may differ only by fp32 accumulation order (1e-4), which pins the MMA
-  operand layout; its solve must still reach the tolerance.
+  the same network that rounds to bf16 exactly where the kernels store bf16
+  (hidden activations, hidden-layer weights) and accumulates in fp64: the
+  two may differ only by fp32 accumulation order, which pins the MMA
+  operand layout (1e-3: accumulation order can flip a few bf16 roundings);
+  its solve must still reach the tolerance.
 * Full solves reach ||f - A u|| / ||f|| <= 1e-6 as measured by the oracle's
   own fp64 apply.
 """
@@ -41,12 +42,17 @@ def bf16(a):
 
 
 def emulated_fast(W, b):
-    """s N(b/s) with single bf16 rounding at the fast kernel's storage points."""
+    """s N(b/s) rounded to bf16 exactly where the fast kernels store bf16: the
+    hidden activations and the hidden layers' weights (the first and last
+    layers run in fp32)."""
     s = np.sqrt(np.sum(b.reshape(b.shape[0], -1) ** 2, axis=1))[:, None, None]
-    x = bf16(b / s)[:, None]
+    x = (b / s)[:, None]
+    last = len(W) - 1
     for i, (w, bias) in enumerate(W):
-        x = ON._conv_same(x, bf16(w), np.asarray(bias, np.float32).astype(np.float64))
-        if i < len(W) - 1:
+        wi = np.asarray(w, np.float32).astype(np.float64) if i in (0, last) else bf16(w)
+        x = ON._conv_same(x, wi, np.asarray(bias, np.float32).astype(np.float64))
+        x = x.astype(np.float32).astype(np.float64)  # the kernels accumulate in fp32
+        if i < last:
             x = bf16(np.maximum(x, 0.0))
     return x[:, 0] * s
 
@@ -88,7 +94,9 @@ def test_fast_smoother_matches_bf16_emulation(ctx):
         m = H.size(l)
         b = rng.standard_normal((3, m, m)) * np.array([1.0, 1e-4, 30.0])[:, None, None]
         b32, h = smooth_gpu(G, l, b)
-        assert rel(h, emulated_fast(W[l], b32)) < 1e-4, l
+        # fp32 accumulation order can flip a few bf16 roundings of hidden
+        # activations (2^-8 each); an operand-layout error would be O(1)
+        assert rel(h, emulated_fast(W[l], b32)) < 1e-3, l
 
 
 @pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine"])
@@ -100,7 +108,7 @@ def test_smoother_small_level_and_zero_rhs(ctx, prec):
     b32, h = smooth_gpu(G, 3, b)
     assert np.all(h[1] == 0.0)
     if prec == "bf16fast_refine":
-        assert rel(h[:1], emulated_fast(W[3], b32[:1])) < 1e-4
+        assert rel(h[:1], emulated_fast(W[3], b32[:1])) < 1e-3
     else:
         assert rel(h[:1], O.smoother(W[3], b32[:1])) < 1e-4
 
