@@ -54,13 +54,17 @@ constexpr int RH = TILE + 2;            // staged input rows
 constexpr int CH_BYTES = RH * RW * 16;  // one 8-channel chunk of the staged tile
 constexpr int WIDTH = 32;
 constexpr int THREADS = 128;
-constexpr int TMEM_COLS = 128;          // 2 accumulators x 2 M tiles x 32 columns
+// MMA N: fast form 32 output channels; split form 64 = [w_hi | w_lo] so that
+// one MMA per A operand forms both a*w_hi and a*w_lo (summed in the epilogue)
+template <int SPLIT> struct NB { static constexpr int value = SPLIT ? 64 : 32; };
+template <int SPLIT> struct TMC { static constexpr int value = SPLIT ? 256 : 128; };  // TMEM columns
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bound of every mbarrier wait
-constexpr int B_HALF = 9 * 4 * WIDTH * 16;  // one bf16 weight block of a hidden layer
+constexpr int B_HALF = 9 * 4 * WIDTH * 16;  // bf16 weights of a hidden layer for N = 32
 
 // per layer: hidden layers use bf16 weights in the MMA B layout
-// [tap 9][kchunk 4][cout 32][8 cin] (SPLIT: hi block then lo block);
-// first/last layers use fp32 weights [c][tap] and fp32 biases.
+// [tap 9][kchunk 4][n NB][8 cin] with n = cout (fast) or n = cout for w_hi and
+// 32 + cout for w_lo (split); first/last layers use fp32 weights [c][tap]
+// and fp32 biases.
 struct LayerPack {
   const __nv_bfloat16* w;
   const float* wf;
@@ -290,6 +294,52 @@ k_last_simt(int n, const __nv_bfloat16* __restrict__ ain, float* __restrict__ ho
   hout[(size_t)b * plane + (size_t)y * n + x] = (float)s * acc;
 }
 
+// All MMAs of one block tile: for each M tile (8-column half), 9 taps x 2 K
+// halves, one MMA per A operand (hi, and lo in the split form).  Descriptors
+// are built once; per MMA only a compile-time offset is added to their
+// start-address field.
+template <int SPLIT, int PITCH>
+__device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base, uint32_t d0) {
+  constexpr int N = NB<SPLIT>::value;
+  constexpr uint32_t idesc = make_idesc(128, N);
+  const uint64_t ad0 = make_desc(a_base, PITCH, RW * 16);
+  const uint64_t bd0 = make_desc(b_base, N * 16, 128);
+#pragma unroll
+  for (int mt = 0; mt < NT; ++mt) {
+    const uint32_t d = d0 + mt * N;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+      for (int kh = 0; kh < 2; ++kh) {
+        const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
+        const uint32_t boff = ((tap * 4 + 2 * kh) * N * 16) >> 4;
+        mma_bf16(d, ad0 + aoff, bd0 + boff, idesc, (tap | kh) ? 1u : 0u);
+        if (SPLIT) mma_bf16(d, ad0 + aoff + ((4 * PITCH) >> 4), bd0 + boff, idesc, 1u);
+      }
+    }
+  }
+}
+
+// bias, ReLU and store of one pixel from 32 (fast) or 64 (split: hi + lo
+// weight halves) accumulator columns
+template <int SPLIT>
+__device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bias,
+                                             __nv_bfloat16* dst, bool store) {
+  float v[32];
+  tmem_ld32(taddr, v);
+  if (SPLIT) {
+    float w[32];
+    tmem_ld32(taddr + 32, w);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] += w[c];
+  }
+  if (store) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias[c], 0.f);
+    store_channels<SPLIT>(dst, v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // hidden layer 32 -> 32 on the tensor cores (pipelined, persistent)
 // ---------------------------------------------------------------------------
@@ -301,6 +351,8 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   constexpr int ACH = SPLIT ? 8 : 4;  // 8-channel chunks per staged pixel
   constexpr int ABUF = ACH * CH_BYTES;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  constexpr int TMEM_COLS = TMC<SPLIT>::value;
+  constexpr int NACC = NT * NB<SPLIT>::value;  // columns of one accumulator
   constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* Bs = smem + 2 * ABUF;
@@ -332,7 +384,6 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const uint32_t a_base0 = smem_u32(smem), b_base = smem_u32(Bs);
-  const uint32_t idesc = make_idesc(128, WIDTH);
   const int tiles_x = (n + TILE - 1) / TILE;
   const int per_img = tiles_x * tiles_x;
   const long long total = (long long)nimg * per_img;
@@ -372,15 +423,12 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
     const int b = (int)(t / per_img), tt = (int)(t % per_img);
     const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
     for (int mt = 0; mt < NT; ++mt) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + acc * (NT * 32) + mt * 32, v);
       const int m = warp * 32 + lane;
       const int y = y0 + (m >> 3), x = x0 + mt * 8 + (m & 7);
-      if (y < n && x < n) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + lp.bias[c], 0.f);
-        store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + x) * CW, v);
-      }
+      const bool in = y < n && x < n;
+      finish_pixel<SPLIT>(tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value,
+                          lp.bias, in ? aout + ((size_t)b * plane + (size_t)y * n + x) * CW : aout,
+                          in);
     }
   };
 
@@ -398,28 +446,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (tid == 0) {
-      const uint32_t a_base = a_base0 + sb * ABUF;
-      for (int mt = 0; mt < NT; ++mt) {
-        const uint32_t d = tmem + sb * (NT * 32) + mt * 32;
-        uint32_t accf = 0;
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3, dx = tap % 3;
-          const uint32_t shift = (dy * RW + 8 * mt + dx) * 16;
-#pragma unroll
-          for (int kh = 0; kh < 2; ++kh) {
-            const uint32_t boff = (tap * 4 + 2 * kh) * WIDTH * 16;
-            const uint64_t ad = make_desc(a_base + 2 * kh * CH_BYTES + shift, CH_BYTES, RW * 16);
-            const uint64_t bd = make_desc(b_base + boff, WIDTH * 16, 128);
-            mma_bf16(d, ad, bd, idesc, accf);
-            accf = 1u;
-            if (SPLIT) {
-              const uint64_t adl = make_desc(a_base + (4 + 2 * kh) * CH_BYTES + shift, CH_BYTES, RW * 16);
-              mma_bf16(d, adl, bd, idesc, 1u);
-              if (lp.has_lo) mma_bf16(d, ad, make_desc(b_base + B_HALF + boff, WIDTH * 16, 128), idesc, 1u);
-            }
-          }
-        }
-      }
+      issue_tile_mmas<SPLIT, CH_BYTES>(a_base0 + sb * ABUF, b_base, tmem + sb * NACC);
       mma_commit(smem_u32(&mbar[sb]));
     }
     const long long nxt = advance(cur);
@@ -489,6 +516,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   constexpr uint32_t TX = ACH * RH * RW * 16;      // bytes the copies of one stage write
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
   constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  constexpr int TMEM_COLS = TMC<SPLIT>::value;
+  constexpr int NACC = NT * NB<SPLIT>::value;
   extern __shared__ __align__(16) unsigned char smem_raw_ws[];
   // stage buffers start on a 1024-byte boundary (TMA destinations need 128)
   unsigned char* smem = smem_raw_ws + ((1024u - (smem_u32(smem_raw_ws) & 1023u)) & 1023u);
@@ -576,7 +605,6 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(128, WIDTH);
       const uint32_t b_base = smem_u32(Bs);
       int i = 0;
       for (long long t = first(); t < total; t = advance(t), ++i) {
@@ -584,28 +612,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         if (!wait(&full[s], (uint32_t)((i / STAGES) & 1))) break;
         if (i >= 2 && !wait(&acc_empty[a], (uint32_t)((i / 2 - 1) & 1))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_base = smem_u32(smem + s * SBYTES);
-        for (int mt = 0; mt < NT; ++mt) {
-          const uint32_t d = tmem + a * (NT * 32) + mt * 32;
-          uint32_t accf = 0;
-          for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
-            const uint32_t shift = (dy * RW + 8 * mt + dx) * 16;
-#pragma unroll
-            for (int kh = 0; kh < 2; ++kh) {
-              const uint32_t boff = (tap * 4 + 2 * kh) * WIDTH * 16;
-              const uint64_t ad = make_desc(a_base + 2 * kh * CH_PITCH + shift, CH_PITCH, RW * 16);
-              const uint64_t bd = make_desc(b_base + boff, WIDTH * 16, 128);
-              mma_bf16(d, ad, bd, idesc, accf);
-              accf = 1u;
-              if (SPLIT) {
-                const uint64_t adl = make_desc(a_base + (4 + 2 * kh) * CH_PITCH + shift, CH_PITCH, RW * 16);
-                mma_bf16(d, adl, bd, idesc, 1u);
-                if (lp.has_lo) mma_bf16(d, ad, make_desc(b_base + B_HALF + boff, WIDTH * 16, 128), idesc, 1u);
-              }
-            }
-          }
-        }
+        issue_tile_mmas<SPLIT, CH_PITCH>(smem_u32(smem + s * SBYTES), b_base, tmem + a * NACC);
         mma_commit(smem_u32(&empty[s]));
         mma_commit(smem_u32(&acc_full[a]));
       }
@@ -618,26 +625,20 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
       const int a = i & 1;
       if (!wait(&acc_full[a], (uint32_t)((i / 2) & 1))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float v0[32], v1[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * (NT * 32), v0);
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * (NT * 32) + 32, v1);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[a]));
       const int b = (int)(t / per_img), tt = (int)(t % per_img);
       const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
       const int m = q * 32 + lane;
       const int y = y0 + (m >> 3);
-      if (y < n) {
-        const int xa = x0 + (m & 7), xb = x0 + 8 + (m & 7);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          v0[c] = fmaxf(v0[c] + lp.bias[c], 0.f);
-          v1[c] = fmaxf(v1[c] + lp.bias[c], 0.f);
-        }
-        if (xa < n) store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + xa) * CW, v0);
-        if (xb < n) store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + xb) * CW, v1);
+      for (int mt = 0; mt < NT; ++mt) {
+        const int x = x0 + mt * 8 + (m & 7);
+        const bool in = y < n && x < n;
+        finish_pixel<SPLIT>(tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value,
+                            lp.bias, in ? aout + ((size_t)b * plane + (size_t)y * n + x) * CW : aout,
+                            in);
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[a]));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -713,11 +714,11 @@ int num_sms() {
 }
 
 template <int SPLIT>
-void launch_hidden(int n, int nimg, const __nv_bfloat16* ain, __nv_bfloat16* aout,
+void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv_bfloat16* aout,
                    const LayerPack& lp, const double* s, const int* active, int* err,
                    cudaStream_t st, LaunchLog& log) {
   constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
-  const CUtensorMap* map = n >= 32 ? act_map(ain, n, nimg, CWs) : nullptr;
+  const CUtensorMap* map = n >= 32 ? act_map(ain, n, map_imgs, CWs) : nullptr;
   if (map) {
     constexpr int STAGES = SPLIT ? 3 : 4;
     constexpr int ACHs = SPLIT ? 8 : 4;
@@ -749,7 +750,7 @@ void launch_hidden(int n, int nimg, const __nv_bfloat16* ain, __nv_bfloat16* aou
 }
 
 template <int SPLIT>
-void run_layers(int n, int B, int layers, const Bf16Pack& P, const float* b, const double* s,
+void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const float* b, const double* s,
                 __nv_bfloat16* a0, __nv_bfloat16* a1, float* h, const int* active, int* err,
                 cudaStream_t st, LaunchLog& log) {
   const int tiles_x = (n + TILE - 1) / TILE;
@@ -761,7 +762,7 @@ void run_layers(int n, int B, int layers, const Bf16Pack& P, const float* b, con
   __nv_bfloat16* cur = a0;
   __nv_bfloat16* nxt = a1;
   for (int li = 1; li < layers - 1; ++li) {
-    launch_hidden<SPLIT>(n, B, cur, nxt, P.l[li], s, active, err, st, log);
+    launch_hidden<SPLIT>(n, B, map_imgs, cur, nxt, P.l[li], s, active, err, st, log);
     __nv_bfloat16* t = cur;
     cur = nxt;
     nxt = t;
@@ -804,8 +805,8 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
       std::memcpy(wl[li].data(), f.data(), wl[li].size());
       continue;
     }
-    const size_t half = (size_t)9 * 4 * WIDTH * 8;
-    std::vector<uint16_t> p(split ? 2 * half : half, 0);
+    const int N = split ? 2 * WIDTH : WIDTH;
+    std::vector<uint16_t> p((size_t)9 * 4 * N * 8, 0);
     for (int co = 0; co < cout; ++co)
       for (int ci = 0; ci < cin; ++ci)
         for (int tap = 0; tap < 9; ++tap) {
@@ -814,11 +815,11 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
           uint32_t u = (uint32_t)hb << 16;
           float hf;
           std::memcpy(&hf, &u, 4);
-          const size_t idx = (((size_t)tap * 4 + ci / 8) * WIDTH + co) * 8 + ci % 8;
-          p[idx] = hb;
+          const size_t row = ((size_t)tap * 4 + ci / 8) * N;
+          p[(row + co) * 8 + ci % 8] = hb;
           if (split) {
             const uint16_t lb = bf16_bits((float)(v - (double)hf));
-            p[half + idx] = lb;
+            p[(row + WIDTH + co) * 8 + ci % 8] = lb;
             if (lb != 0 && lb != 0x8000) has_lo[li] = 1;
           }
         }
@@ -865,11 +866,12 @@ void bf16_cnn_forget(const void* pack) {
 }
 
 // h = s N(b / s) for `B` images of side n; act0/act1 hold NHWC bf16
-// activations (B * n * n * 32 elements, x2 in the split form); err: device
-// error word of the bounded waits.
-void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b, const double* s,
-                     float* act0, float* act1, float* h, const int* active, int* err,
-                     cudaStream_t st, LaunchLog& log) {
+// activations (B * n * n * 32 elements, x2 in the split form), described to
+// the copy engine as map_imgs >= B images so one tensor map serves every
+// chunk; err: device error word of the bounded waits.
+void bf16_cnn_launch(int n, int B, int map_imgs, int layers, const void* pack, const float* b,
+                     const double* s, float* act0, float* act1, float* h, const int* active,
+                     int* err, cudaStream_t st, LaunchLog& log) {
   const Bf16Pack* P = nullptr;
   for (auto& e : g_headers)
     if (e.first == pack) P = &e.second;
@@ -877,9 +879,9 @@ void bf16_cnn_launch(int n, int B, int layers, const void* pack, const float* b,
   __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(act0);
   __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(act1);
   if (P->split)
-    run_layers<1>(n, B, layers, *P, b, s, a0, a1, h, active, err, st, log);
+    run_layers<1>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
   else
-    run_layers<0>(n, B, layers, *P, b, s, a0, a1, h, active, err, st, log);
+    run_layers<0>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
 }
 
 }  // namespace nmg
