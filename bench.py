@@ -164,6 +164,16 @@ def barrier(world):
         dist.barrier()
 
 
+def rank_seed(wl, rank):
+    """Each replica solves its own batch: the right-hand-side seed depends on the rank."""
+    return wl["rhs_seed"] + 7919 * rank
+
+
+def aggregate(batch_per_rank, world, steps, max_total_ms):
+    """Whole-job throughput: right-hand sides of all ranks / slowest rank's time."""
+    return batch_per_rank * world * steps / (max_total_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
@@ -229,7 +239,7 @@ def run_ours(args, wl, world, rank, local):
 
     G = hier(prec)
     B = args.batch or wl["batch"]
-    f_np = make_rhs(wl, B, wl["rhs_seed"] + 7919 * rank)
+    f_np = make_rhs(wl, B, rank_seed(wl, rank))
     refine = prec != "fp32"
     udt = torch.float64 if refine else torch.float32
     f = torch.tensor(f_np, dtype=torch.float32, device="cuda")
@@ -277,7 +287,7 @@ def run_ours(args, wl, world, rank, local):
     launches = ctx.launches() - l0
     clk = clocks.stop()
     total_ms = reduce_max(sum(times), world)
-    value = B * world * args.steps / (total_ms / 1e3)
+    value = aggregate(B, world, args.steps, total_ms)
     converged = bool(all((r[1] == 0).all() for r in res))
     max_relres = float(max(r[2].max() for r in res))
     mean_cycles = float(np.mean([r[0].mean() for r in res]))

@@ -318,6 +318,8 @@ PRESETS = {
     # dim, n, levels, alpha, kernel, batch, epochs
     "c1": dict(dim=1, n=256, levels=3, alpha=1e-3, width_t=0.05, layers=3, width=16, ksize=5),
     "c2": dict(dim=2, n=128, levels=5, alpha=1e-2, sigma=2.0, layers=4, width=32, ksize=3),
+    "c3": dict(dim=2, n=512, levels=7, alpha=1e-3, sigma=4.0, layers=4, width=32, ksize=3,
+               rhs="waves"),
 }
 
 
@@ -366,6 +368,8 @@ def main(argv=None):
     scheds = [torch.optim.lr_scheduler.CosineAnnealingLR(o, a.epochs, eta_min=a.lr * 0.02) for o in opts]
     if dim == 1:
         f_eval, _ = nmg_inputs.rhs_1d_sines_steps(cfg["n"], a.eval_batch, 4242)
+    elif cfg.get("rhs") == "waves":
+        f_eval, _ = nmg_inputs.rhs_2d_waves_rects(cfg["n"], a.eval_batch, 4242, cfg["sigma"])
     else:
         f_eval, _ = nmg_inputs.rhs_2d_ellipses_grf(cfg["n"], a.eval_batch, 4242, cfg["sigma"])
     f_eval = torch.tensor(f_eval, dtype=torch.float32, device=a.device)
