@@ -148,7 +148,8 @@ typedef struct {
 } nmg_solve_info;
 
 /* Create a context on CUDA device `device`.  stream: a cudaStream_t to
- * order work on, or NULL for a library-owned non-blocking stream. */
+ * order work on, or NULL for a library-owned stream that is ordered after
+ * work queued on the legacy default stream. */
 nmg_status nmg_create(nmg_ctx** ctx, int device, void* stream);
 void nmg_destroy(nmg_ctx* ctx);
 
@@ -166,6 +167,24 @@ void nmg_destroy_hier(nmg_hier* h);
 nmg_status nmg_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u,
                      double rtol, int max_cycles, nmg_solve_info* info);
 
+/* One batch of one hierarchy inside a multi-hierarchy solve. */
+typedef struct {
+  nmg_hier* hier;        /* hierarchy of this item (each at most once per call) */
+  int batch;             /* right-hand sides of this item (0 = skip) */
+  const void* f;         /* device, [batch][n][n] (or [batch][n]) of the hierarchy's f type */
+  void* u;               /* device, in/out, the hierarchy's u type */
+  nmg_solve_info* info;  /* host array [batch] or NULL */
+} nmg_solve_item;
+
+/* Solve several batches on different hierarchies (grid sizes, operators,
+ * precisions) together: one outer loop in which every iteration runs one
+ * cycle and one convergence test for every item still active.  With graphs
+ * enabled an iteration of all items is one CUDA graph whose items are
+ * parallel branches, so small grids share the device.  Each item gets the
+ * same results as nmg_solve on it alone.  Synchronous. */
+nmg_status nmg_solve_multi(nmg_ctx* ctx, int nitems, const nmg_solve_item* items, double rtol,
+                           int max_cycles);
+
 /* Same as nmg_solve with HOST f and u: the library copies f (and u) to its
  * own device buffers, solves, and copies u back.  Host buffers may be
  * pageable or pinned.  Synchronous. */
@@ -176,6 +195,37 @@ nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_ho
 /* Exactly one cycle u <- NMGF(u, f) at the finest level for every
  * right-hand side (no convergence test).  Asynchronous. */
 nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u);
+
+/* ---- serving: continuous batching over resident hierarchies ---------------
+ * A server keeps every added operator's hierarchy resident and gives it a
+ * pool of `slots` right-hand-side positions.  Requests are queued on the
+ * host; each nmg_server_step() admits queued requests (arrival order) into
+ * free slots of their operator, runs one outer iteration (one cycle and one
+ * convergence test) for every live request of every operator, and retires
+ * requests that converged (relative residual <= rtol), diverged or used
+ * max_cycles cycles, copying u to the caller's buffer.  Each slot is
+ * computed independently: a request's result does not depend on the other
+ * requests in flight.  The server does not own the hierarchies. */
+typedef struct nmg_server nmg_server;
+/* budget_bytes bounds the device memory of all slot pools. */
+nmg_status nmg_server_create(nmg_ctx* ctx, size_t budget_bytes, double rtol, int max_cycles,
+                             nmg_server** out);
+void nmg_server_destroy(nmg_server* s);
+/* Make hierarchy h servable with `slots` concurrent requests; allocates its
+ * workspace for that many right-hand sides plus slot buffers for f and u
+ * (NMG_ERR_OOM if the budget would be exceeded).  op_id: returned handle. */
+nmg_status nmg_server_add_operator(nmg_server* s, nmg_hier* h, int slots, int* op_id);
+/* Queue one right-hand side (host, the operator's f type, copied now); u_host
+ * (host, the operator's u type) receives the solution when the request is
+ * retired and must stay valid until then.  req_id: returned handle. */
+nmg_status nmg_server_submit(nmg_server* s, int op_id, const void* f_host, void* u_host,
+                             long long* req_id);
+/* One scheduler step (synchronous); completed: requests retired by it. */
+nmg_status nmg_server_step(nmg_server* s, int* completed);
+/* state: 0 queued, 1 running, 2 done; times in seconds since server creation. */
+nmg_status nmg_server_query(nmg_server* s, long long req_id, nmg_solve_info* info, int* state,
+                            double* t_submit, double* t_admit, double* t_done);
+nmg_status nmg_server_stats(const nmg_server* s, int* queued, int* running, size_t* bytes_used);
 
 /* ---- single steps of the cycle (level is 0-based: 0 is the paper's l=1) --
  * Vectors are the hierarchy's level type (see above).  Asynchronous unless
@@ -235,6 +285,12 @@ enum {
 nmg_status nmg_profile_enable(nmg_ctx* ctx, int enable);
 nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double* ms,
                             double* units);
+/* Solve loops replay one captured CUDA graph per outer iteration (cycle +
+ * convergence test; captured on first use for a given batch, f, u and
+ * rtol).  enable = 0 launches every kernel eagerly instead.  Profiling
+ * (nmg_profile_enable) always launches eagerly.  Default: enabled. */
+nmg_status nmg_set_graphs(nmg_ctx* ctx, int enable);
+
 /* Wait for the context's stream. */
 nmg_status nmg_sync(nmg_ctx* ctx);
 const char* nmg_status_str(nmg_status s);

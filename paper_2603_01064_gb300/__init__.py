@@ -17,7 +17,7 @@ import numpy as np
 
 __all__ = [
     "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
-    "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo",
+    "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo", "solve_multi", "Server",
 ]
 
 FP64, FP32, BF16_REFINE, BF16FAST_REFINE = 0, 1, 2, 3
@@ -56,6 +56,11 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double)]
 
 
+class _SolveItem(ctypes.Structure):
+    _fields_ = [("hier", ctypes.c_void_p), ("batch", ctypes.c_int), ("f", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("info", ctypes.POINTER(SolveInfo))]
+
+
 def lib_path() -> str:
     return _LIB_PATH
 
@@ -77,6 +82,15 @@ def lib():
         "nmg_destroy_hier": (V, [P]),
         "nmg_solve": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
         "nmg_solve_host": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
+        "nmg_solve_multi": (I, [P, I, ctypes.POINTER(_SolveItem), D, I]),
+        "nmg_server_create": (I, [P, ctypes.c_size_t, D, I, ctypes.POINTER(P)]),
+        "nmg_server_destroy": (V, [P]),
+        "nmg_server_add_operator": (I, [P, P, I, ctypes.POINTER(I)]),
+        "nmg_server_submit": (I, [P, I, P, P, ctypes.POINTER(ctypes.c_longlong)]),
+        "nmg_server_step": (I, [P, ctypes.POINTER(I)]),
+        "nmg_server_query": (I, [P, ctypes.c_longlong, ctypes.POINTER(SolveInfo), ctypes.POINTER(I),
+                                 ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "nmg_server_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t)]),
         "nmg_cycle": (I, [P, P, I, P, P]),
         "nmg_residual": (I, [P, P, I, I, P, P, P, ctypes.POINTER(D)]),
         "nmg_residual_restrict": (I, [P, P, I, I, P, P, P]),
@@ -89,6 +103,7 @@ def lib():
         "nmg_hier_level_dense": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "nmg_launch_count": (ctypes.c_longlong, [P]),
         "nmg_profile_enable": (I, [P, I]),
+        "nmg_set_graphs": (I, [P, I]),
         "nmg_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                  ctypes.POINTER(D)]),
         "nmg_sync": (I, [P]),
@@ -153,6 +168,10 @@ class Context:
 
     def launches(self) -> int:
         return int(lib().nmg_launch_count(self._h))
+
+    def set_graphs(self, enable: bool):
+        """Replay captured CUDA graphs per outer iteration (default) or launch eagerly."""
+        self.check(lib().nmg_set_graphs(self._h, 1 if enable else 0))
 
     def profile(self, enable: bool):
         self.check(lib().nmg_profile_enable(self._h, 1 if enable else 0))
@@ -275,6 +294,83 @@ class Hierarchy:
     def close(self):
         if self._h:
             lib().nmg_destroy_hier(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_multi(ctx: "Context", items, rtol=1e-6, max_cycles=100):
+    """Solve several (hierarchy, f, u) batches together (nmg_solve_multi).
+    items: list of (Hierarchy, f, u) with torch CUDA tensors; returns a list of
+    (cycles, status, relres) per item."""
+    arr = (_SolveItem * max(len(items), 1))()
+    infos = []
+    for i, (G, f, u) in enumerate(items):
+        B = f.shape[0]
+        inf = (SolveInfo * max(B, 1))()
+        infos.append((inf, B))
+        arr[i] = _SolveItem(G._h.value, B, _ptr(f).value if B else None,
+                            _ptr(u).value if B else None, inf)
+    ctx.check(lib().nmg_solve_multi(ctx._h, len(items), arr, float(rtol), int(max_cycles)))
+    return [_unpack(inf, B) for inf, B in infos]
+
+
+class Server:
+    """Continuous-batching solve server (nmg_server_*): resident hierarchies,
+    per-operator slot pools, one outer iteration per live request per step."""
+
+    def __init__(self, ctx: "Context", budget_bytes: int, rtol=1e-6, max_cycles=100):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        ctx.check(lib().nmg_server_create(ctx._h, int(budget_bytes), float(rtol), int(max_cycles),
+                                          ctypes.byref(self._h)))
+        self._keep = {}
+
+    def add_operator(self, G: "Hierarchy", slots: int) -> int:
+        op = ctypes.c_int()
+        self.ctx.check(lib().nmg_server_add_operator(self._h, G._h, int(slots), ctypes.byref(op)))
+        return op.value
+
+    def submit(self, op: int, f: np.ndarray, u_out: np.ndarray) -> int:
+        """f, u_out: contiguous host arrays of the operator's f and u types;
+        u_out must stay alive until the request is done."""
+        assert f.flags.c_contiguous and u_out.flags.c_contiguous
+        rid = ctypes.c_longlong()
+        self.ctx.check(lib().nmg_server_submit(self._h, int(op), ctypes.c_void_p(f.ctypes.data),
+                                               ctypes.c_void_p(u_out.ctypes.data),
+                                               ctypes.byref(rid)))
+        self._keep[rid.value] = u_out
+        return rid.value
+
+    def step(self) -> int:
+        c = ctypes.c_int()
+        self.ctx.check(lib().nmg_server_step(self._h, ctypes.byref(c)))
+        return c.value
+
+    def query(self, rid: int):
+        """(state, (cycles, status, relres), t_submit, t_admit, t_done)."""
+        info = SolveInfo()
+        st = ctypes.c_int()
+        t = [ctypes.c_double() for _ in range(3)]
+        self.ctx.check(lib().nmg_server_query(self._h, int(rid), ctypes.byref(info), ctypes.byref(st),
+                                              *[ctypes.byref(x) for x in t]))
+        if st.value == 2:
+            self._keep.pop(rid, None)
+        return st.value, (info.cycles, info.status, info.relres), t[0].value, t[1].value, t[2].value
+
+    def stats(self):
+        q, r = ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_size_t()
+        self.ctx.check(lib().nmg_server_stats(self._h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)))
+        return q.value, r.value, b.value
+
+    def close(self):
+        if self._h:
+            lib().nmg_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

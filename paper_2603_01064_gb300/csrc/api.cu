@@ -16,6 +16,7 @@
 // (the cycle's first steps only see y - A x*), this is the same iteration.
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <string>
 #include <vector>
@@ -40,9 +41,19 @@ using namespace nmg;
 struct nmg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   bool own_stream = false;
+  bool graphs = true;                 // replay captured solve iterations
   std::string err;
   LaunchLog log;
+  // multi-hierarchy solves: side streams for parallel graph branches and the
+  // captured iteration of the last item list
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> fork_join;
+  cudaGraphExec_t mexec = nullptr;
+  std::vector<const void*> mkey;
+  double mrtol = -1.0;
+  long long mkernels = 0;
 };
 
 namespace {
@@ -88,7 +99,15 @@ struct Work {
   void* fdev = nullptr;   // nmg_solve_host staging
   void* udev = nullptr;
   size_t part_per_level = 0;
+  size_t bytes = 0;  // device bytes held by this workspace
   std::vector<void*> all;
+  // captured solve iteration (cycle + convergence test) for one (B, f, u, rtol)
+  cudaGraphExec_t gexec = nullptr;
+  int gB = -1;
+  const void* gf = nullptr;
+  const void* gu = nullptr;
+  double grtol = -1.0;
+  long long gkernels = 0;
 };
 
 }  // namespace
@@ -166,6 +185,7 @@ std::vector<float> lo_f(const std::vector<double>& v) {
 }
 
 void free_work(Work& w) {
+  if (w.gexec) cudaGraphExecDestroy(w.gexec);
   for (void* p : w.all) cudaFree(p);
   if (w.h_nactive) cudaFreeHost(w.h_nactive);
   w = Work();
@@ -182,6 +202,7 @@ nmg_status ensure_work(nmg_hier* h, int B) {
     cudaError_t e = cudaMalloc(out, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(workspace)");
     w.all.push_back(*out);
+    w.bytes += bytes;
     return NMG_OK;
   };
 #define AL(bytes, ptr)                                                 \
@@ -405,9 +426,15 @@ void cycle_body(nmg_hier* h, int B, const T* f, T* x0, const T* xstar0, const T*
 void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const float* f,
                                      float* r, double* part, int* nt, const int* active);
 
-template <typename T>
-nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int max_cycles,
-                       nmg_solve_info* info) {
+// Outer iteration shared by all precision forms.  test(): level-1 residual,
+// its norm, per-RHS convergence flags and the count of RHS still active
+// (copied to pinned host memory); step(): one cycle for the active RHS.
+// After the first test, one iteration = step() + test(); it is captured
+// once per (batch, f, u, rtol) into a CUDA graph on a private stream and
+// replayed on the context's stream (eager launches when profiling).
+template <typename Step, typename Test>
+nmg_status run_outer(nmg_hier* h, int B, const void* f, const void* u, double rtol,
+                     int max_cycles, nmg_solve_info* info, Step step, Test test) {
   nmg_ctx* ctx = h->ctx;
   Work& w = h->w;
   cudaStream_t st = ctx->stream;
@@ -418,23 +445,57 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     CK(cudaMemcpyAsync(w.status, nc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
-  int nt = 0;
   ctx->log.active_hint = B;
-  launch_sumsq<T>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, st, ctx->log);
-  launch_norms(w.part[0], nt, B, w.fn, w.ones, st, ctx->log);
-  T* b0 = reinterpret_cast<T*>(w.t[0]);
-  int tau = 0;
-  for (;; ++tau) {
-    nt = op_residual<T>(h, 0, B, u, f, b0, w.part[0], w.active);
-    launch_norms(w.part[0], nt, B, w.s[0], w.active, st, ctx->log);
-    CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), st));
-    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, st, ctx->log);
-    CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+  test();
+  CK(cudaStreamSynchronize(st));
+  int nactive = *w.h_nactive;
+  ctx->log.active_hint = nactive;
+  cudaGraphExec_t exec = nullptr;
+  if (ctx->graphs && !ctx->log.prof && nactive > 0 && max_cycles > 0) {
+    if (w.gexec && w.gB == B && w.gf == f && w.gu == u && w.grtol == rtol) {
+      exec = w.gexec;
+    } else {
+      if (w.gexec) cudaGraphExecDestroy(w.gexec);
+      w.gexec = nullptr;
+      const long long l0 = ctx->log.launches;
+      ctx->stream = ctx->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        step();
+        test();
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+      ctx->stream = st;
+      if (e == cudaSuccess && e2 == cudaSuccess && g) {
+        e = cudaGraphInstantiate(&w.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+          w.gB = B;
+          w.gf = f;
+          w.gu = u;
+          w.grtol = rtol;
+          w.gkernels = ctx->log.launches - l0;
+          exec = w.gexec;
+        } else {
+          w.gexec = nullptr;
+        }
+      }
+      ctx->log.launches = l0;
+      cudaGetLastError();  // a failed capture falls back to eager launches
+    }
+  }
+  for (int tau = 0; nactive > 0 && tau < max_cycles; ++tau) {
+    if (exec) {
+      CK(cudaGraphLaunch(exec, st));
+      ctx->log.launches += w.gkernels;
+    } else {
+      step();
+      test();
+    }
     CK(cudaStreamSynchronize(st));
-    ctx->log.active_hint = *w.h_nactive;
-    if (*w.h_nactive == 0 || tau >= max_cycles) break;
-    cycle_body<T>(h, B, f, u, u, b0, w.s[0], w.active);
-    launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
+    nactive = *w.h_nactive;
+    ctx->log.active_hint = nactive;
   }
   CK(cudaGetLastError());
   {
@@ -443,7 +504,7 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     CK(cudaStreamSynchronize(st));
     if (herr) {
       cudaMemsetAsync(w.err, 0, sizeof(int), st);
-      return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its iteration limit");
+      return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its time limit");
     }
   }
   if (info) {
@@ -458,45 +519,171 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
   return NMG_OK;
 }
 
+// Several hierarchies' batches in one outer loop.  Each item contributes a
+// test() and a step() as in run_outer; one iteration of all items is one
+// CUDA graph in which every item's work is a parallel branch (captured on
+// side streams forked from and joined to the capture stream), so items of
+// different grid sizes overlap on the device.
+struct OuterItem {
+  nmg_hier* h;
+  int B;
+  std::function<void()> test, step;
+  std::function<nmg_status()> finish;
+};
+
+nmg_status run_outer_multi(nmg_ctx* ctx, std::vector<OuterItem>& items, const std::vector<const void*>& key,
+                           double rtol, int max_cycles) {
+  cudaStream_t st = ctx->stream;
+  const int m = (int)items.size();
+  for (auto& it : items) {
+    Work& w = it.h->w;
+    CK(cudaMemcpyAsync(w.active, w.ones, it.B * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(w.cycles, 0, it.B * sizeof(int), st));
+    std::vector<int> nc(it.B, NMG_NOT_CONVERGED);
+    CK(cudaMemcpyAsync(w.status, nc.data(), it.B * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  for (auto& it : items) it.test();
+  CK(cudaStreamSynchronize(st));
+  auto any_active = [&]() {
+    int tot = 0;
+    for (auto& it : items) tot += *it.h->w.h_nactive;
+    return tot;
+  };
+  int nact = any_active();
+  while ((int)ctx->side.size() < m) {
+    cudaStream_t sd;
+    CK(cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking));
+    ctx->side.push_back(sd);
+  }
+  while ((int)ctx->fork_join.size() < m + 1) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->fork_join.push_back(ev);
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (ctx->graphs && !ctx->log.prof && nact > 0 && max_cycles > 0) {
+    if (ctx->mexec && ctx->mkey == key && ctx->mrtol == rtol) {
+      exec = ctx->mexec;
+    } else {
+      if (ctx->mexec) cudaGraphExecDestroy(ctx->mexec);
+      ctx->mexec = nullptr;
+      const long long l0 = ctx->log.launches;
+      cudaStream_t cap = ctx->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        cudaEventRecord(ctx->fork_join[m], cap);
+        for (int i = 0; i < m; ++i) {
+          cudaStreamWaitEvent(ctx->side[i], ctx->fork_join[m], 0);
+          ctx->stream = ctx->side[i];
+          items[i].step();
+          items[i].test();
+          cudaEventRecord(ctx->fork_join[i], ctx->side[i]);
+          cudaStreamWaitEvent(cap, ctx->fork_join[i], 0);
+        }
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      ctx->stream = st;
+      if (e == cudaSuccess && e2 == cudaSuccess && g) {
+        e = cudaGraphInstantiate(&ctx->mexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+          ctx->mkey = key;
+          ctx->mrtol = rtol;
+          ctx->mkernels = ctx->log.launches - l0;
+          exec = ctx->mexec;
+        } else {
+          ctx->mexec = nullptr;
+        }
+      }
+      ctx->log.launches = l0;
+      cudaGetLastError();
+    }
+  }
+  for (int tau = 0; nact > 0 && tau < max_cycles; ++tau) {
+    if (exec) {
+      CK(cudaGraphLaunch(exec, st));
+      ctx->log.launches += ctx->mkernels;
+    } else {
+      for (auto& it : items) {
+        if (*it.h->w.h_nactive == 0) continue;
+        it.step();
+        it.test();
+      }
+    }
+    CK(cudaStreamSynchronize(st));
+    nact = any_active();
+  }
+  CK(cudaGetLastError());
+  for (auto& it : items) {
+    nmg_status r = it.finish();
+    if (r != NMG_OK) return r;
+  }
+  return NMG_OK;
+}
+
+template <typename T>
+nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int max_cycles,
+                       nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  int nt = 0;
+  ctx->log.active_hint = B;
+  launch_sumsq<T>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, ctx->stream, ctx->log);
+  launch_norms(w.part[0], nt, B, w.fn, w.ones, ctx->stream, ctx->log);
+  T* b0 = reinterpret_cast<T*>(w.t[0]);
+  auto test = [&]() {
+    int ntl = op_residual<T>(h, 0, B, u, f, b0, w.part[0], w.active);
+    launch_norms(w.part[0], ntl, B, w.s[0], w.active, ctx->stream, ctx->log);
+    cudaMemsetAsync(w.nactive, 0, sizeof(int), ctx->stream);
+    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, ctx->stream,
+                    ctx->log);
+    cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  };
+  auto step = [&]() {
+    cycle_body<T>(h, B, f, u, u, b0, w.s[0], w.active);
+    launch_count_cycles(B, w.active, w.cycles, ctx->stream, ctx->log);
+  };
+  return run_outer(h, B, f, u, rtol, max_cycles, info, step, test);
+}
+
 nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rtol,
                         int max_cycles, nmg_solve_info* info) {
   nmg_ctx* ctx = h->ctx;
   Work& w = h->w;
-  cudaStream_t st = ctx->stream;
-  CK(cudaMemcpyAsync(w.active, w.ones, B * sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(w.cycles, 0, B * sizeof(int), st));
-  {
-    std::vector<int> nc(B, NMG_NOT_CONVERGED);
-    CK(cudaMemcpyAsync(w.status, nc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-  }
   int nt = 0;
   ctx->log.active_hint = B;
-  launch_sumsq<float>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, st, ctx->log);
-  launch_norms(w.part[0], nt, B, w.fn, w.ones, st, ctx->log);
-  for (int tau = 0;; ++tau) {
-    launch_refine_residual_dispatch(h, B, u, f, w.r32, w.part[0], &nt, w.active);
-    launch_norms(w.part[0], nt, B, w.s[0], w.active, st, ctx->log);
-    CK(cudaMemsetAsync(w.nactive, 0, sizeof(int), st));
-    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, st, ctx->log);
-    CK(cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    ctx->log.active_hint = *w.h_nactive;
-    if (*w.h_nactive == 0 || tau >= max_cycles) break;
-    // inner bf16 cycle on (0, r): d = NMGF(0, r)
+  launch_sumsq<float>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, ctx->stream, ctx->log);
+  launch_norms(w.part[0], nt, B, w.fn, w.ones, ctx->stream, ctx->log);
+  auto test = [&]() {
+    int ntl = 0;
+    launch_refine_residual_dispatch(h, B, u, f, w.r32, w.part[0], &ntl, w.active);
+    launch_norms(w.part[0], ntl, B, w.s[0], w.active, ctx->stream, ctx->log);
+    cudaMemsetAsync(w.nactive, 0, sizeof(int), ctx->stream);
+    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, ctx->stream,
+                    ctx->log);
+    cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  };
+  auto step = [&]() {
+    // inner bf16 cycle on (0, r): d = NMGF(0, r); u += d in fp64
     cycle_body<float>(h, B, w.r32, w.d32, nullptr, w.r32, w.s[0], w.active);
-    launch_update_f64((long long)plane(h, 0), B, w.d32, u, w.active, st, ctx->log);
-    launch_count_cycles(B, w.active, w.cycles, st, ctx->log);
-  }
-  CK(cudaGetLastError());
-  {
-    int herr = 0;
-    CK(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (herr) {
-      cudaMemsetAsync(w.err, 0, sizeof(int), st);
-      return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its iteration limit");
-    }
+    launch_update_f64((long long)plane(h, 0), B, w.d32, u, w.active, ctx->stream, ctx->log);
+    launch_count_cycles(B, w.active, w.cycles, ctx->stream, ctx->log);
+  };
+  return run_outer(h, B, f, u, rtol, max_cycles, info, step, test);
+}
+
+nmg_status finish_item(nmg_hier* h, int B, nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  cudaStream_t st = ctx->stream;
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) {
+    cudaMemsetAsync(w.err, 0, sizeof(int), st);
+    return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its time limit");
   }
   if (info) {
     std::vector<int> cyc(B), stt(B);
@@ -508,6 +695,68 @@ nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rt
     for (int b = 0; b < B; ++b) info[b] = nmg_solve_info{cyc[b], stt[b], rr[b]};
   }
   return NMG_OK;
+}
+
+// one item of a multi-hierarchy solve: ||f|| now, test/step/finish closures
+OuterItem make_item(nmg_hier* h, int B, const void* f, void* u, double rtol,
+                    nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work* w = &h->w;
+  int nt = 0;
+  OuterItem it;
+  it.h = h;
+  it.B = B;
+  it.finish = [h, B, info]() { return finish_item(h, B, info); };
+  if (h->precision == NMG_FP64 || h->precision == NMG_FP32) {
+    const bool dbl = h->precision == NMG_FP64;
+    if (dbl)
+      launch_sumsq<double>((const double*)f, (long long)plane(h, 0), B, w->part[0], &nt, w->ones, ctx->stream, ctx->log);
+    else
+      launch_sumsq<float>((const float*)f, (long long)plane(h, 0), B, w->part[0], &nt, w->ones, ctx->stream, ctx->log);
+    launch_norms(w->part[0], nt, B, w->fn, w->ones, ctx->stream, ctx->log);
+    it.test = [h, B, f, u, rtol, w, dbl]() {
+      nmg_ctx* c = h->ctx;
+      int ntl = dbl ? op_residual<double>(h, 0, B, (const double*)u, (const double*)f,
+                                          reinterpret_cast<double*>(w->t[0]), w->part[0], w->active)
+                    : op_residual<float>(h, 0, B, (const float*)u, (const float*)f,
+                                         reinterpret_cast<float*>(w->t[0]), w->part[0], w->active);
+      launch_norms(w->part[0], ntl, B, w->s[0], w->active, c->stream, c->log);
+      cudaMemsetAsync(w->nactive, 0, sizeof(int), c->stream);
+      launch_converge(w->s[0], w->fn, rtol, B, w->active, w->relres, w->status, w->nactive,
+                      c->stream, c->log);
+      cudaMemcpyAsync(w->h_nactive, w->nactive, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    };
+    it.step = [h, B, f, u, w, dbl]() {
+      nmg_ctx* c = h->ctx;
+      if (dbl)
+        cycle_body<double>(h, B, (const double*)f, (double*)u, (const double*)u,
+                           reinterpret_cast<const double*>(w->t[0]), w->s[0], w->active);
+      else
+        cycle_body<float>(h, B, (const float*)f, (float*)u, (const float*)u,
+                          reinterpret_cast<const float*>(w->t[0]), w->s[0], w->active);
+      launch_count_cycles(B, w->active, w->cycles, c->stream, c->log);
+    };
+  } else {
+    launch_sumsq<float>((const float*)f, (long long)plane(h, 0), B, w->part[0], &nt, w->ones, ctx->stream, ctx->log);
+    launch_norms(w->part[0], nt, B, w->fn, w->ones, ctx->stream, ctx->log);
+    it.test = [h, B, f, u, rtol, w]() {
+      nmg_ctx* c = h->ctx;
+      int ntl = 0;
+      launch_refine_residual_dispatch(h, B, (const double*)u, (const float*)f, w->r32, w->part[0], &ntl, w->active);
+      launch_norms(w->part[0], ntl, B, w->s[0], w->active, c->stream, c->log);
+      cudaMemsetAsync(w->nactive, 0, sizeof(int), c->stream);
+      launch_converge(w->s[0], w->fn, rtol, B, w->active, w->relres, w->status, w->nactive,
+                      c->stream, c->log);
+      cudaMemcpyAsync(w->h_nactive, w->nactive, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    };
+    it.step = [h, B, u, w]() {
+      nmg_ctx* c = h->ctx;
+      cycle_body<float>(h, B, w->r32, w->d32, nullptr, w->r32, w->s[0], w->active);
+      launch_update_f64((long long)plane(h, 0), B, w->d32, (double*)u, w->active, c->stream, c->log);
+      launch_count_cycles(B, w->active, w->cycles, c->stream, c->log);
+    };
+  }
+  return it;
 }
 
 nmg_status check_common(nmg_ctx* ctx, const nmg_hier* h, int batch) {
@@ -543,10 +792,14 @@ nmg_status nmg_create(nmg_ctx** out, int device, void* stream) {
   if (stream) {
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
   } else {
-    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    // a blocking stream: ordered after work the caller queued on the legacy
+    // default stream (e.g. a framework's default-stream fills of f or u)
+    e = cudaStreamCreate(&ctx->stream);
     if (e != cudaSuccess) return NMG_ERR_CUDA;
     ctx->own_stream = true;
   }
+  e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return NMG_ERR_CUDA;
   *out = ctx.release();
   return NMG_OK;
 }
@@ -559,6 +812,10 @@ void nmg_destroy(nmg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaStreamDestroy(ctx->stream);
   }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->mexec) cudaGraphExecDestroy(ctx->mexec);
+  for (cudaStream_t sd : ctx->side) cudaStreamDestroy(sd);
+  for (cudaEvent_t ev : ctx->fork_join) cudaEventDestroy(ev);
   delete ctx;
 }
 
@@ -724,6 +981,13 @@ void nmg_destroy_hier(nmg_hier* h) {
   if (!h) return;
   cudaSetDevice(h->ctx->device);
   cudaStreamSynchronize(h->ctx->stream);
+  for (const void* k : h->ctx->mkey)
+    if (k == h) {
+      if (h->ctx->mexec) cudaGraphExecDestroy(h->ctx->mexec);
+      h->ctx->mexec = nullptr;
+      h->ctx->mkey.clear();
+      break;
+    }
   for (DevLevel& d : h->lv)
     if (d.bf16_pack) bf16_cnn_forget(d.bf16_pack);
   free_work(h->w);
@@ -748,6 +1012,36 @@ nmg_status nmg_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* 
     default:
       return solve_refine(h, batch, (const float*)f, (double*)u, rtol, max_cycles, info);
   }
+}
+
+nmg_status nmg_solve_multi(nmg_ctx* ctx, int nitems, const nmg_solve_item* items, double rtol,
+                           int max_cycles) {
+  if (!ctx || nitems < 0 || (nitems > 0 && !items)) return fail(ctx, NMG_ERR_ARG, "bad item list");
+  if (!(rtol >= 0.0) || max_cycles < 0) return fail(ctx, NMG_ERR_ARG, "bad rtol or max_cycles");
+  nmg_status s = set_device(ctx);
+  if (s != NMG_OK) return s;
+  std::vector<OuterItem> its;
+  std::vector<const void*> key;
+  for (int i = 0; i < nitems; ++i) {
+    const nmg_solve_item& q = items[i];
+    if ((s = check_common(ctx, q.hier, q.batch)) != NMG_OK) return s;
+    for (int j = 0; j < i; ++j)
+      if (items[j].hier == q.hier) return fail(ctx, NMG_ERR_ARG, "a hierarchy appears twice");
+    if (q.batch == 0) continue;
+    if (!q.f || !q.u) return fail(ctx, NMG_ERR_ARG, "null f or u");
+    if ((s = ensure_work(q.hier, q.batch)) != NMG_OK) return s;
+  }
+  for (int i = 0; i < nitems; ++i) {
+    const nmg_solve_item& q = items[i];
+    if (q.batch == 0) continue;
+    its.push_back(make_item(q.hier, q.batch, q.f, q.u, rtol, q.info));
+    key.push_back(q.hier);
+    key.push_back(reinterpret_cast<const void*>((size_t)q.batch));
+    key.push_back(q.f);
+    key.push_back(q.u);
+  }
+  if (its.empty()) return NMG_OK;
+  return run_outer_multi(ctx, its, key, rtol, max_cycles);
 }
 
 nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host, void* u_host,
@@ -952,6 +1246,12 @@ nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double*
 
 long long nmg_launch_count(const nmg_ctx* ctx) { return ctx ? ctx->log.launches : 0; }
 
+nmg_status nmg_set_graphs(nmg_ctx* ctx, int enable) {
+  if (!ctx) return NMG_ERR_ARG;
+  ctx->graphs = enable != 0;
+  return NMG_OK;
+}
+
 nmg_status nmg_profile_enable(nmg_ctx* ctx, int enable) {
   if (!ctx) return NMG_ERR_ARG;
   if (enable) {
@@ -996,6 +1296,364 @@ const char* nmg_status_str(nmg_status s) {
 }
 
 const char* nmg_last_error(const nmg_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Serving loop: continuous batching over resident hierarchies
+// ===========================================================================
+//
+// Every operator added to a server keeps its hierarchy, Cholesky factor and
+// smoother weights resident and owns a pool of `slots` right-hand-side
+// positions (its workspace is sized for the pool).  Requests are queued on
+// the host; a scheduler step (nmg_server_step)
+//   1. admits queued requests in arrival order into free slots of their
+//      operator (copies f in, zeroes u, computes ||f|| and the first
+//      residual test for the new slots only, then joins them to the active
+//      set) -- admission is bounded by the slots, whose memory was checked
+//      against the server's byte budget when the operator was added;
+//   2. runs one outer iteration (one cycle + convergence test) for every
+//      live request of every operator: one captured graph per operator;
+//   3. retires requests that converged, diverged or used their cycles
+//      (copies u out) and frees their slots.
+// Requests that arrive while others are running join at the next step, and
+// every slot is computed independently of the others, so a request's result
+// does not depend on what else is in flight.
+#include <chrono>
+#include <deque>
+#include <map>
+
+struct SrvReq {
+  int op = 0;
+  std::vector<unsigned char> f;  // host copy of the right-hand side
+  void* u_out = nullptr;         // caller's host buffer for the solution
+  int slot = -1;
+  int state = 0;                 // 0 queued, 1 running, 2 done
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  nmg_solve_info info{0, NMG_NOT_CONVERGED, 0.0};
+};
+
+struct SrvOp {
+  nmg_hier* h = nullptr;
+  int cap = 0;
+  void* f = nullptr;  // device slot buffers
+  void* u = nullptr;
+  int* d_new = nullptr;
+  int* h_new = nullptr;  // pinned
+  int* h_status = nullptr;
+  int* h_cycles = nullptr;
+  double* h_relres = nullptr;
+  int* h_zero = nullptr;
+  std::vector<long long> slot;  // request id per slot, -1 if free
+  int live = 0;
+  size_t fes = 4, ues = 4, pl = 0, bytes = 0;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
+struct nmg_server {
+  nmg_ctx* ctx = nullptr;
+  size_t budget = 0, used = 0;
+  double rtol = 1e-6;
+  int max_cycles = 100;
+  std::vector<SrvOp> ops;
+  std::deque<long long> queue;
+  std::map<long long, SrvReq> reqs;
+  long long next_id = 1;
+  std::chrono::steady_clock::time_point t0;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+// residual test of the slots flagged in `act` (level-1 residual, norms,
+// convergence flags) for a serving pool
+void srv_test(SrvOp& o, double rtol, int* act) {
+  nmg_hier* h = o.h;
+  nmg_ctx* c = h->ctx;
+  Work& w = h->w;
+  int nt = 0;
+  if (h->precision == NMG_FP64)
+    nt = op_residual<double>(h, 0, o.cap, (const double*)o.u, (const double*)o.f,
+                             reinterpret_cast<double*>(w.t[0]), w.part[0], act);
+  else if (h->precision == NMG_FP32)
+    nt = op_residual<float>(h, 0, o.cap, (const float*)o.u, (const float*)o.f,
+                            reinterpret_cast<float*>(w.t[0]), w.part[0], act);
+  else
+    launch_refine_residual_dispatch(h, o.cap, (const double*)o.u, (const float*)o.f, w.r32,
+                                    w.part[0], &nt, act);
+  launch_norms(w.part[0], nt, o.cap, w.s[0], act, c->stream, c->log);
+  launch_converge(w.s[0], w.fn, rtol, o.cap, act, w.relres, w.status, w.nactive, c->stream, c->log);
+}
+
+void srv_step(SrvOp& o) {
+  nmg_hier* h = o.h;
+  nmg_ctx* c = h->ctx;
+  Work& w = h->w;
+  if (h->precision == NMG_FP64)
+    cycle_body<double>(h, o.cap, (const double*)o.f, (double*)o.u, (const double*)o.u,
+                       reinterpret_cast<const double*>(w.t[0]), w.s[0], w.active);
+  else if (h->precision == NMG_FP32)
+    cycle_body<float>(h, o.cap, (const float*)o.f, (float*)o.u, (const float*)o.u,
+                      reinterpret_cast<const float*>(w.t[0]), w.s[0], w.active);
+  else {
+    cycle_body<float>(h, o.cap, w.r32, w.d32, nullptr, w.r32, w.s[0], w.active);
+    launch_update_f64((long long)o.pl, o.cap, w.d32, (double*)o.u, w.active, c->stream, c->log);
+  }
+  launch_count_cycles(o.cap, w.active, w.cycles, c->stream, c->log);
+}
+
+void free_op(SrvOp& o) {
+  if (o.exec) cudaGraphExecDestroy(o.exec);
+  if (o.f) cudaFree(o.f);
+  if (o.u) cudaFree(o.u);
+  if (o.d_new) cudaFree(o.d_new);
+  if (o.h_new) cudaFreeHost(o.h_new);
+  if (o.h_status) cudaFreeHost(o.h_status);
+  if (o.h_cycles) cudaFreeHost(o.h_cycles);
+  if (o.h_relres) cudaFreeHost(o.h_relres);
+  if (o.h_zero) cudaFreeHost(o.h_zero);
+}
+
+}  // namespace
+
+extern "C" {
+
+nmg_status nmg_server_create(nmg_ctx* ctx, size_t budget_bytes, double rtol, int max_cycles,
+                             nmg_server** out) {
+  if (!ctx || !out || !(rtol >= 0.0) || max_cycles < 1) return fail(ctx, NMG_ERR_ARG, "bad server arguments");
+  nmg_server* s = new nmg_server();
+  s->ctx = ctx;
+  s->budget = budget_bytes;
+  s->rtol = rtol;
+  s->max_cycles = max_cycles;
+  s->t0 = std::chrono::steady_clock::now();
+  *out = s;
+  return NMG_OK;
+}
+
+void nmg_server_destroy(nmg_server* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->ctx->stream);
+  for (SrvOp& o : s->ops) free_op(o);
+  delete s;
+}
+
+nmg_status nmg_server_add_operator(nmg_server* s, nmg_hier* h, int slots, int* op_id) {
+  if (!s || !h || slots < 1 || !op_id) return fail(s ? s->ctx : nullptr, NMG_ERR_ARG, "bad operator");
+  nmg_ctx* ctx = s->ctx;
+  if (h->ctx != ctx) return fail(ctx, NMG_ERR_ARG, "hierarchy belongs to another context");
+  for (const SrvOp& o : s->ops)
+    if (o.h == h) return fail(ctx, NMG_ERR_ARG, "operator already added");
+  nmg_status st = set_device(ctx);
+  if (st != NMG_OK) return st;
+  SrvOp o;
+  o.h = h;
+  o.cap = slots;
+  o.pl = plane(h, 0);
+  o.fes = h->precision == NMG_FP64 ? 8 : 4;
+  o.ues = h->precision == NMG_FP32 ? 4 : 8;
+  const size_t before = h->w.bytes;
+  if ((st = ensure_work(h, slots)) != NMG_OK) return st;
+  o.bytes = (h->w.bytes > before ? h->w.bytes - before : 0) + o.pl * slots * (o.fes + o.ues);
+  if (s->used + o.bytes > s->budget)
+    return fail(ctx, NMG_ERR_OOM, "operator's slot pool exceeds the server's memory budget");
+  CK(cudaMalloc(&o.f, o.pl * slots * o.fes));
+  CK(cudaMalloc(&o.u, o.pl * slots * o.ues));
+  CK(cudaMalloc(&o.d_new, slots * sizeof(int)));
+  CK(cudaMallocHost(&o.h_new, slots * sizeof(int)));
+  CK(cudaMallocHost(&o.h_status, slots * sizeof(int)));
+  CK(cudaMallocHost(&o.h_cycles, slots * sizeof(int)));
+  CK(cudaMallocHost(&o.h_relres, slots * sizeof(double)));
+  CK(cudaMallocHost(&o.h_zero, sizeof(int)));
+  *o.h_zero = 0;
+  std::memset(o.h_new, 0, slots * sizeof(int));
+  CK(cudaMemsetAsync(h->w.active, 0, slots * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(h->w.cycles, 0, slots * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(o.f, 0, o.pl * slots * o.fes, ctx->stream));
+  CK(cudaMemsetAsync(o.u, 0, o.pl * slots * o.ues, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  o.slot.assign(slots, -1);
+  s->used += o.bytes;
+  *op_id = (int)s->ops.size();
+  s->ops.push_back(o);
+  return NMG_OK;
+}
+
+nmg_status nmg_server_submit(nmg_server* s, int op_id, const void* f_host, void* u_host,
+                             long long* req_id) {
+  if (!s || op_id < 0 || op_id >= (int)s->ops.size() || !f_host || !u_host || !req_id)
+    return fail(s ? s->ctx : nullptr, NMG_ERR_ARG, "bad request");
+  const SrvOp& o = s->ops[op_id];
+  SrvReq r;
+  r.op = op_id;
+  r.f.assign((const unsigned char*)f_host, (const unsigned char*)f_host + o.pl * o.fes);
+  r.u_out = u_host;
+  r.t_submit = s->now();
+  const long long id = s->next_id++;
+  s->reqs.emplace(id, std::move(r));
+  s->queue.push_back(id);
+  *req_id = id;
+  return NMG_OK;
+}
+
+nmg_status nmg_server_step(nmg_server* s, int* completed) {
+  if (!s) return NMG_ERR_ARG;
+  nmg_ctx* ctx = s->ctx;
+  cudaStream_t st = ctx->stream;
+  nmg_status rs = set_device(ctx);
+  if (rs != NMG_OK) return rs;
+  int done = 0;
+  // ---- 1. admission in arrival order into free slots
+  std::vector<int> admitted(s->ops.size(), 0);
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    SrvReq& r = s->reqs[*it];
+    SrvOp& o = s->ops[r.op];
+    int slot = -1;
+    if (o.live < o.cap)
+      for (int j = 0; j < o.cap; ++j)
+        if (o.slot[j] < 0) {
+          slot = j;
+          break;
+        }
+    if (slot < 0) {
+      ++it;
+      continue;
+    }
+    o.slot[slot] = *it;
+    ++o.live;
+    r.slot = slot;
+    r.state = 1;
+    r.t_admit = s->now();
+    CK(cudaMemcpyAsync((unsigned char*)o.f + slot * o.pl * o.fes, r.f.data(), o.pl * o.fes,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync((unsigned char*)o.u + slot * o.pl * o.ues, 0, o.pl * o.ues, st));
+    CK(cudaMemsetAsync(o.h->w.cycles + slot, 0, sizeof(int), st));
+    const int nc = NMG_NOT_CONVERGED;
+    CK(cudaMemcpyAsync(o.h->w.status + slot, &nc, sizeof(int), cudaMemcpyHostToDevice, st));
+    o.h_new[slot] = 1;
+    ++admitted[r.op];
+    it = s->queue.erase(it);
+  }
+  for (size_t k = 0; k < s->ops.size(); ++k) {
+    if (!admitted[k]) continue;
+    SrvOp& o = s->ops[k];
+    Work& w = o.h->w;
+    CK(cudaMemcpyAsync(o.d_new, o.h_new, o.cap * sizeof(int), cudaMemcpyHostToDevice, st));
+    int nt = 0;
+    ctx->log.active_hint = admitted[k];
+    if (o.h->precision == NMG_FP64)
+      launch_sumsq<double>((const double*)o.f, (long long)o.pl, o.cap, w.part[0], &nt, o.d_new, st, ctx->log);
+    else
+      launch_sumsq<float>((const float*)o.f, (long long)o.pl, o.cap, w.part[0], &nt, o.d_new, st, ctx->log);
+    launch_norms(w.part[0], nt, o.cap, w.fn, o.d_new, st, ctx->log);
+    srv_test(o, s->rtol, o.d_new);  // first test of the new slots only
+    launch_admit(o.cap, o.d_new, w.active, st, ctx->log);
+    CK(cudaStreamSynchronize(st));  // h_new is reused below
+    std::memset(o.h_new, 0, o.cap * sizeof(int));
+  }
+  // ---- 2. one outer iteration for every live request (one graph per operator)
+  for (SrvOp& o : s->ops) {
+    if (o.live == 0) continue;
+    ctx->log.active_hint = o.live;
+    if (ctx->graphs && !ctx->log.prof && !o.exec) {
+      const long long l0 = ctx->log.launches;
+      ctx->stream = ctx->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        srv_step(o);
+        srv_test(o, s->rtol, o.h->w.active);
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+      ctx->stream = st;
+      if (e == cudaSuccess && e2 == cudaSuccess && g) {
+        if (cudaGraphInstantiate(&o.exec, g, 0) != cudaSuccess) o.exec = nullptr;
+        cudaGraphDestroy(g);
+        o.kernels = ctx->log.launches - l0;
+      }
+      ctx->log.launches = l0;
+      cudaGetLastError();
+    }
+    if (o.exec && ctx->graphs && !ctx->log.prof) {
+      CK(cudaGraphLaunch(o.exec, st));
+      ctx->log.launches += o.kernels;
+    } else {
+      srv_step(o);
+      srv_test(o, s->rtol, o.h->w.active);
+    }
+  }
+  // ---- 3. retire finished requests
+  for (SrvOp& o : s->ops) {
+    if (o.live == 0) continue;
+    Work& w = o.h->w;
+    CK(cudaMemcpyAsync(o.h_status, w.status, o.cap * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(o.h_cycles, w.cycles, o.cap * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(o.h_relres, w.relres, o.cap * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  {
+    int herr = 0;
+    for (SrvOp& o : s->ops) {
+      if (o.live == 0) continue;
+      CK(cudaMemcpy(&herr, o.h->w.err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (herr) {
+        cudaMemset(o.h->w.err, 0, sizeof(int));
+        return fail(ctx, NMG_ERR_TIMEOUT, "a tensor-core wait exceeded its time limit");
+      }
+    }
+  }
+  for (SrvOp& o : s->ops) {
+    if (o.live == 0) continue;
+    for (int j = 0; j < o.cap; ++j) {
+      if (o.slot[j] < 0) continue;
+      const bool finished = o.h_status[j] != NMG_NOT_CONVERGED || o.h_cycles[j] >= s->max_cycles;
+      if (!finished) continue;
+      SrvReq& r = s->reqs[o.slot[j]];
+      if (o.h_status[j] == NMG_NOT_CONVERGED)  // out of cycles: leave the active set
+        CK(cudaMemcpyAsync(o.h->w.active + j, o.h_zero, sizeof(int), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(r.u_out, (unsigned char*)o.u + j * o.pl * o.ues, o.pl * o.ues,
+                         cudaMemcpyDeviceToHost, st));
+      r.info = nmg_solve_info{o.h_cycles[j], o.h_status[j], o.h_relres[j]};
+      r.state = 2;
+      o.slot[j] = -1;
+      --o.live;
+      ++done;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  const double t = s->now();
+  for (auto& kv : s->reqs)
+    if (kv.second.state == 2 && kv.second.t_done == 0.0) kv.second.t_done = t;
+  if (completed) *completed = done;
+  return NMG_OK;
+}
+
+nmg_status nmg_server_query(nmg_server* s, long long req_id, nmg_solve_info* info, int* state,
+                            double* t_submit, double* t_admit, double* t_done) {
+  if (!s) return NMG_ERR_ARG;
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end()) return fail(s->ctx, NMG_ERR_ARG, "unknown request");
+  const SrvReq& r = it->second;
+  if (info) *info = r.info;
+  if (state) *state = r.state;
+  if (t_submit) *t_submit = r.t_submit;
+  if (t_admit) *t_admit = r.t_admit;
+  if (t_done) *t_done = r.t_done;
+  return NMG_OK;
+}
+
+nmg_status nmg_server_stats(const nmg_server* s, int* queued, int* running, size_t* bytes_used) {
+  if (!s) return NMG_ERR_ARG;
+  int run = 0;
+  for (const SrvOp& o : s->ops) run += o.live;
+  if (queued) *queued = (int)s->queue.size();
+  if (running) *running = run;
+  if (bytes_used) *bytes_used = s->used;
+  return NMG_OK;
+}
 
 }  // extern "C"
 

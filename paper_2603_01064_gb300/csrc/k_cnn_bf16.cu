@@ -70,6 +70,8 @@ struct LayerPack {
   const float* wf;
   const float* bias;
   int has_lo;
+  float bias0;          // host copy of the output layer's bias
+  int bias_host_valid;
 };
 struct Bf16Pack {
   int layers;
@@ -185,6 +187,32 @@ __device__ __forceinline__ void store_channels(__nv_bfloat16* dst_px, const floa
   }
 }
 
+// Warp-collective store of 32 pixels' channels: every lane converts its
+// pixel into the warp's shared staging area (144-byte pitch: conflict-free
+// 16-byte accesses), then the warp writes 16-byte pieces so that each store
+// instruction covers consecutive bytes of consecutive pixels.  dst: this
+// lane's pixel in global memory, or nullptr if the pixel is not stored.
+constexpr int STG_PITCH = 144;
+constexpr int STG_WARP = 32 * STG_PITCH;
+template <int SPLIT>
+__device__ __forceinline__ void warp_store_pixels(unsigned char* stg, int lane, const float* a,
+                                                  __nv_bfloat16* dst) {
+  constexpr int Q = SPLIT ? 8 : 4;  // 16-byte pieces per pixel
+  if (dst) store_channels<SPLIT>(reinterpret_cast<__nv_bfloat16*>(stg + lane * STG_PITCH), a);
+  __syncwarp();
+  const unsigned long long mine = reinterpret_cast<unsigned long long>(dst);
+#pragma unroll
+  for (int it = 0; it < Q; ++it) {
+    const int chunk = it * 32 + lane, px = chunk / Q, part = chunk % Q;
+    const unsigned long long d = __shfl_sync(0xffffffffu, mine, px);
+    if (d) {
+      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(d) + part * 16) =
+          *reinterpret_cast<const uint4*>(stg + px * STG_PITCH + part * 16);
+    }
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // first layer 1 -> 32 (fp32 SIMT): a = ReLU(b1 + W1 * (b / s)), stored bf16
 // ---------------------------------------------------------------------------
@@ -216,7 +244,7 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   __syncthreads();
   const int ry = tid / TILE, rx = tid % TILE;
   const int y = y0 + ry, x = x0 + rx;
-  if (y >= n || x >= n) return;
+  const bool in = y < n && x < n;
   float v[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) v[t] = xs[ry + t / 3][rx + t % 3];
@@ -228,7 +256,9 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
     for (int t = 0; t < 9; ++t) acc = fmaf(ws[c * 9 + t], v[t], acc);
     a[c] = fmaxf(acc, 0.f);
   }
-  store_channels<SPLIT>(aout + ((size_t)b * plane + (size_t)y * n + x) * CW, a);
+  extern __shared__ __align__(16) unsigned char stg_first[];
+  warp_store_pixels<SPLIT>(stg_first + (tid >> 5) * STG_WARP, tid & 31, a,
+                           in ? aout + ((size_t)b * plane + (size_t)y * n + x) * CW : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -320,11 +350,16 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
   }
 }
 
-// bias, ReLU and store of one pixel from 32 (fast) or 64 (split: hi + lo
-// weight halves) accumulator columns
-template <int SPLIT>
+// Epilogue of one pixel from 32 (fast) or 64 (split: hi + lo weight halves)
+// accumulator columns: bias, ReLU, then either the bf16 activation store
+// (FUSE = 0) or, for the last hidden layer (FUSE = 1), the contraction with
+// the 32 -> 1 output layer's weights w4[c][tap] into 9 per-tap partial sums
+// written as fp32 planes g[tap][pixel] (plane stride gstride).
+template <int SPLIT, int FUSE>
 __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bias,
-                                             __nv_bfloat16* dst, bool store) {
+                                             __nv_bfloat16* dst, float* gdst, size_t gstride,
+                                             const float* __restrict__ w4, bool store,
+                                             unsigned char* stg, int lane) {
   float v[32];
   tmem_ld32(taddr, v);
   if (SPLIT) {
@@ -333,20 +368,40 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
 #pragma unroll
     for (int c = 0; c < 32; ++c) v[c] += w[c];
   }
-  if (store) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias[c], 0.f);
-    store_channels<SPLIT>(dst, v);
+  for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias[c], 0.f);
+  if (!FUSE) {
+    warp_store_pixels<SPLIT>(stg, lane, v, store ? dst : nullptr);  // warp-collective
+    return;
+  }
+  if (!store) return;
+  {
+    // w4 is staged in shared memory as [tap][32 channels]
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const float4* wt = reinterpret_cast<const float4*>(w4 + t * 32);
+      float g = 0.f;
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 w = wt[c4];
+        g = fmaf(w.x, v[4 * c4], g);
+        g = fmaf(w.y, v[4 * c4 + 1], g);
+        g = fmaf(w.z, v[4 * c4 + 2], g);
+        g = fmaf(w.w, v[4 * c4 + 3], g);
+      }
+      gdst[t * gstride] = g;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // hidden layer 32 -> 32 on the tensor cores (pipelined, persistent)
 // ---------------------------------------------------------------------------
-template <int SPLIT>
+template <int SPLIT, int FUSE>
 __global__ void __launch_bounds__(THREADS)
 k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
-            __nv_bfloat16* __restrict__ aout, LayerPack lp, const double* __restrict__ snorm,
+            __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
+            const float* __restrict__ w4, const double* __restrict__ snorm,
             const int* __restrict__ active, int* __restrict__ err) {
   constexpr int ACH = SPLIT ? 8 : 4;  // 8-channel chunks per staged pixel
   constexpr int ABUF = ACH * CH_BYTES;
@@ -360,11 +415,14 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
+  __shared__ __align__(16) float w4s[FUSE ? 9 * 32 : 4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
     for (int i = tid; i < B_BYTES / 16; i += THREADS) dst[i] = src[i];
+    if (FUSE)
+      for (int i = tid; i < 9 * 32; i += THREADS) w4s[i] = w4[(i % 32) * 9 + i / 32];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -426,9 +484,11 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       const int m = warp * 32 + lane;
       const int y = y0 + (m >> 3), x = x0 + mt * 8 + (m & 7);
       const bool in = y < n && x < n;
-      finish_pixel<SPLIT>(tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value,
-                          lp.bias, in ? aout + ((size_t)b * plane + (size_t)y * n + x) * CW : aout,
-                          in);
+      const size_t pix = (size_t)b * plane + (size_t)y * n + x;
+      finish_pixel<SPLIT, FUSE>(
+          tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, lp.bias,
+          in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
+          Bs + B_BYTES + warp * STG_WARP, lane);
     }
   };
 
@@ -506,10 +566,11 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-template <int SPLIT, int STAGES>
+template <int SPLIT, int STAGES, int FUSE>
 __global__ void __launch_bounds__(WS_THREADS)
 k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
-            __nv_bfloat16* __restrict__ aout, LayerPack lp, const double* __restrict__ snorm,
+            __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
+            const float* __restrict__ w4, const double* __restrict__ snorm,
             const int* __restrict__ active, int* __restrict__ err) {
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int SBYTES = ACH * CH_PITCH;           // one stage
@@ -526,11 +587,14 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
+  __shared__ __align__(16) float w4s[FUSE ? 9 * 32 : 4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
     for (int i = tid; i < B_BYTES / 16; i += WS_THREADS) dst[i] = src[i];
+    if (FUSE)
+      for (int i = tid; i < 9 * 32; i += WS_THREADS) w4s[i] = w4[(i % 32) * 9 + i / 32];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -632,9 +696,11 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
       for (int mt = 0; mt < NT; ++mt) {
         const int x = x0 + mt * 8 + (m & 7);
         const bool in = y < n && x < n;
-        finish_pixel<SPLIT>(tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value,
-                            lp.bias, in ? aout + ((size_t)b * plane + (size_t)y * n + x) * CW : aout,
-                            in);
+        const size_t pix = (size_t)b * plane + (size_t)y * n + x;
+        finish_pixel<SPLIT, FUSE>(
+            tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value, lp.bias,
+            in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
+            Bs + B_BYTES + (warp - 2) * STG_WARP, lane);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -694,6 +760,32 @@ const CUtensorMap* act_map(const void* ptr, int n, int nimg, int cw) {
   return &map_cache().back().map;
 }
 
+// last layer from the fused partial sums: h[p] = s (b4 + sum_tap g[tap][p + off(tap)])
+// with zero padding outside the image
+__global__ void __launch_bounds__(256)
+k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ hout,
+              float bias0, const double* __restrict__ snorm, const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const double s = snorm[b];
+  const size_t plane = (size_t)n * n, gstride = (size_t)nimg * plane;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)plane; p += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    if (s != 0.0) {
+      const int y = p / n, x = p % n;
+      acc = bias0;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        if (yy >= 0 && yy < n && xx >= 0 && xx < n)
+          acc += g[t * gstride + (size_t)b * plane + (size_t)yy * n + xx];
+      }
+      acc *= (float)s;
+    }
+    hout[(size_t)b * plane + p] = acc;
+  }
+}
+
 // host bf16 round-to-nearest-even of a finite float
 uint16_t bf16_bits(float f) {
   uint32_t u;
@@ -713,39 +805,39 @@ int num_sms() {
   return g_num_sms;
 }
 
-template <int SPLIT>
+template <int SPLIT, int FUSE>
 void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv_bfloat16* aout,
-                   const LayerPack& lp, const double* s, const int* active, int* err,
-                   cudaStream_t st, LaunchLog& log) {
+                   float* gout, const LayerPack& lp, const float* w4, const double* s,
+                   const int* active, int* err, cudaStream_t st, LaunchLog& log) {
   constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
   const CUtensorMap* map = n >= 32 ? act_map(ain, n, map_imgs, CWs) : nullptr;
   if (map) {
-    constexpr int STAGES = SPLIT ? 3 : 4;
+    constexpr int STAGES = 3;
     constexpr int ACHs = SPLIT ? 8 : 4;
     constexpr int B_BYTESs = SPLIT ? 2 * B_HALF : B_HALF;
-    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + 1024;
+    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + 4 * STG_WARP + 1024;
     const int tiles_x = (n + TILE - 1) / TILE;
     long long total = (long long)nimg * tiles_x * tiles_x;
     long long grid = (long long)num_sms() * (SPLIT ? 1 : 2);
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
-    cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int pi_ = log.begin(K_CNN_HIDDEN, st);
-    k_hidden_ws<SPLIT, STAGES><<<(int)grid, WS_THREADS, sm, st>>>(*map, n, nimg, aout, lp, s, active, err);
+    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WS_THREADS, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, s, active, err);
     log.end(pi_, st, (double)n * n * log.active_hint);
     return;
   }
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
-  const size_t sm = 2 * ACH * CH_BYTES + B_BYTES;
+  const size_t sm = 2 * ACH * CH_BYTES + B_BYTES + 4 * STG_WARP;
   const int tiles_x = (n + TILE - 1) / TILE;
   long long total = (long long)nimg * tiles_x * tiles_x;
   long long grid = (long long)num_sms() * (SPLIT ? 1 : 3);
   if (grid > total) grid = total;
   if (grid < 1) grid = 1;
-  cudaFuncSetAttribute(k_hidden_tc<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_hidden_tc<SPLIT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int pi_ = log.begin(K_CNN_HIDDEN, st);
-  k_hidden_tc<SPLIT><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, lp, s, active, err);
+  k_hidden_tc<SPLIT, FUSE><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, gout, lp, w4, s, active, err);
   log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
@@ -757,21 +849,31 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   dim3 grid(tiles_x * tiles_x, B);
   const double units = (double)n * n * log.active_hint;
   int pi_ = log.begin(K_CNN_FIRST, st);
-  k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.l[0], s, active, tiles_x);
+  const size_t smf = 8 * STG_WARP;
+  cudaFuncSetAttribute(k_first_simt<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+  k_first_simt<SPLIT><<<grid, 256, smf, st>>>(n, b, a0, P.l[0], s, active, tiles_x);
   log.end(pi_, st, units);
   __nv_bfloat16* cur = a0;
   __nv_bfloat16* nxt = a1;
+  // hidden layers; the last one also applies the 32 -> 1 output layer's
+  // weights in its epilogue and writes 9 per-tap partial-sum planes
+  const LayerPack& L4 = P.l[layers - 1];
   for (int li = 1; li < layers - 1; ++li) {
-    launch_hidden<SPLIT>(n, B, map_imgs, cur, nxt, P.l[li], s, active, err, st, log);
-    __nv_bfloat16* t = cur;
-    cur = nxt;
-    nxt = t;
+    if (li < layers - 2) {
+      launch_hidden<SPLIT, 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[li], nullptr, s, active, err, st, log);
+      __nv_bfloat16* t = cur;
+      cur = nxt;
+      nxt = t;
+    } else {
+      launch_hidden<SPLIT, 1>(n, B, map_imgs, cur, nxt, reinterpret_cast<float*>(nxt), P.l[li],
+                              L4.wf, s, active, err, st, log);
+    }
   }
-  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
-  const size_t sm = WIDTH * 9 * sizeof(float) + (size_t)RH * RW * (CW * 2 + 16);
-  cudaFuncSetAttribute(k_last_simt<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  float bias0 = 0.f;
+  if (L4.bias_host_valid) bias0 = L4.bias0;
   pi_ = log.begin(K_CNN_LAST, st);
-  k_last_simt<SPLIT><<<grid, 256, sm, st>>>(n, cur, h, P.l[layers - 1], s, active, tiles_x);
+  k_last_gather<<<dim3(ceil_div(n * n, 256) < 64 ? ceil_div(n * n, 256) : 64, B), 256, 0, st>>>(
+      n, map_imgs, reinterpret_cast<const float*>(nxt), h, bias0, s, active);
   log.end(pi_, st, units);
 }
 
@@ -848,6 +950,8 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
     hdr.l[li].wf = simt ? reinterpret_cast<const float*>(dptr + woff[li]) : nullptr;
     hdr.l[li].bias = reinterpret_cast<const float*>(dptr + boff[li]);
     hdr.l[li].has_lo = split ? has_lo[li] : 0;
+    hdr.l[li].bias0 = (float)bias[li][0];
+    hdr.l[li].bias_host_valid = 1;
   }
   if (cudaMemcpy(dptr, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(dptr);

@@ -154,6 +154,87 @@ __global__ void k_fft_rows_inv(int n, int logn, int rpc, const Cx<T>* __restrict
   }
 }
 
+// Whole filter of one right-hand side in shared memory (levels whose complex
+// n x n image fits): row FFTs, column FFTs, mask, inverse column FFTs,
+// inverse row FFTs, update.  One launch, h read once and x written once.
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_filter_fused(int n, int logn, const T* xstar, const T* __restrict__ h, T* x,
+               const Cx<T>* __restrict__ twg, const double* __restrict__ mtab,
+               const int* __restrict__ active) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<T>* tw = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* buf = tw + n / 2;
+  const int nn = n * n, halfn = n / 2;
+  for (int k = threadIdx.x; k < halfn; k += blockDim.x) tw[k] = twg[k];
+  const size_t base = (size_t)b * nn;
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int r = idx / n, c = idx % n;
+    buf[r * n + bitrev(c, logn)] = Cx<T>{h[base + idx], T(0)};
+  }
+  __syncthreads();
+  fft_stages(buf, n, logn, n, tw, +1);  // rows
+  // rows into bit-reversed order for the column transform
+  auto permute_rows = [&]() {
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int r = idx / n, c = idx % n, rr = bitrev(r, logn);
+      if (r < rr) {
+        Cx<T> t = buf[r * n + c];
+        buf[r * n + c] = buf[rr * n + c];
+        buf[rr * n + c] = t;
+      }
+    }
+    __syncthreads();
+  };
+  auto col_stages = [&](int sign) {
+    for (int st = 1; st <= logn; ++st) {
+      const int half = 1 << (st - 1), tstride = n >> st;
+      for (int t = threadIdx.x; t < halfn * n; t += blockDim.x) {
+        const int c = t % n, k = t / n;
+        const int grp = k / half, pos = k % half;
+        const int i = (grp * 2 * half + pos) * n + c, j = i + half * n;
+        Cx<T> w = tw[pos * tstride];
+        if (sign < 0) w.y = -w.y;
+        const Cx<T> a = buf[i], bb = buf[j];
+        const Cx<T> p{w.x * bb.x - w.y * bb.y, w.x * bb.y + w.y * bb.x};
+        buf[i] = Cx<T>{a.x + p.x, a.y + p.y};
+        buf[j] = Cx<T>{a.x - p.x, a.y - p.y};
+      }
+      __syncthreads();
+    }
+  };
+  permute_rows();
+  col_stages(+1);
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int k1 = idx / n, k2 = idx % n;
+    const int f1 = k1 < n - k1 ? k1 : n - k1, f2 = k2 < n - k2 ? k2 : n - k2;
+    const T m = (T)mtab[f1 > f2 ? f1 : f2];
+    buf[idx].x *= m;
+    buf[idx].y *= m;
+  }
+  __syncthreads();
+  permute_rows();
+  col_stages(-1);
+  // columns of every row into bit-reversed order for the inverse row transform
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int r = idx / n, c = idx % n, rc = bitrev(c, logn);
+    if (c < rc) {
+      Cx<T> t = buf[r * n + c];
+      buf[r * n + c] = buf[r * n + rc];
+      buf[r * n + rc] = t;
+    }
+  }
+  __syncthreads();
+  fft_stages(buf, n, logn, n, tw, -1);
+  const T scale = T(1.0 / ((double)n * (double)n));
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const T bv = xstar ? xstar[base + idx] : T(0);
+    x[base + idx] = bv + buf[idx].x * scale;
+  }
+}
+
 // 1D: x[b][i] = x*[b][i] + sum_k c[(i - k) mod n] h[b][k]; one warp per output
 template <typename T>
 __global__ void k_filter1d(int n, const T* xs, const T* __restrict__ h, T* x, const double* __restrict__ circ,
@@ -192,6 +273,15 @@ void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
   while (n % per) --per;
   Cx<T>* C = reinterpret_cast<Cx<T>*>(cbuf);
   const Cx<T>* tw = reinterpret_cast<const Cx<T>*>(twiddles);
+  const size_t fused_sm = (size_t)(n / 2 + n * n) * sizeof(Cx<T>);
+  if (fused_sm <= 160 * 1024) {
+    cudaFuncSetAttribute(k_filter_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_sm);
+    const int threads = n * n / 2 < 512 ? (n * n / 2 < 32 ? 32 : n * n / 2) : 512;
+    int pi_ = log.begin(K_FILTER, st);
+    k_filter_fused<T><<<B, threads, fused_sm, st>>>(n, logn, xstar, h, x, tw, mask_tab, active);
+    log.end(pi_, st, (double)n * n * log.active_hint);
+    return;
+  }
   size_t sm = (size_t)(n / 2 + per * n) * sizeof(Cx<T>);
   cudaFuncSetAttribute(k_fft_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_fft_cols_mask<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

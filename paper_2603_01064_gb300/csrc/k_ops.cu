@@ -64,10 +64,16 @@ k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
     RW = min(tile, n - c0);
   }
   const int XH = RH + 2 * W, XW = RW + 2 * W;
+  const int nk = 2 * wK + 1, nm = 2 * wM + 1;
   T* xs = sm;
   T* tk = xs + XH * XW;
   T* tm = tk + (RH + 2 * wK) * RW;
   T* rs = tm + (RH + 2 * wM) * RW;
+  // banded coefficients of the tile's columns (row pass) and rows (column pass)
+  T* kcol = rs + (RESTRICT ? RH * RW : 0);
+  T* mcol = kcol + RW * nk;
+  T* krow = mcol + RW * nm;
+  T* mrow = krow + RH * nk;
   const size_t plane = (size_t)n * n;
   const T* xb = x + (size_t)b * plane;
   const T* yb = y ? y + (size_t)b * plane : nullptr;
@@ -77,31 +83,41 @@ k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
     int gr = r0 - W + a, gc = c0 - W + c;
     xs[idx] = (gr >= 0 && gr < n && gc >= 0 && gc < n) ? xb[(size_t)gr * n + gc] : T(0);
   }
+  for (int idx = threadIdx.x; idx < RW * nk; idx += blockDim.x) {
+    int j = idx / nk, g = c0 + j;
+    kcol[idx] = (g >= 0 && g < n) ? op.Kd[(size_t)g * nk + idx % nk] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < RW * nm; idx += blockDim.x) {
+    int j = idx / nm, g = c0 + j;
+    mcol[idx] = (g >= 0 && g < n) ? op.Md[(size_t)g * nm + idx % nm] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < RH * nk; idx += blockDim.x) {
+    int i = idx / nk, g = r0 + i;
+    krow[idx] = (g >= 0 && g < n) ? op.Kd[(size_t)g * nk + idx % nk] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < RH * nm; idx += blockDim.x) {
+    int i = idx / nm, g = r0 + i;
+    mrow[idx] = (g >= 0 && g < n) ? op.Md[(size_t)g * nm + idx % nm] : T(0);
+  }
   __syncthreads();
   // row pass: tk[a][j] = sum_d K[gj][gj+d-wK] x[row][gj+d-wK]
+  // (coefficients of out-of-range columns are staged as zero)
   {
-    const int nk = 2 * wK + 1, nm = 2 * wM + 1;
     const int HK = RH + 2 * wK, HM = RH + 2 * wM;
     for (int idx = threadIdx.x; idx < HK * RW; idx += blockDim.x) {
       int a = idx / RW, j = idx % RW;
-      int gj = c0 + j;
+      const T* kr = kcol + j * nk;
+      const T* xr = xs + (a + W - wK) * XW + (j + W - wK);
       T acc = T(0);
-      if (gj >= 0 && gj < n) {
-        const T* kr = op.Kd + (size_t)gj * nk;
-        const T* xr = xs + (a + W - wK) * XW + (j + W - wK);
-        for (int d = 0; d < nk; ++d) acc += kr[d] * xr[d];
-      }
+      for (int d = 0; d < nk; ++d) acc += kr[d] * xr[d];
       tk[idx] = acc;
     }
     for (int idx = threadIdx.x; idx < HM * RW; idx += blockDim.x) {
       int a = idx / RW, j = idx % RW;
-      int gj = c0 + j;
+      const T* mr = mcol + j * nm;
+      const T* xr = xs + (a + W - wM) * XW + (j + W - wM);
       T acc = T(0);
-      if (gj >= 0 && gj < n) {
-        const T* mr = op.Md + (size_t)gj * nm;
-        const T* xr = xs + (a + W - wM) * XW + (j + W - wM);
-        for (int d = 0; d < nm; ++d) acc += mr[d] * xr[d];
-      }
+      for (int d = 0; d < nm; ++d) acc += mr[d] * xr[d];
       tm[idx] = acc;
     }
   }
@@ -109,14 +125,13 @@ k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
   // column pass and residual
   double ss = 0.0;
   {
-    const int nk = 2 * wK + 1, nm = 2 * wM + 1;
     for (int idx = threadIdx.x; idx < RH * RW; idx += blockDim.x) {
       int i = idx / RW, j = idx % RW;
       int gi = r0 + i, gj = c0 + j;
       T r = T(0);
       if (gi >= 0 && gi < n && gj >= 0 && gj < n) {
-        const T* kr = op.Kd + (size_t)gi * nk;
-        const T* mr = op.Md + (size_t)gi * nm;
+        const T* kr = krow + i * nk;
+        const T* mr = mrow + i * nm;
         T zk = T(0), zm = T(0);
         for (int d = 0; d < nk; ++d) zk += kr[d] * tk[(i + d) * RW + j];
         for (int d = 0; d < nm; ++d) zm += mr[d] * tm[(i + d) * RW + j];
@@ -331,6 +346,12 @@ __global__ void k_count_cycles(int B, const int* __restrict__ active, int* __res
   if (b < B && active[b]) cycles[b] += 1;
 }
 
+// slots newly admitted into a serving pool join the active set
+__global__ void k_admit(int B, const int* __restrict__ newmask, int* __restrict__ active) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B && newmask[b]) active[b] = 1;
+}
+
 int grid_for(long long total, int threads) {
   long long g = (total + threads - 1) / threads;
   if (g > 152LL * 16) g = 152LL * 16;
@@ -342,7 +363,8 @@ template <typename T>
 size_t residual_smem(int RH, int RW, int wK, int wM, bool restrict_) {
   int W = wK > wM ? wK : wM;
   size_t e = (size_t)(RH + 2 * W) * (RW + 2 * W) + (size_t)(RH + 2 * wK) * RW +
-             (size_t)(RH + 2 * wM) * RW + (restrict_ ? (size_t)RH * RW : 0);
+             (size_t)(RH + 2 * wM) * RW + (restrict_ ? (size_t)RH * RW : 0) +
+             (size_t)(RW + RH) * (2 * wK + 1 + 2 * wM + 1);
   return e * sizeof(T);
 }
 
@@ -473,6 +495,12 @@ void launch_axpy_update(long long len, int B, const T* xstar, const T* h, T* x,
 void launch_count_cycles(int B, const int* active, int* cycles, cudaStream_t st, LaunchLog& log) {
   int pi_ = log.begin(K_OTHER, st);
   k_count_cycles<<<ceil_div(B, 128), 128, 0, st>>>(B, active, cycles);
+  log.end(pi_, st, 0.0);
+}
+
+void launch_admit(int B, const int* newmask, int* active, cudaStream_t st, LaunchLog& log) {
+  int pi_ = log.begin(K_OTHER, st);
+  k_admit<<<ceil_div(B, 128), 128, 0, st>>>(B, newmask, active);
   log.end(pi_, st, 0.0);
 }
 

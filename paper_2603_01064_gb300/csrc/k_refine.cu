@@ -58,9 +58,15 @@ k_refine_residual2d(Band2D<float> op, const float* __restrict__ Klo, const float
   const int r0 = ty * tile, c0 = tx * tile;
   const int RH = min(tile, n - r0), RW = min(tile, n - c0);
   const int XH = RH + 2 * W, XW = RW + 2 * W;
+  const int nk = 2 * wK + 1, nm = 2 * wM + 1;
   DF* xs = reinterpret_cast<DF*>(smem_raw);
   DF* tk = xs + XH * XW;
   DF* tm = tk + (RH + 2 * wK) * RW;
+  // banded coefficients (hi, lo) of the tile's columns and rows
+  DF* kcol = tm + (RH + 2 * wM) * RW;
+  DF* mcol = kcol + RW * nk;
+  DF* krow = mcol + RW * nm;
+  DF* mrow = krow + RH * nk;
   const size_t plane = (size_t)n * n;
   const double* ub = u + (size_t)b * plane;
   for (int idx = threadIdx.x; idx < XH * XW; idx += blockDim.x) {
@@ -70,26 +76,41 @@ k_refine_residual2d(Band2D<float> op, const float* __restrict__ Klo, const float
     float hi = (float)v;
     xs[idx] = DF{hi, (float)(v - (double)hi)};
   }
+  for (int idx = threadIdx.x; idx < RW * nk; idx += blockDim.x) {
+    const size_t g = (size_t)(c0 + idx / nk) * nk + idx % nk;
+    kcol[idx] = DF{op.Kd[g], Klo[g]};
+  }
+  for (int idx = threadIdx.x; idx < RW * nm; idx += blockDim.x) {
+    const size_t g = (size_t)(c0 + idx / nm) * nm + idx % nm;
+    mcol[idx] = DF{op.Md[g], Mlo[g]};
+  }
+  for (int idx = threadIdx.x; idx < RH * nk; idx += blockDim.x) {
+    const size_t g = (size_t)(r0 + idx / nk) * nk + idx % nk;
+    krow[idx] = DF{op.Kd[g], Klo[g]};
+  }
+  for (int idx = threadIdx.x; idx < RH * nm; idx += blockDim.x) {
+    const size_t g = (size_t)(r0 + idx / nm) * nm + idx % nm;
+    mrow[idx] = DF{op.Md[g], Mlo[g]};
+  }
   __syncthreads();
-  const int nk = 2 * wK + 1, nm = 2 * wM + 1;
   for (int idx = threadIdx.x; idx < (RH + 2 * wK) * RW; idx += blockDim.x) {
     int a = idx / RW, j = idx % RW;
     int gj = c0 + j;
+    (void)gj;
     DF acc{0.f, 0.f};
-    const float* kh = op.Kd + (size_t)gj * nk;
-    const float* kl = Klo + (size_t)gj * nk;
+    const DF* kc = kcol + j * nk;
     const DF* xr = xs + (a + W - wK) * XW + (j + W - wK);
-    for (int d = 0; d < nk; ++d) df_fma(acc, kh[d], kl[d], xr[d].h, xr[d].l);
+    for (int d = 0; d < nk; ++d) df_fma(acc, kc[d].h, kc[d].l, xr[d].h, xr[d].l);
     tk[idx] = df_norm(acc);
   }
   for (int idx = threadIdx.x; idx < (RH + 2 * wM) * RW; idx += blockDim.x) {
     int a = idx / RW, j = idx % RW;
     int gj = c0 + j;
+    (void)gj;
     DF acc{0.f, 0.f};
-    const float* mh = op.Md + (size_t)gj * nm;
-    const float* ml = Mlo + (size_t)gj * nm;
+    const DF* mc = mcol + j * nm;
     const DF* xr = xs + (a + W - wM) * XW + (j + W - wM);
-    for (int d = 0; d < nm; ++d) df_fma(acc, mh[d], ml[d], xr[d].h, xr[d].l);
+    for (int d = 0; d < nm; ++d) df_fma(acc, mc[d].h, mc[d].l, xr[d].h, xr[d].l);
     tm[idx] = df_norm(acc);
   }
   __syncthreads();
@@ -98,17 +119,15 @@ k_refine_residual2d(Band2D<float> op, const float* __restrict__ Klo, const float
     int i = idx / RW, j = idx % RW;
     int gi = r0 + i, gj = c0 + j;
     DF zk{0.f, 0.f}, zm{0.f, 0.f};
-    const float* kh = op.Kd + (size_t)gi * nk;
-    const float* kl = Klo + (size_t)gi * nk;
-    const float* mh = op.Md + (size_t)gi * nm;
-    const float* ml = Mlo + (size_t)gi * nm;
+    const DF* kr = krow + i * nk;
+    const DF* mr = mrow + i * nm;
     for (int d = 0; d < nk; ++d) {
       DF t = tk[(i + d) * RW + j];
-      df_fma(zk, kh[d], kl[d], t.h, t.l);
+      df_fma(zk, kr[d].h, kr[d].l, t.h, t.l);
     }
     for (int d = 0; d < nm; ++d) {
       DF t = tm[(i + d) * RW + j];
-      df_fma(zm, mh[d], ml[d], t.h, t.l);
+      df_fma(zm, mr[d].h, mr[d].l, t.h, t.l);
     }
     size_t gidx = (size_t)b * plane + (size_t)gi * n + gj;
     double az = alpha * ((double)zm.h + (double)zm.l) + ((double)zk.h + (double)zk.l);
@@ -136,7 +155,8 @@ void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float*
   int tile = hi.n < 64 ? hi.n : 64;
   auto smem = [&](int t) {
     return ((size_t)(t + 2 * W) * (t + 2 * W) + (size_t)(t + 2 * hi.wK) * t +
-            (size_t)(t + 2 * hi.wM) * t) * sizeof(DF);
+            (size_t)(t + 2 * hi.wM) * t + (size_t)2 * t * (2 * hi.wK + 1 + 2 * hi.wM + 1)) *
+           sizeof(DF);
   };
   while (tile > 4 && smem(tile) > 200 * 1024) tile /= 2;
   int tx = ceil_div(hi.n, tile);

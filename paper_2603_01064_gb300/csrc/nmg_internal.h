@@ -191,6 +191,9 @@ template <typename T>
 void launch_coarse_solve(int nc, const double* L, int B, const T* y, T* x, const int* active,
                          cudaStream_t st, LaunchLog& log);
 
+// active[b] = 1 where newmask[b] (serving admission)
+void launch_admit(int B, const int* newmask, int* active, cudaStream_t st, LaunchLog& log);
+
 // cycles[b] += 1 for active items
 void launch_count_cycles(int B, const int* active, int* cycles, cudaStream_t st, LaunchLog& log);
 

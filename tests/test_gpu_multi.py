@@ -1,0 +1,79 @@
+"""Mixed-size batched solve (nmg_solve_multi): batches on hierarchies of
+different grid sizes, operators and precisions solved in one outer loop
+(one CUDA graph per iteration, items as parallel branches) give exactly the
+results each batch gets when solved alone."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import nmg_inputs as I  # noqa: E402
+import oracle as O  # noqa: E402
+import paper_2603_01064_gb300 as nmg  # noqa: E402
+
+WDIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_2603_01064_gb300", "weights")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return nmg.Context(0)
+
+
+def items_spec():
+    W = nmg.load_weights(os.path.join(WDIR, "c2_2d_n128_s2_a1e-2.npz"))
+    # (n, levels, sigma, alpha, precision, batch); smoothers trained on the
+    # sigma-2 operator serve every grid size (per-level operators coincide)
+    return W, [(128, 5, 2.0, 1e-2, "bf16_refine", 6), (64, 4, 2.0, 1e-2, "bf16_refine", 9),
+               (64, 4, 2.0, 1e-2, "fp32", 5), (32, 3, 1.0, 1e-2, "bf16fast_refine", 4)]
+
+
+def build(ctx, W, spec, seed):
+    out = []
+    for k, (n, L, sg, al, prec, B) in enumerate(spec):
+        taps = I.gaussian_taps(sg)
+        G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=al, taps=taps, precision=prec,
+                          weights=W)
+        f, _ = I.rhs_2d_waves_rects(n, B, seed + k, sg)
+        fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+        ud = torch.zeros(fd.shape, dtype=torch.float32 if prec == "fp32" else torch.float64,
+                         device="cuda")
+        out.append((G, fd, ud, taps))
+    return out
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_multi_equals_alone(ctx, graphs):
+    W, spec = items_spec()
+    ctx.set_graphs(graphs)
+    try:
+        alone = build(ctx, W, spec, 500)
+        res_alone = [G.solve(f, u, rtol=1e-6, max_cycles=80) for G, f, u, _ in alone]
+        together = build(ctx, W, spec, 500)
+        res_multi = nmg.solve_multi(ctx, [(G, f, u) for G, f, u, _ in together], rtol=1e-6,
+                                    max_cycles=80)
+    finally:
+        ctx.set_graphs(True)
+    for (Ga, fa, ua, _), (Gm, fm, um, _), ra, rm in zip(alone, together, res_alone, res_multi):
+        assert np.array_equal(ra[0], rm[0])                       # cycles
+        assert np.array_equal(ra[1], rm[1])                       # status
+        assert torch.equal(ua, um)                                # iterates, bitwise
+    # the sigma-2 items converge to 1e-6, checked with the oracle's own apply
+    for (G, f, u, taps), (n, L, sg, al, prec, B), r in zip(together, spec, res_multi):
+        if sg == 2.0:
+            assert np.all(r[1] == 0)
+            H = O.build_hierarchy_2d(taps, n, al, L)
+            rr = O.relres(H, f.double().cpu().numpy(), u.double().cpu().numpy())
+            assert np.all(rr <= (1.5e-6 if prec == "fp32" else 1.01e-6)), rr
+
+
+def test_multi_rejects_duplicate_hierarchy(ctx):
+    W, spec = items_spec()
+    (G, f, u, _), = build(ctx, W, spec[:1], 1)
+    with pytest.raises(nmg.NMGError):
+        nmg.solve_multi(ctx, [(G, f, u), (G, f, u)])
