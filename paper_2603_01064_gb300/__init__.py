@@ -292,9 +292,11 @@ class Hierarchy:
         return (K, M) if self.dim == 2 else K
 
     def close(self):
-        if self._h:
+        # a hierarchy finalised after its context (interpreter shutdown) is
+        # left to the process exit: its context's device state is gone
+        if self._h and self.ctx._h:
             lib().nmg_destroy_hier(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -369,9 +371,9 @@ class Server:
         return q.value, r.value, b.value
 
     def close(self):
-        if self._h:
+        if self._h and self.ctx._h:
             lib().nmg_server_destroy(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:

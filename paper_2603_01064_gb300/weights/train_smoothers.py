@@ -272,7 +272,7 @@ def evaluate(prob, nets, f, rtol=1e-6, max_cycles=60):
     """Outer iteration from zero; returns per-RHS cycles to rtol (max_cycles+1 if not)."""
     u = torch.zeros_like(f)
     fn = _norm(f).flatten()
-    cyc = torch.full((f.shape[0],), max_cycles + 1)
+    cyc = torch.full((f.shape[0],), max_cycles + 1, device=f.device)
     hist = []
     for t in range(1, max_cycles + 1):
         u = cycle(prob, nets, 0, f, u)

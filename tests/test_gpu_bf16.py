@@ -43,8 +43,9 @@ def bf16(a):
 
 def emulated_fast(W, b):
     """s N(b/s) rounded to bf16 exactly where the fast kernels store bf16: the
-    hidden activations and the hidden layers' weights (the first and last
-    layers run in fp32)."""
+    activations that feed a hidden layer and the hidden layers' weights (the
+    first and the output layer run in fp32; the last hidden layer's
+    activations go to the fused output layer in fp32)."""
     s = np.sqrt(np.sum(b.reshape(b.shape[0], -1) ** 2, axis=1))[:, None, None]
     x = (b / s)[:, None]
     last = len(W) - 1
@@ -53,7 +54,9 @@ def emulated_fast(W, b):
         x = ON._conv_same(x, wi, np.asarray(bias, np.float32).astype(np.float64))
         x = x.astype(np.float32).astype(np.float64)  # the kernels accumulate in fp32
         if i < last:
-            x = bf16(np.maximum(x, 0.0))
+            x = np.maximum(x, 0.0)
+            if i < last - 1:
+                x = bf16(x)
     return x[:, 0] * s
 
 
