@@ -239,6 +239,7 @@ def run_ours(args, wl, world, rank, local):
 
     G = hier(prec)
     B = args.batch or wl["batch"]
+    G.autotune(B)  # launch shapes per level, timed on this GPU (outside the timed region)
     f_np = make_rhs(wl, B, rank_seed(wl, rank))
     refine = prec != "fp32"
     udt = torch.float64 if refine else torch.float32
@@ -343,6 +344,7 @@ def run_ours(args, wl, world, rank, local):
             if p == prec:
                 continue
             Gp = hier(p)
+            Gp.autotune(B)
             up = torch.zeros(f.shape, dtype=torch.float32 if p == "fp32" else torch.float64,
                              device="cuda")
             step_p = (lambda Gp=Gp, up=up: step(Gp, f, up))

@@ -285,6 +285,19 @@ enum {
 nmg_status nmg_profile_enable(nmg_ctx* ctx, int enable);
 nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double* ms,
                             double* units);
+/* Autotuner: for every level of a 2D hierarchy, time the candidate launch
+ * shapes (tile sides of the residual, the fused residual + restriction and
+ * the compensated outer residual; single-kernel or three-pass output
+ * filter) on the hierarchy's workspace with `batch` right-hand sides, and
+ * keep the fastest for later solves.  cache_path (may be NULL): a text file
+ * from which choices for the same operator shape, precision and batch are
+ * read instead of timed, and to which new choices are appended.  No effect
+ * on results beyond fp rounding order. */
+nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_path);
+/* The launch choices of one level (0 / -1: built-in defaults). */
+nmg_status nmg_hier_tuning(const nmg_hier* h, int level, int* res_tile, int* rst_tile,
+                           int* ref_tile, int* filt_mode);
+
 /* Solve loops replay one captured CUDA graph per outer iteration (cycle +
  * convergence test; captured on first use for a given batch, f, u and
  * rtol).  enable = 0 launches every kernel eagerly instead.  Profiling

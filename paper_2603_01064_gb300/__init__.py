@@ -104,6 +104,9 @@ def lib():
         "nmg_launch_count": (ctypes.c_longlong, [P]),
         "nmg_profile_enable": (I, [P, I]),
         "nmg_set_graphs": (I, [P, I]),
+        "nmg_autotune": (I, [P, P, I, ctypes.c_char_p]),
+        "nmg_hier_tuning": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                ctypes.POINTER(I)]),
         "nmg_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                  ctypes.POINTER(D)]),
         "nmg_sync": (I, [P]),
@@ -280,6 +283,16 @@ class Hierarchy:
     def prolong_correct(self, level, e, x):
         self.ctx.check(lib().nmg_prolong_correct(self.ctx._h, self._h, level, x.shape[0],
                                                  _ptr(e), _ptr(x)))
+
+    def autotune(self, batch: int, cache_path: str | None = None):
+        """Time the candidate launch shapes per level and keep the fastest."""
+        self.ctx.check(lib().nmg_autotune(self.ctx._h, self._h, int(batch),
+                                          cache_path.encode() if cache_path else None))
+
+    def tuning(self, level: int):
+        v = [ctypes.c_int() for _ in range(4)]
+        self.ctx.check(lib().nmg_hier_tuning(self._h, level, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["res_tile", "rst_tile", "ref_tile", "filt_mode"], [x.value for x in v]))
 
     # ---- inspection
     def level_dense(self, level):

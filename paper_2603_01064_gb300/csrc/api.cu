@@ -33,7 +33,7 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::
 void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
                        double alpha, int B, const double* u, const float* f, float* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
-                       LaunchLog& log);
+                       LaunchLog& log, int tile_req);
 }  // namespace nmg
 
 using namespace nmg;
@@ -75,6 +75,8 @@ struct DevLevel {
   double* wp_d = nullptr;  // 1D packed
   float* wp_f = nullptr;
   void* bf16_pack = nullptr;  // bf16 tensor-core weight pack (2D)
+  // launch choices (0 / -1 = built-in defaults), set by nmg_autotune
+  int res_tile = 0, rst_tile = 0, ref_tile = 0, filt_mode = -1;
 };
 
 struct Work {
@@ -295,7 +297,8 @@ int op_residual(nmg_hier* h, int l, int B, const T* x, const T* y, T* r, double*
   int nt = 0;
   nmg_ctx* c = h->ctx;
   if (h->dim == 2)
-    launch_residual2d<T>(band<T>(h, l), B, x, y, r, part, &nt, active, c->stream, c->log);
+    launch_residual2d<T>(band<T>(h, l), B, x, y, r, part, &nt, active, c->stream, c->log,
+                         h->lv[l].res_tile);
   else
     launch_residual1d<T>(h->lv[l].n, Ad<T>(h->lv[l]), B, x, y, r, part, &nt, active, c->stream,
                          c->log);
@@ -309,7 +312,7 @@ int op_residual_restrict(nmg_hier* h, int l, int B, const T* x, const T* y, T* y
   nmg_ctx* c = h->ctx;
   if (h->dim == 2) {
     launch_residual_restrict2d<T>(band<T>(h, l), B, x, y, yc, part, &nt, active, c->stream,
-                                  c->log);
+                                  c->log, h->lv[l].rst_tile);
   } else {
     T* tmp = reinterpret_cast<T*>(h->w.t[l]);
     launch_residual1d<T>(h->lv[l].n, Ad<T>(h->lv[l]), B, x, y, tmp, nullptr, nullptr, active,
@@ -371,7 +374,7 @@ void op_filter(nmg_hier* h, int l, int B, const T* xstar, const T* hv, T* x, con
     launch_axpy_update<T>((long long)plane(h, l), B, xstar, hv, x, active, c->stream, c->log);
   } else if (h->dim == 2) {
     launch_filter2d<T>(d.n, B, xstar, hv, x, h->w.cbuf, Tw<T>(d), d.mtab, active, c->stream,
-                       c->log);
+                       c->log, d.filt_mode);
   } else {
     launch_filter1d<T>(d.n, B, xstar, hv, x, d.circ, active, c->stream, c->log);
   }
@@ -1214,6 +1217,171 @@ nmg_status nmg_prolong_correct(nmg_ctx* ctx, nmg_hier* h, int level, int batch, 
   return NMG_OK;
 }
 
+// ---- autotuner ----------------------------------------------------------------
+// For every level of a 2D hierarchy, times each candidate launch shape on
+// the hierarchy's own workspace with `batch` right-hand sides (1 warm-up +
+// 3 timed launches, CUDA events on the context's stream) and keeps the
+// fastest: tile side of the residual (16/32/64), of the fused residual +
+// restriction (8/16/32 coarse), of the compensated outer residual
+// (16/32/64), and the single-kernel vs three-pass output filter.  With
+// cache_path, choices are read from / appended to a text file keyed by the
+// operator shape, precision and batch.
+static std::string tune_key(const nmg_hier* h, int batch) {
+  std::string k = "nmg-tune dim=" + std::to_string(h->dim) + " n=" + std::to_string(h->n) +
+                  " L=" + std::to_string(h->L) + " prec=" + std::to_string(h->precision) +
+                  " batch=" + std::to_string(batch);
+  for (const DevLevel& d : h->lv) k += " w=" + std::to_string(d.wK) + "," + std::to_string(d.wM);
+  return k;
+}
+
+nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_path) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (batch < 1) return fail(ctx, NMG_ERR_ARG, "batch < 1");
+  if (h->dim != 2) return NMG_OK;  // the 1D path has no launch choices
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  const std::string key = tune_key(h, batch);
+  if (cache_path && cache_path[0]) {
+    FILE* fp = std::fopen(cache_path, "r");
+    if (fp) {
+      char line[4096];
+      while (std::fgets(line, sizeof line, fp)) {
+        std::string ln(line);
+        while (!ln.empty() && (ln.back() == '\n' || ln.back() == '\r')) ln.pop_back();
+        const size_t bar = ln.find(" | ");
+        if (bar == std::string::npos || ln.substr(0, bar) != key) continue;
+        const char* p = ln.c_str() + bar + 3;
+        for (DevLevel& d : h->lv) {
+          int a, b, c, e, used = 0;
+          if (std::sscanf(p, "%d,%d,%d,%d;%n", &a, &b, &c, &e, &used) != 4) break;
+          d.res_tile = a;
+          d.rst_tile = b;
+          d.ref_tile = c;
+          d.filt_mode = e;
+          p += used;
+        }
+        std::fclose(fp);
+        return NMG_OK;
+      }
+      std::fclose(fp);
+    }
+  }
+  if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  Work& w = h->w;
+  cudaStream_t st = ctx->stream;
+  const bool was_prof = ctx->log.prof;
+  ctx->log.prof = false;
+  ctx->log.active_hint = batch;
+  CK(cudaMemcpyAsync(w.active, w.ones, batch * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  const size_t es = elem_size(h->precision);
+  for (int l = 0; l < h->L; ++l) {
+    // deterministic nonzero contents
+    CK(cudaMemsetAsync(w.x[l], 0x3C, plane(h, l) * batch * es, st));
+    CK(cudaMemsetAsync(w.y[l], 0x3D, plane(h, l) * batch * es, st));
+    CK(cudaMemsetAsync(w.h[l], 0x3B, plane(h, l) * batch * es, st));
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timeit = [&](const std::function<void()>& fn) -> float {
+    fn();
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) fn();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  const bool dbl = h->precision == NMG_FP64;
+  for (int l = 0; l < h->L; ++l) {
+    DevLevel& d = h->lv[l];
+    float best = 1e30f;
+    if (l < h->L - 1) {
+      int keep = 0;
+      for (int t : {8, 16, 32}) {
+        d.rst_tile = t;
+        float ms = timeit([&]() {
+          if (dbl) op_residual_restrict<double>(h, l, batch, (double*)w.x[l], (double*)w.y[l], (double*)w.y[l + 1], w.part[l + 1], w.active);
+          else op_residual_restrict<float>(h, l, batch, (float*)w.x[l], (float*)w.y[l], (float*)w.y[l + 1], w.part[l + 1], w.active);
+        });
+        if (ms < best) { best = ms; keep = t; }
+      }
+      d.rst_tile = keep;
+      best = 1e30f;
+      int keepm = -1;
+      for (int m : {0, 1}) {
+        d.filt_mode = m;
+        float ms = timeit([&]() {
+          if (dbl) op_filter<double>(h, l, batch, (double*)w.x[l], (double*)w.h[l], (double*)w.x[l], w.active);
+          else op_filter<float>(h, l, batch, (float*)w.x[l], (float*)w.h[l], (float*)w.x[l], w.active);
+        });
+        if (ms < best) { best = ms; keepm = m; }
+      }
+      d.filt_mode = keepm;
+    }
+    if (l == 0 && is_refine(h->precision)) {
+      // u is fp64 for the outer residual: reuse the complex filter scratch
+      best = 1e30f;
+      int keep = 0;
+      for (int t : {16, 32, 64}) {
+        d.ref_tile = t;
+        float ms = timeit([&]() {
+          int nt = 0;
+          launch_refine_residual_dispatch(h, batch, (const double*)w.cbuf, (const float*)w.y[0], w.r32, w.part[0], &nt, w.active);
+        });
+        if (ms < best) { best = ms; keep = t; }
+      }
+      d.ref_tile = keep;
+    }
+  }
+  for (int l = 0; l < h->L; ++l) {
+    DevLevel& d = h->lv[l];
+    float best = 1e30f;
+    int keep = 0;
+    for (int t : {16, 32, 64}) {
+      d.res_tile = t;
+      float ms = timeit([&]() {
+        if (dbl) op_residual<double>(h, l, batch, (double*)w.x[l], (double*)w.y[l], (double*)w.t[l], w.part[l], w.active);
+        else op_residual<float>(h, l, batch, (float*)w.x[l], (float*)w.y[l], (float*)w.t[l], w.part[l], w.active);
+      });
+      if (ms < best) { best = ms; keep = t; }
+    }
+    d.res_tile = keep;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->log.prof = was_prof;
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  if (w.gexec) {  // captured graphs hold the old launch shapes
+    cudaGraphExecDestroy(w.gexec);
+    w.gexec = nullptr;
+  }
+  if (cache_path && cache_path[0]) {
+    FILE* fp = std::fopen(cache_path, "a");
+    if (fp) {
+      std::fprintf(fp, "%s | ", key.c_str());
+      for (const DevLevel& d : h->lv)
+        std::fprintf(fp, "%d,%d,%d,%d;", d.res_tile, d.rst_tile, d.ref_tile, d.filt_mode);
+      std::fprintf(fp, "\n");
+      std::fclose(fp);
+    }
+  }
+  return NMG_OK;
+}
+
+nmg_status nmg_hier_tuning(const nmg_hier* h, int level, int* res_tile, int* rst_tile,
+                           int* ref_tile, int* filt_mode) {
+  if (!h || level < 0 || level >= h->L) return NMG_ERR_ARG;
+  const DevLevel& d = h->lv[level];
+  if (res_tile) *res_tile = d.res_tile;
+  if (rst_tile) *rst_tile = d.rst_tile;
+  if (ref_tile) *ref_tile = d.ref_tile;
+  if (filt_mode) *filt_mode = d.filt_mode;
+  return NMG_OK;
+}
+
 nmg_status nmg_hier_info(const nmg_hier* h, int level, int* n, int* wK, int* wM, int* precision) {
   if (!h || level < 0 || level >= h->L) return NMG_ERR_ARG;
   if (n) *n = h->lv[level].n;
@@ -1678,6 +1846,6 @@ void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const 
   const DevLevel& d = h->lv[0];
   Band2D<float> hi{d.n, d.wK, d.wM, d.Kd_f, d.Md_f, (float)h->alpha};
   refine_residual2d(hi, d.Kd_lo, d.Md_lo, h->alpha, B, u, f, r, part, nt, active, h->ctx->stream,
-                    h->ctx->log);
+                    h->ctx->log, d.ref_tile);
 }
 }  // namespace

@@ -263,7 +263,7 @@ __global__ void k_filter1d(int n, const T* xs, const T* __restrict__ h, T* x, co
 template <typename T>
 void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
                      const T* twiddles, const double* mask_tab, const int* active,
-                     cudaStream_t st, LaunchLog& log) {
+                     cudaStream_t st, LaunchLog& log, int mode) {
   const int logn = ilog2(n);
   // sequences per block: about 64 KB of complex data
   int per = (int)((64 * 1024) / (n * sizeof(Cx<T>)));
@@ -274,7 +274,7 @@ void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
   Cx<T>* C = reinterpret_cast<Cx<T>*>(cbuf);
   const Cx<T>* tw = reinterpret_cast<const Cx<T>*>(twiddles);
   const size_t fused_sm = (size_t)(n / 2 + n * n) * sizeof(Cx<T>);
-  if (fused_sm <= 160 * 1024) {
+  if (fused_sm <= 160 * 1024 && mode != 0) {
     cudaFuncSetAttribute(k_filter_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_sm);
     const int threads = n * n / 2 < 512 ? (n * n / 2 < 32 ? 32 : n * n / 2) : 512;
     int pi_ = log.begin(K_FILTER, st);
@@ -310,10 +310,10 @@ void launch_filter1d(int n, int B, const T* xstar, const T* h, T* x, const doubl
 
 template void launch_filter2d<float>(int, int, const float*, const float*, float*, void*,
                                      const float*, const double*, const int*, cudaStream_t,
-                                     LaunchLog&);
+                                     LaunchLog&, int);
 template void launch_filter2d<double>(int, int, const double*, const double*, double*, void*,
                                       const double*, const double*, const int*, cudaStream_t,
-                                      LaunchLog&);
+                                      LaunchLog&, int);
 template void launch_filter1d<float>(int, int, const float*, const float*, float*,
                                      const double*, const int*, cudaStream_t, LaunchLog&);
 template void launch_filter1d<double>(int, int, const double*, const double*, double*,

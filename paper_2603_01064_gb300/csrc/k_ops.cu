@@ -370,9 +370,13 @@ size_t residual_smem(int RH, int RW, int wK, int wM, bool restrict_) {
 
 // tile sizes: fine tile for the residual, coarse tile for residual+restrict;
 // shrunk until the shared-memory footprint fits in 200 KB
+// tile side: the requested one (0 = default: 64 fine / 32 coarse), clipped to
+// the grid, halved until the shared-memory footprint fits in 200 KB, and
+// doubled while one right-hand side would need more than 4096 tiles (the
+// partial-sum slots per item)
 template <typename T>
-int pick_tile(int n, int wK, int wM, bool restrict_) {
-  int t = restrict_ ? 32 : 64;
+int pick_tile(int n, int wK, int wM, bool restrict_, int req) {
+  int t = req > 0 ? req : (restrict_ ? 32 : 64);
   int lim = restrict_ ? n / 2 : n;
   if (t > lim) t = lim;
   while (t > 4) {
@@ -380,6 +384,7 @@ int pick_tile(int n, int wK, int wM, bool restrict_) {
     if (residual_smem<T>(R, R, wK, wM, restrict_) <= 200 * 1024) break;
     t /= 2;
   }
+  while (t < lim && (long long)ceil_div(lim, t) * ceil_div(lim, t) > 4096) t *= 2;
   return t;
 }
 
@@ -388,8 +393,8 @@ int pick_tile(int n, int wK, int wM, bool restrict_) {
 template <typename T>
 void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
-                       LaunchLog& log) {
-  int tile = pick_tile<T>(op.n, op.wK, op.wM, false);
+                       LaunchLog& log, int tile_req) {
+  int tile = pick_tile<T>(op.n, op.wK, op.wM, false, tile_req);
   int tx = ceil_div(op.n, tile);
   size_t sm = residual_smem<T>(tile, tile, op.wK, op.wM, false);
   auto kern = k_residual2d<T, false>;
@@ -404,8 +409,8 @@ void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
 template <typename T>
 void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T* y, T* yc,
                                 double* partials, int* ntiles, const int* active,
-                                cudaStream_t st, LaunchLog& log) {
-  int tile = pick_tile<T>(op.n, op.wK, op.wM, true);
+                                cudaStream_t st, LaunchLog& log, int tile_req) {
+  int tile = pick_tile<T>(op.n, op.wK, op.wM, true, tile_req);
   int nc = op.n / 2;
   int tx = ceil_div(nc, tile);
   size_t sm = residual_smem<T>(2 * tile + 1, 2 * tile + 1, op.wK, op.wM, true);
@@ -513,10 +518,10 @@ void launch_update_f64(long long len, int B, const float* d, double* u, const in
 
 #define NMG_INST(T)                                                                          \
   template void launch_residual2d<T>(const Band2D<T>&, int, const T*, const T*, T*, double*, \
-                                     int*, const int*, cudaStream_t, LaunchLog&);            \
+                                     int*, const int*, cudaStream_t, LaunchLog&, int);       \
   template void launch_residual_restrict2d<T>(const Band2D<T>&, int, const T*, const T*,     \
                                               T*, double*, int*, const int*, cudaStream_t,   \
-                                              LaunchLog&);                                   \
+                                              LaunchLog&, int);                              \
   template void launch_prolong2d<T>(int, int, const T*, T*, const int*, cudaStream_t,        \
                                     LaunchLog&);                                             \
   template void launch_residual1d<T>(int, const T*, int, const T*, const T*, T*, double*,    \

@@ -150,15 +150,17 @@ k_refine_residual2d(Band2D<float> op, const float* __restrict__ Klo, const float
 void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
                        double alpha, int B, const double* u, const float* f, float* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
-                       LaunchLog& log) {
+                       LaunchLog& log, int tile_req) {
   const int W = hi.wK > hi.wM ? hi.wK : hi.wM;
-  int tile = hi.n < 64 ? hi.n : 64;
+  int tile = tile_req > 0 ? tile_req : 32;
+  if (tile > hi.n) tile = hi.n;
   auto smem = [&](int t) {
     return ((size_t)(t + 2 * W) * (t + 2 * W) + (size_t)(t + 2 * hi.wK) * t +
             (size_t)(t + 2 * hi.wM) * t + (size_t)2 * t * (2 * hi.wK + 1 + 2 * hi.wM + 1)) *
            sizeof(DF);
   };
   while (tile > 4 && smem(tile) > 200 * 1024) tile /= 2;
+  while (tile < hi.n && (long long)ceil_div(hi.n, tile) * ceil_div(hi.n, tile) > 4096) tile *= 2;
   int tx = ceil_div(hi.n, tile);
   size_t sm = smem(tile);
   cudaFuncSetAttribute(k_refine_residual2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -120,15 +120,16 @@ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 // ---------------------------------------------------------------------------
 
 // r = y - A x on a 2D level (+ per-tile partial sums of r^2 if partials)
+// tile_req: requested tile side (0 = default), see pick_tile
 template <typename T>
 void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
-                       LaunchLog& log);
+                       LaunchLog& log, int tile_req = 0);
 // yc = R (y - A x) on a 2D level (+ partial sums of yc^2)
 template <typename T>
 void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T* y, T* yc,
                                 double* partials, int* ntiles, const int* active,
-                                cudaStream_t st, LaunchLog& log);
+                                cudaStream_t st, LaunchLog& log, int tile_req = 0);
 // x += P e (2D)
 template <typename T>
 void launch_prolong2d(int n, int B, const T* e, T* x, const int* active, cudaStream_t st,
@@ -172,10 +173,12 @@ void launch_cnn1d(int n, int B, int layers, int width, int ksize, const T* wpack
                   LaunchLog& log);
 
 // filter: x = xstar + F'(h) (2D FFT passes); xstar may be null; x may alias xstar
+// mode: -1 default (single kernel when the complex image fits in shared
+// memory), 0 three passes, 1 single kernel (if it fits)
 template <typename T>
 void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
                      const T* twiddles, const double* mask_tab, const int* active,
-                     cudaStream_t st, LaunchLog& log);
+                     cudaStream_t st, LaunchLog& log, int mode = -1);
 template <typename T>
 void launch_filter1d(int n, int B, const T* xstar, const T* h, T* x, const double* circ,
                      const int* active, cudaStream_t st, LaunchLog& log);
