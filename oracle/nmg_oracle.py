@@ -211,7 +211,8 @@ def prolong(H: Hierarchy, l: int, e: np.ndarray) -> np.ndarray:
 def _conv_same(x: np.ndarray, W: np.ndarray, bias: np.ndarray) -> np.ndarray:
     """Cross-correlation with zero 'same' padding, PyTorch Conv semantics:
     out[b, o, p] = bias[o] + sum_{c, t} W[o, c, t] x[b, c, p + t - k//2].
-    x is [B, Cin, n] (1D) or [B, Cin, n, n] (2D)."""
+    x is [B, Cin, n] (1D) or [B, Cin, n, n] (2D).  The channel sum of each
+    tap is one matrix product (numpy's BLAS)."""
     dim = W.ndim - 2
     k = W.shape[-1]
     p = k // 2
@@ -222,13 +223,14 @@ def _conv_same(x: np.ndarray, W: np.ndarray, bias: np.ndarray) -> np.ndarray:
         xp = np.pad(x, ((0, 0), (0, 0), (p, p)))
         out = np.broadcast_to(bias[None, :, None], (B, Cout, n)).copy()
         for t in range(k):
-            out += np.einsum("oc,bcn->bon", W[:, :, t], xp[:, :, t:t + n])
+            out += np.einsum("oc,bcn->bon", W[:, :, t], xp[:, :, t:t + n], optimize=True)
         return out
     xp = np.pad(x, ((0, 0), (0, 0), (p, p), (p, p)))
     out = np.broadcast_to(bias[None, :, None, None], (B, Cout, n, n)).copy()
     for ty in range(k):
         for tx in range(k):
-            out += np.einsum("oc,bcij->boij", W[:, :, ty, tx], xp[:, :, ty:ty + n, tx:tx + n])
+            out += np.einsum("oc,bcij->boij", W[:, :, ty, tx], xp[:, :, ty:ty + n, tx:tx + n],
+                             optimize=True)
     return out
 
 
