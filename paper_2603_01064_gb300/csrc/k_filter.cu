@@ -1,14 +1,15 @@
 // Output filter of the cycle, x = x* + F'_l(h) with
 // F'_l(h) = Re(IDFT(m'_l . DFT(h))) (Sections 3.2 and 3.3).
 //
-// 2D: three passes over a complex [B][n][n] buffer, each an in-shared-memory
-// radix-2 Cooley-Tukey FFT over whole rows/columns:
-//   1. forward FFT of every row of h (real input);
-//   2. per block of columns: forward FFT down the column, multiply by the
-//      mask m'(k1, k2) = sqrt(max(|w1|, |w2|) / pi), inverse FFT;
-//   3. inverse FFT of every row, x = x* + Re(.) / n^2.
-// The mask is real and even in each axis, so the result is real up to
-// rounding, which Re(.) drops as the paper states.
+// 2D: in-shared-memory radix-2 Cooley-Tukey FFTs over whole rows/columns on
+// the half spectrum of each real image (row pairs packed as one complex
+// row, see the layout note below); the mask
+// m'(k1, k2) = sqrt(max(|w1|, |w2|) / pi) is real and even in each axis, so
+// the filtered image is real and is produced as such (the Re(.) of the
+// definition is implied).  Levels whose n/2 x n complex layout fits in
+// shared memory run one fused launch per image; larger levels run three
+// passes over a [B][n/2][n] complex buffer (row pairs, column pairs, row
+// pairs).
 // 1D: x = x* + C h with C the real symmetric circulant of the filter,
 // applied directly from its first column.
 #include "nmg_internal.h"
@@ -50,7 +51,209 @@ __device__ void fft_stages(Cx<T>* buf, int n, int logn, int cnt, const Cx<T>* tw
   }
 }
 
-// pass 1: rows of real h -> complex spectrum rows
+// ---------------------------------------------------------------------------
+// Half-spectrum 2D transform of one real image.
+//
+// h is real and the mask is real and even in both axes, so only the n/2 + 1
+// column frequencies 0..n/2 of the row spectra are needed.  Rows 2k and
+// 2k+1 travel together as one complex row z_k = h[2k] + i h[2k+1]
+// ("row-pair layout", n/2 rows of n complex values):
+//   after the row FFT and the split below, row k holds
+//     position t, 0 < t < n/2 : X_{2k}[t]      (spectrum of row 2k)
+//     position n - t          : X_{2k+1}[t]    (spectrum of row 2k+1)
+//     position 0              : X_{2k}[0]   + i X_{2k}[n/2]
+//     position n/2            : X_{2k+1}[0] + i X_{2k+1}[n/2]
+//   (the four values at 0 and n/2 are real for real rows).
+// Column j (0 < j < n/2) of the full row-spectrum array is then split by
+// row parity between layout columns j (even rows) and n - j (odd rows):
+// the first decimation-in-time step of the length-n column FFT.  Columns 0
+// and n/2 of the spectrum, both real sequences, travel together as the
+// complex sequence q[r] = X_r[0] + i X_r[n/2], even rows in layout column 0
+// and odd rows in layout column n/2; their different masks are applied
+// after separating the two real sequences' spectra by Hermitian symmetry.
+// Everything a right-hand side's result depends on is that right-hand
+// side's own image: results do not depend on the batch composition.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int bitrev_bits(int v, int bits) { return bits ? bitrev(v, bits) : 0; }
+
+// Separate the FFTs of the row pairs of `nrows` layout rows (natural order)
+// into the row-pair layout above.  Each (row, t) touches only positions t
+// and n - t of its row: no synchronisation inside.
+template <typename T>
+__device__ void rows_split(Cx<T>* buf, int nrows, int n) {
+  const int halfn = n >> 1;
+  for (int idx = threadIdx.x; idx < nrows * halfn; idx += blockDim.x) {
+    const int k = idx / halfn, t = idx % halfn;
+    Cx<T>* row = buf + (size_t)k * n;
+    if (t == 0) {
+      const Cx<T> a = row[0], b = row[halfn];
+      row[0] = Cx<T>{a.x, b.x};
+      row[halfn] = Cx<T>{a.y, b.y};
+    } else {
+      const Cx<T> za = row[t], zb = row[n - t];
+      // X_a = (Z[t] + conj Z[n-t]) / 2,  X_b = (Z[t] - conj Z[n-t]) / 2i
+      row[t] = Cx<T>{T(0.5) * (za.x + zb.x), T(0.5) * (za.y - zb.y)};
+      row[n - t] = Cx<T>{T(0.5) * (za.y + zb.y), T(0.5) * (zb.x - za.x)};
+    }
+  }
+}
+
+// Inverse of rows_split: rebuild the full spectrum of z_k = row 2k + i row
+// 2k+1 from the row-pair layout, Z[t] = X_a[t] + i X_b[t] for all t, using
+// X[n - t] = conj X[t].  Natural order in and out.
+template <typename T>
+__device__ void rows_join(Cx<T>* buf, int nrows, int n) {
+  const int halfn = n >> 1;
+  for (int idx = threadIdx.x; idx < nrows * halfn; idx += blockDim.x) {
+    const int k = idx / halfn, t = idx % halfn;
+    Cx<T>* row = buf + (size_t)k * n;
+    if (t == 0) {
+      const Cx<T> a = row[0], b = row[halfn];
+      row[0] = Cx<T>{a.x, b.x};
+      row[halfn] = Cx<T>{a.y, b.y};
+    } else {
+      const Cx<T> xa = row[t], xb = row[n - t];
+      row[t] = Cx<T>{xa.x - xb.y, xa.y + xb.x};
+      row[n - t] = Cx<T>{xa.x + xb.y, xb.x - xa.y};
+    }
+  }
+}
+
+// Bit-reverse the element order within each of `nrows` rows of length n.
+template <typename T>
+__device__ void rows_bitrev(Cx<T>* buf, int nrows, int n, int logn) {
+  for (int idx = threadIdx.x; idx < nrows * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx % n, rc = bitrev(c, logn);
+    if (c < rc) {
+      Cx<T> t = buf[r * n + c];
+      buf[r * n + c] = buf[r * n + rc];
+      buf[r * n + rc] = t;
+    }
+  }
+}
+
+// Bit-reverse the row order of a [len][pitch] array (every column at once).
+template <typename T>
+__device__ void cols_bitrev(Cx<T>* buf, int pitch, int ncols, int len, int loglen) {
+  for (int idx = threadIdx.x; idx < len * ncols; idx += blockDim.x) {
+    const int k = idx / ncols, c = idx % ncols, rk = bitrev_bits(k, loglen);
+    if (k < rk) {
+      Cx<T> t = buf[k * pitch + c];
+      buf[k * pitch + c] = buf[rk * pitch + c];
+      buf[rk * pitch + c] = t;
+    }
+  }
+}
+
+// Radix-2 DIT FFT of length len = 2^loglen down each of ncols columns of a
+// [len][pitch] array (rows in bit-reversed order in, natural order out).
+// tw is the length-n table exp(-2 pi i k / n), k < n/2, with len <= n.
+template <typename T>
+__device__ void cols_fft(Cx<T>* buf, int pitch, int ncols, int loglen, int n, const Cx<T>* tw,
+                         int sign) {
+  const int len = 1 << loglen;
+  for (int s = 1; s <= loglen; ++s) {
+    const int half = 1 << (s - 1), tstride = n >> s;
+    for (int t = threadIdx.x; t < (len >> 1) * ncols; t += blockDim.x) {
+      const int c = t % ncols, k = t / ncols;
+      const int grp = k / half, pos = k % half;
+      const int i = (grp * 2 * half + pos) * pitch + c, j = i + half * pitch;
+      Cx<T> w = tw[pos * tstride];
+      if (sign < 0) w.y = -w.y;
+      const Cx<T> a = buf[i], bb = buf[j];
+      const Cx<T> p{w.x * bb.x - w.y * bb.y, w.x * bb.y + w.y * bb.x};
+      buf[i] = Cx<T>{a.x + p.x, a.y + p.y};
+      buf[j] = Cx<T>{a.x - p.x, a.y - p.y};
+    }
+    __syncthreads();
+  }
+}
+
+// Column pairs of the row-pair layout in shared memory: pair p has its
+// even-row column at slot ev(p), its odd-row column at slot od(p) and
+// column frequency fr(p) (0 means the packed pair of frequencies 0 and n/2).
+struct FusedPairs {  // whole image: slots are layout columns
+  int n;
+  __device__ int ev(int p) const { return p; }
+  __device__ int od(int p) const { return p == 0 ? n / 2 : n - p; }
+  __device__ int fr(int p) const { return p; }
+  __device__ int special() const { return 0; }
+};
+struct BlockPairs {  // a block of cpc frequencies j0..j0+cpc-1
+  int cpc, j0;
+  __device__ int ev(int p) const { return p; }
+  __device__ int od(int p) const { return cpc + p; }
+  __device__ int fr(int p) const { return j0 + p; }
+  __device__ int special() const { return j0 == 0 ? 0 : -1; }
+};
+
+// Given the length-n/2 column FFTs of both halves of every pair (natural
+// order), finish the length-n column transform, multiply by the mask and
+// undo the last step again, leaving for every pair the length-n/2 spectra
+// of the even and odd rows of the masked column's inverse:
+//   Y[k1] = E[k1] + w^k1 O[k1],  Y[k1 + n/2] = E[k1] - w^k1 O[k1]
+//   Y *= m';  E' = Y[k1] + Y[k1 + n/2],  O' = (Y[k1] - Y[k1 + n/2]) conj(w^k1)
+// Column frequency j > 0: Y is the column spectrum itself, mask
+// m'(k1, j) = mtab[max(fold(k1), j)].  The packed pair (frequency 0 and n/2)
+// holds Q = A + iB with A, B the spectra of two real sequences; with
+// masks m_a(K) = mtab[fold(K)], m_b(K) = mtab[n/2]:
+//   Q'[K] = (m_a + m_b)/2 Q[K] + (m_a - m_b)/2 conj Q[n - K].
+template <typename T, typename Map>
+__device__ void spectral_pairs(Cx<T>* buf, int pitch, int npairs, Map map, int n,
+                               const Cx<T>* tw, const double* __restrict__ mtab) {
+  const int halfn = n >> 1;
+  for (int idx = threadIdx.x; idx < npairs * halfn; idx += blockDim.x) {
+    const int p = idx % npairs, k1 = idx / npairs;
+    const int j = map.fr(p);
+    Cx<T>* pe = buf + k1 * pitch + map.ev(p);
+    Cx<T>* po = buf + k1 * pitch + map.od(p);
+    const Cx<T> w = tw[k1];
+    const Cx<T> e = *pe, o = *po;
+    const Cx<T> wo{w.x * o.x - w.y * o.y, w.x * o.y + w.y * o.x};
+    Cx<T> y0{e.x + wo.x, e.y + wo.y}, y1{e.x - wo.x, e.y - wo.y};
+    if (j == 0) {  // packed pair: separation needs K and n - K, done below
+      *pe = y0;
+      *po = y1;
+      continue;
+    }
+    const T m0 = (T)mtab[k1 > j ? k1 : j];
+    const T m1 = (T)mtab[halfn - k1 > j ? halfn - k1 : j];
+    y0.x *= m0; y0.y *= m0;
+    y1.x *= m1; y1.y *= m1;
+    const Cx<T> d{y0.x - y1.x, y0.y - y1.y};
+    *pe = Cx<T>{y0.x + y1.x, y0.y + y1.y};
+    *po = Cx<T>{w.x * d.x + w.y * d.y, w.x * d.y - w.y * d.x};
+  }
+  const int sp = map.special();
+  if (sp < 0) return;  // uniform across the block: no barrier skipped unevenly
+  __syncthreads();
+  Cx<T>* ce = buf + map.ev(sp);
+  Cx<T>* co = buf + map.od(sp);
+  // Q[K] sits at row K of ce for K < n/2, at row K - n/2 of co otherwise
+  auto at = [&](int K) -> Cx<T>* { return K < halfn ? ce + K * pitch : co + (K - halfn) * pitch; };
+  const T mb = (T)mtab[halfn];
+  for (int K = threadIdx.x; K <= halfn; K += blockDim.x) {
+    const int Kp = K == 0 ? 0 : n - K;
+    const T ma = (T)mtab[K];
+    const T c1 = T(0.5) * (ma + mb), c2 = T(0.5) * (ma - mb);
+    Cx<T>* a = at(K);
+    Cx<T>* b = at(Kp);
+    const Cx<T> qa = *a, qb = *b;
+    *a = Cx<T>{c1 * qa.x + c2 * qb.x, c1 * qa.y - c2 * qb.y};
+    if (Kp != K) *b = Cx<T>{c1 * qb.x + c2 * qa.x, c1 * qb.y - c2 * qa.y};
+  }
+  __syncthreads();
+  for (int k1 = threadIdx.x; k1 < halfn; k1 += blockDim.x) {
+    const Cx<T> w = tw[k1];
+    const Cx<T> y0 = ce[k1 * pitch], y1 = co[k1 * pitch];
+    const Cx<T> d{y0.x - y1.x, y0.y - y1.y};
+    ce[k1 * pitch] = Cx<T>{y0.x + y1.x, y0.y + y1.y};
+    co[k1 * pitch] = Cx<T>{w.x * d.x + w.y * d.y, w.x * d.y - w.y * d.x};
+  }
+}
+
+// pass 1: row pairs of real h -> row-pair layout spectra in C ([B][n/2][n])
 template <typename T>
 __global__ void k_fft_rows_fwd(int n, int logn, int rpc, const T* __restrict__ h,
                                Cx<T>* __restrict__ C, const Cx<T>* __restrict__ twg,
@@ -61,22 +264,24 @@ __global__ void k_fft_rows_fwd(int n, int logn, int rpc, const T* __restrict__ h
   Cx<T>* tw = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* buf = tw + n / 2;
   for (int k = threadIdx.x; k < n / 2; k += blockDim.x) tw[k] = twg[k];
-  const int row0 = blockIdx.x * rpc;
+  const int k0 = blockIdx.x * rpc;  // first layout row (row pair)
   const size_t plane = (size_t)n * n;
+  const T* hb = h + (size_t)b * plane;
   for (int t = threadIdx.x; t < rpc * n; t += blockDim.x) {
-    int r = t / n, j = t % n;
-    T v = h[(size_t)b * plane + (size_t)(row0 + r) * n + j];
-    buf[r * n + bitrev(j, logn)] = Cx<T>{v, T(0)};
+    const int r = t / n, j = t % n;
+    const size_t g = (size_t)(2 * (k0 + r)) * n + j;
+    buf[r * n + bitrev(j, logn)] = Cx<T>{hb[g], hb[g + n]};
   }
   __syncthreads();
   fft_stages(buf, n, logn, rpc, tw, +1);
-  for (int t = threadIdx.x; t < rpc * n; t += blockDim.x) {
-    int r = t / n, j = t % n;
-    C[(size_t)b * plane + (size_t)(row0 + r) * n + j] = buf[t];
-  }
+  rows_split(buf, rpc, n);
+  __syncthreads();
+  Cx<T>* Cb = C + (size_t)b * (plane / 2);
+  for (int t = threadIdx.x; t < rpc * n; t += blockDim.x) Cb[(size_t)k0 * n + t] = buf[t];
 }
 
-// pass 2: column FFT, mask, inverse column FFT (in place on C)
+// pass 2: column transforms, mask, inverse column transforms for cpc column
+// frequencies j0..j0+cpc-1 (in place on C)
 template <typename T>
 __global__ void k_fft_cols_mask(int n, int logn, int cpc, Cx<T>* __restrict__ C,
                                 const Cx<T>* __restrict__ twg, const double* __restrict__ mtab,
@@ -85,48 +290,34 @@ __global__ void k_fft_cols_mask(int n, int logn, int cpc, Cx<T>* __restrict__ C,
   if (!active[b]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<T>* tw = reinterpret_cast<Cx<T>*>(smem_raw);
-  Cx<T>* buf = tw + n / 2;  // cpc sequences of length n (one per column)
-  for (int k = threadIdx.x; k < n / 2; k += blockDim.x) tw[k] = twg[k];
-  const int col0 = blockIdx.x * cpc;
-  const size_t plane = (size_t)n * n;
-  Cx<T>* Cb = C + (size_t)b * plane;
-  for (int t = threadIdx.x; t < cpc * n; t += blockDim.x) {
-    int r = t / cpc, c = t % cpc;  // consecutive threads: consecutive columns
-    buf[c * n + bitrev(r, logn)] = Cb[(size_t)r * n + col0 + c];
+  Cx<T>* buf = tw + n / 2;  // [n/2][2 cpc]: even-row columns, then odd-row columns
+  const int halfn = n / 2, pitch = 2 * cpc;
+  for (int k = threadIdx.x; k < halfn; k += blockDim.x) tw[k] = twg[k];
+  const BlockPairs map{cpc, (int)blockIdx.x * cpc};
+  Cx<T>* Cb = C + (size_t)b * ((size_t)n * n / 2);
+  // layout column of slot s: even slots j0 + s, odd slots their partners
+  auto gcol = [&](int s) {
+    const int j = map.j0 + (s < cpc ? s : s - cpc);
+    return s < cpc ? j : (j == 0 ? halfn : n - j);
+  };
+  for (int t = threadIdx.x; t < halfn * pitch; t += blockDim.x) {
+    const int k = t / pitch, s = t % pitch;
+    buf[bitrev_bits(k, logn - 1) * pitch + s] = Cb[(size_t)k * n + gcol(s)];
   }
   __syncthreads();
-  fft_stages(buf, n, logn, cpc, tw, +1);
-  // mask, then back to bit-reversed order for the inverse transform
-  for (int t = threadIdx.x; t < cpc * n; t += blockDim.x) {
-    int c = t / n, k1 = t % n;
-    int k2 = col0 + c;
-    int f1 = k1 < n - k1 ? k1 : n - k1;
-    int f2 = k2 < n - k2 ? k2 : n - k2;
-    T m = (T)mtab[f1 > f2 ? f1 : f2];
-    Cx<T> v = buf[t];
-    v.x *= m;
-    v.y *= m;
-    buf[t] = v;
-  }
+  cols_fft(buf, pitch, pitch, logn - 1, n, tw, +1);
+  spectral_pairs(buf, pitch, cpc, map, n, tw, mtab);
   __syncthreads();
-  for (int t = threadIdx.x; t < cpc * n; t += blockDim.x) {
-    int c = t / n, k = t % n;
-    int rk = bitrev(k, logn);
-    if (k < rk) {
-      Cx<T> a = buf[c * n + k];
-      buf[c * n + k] = buf[c * n + rk];
-      buf[c * n + rk] = a;
-    }
-  }
+  cols_bitrev(buf, pitch, pitch, halfn, logn - 1);
   __syncthreads();
-  fft_stages(buf, n, logn, cpc, tw, -1);
-  for (int t = threadIdx.x; t < cpc * n; t += blockDim.x) {
-    int r = t / cpc, c = t % cpc;
-    Cb[(size_t)r * n + col0 + c] = buf[c * n + r];
+  cols_fft(buf, pitch, pitch, logn - 1, n, tw, -1);
+  for (int t = threadIdx.x; t < halfn * pitch; t += blockDim.x) {
+    const int k = t / pitch, s = t % pitch;
+    Cb[(size_t)k * n + gcol(s)] = buf[t];
   }
 }
 
-// pass 3: inverse row FFT and the update x = x* + Re(.) / n^2
+// pass 3: rebuild the row-pair spectra, inverse row FFT, x = x* + z / n^2
 template <typename T>
 __global__ void k_fft_rows_inv(int n, int logn, int rpc, const Cx<T>* __restrict__ C,
                                const T* xstar, T* x,
@@ -137,26 +328,30 @@ __global__ void k_fft_rows_inv(int n, int logn, int rpc, const Cx<T>* __restrict
   Cx<T>* tw = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* buf = tw + n / 2;
   for (int k = threadIdx.x; k < n / 2; k += blockDim.x) tw[k] = twg[k];
-  const int row0 = blockIdx.x * rpc;
+  const int k0 = blockIdx.x * rpc;
   const size_t plane = (size_t)n * n;
-  for (int t = threadIdx.x; t < rpc * n; t += blockDim.x) {
-    int r = t / n, j = t % n;
-    buf[r * n + bitrev(j, logn)] = C[(size_t)b * plane + (size_t)(row0 + r) * n + j];
-  }
+  const Cx<T>* Cb = C + (size_t)b * (plane / 2);
+  for (int t = threadIdx.x; t < rpc * n; t += blockDim.x) buf[t] = Cb[(size_t)k0 * n + t];
+  __syncthreads();
+  rows_join(buf, rpc, n);
+  __syncthreads();
+  rows_bitrev(buf, rpc, n, logn);
   __syncthreads();
   fft_stages(buf, n, logn, rpc, tw, -1);
   const T scale = T(1.0 / ((double)n * (double)n));
   for (int t = threadIdx.x; t < rpc * n; t += blockDim.x) {
-    int r = t / n, j = t % n;
-    size_t gi = (size_t)b * plane + (size_t)(row0 + r) * n + j;
-    T base = xstar ? xstar[gi] : T(0);
-    x[gi] = base + buf[t].x * scale;
+    const int r = t / n, j = t % n;
+    const size_t g = (size_t)b * plane + (size_t)(2 * (k0 + r)) * n + j;
+    const T b0 = xstar ? xstar[g] : T(0), b1 = xstar ? xstar[g + n] : T(0);
+    x[g] = b0 + buf[t].x * scale;
+    x[g + n] = b1 + buf[t].y * scale;
   }
 }
 
-// Whole filter of one right-hand side in shared memory (levels whose complex
-// n x n image fits): row FFTs, column FFTs, mask, inverse column FFTs,
-// inverse row FFTs, update.  One launch, h read once and x written once.
+// Whole filter of one right-hand side in shared memory (levels whose
+// row-pair layout, n/2 x n complex values, fits): row transforms, column
+// transforms, mask, inverse column and row transforms and the update in one
+// launch; h read once and x written once.
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_filter_fused(int n, int logn, const T* xstar, const T* __restrict__ h, T* x,
@@ -167,71 +362,38 @@ k_filter_fused(int n, int logn, const T* xstar, const T* __restrict__ h, T* x,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<T>* tw = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* buf = tw + n / 2;
-  const int nn = n * n, halfn = n / 2;
+  const int halfn = n / 2, nh = n * halfn;
   for (int k = threadIdx.x; k < halfn; k += blockDim.x) tw[k] = twg[k];
-  const size_t base = (size_t)b * nn;
-  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-    const int r = idx / n, c = idx % n;
-    buf[r * n + bitrev(c, logn)] = Cx<T>{h[base + idx], T(0)};
+  const size_t base = (size_t)b * n * n;
+  for (int idx = threadIdx.x; idx < nh; idx += blockDim.x) {
+    const int k = idx / n, c = idx % n;
+    const size_t g = base + (size_t)(2 * k) * n + c;
+    buf[k * n + bitrev(c, logn)] = Cx<T>{h[g], h[g + n]};
   }
   __syncthreads();
-  fft_stages(buf, n, logn, n, tw, +1);  // rows
-  // rows into bit-reversed order for the column transform
-  auto permute_rows = [&]() {
-    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-      const int r = idx / n, c = idx % n, rr = bitrev(r, logn);
-      if (r < rr) {
-        Cx<T> t = buf[r * n + c];
-        buf[r * n + c] = buf[rr * n + c];
-        buf[rr * n + c] = t;
-      }
-    }
-    __syncthreads();
-  };
-  auto col_stages = [&](int sign) {
-    for (int st = 1; st <= logn; ++st) {
-      const int half = 1 << (st - 1), tstride = n >> st;
-      for (int t = threadIdx.x; t < halfn * n; t += blockDim.x) {
-        const int c = t % n, k = t / n;
-        const int grp = k / half, pos = k % half;
-        const int i = (grp * 2 * half + pos) * n + c, j = i + half * n;
-        Cx<T> w = tw[pos * tstride];
-        if (sign < 0) w.y = -w.y;
-        const Cx<T> a = buf[i], bb = buf[j];
-        const Cx<T> p{w.x * bb.x - w.y * bb.y, w.x * bb.y + w.y * bb.x};
-        buf[i] = Cx<T>{a.x + p.x, a.y + p.y};
-        buf[j] = Cx<T>{a.x - p.x, a.y - p.y};
-      }
-      __syncthreads();
-    }
-  };
-  permute_rows();
-  col_stages(+1);
-  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-    const int k1 = idx / n, k2 = idx % n;
-    const int f1 = k1 < n - k1 ? k1 : n - k1, f2 = k2 < n - k2 ? k2 : n - k2;
-    const T m = (T)mtab[f1 > f2 ? f1 : f2];
-    buf[idx].x *= m;
-    buf[idx].y *= m;
-  }
+  fft_stages(buf, n, logn, halfn, tw, +1);
+  rows_split(buf, halfn, n);
   __syncthreads();
-  permute_rows();
-  col_stages(-1);
-  // columns of every row into bit-reversed order for the inverse row transform
-  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-    const int r = idx / n, c = idx % n, rc = bitrev(c, logn);
-    if (c < rc) {
-      Cx<T> t = buf[r * n + c];
-      buf[r * n + c] = buf[r * n + rc];
-      buf[r * n + rc] = t;
-    }
-  }
+  cols_bitrev(buf, n, n, halfn, logn - 1);
   __syncthreads();
-  fft_stages(buf, n, logn, n, tw, -1);
+  cols_fft(buf, n, n, logn - 1, n, tw, +1);
+  spectral_pairs(buf, n, halfn, FusedPairs{n}, n, tw, mtab);
+  __syncthreads();
+  cols_bitrev(buf, n, n, halfn, logn - 1);
+  __syncthreads();
+  cols_fft(buf, n, n, logn - 1, n, tw, -1);
+  rows_join(buf, halfn, n);
+  __syncthreads();
+  rows_bitrev(buf, halfn, n, logn);
+  __syncthreads();
+  fft_stages(buf, n, logn, halfn, tw, -1);
   const T scale = T(1.0 / ((double)n * (double)n));
-  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-    const T bv = xstar ? xstar[base + idx] : T(0);
-    x[base + idx] = bv + buf[idx].x * scale;
+  for (int idx = threadIdx.x; idx < nh; idx += blockDim.x) {
+    const int k = idx / n, c = idx % n;
+    const size_t g = base + (size_t)(2 * k) * n + c;
+    const T b0 = xstar ? xstar[g] : T(0), b1 = xstar ? xstar[g + n] : T(0);
+    x[g] = b0 + buf[idx].x * scale;
+    x[g + n] = b1 + buf[idx].y * scale;
   }
 }
 
@@ -264,38 +426,44 @@ template <typename T>
 void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
                      const T* twiddles, const double* mask_tab, const int* active,
                      cudaStream_t st, LaunchLog& log, int mode) {
-  const int logn = ilog2(n);
-  // sequences per block: about 64 KB of complex data
-  int per = (int)((64 * 1024) / (n * sizeof(Cx<T>)));
-  if (per < 1) per = 1;
-  if (per > n) per = n;
-  if (per > 32) per = 32;
-  while (n % per) --per;
+  const int logn = ilog2(n), halfn = n / 2;
   Cx<T>* C = reinterpret_cast<Cx<T>*>(cbuf);
   const Cx<T>* tw = reinterpret_cast<const Cx<T>*>(twiddles);
-  const size_t fused_sm = (size_t)(n / 2 + n * n) * sizeof(Cx<T>);
+  const double units = (double)n * n * log.active_hint;
+  const size_t fused_sm = (size_t)(halfn + (size_t)n * halfn) * sizeof(Cx<T>);
   if (fused_sm <= 160 * 1024 && mode != 0) {
     cudaFuncSetAttribute(k_filter_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_sm);
-    const int threads = n * n / 2 < 512 ? (n * n / 2 < 32 ? 32 : n * n / 2) : 512;
+    const int work = n * n / 4;
+    const int threads = work < 32 ? 32 : (work > 512 ? 512 : work);
     int pi_ = log.begin(K_FILTER, st);
     k_filter_fused<T><<<B, threads, fused_sm, st>>>(n, logn, xstar, h, x, tw, mask_tab, active);
-    log.end(pi_, st, (double)n * n * log.active_hint);
+    log.end(pi_, st, units);
     return;
   }
-  size_t sm = (size_t)(n / 2 + per * n) * sizeof(Cx<T>);
-  cudaFuncSetAttribute(k_fft_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_fft_cols_mask<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_fft_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  dim3 grid(n / per, B);
-  const double units = (double)n * n * log.active_hint;
+  // row pairs per block (rows passes) and column frequencies per block
+  // (column pass): about 64 KB of complex data per block
+  int per = (int)((64 * 1024) / (n * sizeof(Cx<T>)));
+  per = per < 1 ? 1 : (per > 32 ? 32 : per);
+  if (per > halfn) per = halfn;
+  while (halfn % per) --per;
+  int cpc = (int)((64 * 1024) / (n * sizeof(Cx<T>)));
+  cpc = cpc < 1 ? 1 : (cpc > 16 ? 16 : cpc);
+  if (cpc > halfn) cpc = halfn;
+  while (halfn % cpc) --cpc;
+  const size_t sm_rows = (size_t)(halfn + per * n) * sizeof(Cx<T>);
+  const size_t sm_cols = (size_t)(halfn + 2 * cpc * halfn) * sizeof(Cx<T>);
+  cudaFuncSetAttribute(k_fft_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rows);
+  cudaFuncSetAttribute(k_fft_cols_mask<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cols);
+  cudaFuncSetAttribute(k_fft_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_rows);
+  const dim3 grows(halfn / per, B), gcols(halfn / cpc, B);
   int pi_ = log.begin(K_FILTER, st);
-  k_fft_rows_fwd<T><<<grid, 256, sm, st>>>(n, logn, per, h, C, tw, active);
+  k_fft_rows_fwd<T><<<grows, 256, sm_rows, st>>>(n, logn, per, h, C, tw, active);
   log.end(pi_, st, units);
   pi_ = log.begin(K_FILTER, st);
-  k_fft_cols_mask<T><<<grid, 256, sm, st>>>(n, logn, per, C, tw, mask_tab, active);
+  k_fft_cols_mask<T><<<gcols, 256, sm_cols, st>>>(n, logn, cpc, C, tw, mask_tab, active);
   log.end(pi_, st, units);
   pi_ = log.begin(K_FILTER, st);
-  k_fft_rows_inv<T><<<grid, 256, sm, st>>>(n, logn, per, C, xstar, x, tw, active);
+  k_fft_rows_inv<T><<<grows, 256, sm_rows, st>>>(n, logn, per, C, xstar, x, tw, active);
   log.end(pi_, st, units);
 }
 

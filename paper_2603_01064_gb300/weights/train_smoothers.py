@@ -293,6 +293,13 @@ def nets_to_npz(nets, path, meta):
             g = net.gain if i == last else 1.0
             arrs[f"l{l}_w{i}"] = g * c.weight.detach().cpu().double().numpy()
             arrs[f"l{l}_b{i}"] = g * c.bias.detach().cpu().double().numpy()
+        # The output layer's bias adds a constant to h, and the cycle only
+        # uses F'(h): the mask is zero at zero frequency, so the constant
+        # never reaches the iterate.  Left in, it can grow far larger than
+        # the filtered part (it sets ||h|| / ||F'h||, the factor by which
+        # rounding in the smoother is amplified in the cycle's result), so
+        # it is dropped on export; the filtered cycle is unchanged.
+        arrs[f"l{l}_b{last}"] = np.zeros_like(arrs[f"l{l}_b{last}"])
     for k, v in meta.items():
         arrs["meta_" + k] = np.array(v)
     np.savez(path, **arrs)
