@@ -250,6 +250,50 @@ nmg_status nmg_coarse_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* y,
 nmg_status nmg_prolong_correct(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
                                const void* e, void* x);
 
+/* ---- residual step without device allocation ---------------------------
+ * The paper has no counterpart: this entry point serves callers that must
+ * not allocate device memory at call time.  nmg_residual above may grow the
+ * hierarchy's workspace with cudaMalloc the first time it sees a larger
+ * batch, and cudaMalloc / cudaFree can stall every stream on the device or
+ * fail outright in a process whose device memory has been reserved up front
+ * by a pooling allocator (a framework's caching allocator, a serving arena
+ * with a fixed, audited footprint).  Such callers use this variant.
+ *
+ * It computes exactly what nmg_residual computes, with the same kernels:
+ * r = y - A_l x on `level` for `batch` right-hand sides (vectors of the
+ * hierarchy's level type, device memory, x and y unchanged, r caller-owned)
+ * and, if norms is not NULL, ||r||_2 per right-hand side into the host
+ * array norms[batch] (the call then waits for the context's stream).
+ *
+ * Its scratch (per-tile partial sums of r^2, the norms before they are
+ * copied out, and the active flags) lives in one array of
+ * NMG_NOALLOC_SCRATCH_BYTES bytes compiled into the library, one per
+ * device.  The call allocates no device memory, calls no cudaMalloc or
+ * cudaFree, and is not recorded by the nmg_profile_* timing (which creates
+ * events); nmg_launch_count counts its launches.
+ *   - Size limit: the call needs 4 B per right-hand side for the flags,
+ *     8 B per right-hand side and residual tile for the partial sums and
+ *     8 B per right-hand side for the norms, each part rounded up to 256 B;
+ *     beyond NMG_NOALLOC_SCRATCH_BYTES it returns NMG_ERR_ARG before any
+ *     launch, and nmg_last_error states the bytes needed and the limit.
+ *     (At 512 x 512 with 64 x 64 residual tiles, 64 per image, that is
+ *     about 2,000 right-hand sides; nmg_autotune may pick other tiles.)
+ *   - Set-up: the first call on a device, with the context's device made
+ *     current, looks up the array's device address once; later calls reuse
+ *     it for the life of the process (a cudaDeviceReset of that device,
+ *     which also invalidates every context and hierarchy of this library,
+ *     ends its use).  Make that first call before any stream capture.
+ *   - Sharing: every call on a device uses the same array.  Each call writes
+ *     everything it reads back from it (nothing has to start at zero), but
+ *     calls whose work overlaps on the GPU (other streams, other contexts on
+ *     the same device, other host threads) race on the array and corrupt
+ *     each other's norms; serialise them.
+ * Errors: NMG_ERR_ARG (null pointers, level, batch, size limit),
+ * NMG_ERR_CUDA. */
+#define NMG_NOALLOC_SCRATCH_BYTES (1u << 20)
+nmg_status nmg_residual_noalloc(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                                const void* x, const void* y, void* r, double* norms);
+
 /* ---- inspection ------------------------------------------------------- */
 /* Level side length, band half-widths and precision. */
 nmg_status nmg_hier_info(const nmg_hier* h, int level, int* n, int* wK, int* wM,

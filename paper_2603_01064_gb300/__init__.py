@@ -18,6 +18,7 @@ import numpy as np
 __all__ = [
     "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
     "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo", "solve_multi", "Server",
+    "NOALLOC_SCRATCH_BYTES",
 ]
 
 FP64, FP32, BF16_REFINE, BF16FAST_REFINE = 0, 1, 2, 3
@@ -27,6 +28,7 @@ KERNEL_CLASSES = ["residual", "restrict", "cnn_first", "cnn_hidden", "cnn_last",
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE,
               "bf16fast_refine": BF16FAST_REFINE}
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
+NOALLOC_SCRATCH_BYTES = 1 << 20  # NMG_NOALLOC_SCRATCH_BYTES in nmg.h
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libnmg.so")
@@ -94,6 +96,7 @@ def lib():
         "nmg_cycle": (I, [P, P, I, P, P]),
         "nmg_residual": (I, [P, P, I, I, P, P, P, ctypes.POINTER(D)]),
         "nmg_residual_restrict": (I, [P, P, I, I, P, P, P]),
+        "nmg_residual_noalloc": (I, [P, P, I, I, P, P, P, ctypes.POINTER(D)]),
         "nmg_smooth": (I, [P, P, I, I, P, P]),
         "nmg_filter_update": (I, [P, P, I, I, P, P, P]),
         "nmg_coarse_solve": (I, [P, P, I, P, P]),
@@ -264,6 +267,16 @@ class Hierarchy:
         out = (ctypes.c_double * max(B, 1))() if norms else None
         self.ctx.check(lib().nmg_residual(self.ctx._h, self._h, level, B, _ptr(x), _ptr(y),
                                           _ptr(r), out))
+        return np.array(out[:B]) if norms else None
+
+    def residual_noalloc(self, level, x, y, r, norms=False):
+        """nmg_residual with its scratch in the library's fixed array: no
+        device allocation (limit NOALLOC_SCRATCH_BYTES; calls that overlap
+        on the device race on the shared array)."""
+        B = x.shape[0]
+        out = (ctypes.c_double * max(B, 1))() if norms else None
+        self.ctx.check(lib().nmg_residual_noalloc(self.ctx._h, self._h, level, B, _ptr(x),
+                                                  _ptr(y), _ptr(r), out))
         return np.array(out[:B]) if norms else None
 
     def residual_restrict(self, level, x, y, yc):

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1849,3 +1850,112 @@ void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const 
                     h->ctx->log, d.ref_tile);
 }
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// nmg_residual_noalloc: the residual step with its scratch in a fixed array
+// compiled into the library (for callers that must not allocate device
+// memory at call time; the contract is stated in the public header).
+// ---------------------------------------------------------------------------
+
+// One per device: [active flags | per-tile partial sums | norms], each part
+// starting on a 256-byte boundary.  Every call writes what it reads back.
+static __device__ __align__(256) unsigned char nmg_noalloc_scratch[NMG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoallocMaxDevices] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of this device's copy of the array, looked up once per
+// device with that device current (the caller has made it current).
+nmg_status noalloc_base(nmg_ctx* ctx, unsigned char** out) {
+  if (ctx->device < 0 || ctx->device >= kNoallocMaxDevices)
+    return fail(ctx, NMG_ERR_ARG, "nmg_residual_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[ctx->device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, nmg_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return cuda_fail(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                       "nmg_residual_noalloc: cudaGetSymbolAddress(scratch)");
+    g_noalloc_base[ctx->device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_base[ctx->device]);
+  return NMG_OK;
+}
+
+__global__ void k_noalloc_ones(int* flags, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flags[i] = 1;
+}
+
+template <typename T>
+int noalloc_tiles(nmg_hier* h, int l) {
+  return h->dim == 2 ? residual2d_tiles<T>(band<T>(h, l), h->lv[l].res_tile)
+                     : residual1d_tiles(h->lv[l].n);
+}
+
+}  // namespace
+
+extern "C" nmg_status nmg_residual_noalloc(nmg_ctx* ctx, nmg_hier* h, int level, int batch,
+                                           const void* x, const void* y, void* r,
+                                           double* norms) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (level < 0 || level > h->L - 1) return fail(ctx, NMG_ERR_ARG, "level out of range");
+  if (batch == 0) return NMG_OK;
+  if (!x || !r) return fail(ctx, NMG_ERR_ARG, "null x or r");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  const bool f64 = h->precision == NMG_FP64;
+  const int nt = f64 ? noalloc_tiles<double>(h, level) : noalloc_tiles<float>(h, level);
+  const size_t off_part = round256((size_t)batch * sizeof(int));
+  const size_t off_norm = off_part + round256((size_t)batch * nt * sizeof(double));
+  const size_t need = off_norm + round256((size_t)batch * sizeof(double));
+  if (need > NMG_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, NMG_ERR_ARG,
+                "nmg_residual_noalloc: " + std::to_string(batch) + " right-hand sides x " +
+                    std::to_string(nt) + " residual tiles need " + std::to_string(need) +
+                    " bytes of scratch; the fixed array holds " +
+                    std::to_string((size_t)NMG_NOALLOC_SCRATCH_BYTES));
+  unsigned char* base = nullptr;
+  if ((s = noalloc_base(ctx, &base)) != NMG_OK) return s;
+  int* active = reinterpret_cast<int*>(base);
+  double* part = reinterpret_cast<double*>(base + off_part);
+  double* nrm = reinterpret_cast<double*>(base + off_norm);
+  // a private, non-recording log: profiling would create events
+  LaunchLog quiet;
+  quiet.active_hint = batch;
+  k_noalloc_ones<<<ceil_div(batch, 256), 256, 0, ctx->stream>>>(active, batch);
+  ++quiet.launches;
+  int launched_nt = 0;  // equals nt: both come from the launchers' tile choice
+  if (h->dim == 2) {
+    if (f64)
+      launch_residual2d<double>(band<double>(h, level), batch, (const double*)x, (const double*)y,
+                                (double*)r, part, &launched_nt, active, ctx->stream, quiet,
+                                h->lv[level].res_tile);
+    else
+      launch_residual2d<float>(band<float>(h, level), batch, (const float*)x, (const float*)y,
+                               (float*)r, part, &launched_nt, active, ctx->stream, quiet,
+                               h->lv[level].res_tile);
+  } else {
+    if (f64)
+      launch_residual1d<double>(h->lv[level].n, Ad<double>(h->lv[level]), batch, (const double*)x,
+                                (const double*)y, (double*)r, part, &launched_nt, active,
+                                ctx->stream, quiet);
+    else
+      launch_residual1d<float>(h->lv[level].n, Ad<float>(h->lv[level]), batch, (const float*)x,
+                               (const float*)y, (float*)r, part, &launched_nt, active, ctx->stream,
+                               quiet);
+  }
+  if (norms) launch_norms(part, nt, batch, nrm, active, ctx->stream, quiet);
+  ctx->log.launches += quiet.launches;
+  CK(cudaGetLastError());
+  if (norms) {
+    CK(cudaMemcpyAsync(norms, nrm, batch * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return NMG_OK;
+}

@@ -406,6 +406,14 @@ void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
   log.end(pi_, st, (double)op.n * op.n * log.active_hint);
 }
 
+// Partial sums launch_residual2d writes per right-hand side (one per tile),
+// for a caller that has to size their buffer before the launch.
+template <typename T>
+int residual2d_tiles(const Band2D<T>& op, int tile_req) {
+  const int tx = ceil_div(op.n, pick_tile<T>(op.n, op.wK, op.wM, false, tile_req));
+  return tx * tx;
+}
+
 template <typename T>
 void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T* y, T* yc,
                                 double* partials, int* ntiles, const int* active,
@@ -443,6 +451,10 @@ void launch_residual1d(int n, const T* A, int B, const T* x, const T* y, T* r,
   if (ntiles) *ntiles = grid.x;
   log.end(pi_, st, (double)n * log.active_hint);
 }
+
+// Partial sums launch_residual1d writes per right-hand side: one per block
+// of 8 rows (its grid).
+int residual1d_tiles(int n) { return ceil_div(n, 8); }
 
 template <typename T>
 void launch_restrict1d(int n, int B, const T* r, T* yc, double* partials, int* ntiles,
@@ -519,6 +531,7 @@ void launch_update_f64(long long len, int B, const float* d, double* u, const in
 #define NMG_INST(T)                                                                          \
   template void launch_residual2d<T>(const Band2D<T>&, int, const T*, const T*, T*, double*, \
                                      int*, const int*, cudaStream_t, LaunchLog&, int);       \
+  template int residual2d_tiles<T>(const Band2D<T>&, int);                                   \
   template void launch_residual_restrict2d<T>(const Band2D<T>&, int, const T*, const T*,     \
                                               T*, double*, int*, const int*, cudaStream_t,   \
                                               LaunchLog&, int);                              \

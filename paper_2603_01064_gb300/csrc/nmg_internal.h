@@ -125,6 +125,10 @@ template <typename T>
 void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
                        LaunchLog& log, int tile_req = 0);
+// number of partial sums per right-hand side the two residual launchers write
+template <typename T>
+int residual2d_tiles(const Band2D<T>& op, int tile_req);
+int residual1d_tiles(int n);
 // yc = R (y - A x) on a 2D level (+ partial sums of yc^2)
 template <typename T>
 void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T* y, T* yc,
