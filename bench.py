@@ -10,7 +10,7 @@ right-hand side meets the tolerance.  Inputs are resident in HBM when the
 timed region starts; L2 is flushed (a 256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision bf16_refine|bf16fast_refine|fp32]
+                  [--precision bf16_refine|bf16fast_refine|fp16_refine|fp32]
 
 The headline is the bf16 refinement form solving the whole batch at once;
 the same run also times, on the same GPU and right-hand sides, the fp32
@@ -53,9 +53,13 @@ PRECISION_TEXT = {
                    "fp32 cycle vectors, compensated-fp32 outer residual, fp64 update and coarse solve",
     "bf16fast_refine": "bf16 tensor-core smoother (one bf16 per operand, fp32 accumulation), fp32 "
                        "cycle vectors, compensated-fp32 outer residual, fp64 update and coarse solve",
+    "fp16_refine": "fp16 tensor-core smoother with split hi+lo fp16 operands (power-of-two scaled "
+                   "network) and fp32 accumulation, fp32 cycle vectors, compensated-fp32 outer "
+                   "residual, fp64 update and coarse solve",
     "fp32": "fp32 throughout (SIMT smoother), fp64 coarse solve",
 }
-DTYPE = {"bf16_refine": "bf16x2+f32+f64", "bf16fast_refine": "bf16+f32+f64", "fp32": "f32"}
+DTYPE = {"bf16_refine": "bf16x2+f32+f64", "bf16fast_refine": "bf16+f32+f64",
+         "fp16_refine": "f16x2+f32+f64", "fp32": "f32"}
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x fp32 lanes x FMA x max clock
 FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_last": 2 * 9 * 32}
@@ -65,6 +69,7 @@ MMA_FLOPS_PER_PX = {
     # split form: two A operands (hi, lo) x N = 64 ([w_hi | w_lo]) per tap and K half
     "bf16_refine": {"cnn_hidden": 2 * 2 * 9 * 32 * 64},
     "bf16fast_refine": {"cnn_hidden": 2 * 9 * 32 * 32},
+    "fp16_refine": {"cnn_hidden": 2 * 2 * 9 * 32 * 64},
 }
 
 
@@ -340,7 +345,7 @@ def run_ours(args, wl, world, rank, local):
     compare = {}
     if not args.no_compare:
         f32 = torch.zeros(f.shape, dtype=torch.float32, device="cuda")
-        for p in ["fp32", "bf16fast_refine", "bf16_refine"]:
+        for p in ["fp32", "bf16fast_refine", "bf16_refine", "fp16_refine"]:
             if p == prec:
                 continue
             Gp = hier(p)

@@ -32,10 +32,10 @@
  *      NMG_FP64          f, u, every level vector: double
  *      NMG_FP32          f, u, every level vector: float
  *      NMG_BF16_REFINE,
- *      NMG_BF16FAST_REFINE
- *                        f: float, u: double; level vectors of the inner
+ *      NMG_BF16FAST_REFINE,
+ *      NMG_FP16_REFINE   f: float, u: double; level vectors of the inner
  *                        cycle (step entry points): float.  The smoother
- *                        runs on bf16 tensor cores with fp32 accumulation.
+ *                        runs on 16-bit tensor cores with fp32 accumulation.
  */
 #ifndef NMG_H
 #define NMG_H
@@ -63,22 +63,29 @@ typedef enum {
 /* per right-hand-side outcome, in nmg_solve_info.status */
 enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };
 
-/* Precision forms.  The two bf16 forms run the cycle as an inner solve of
+/* Precision forms.  The refinement forms run the cycle as an inner solve of
  * an outer iterative refinement (residual in compensated fp32, update in
- * fp64) with the smoother on bf16 tensor cores and fp32 accumulation:
- *   NMG_BF16_REFINE      every smoother operand is a pair of bf16 values
- *                        (hi + lo), 2-3 MMAs per product; per-cycle
- *                        iterates agree with fp64 to about 1e-4.
+ * fp64) with the smoother's hidden layers on 16-bit tensor cores and fp32
+ * accumulation:
+ *   NMG_BF16_REFINE      every hidden-layer operand is a pair of bf16
+ *                        values (hi + lo, 2^-16 relative), 2 MMAs per
+ *                        product; per-cycle iterates agree with fp64 to
+ *                        1e-4..1e-3 depending on how strongly the trained
+ *                        smoother amplifies rounding.
  *   NMG_BF16FAST_REFINE  one bf16 value per operand, 1 MMA per product;
  *                        the cycle converges at the same rate but single
- *                        cycles differ from fp64 by up to ~20%, because the
- *                        smoother's output carries a large near-constant
- *                        part that the output filter removes. */
+ *                        cycles differ from fp64 by percents.
+ *   NMG_FP16_REFINE      as NMG_BF16_REFINE with fp16 pairs (2^-22
+ *                        relative) at the same cost; the network runs on
+ *                        power-of-two-scaled values to stay inside fp16's
+ *                        range (activations above 65504 are clamped).
+ * All three take f: float, u: double, like NMG_BF16_REFINE above. */
 typedef enum {
   NMG_FP64 = 0,
   NMG_FP32 = 1,
   NMG_BF16_REFINE = 2,
-  NMG_BF16FAST_REFINE = 3
+  NMG_BF16FAST_REFINE = 3,
+  NMG_FP16_REFINE = 4
 } nmg_precision;
 
 /*

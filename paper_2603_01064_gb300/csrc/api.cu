@@ -157,7 +157,8 @@ nmg_status cuda_fail(nmg_ctx* c, cudaError_t e, const char* where) {
 
 size_t elem_size(int precision) { return precision == NMG_FP64 ? 8 : 4; }
 bool is_refine(int precision) {
-  return precision == NMG_BF16_REFINE || precision == NMG_BF16FAST_REFINE;
+  return precision == NMG_BF16_REFINE || precision == NMG_BF16FAST_REFINE ||
+         precision == NMG_FP16_REFINE;
 }
 
 size_t plane(const nmg_hier* h, int l) {
@@ -827,7 +828,7 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
                      nmg_hier** out) {
   if (!ctx || !op || !out) return fail(ctx, NMG_ERR_ARG, "null argument to nmg_setup");
   *out = nullptr;
-  if (op->precision < NMG_FP64 || op->precision > NMG_BF16FAST_REFINE)
+  if (op->precision < NMG_FP64 || op->precision > NMG_FP16_REFINE)
     return fail(ctx, NMG_ERR_ARG, "unknown precision");
   if (is_refine(op->precision) && op->dim != 2)
     return fail(ctx, NMG_ERR_UNSUPPORTED, "the bf16 refinement form is 2D only");
@@ -944,7 +945,10 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
           bp.push_back(base + o);
           o += cout;
         }
-        d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp, h->precision == NMG_BF16_REFINE ? 1 : 0);
+        const int split = h->precision == NMG_BF16_REFINE   ? 1
+                          : h->precision == NMG_FP16_REFINE ? 2
+                                                            : 0;
+        d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp, split);
         if (!d.bf16_pack) st = fail(ctx, NMG_ERR_UNSUPPORTED, "bf16 tensor-core smoother unavailable");
         else h->allocs.push_back(d.bf16_pack);
       }

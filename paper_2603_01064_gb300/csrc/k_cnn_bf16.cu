@@ -35,7 +35,18 @@
 // MMAs a_hi*w_hi + a_lo*w_hi (+ a_hi*w_lo when the weights are not
 // bf16-exact), accumulated in fp32.  The SIMT layers read and write the
 // pairs and compute in fp32.
+//
+// fp16 split form (SPLIT = 2): the same [hi | lo] pairs and MMAs with fp16
+// operands (11-bit significands: hi + lo carries 2^-22 instead of 2^-16).
+// fp16's range is narrow, so the network runs on sigma-scaled values: the
+// input b / ||b|| (RMS 1/n on an n x n level) is multiplied by sigma =
+// max(1, n/4), every bias by sigma, and the output by 1/sigma.  ReLU is
+// positively homogeneous and sigma is a power of two, so the scaling is
+// exact; hidden activations then have RMS between about 0.25 and 10, and
+// values above fp16's largest finite value are clamped to it rather than
+// becoming infinite.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 #include <cstring>
@@ -94,10 +105,18 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// instruction descriptor, kind::f16: bf16 A and B, fp32 D, both K-major
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+// instruction descriptor, kind::f16: bf16 (f16 = false) or fp16 A and B
+// (format fields 0 = f16, 1 = bf16), fp32 D, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, bool f16 = false) {
+  return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// scale of the fp16 split form's network values on an n x n level (see the
+// header comment); 1 for the bf16 forms
+template <int SPLIT>
+__host__ __device__ __forceinline__ float net_scale(int n) {
+  return SPLIT == 2 ? (float)(n >= 4 ? n / 4 : 1) : 1.f;
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -163,12 +182,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// write 32 channel values of one pixel as bf16 (SPLIT: hi block then lo block)
+// write 32 channel values (>= 0: post-ReLU) of one pixel as 16-bit values:
+// bf16 (SPLIT 0, 1) or fp16 (SPLIT 2); split forms: hi block then lo block
 template <int SPLIT>
 __device__ __forceinline__ void store_channels(__nv_bfloat16* dst_px, const float* a) {
   uint32_t pk[16], pl[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
+    if (SPLIT == 2) {
+      const float a0 = fminf(a[2 * c], 65504.f), a1 = fminf(a[2 * c + 1], 65504.f);
+      __half2 h2 = __floats2half2_rn(a0, a1);
+      pk[c] = *reinterpret_cast<uint32_t*>(&h2);
+      __half2 l2 = __floats2half2_rn(a0 - __low2float(h2), a1 - __high2float(h2));
+      pl[c] = *reinterpret_cast<uint32_t*>(&l2);
+      continue;
+    }
     __nv_bfloat162 h2 = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
     pk[c] = *reinterpret_cast<uint32_t*>(&h2);
     if (SPLIT) {
@@ -214,7 +242,8 @@ __device__ __forceinline__ void warp_store_pixels(unsigned char* stg, int lane, 
 }
 
 // ---------------------------------------------------------------------------
-// first layer 1 -> 32 (fp32 SIMT): a = ReLU(b1 + W1 * (b / s)), stored bf16
+// first layer 1 -> 32 (fp32 SIMT): a = ReLU(b1 + W1 * (b / s)), stored as
+// 16-bit values (fp16 split form: a = ReLU(sigma b1 + W1 * (sigma b / s)))
 // ---------------------------------------------------------------------------
 template <int SPLIT>
 __global__ void __launch_bounds__(256)
@@ -231,10 +260,11 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   __shared__ float bs[WIDTH];
   const int tid = threadIdx.x;
   for (int i = tid; i < WIDTH * 9; i += 256) ws[i] = lp.wf[i];
-  if (tid < WIDTH) bs[tid] = lp.bias[tid];
+  const float sig = net_scale<SPLIT>(n);
+  if (tid < WIDTH) bs[tid] = sig * lp.bias[tid];
   const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
   const size_t plane = (size_t)n * n;
-  const float inv = (float)(1.0 / s);
+  const float inv = (float)((double)sig / s);
   const float* bb = bsrc + (size_t)b * plane;
   for (int i = tid; i < RH * RW; i += 256) {
     int ry = i / RW, rx = i % RW;
@@ -331,7 +361,7 @@ k_last_simt(int n, const __nv_bfloat16* __restrict__ ain, float* __restrict__ ho
 template <int SPLIT, int PITCH>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base, uint32_t d0) {
   constexpr int N = NB<SPLIT>::value;
-  constexpr uint32_t idesc = make_idesc(128, N);
+  constexpr uint32_t idesc = make_idesc(128, N, SPLIT == 2);
   const uint64_t ad0 = make_desc(a_base, PITCH, RW * 16);
   const uint64_t bd0 = make_desc(b_base, N * 16, 128);
 #pragma unroll
@@ -357,9 +387,9 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
 // written as fp32 planes g[tap][pixel] (plane stride gstride).
 template <int SPLIT, int FUSE>
 __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bias,
-                                             __nv_bfloat16* dst, float* gdst, size_t gstride,
-                                             const float* __restrict__ w4, bool store,
-                                             unsigned char* stg, int lane) {
+                                             float bscale, __nv_bfloat16* dst, float* gdst,
+                                             size_t gstride, const float* __restrict__ w4,
+                                             bool store, unsigned char* stg, int lane) {
   float v[32];
   tmem_ld32(taddr, v);
   if (SPLIT) {
@@ -369,7 +399,7 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
     for (int c = 0; c < 32; ++c) v[c] += w[c];
   }
 #pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias[c], 0.f);
+  for (int c = 0; c < 32; ++c) v[c] = fmaxf(fmaf(bscale, bias[c], v[c]), 0.f);
   if (!FUSE) {
     warp_store_pixels<SPLIT>(stg, lane, v, store ? dst : nullptr);  // warp-collective
     return;
@@ -487,7 +517,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       const size_t pix = (size_t)b * plane + (size_t)y * n + x;
       finish_pixel<SPLIT, FUSE>(
           tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, lp.bias,
-          in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
+          net_scale<SPLIT>(n), in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
           Bs + B_BYTES + warp * STG_WARP, lane);
     }
   };
@@ -699,7 +729,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const size_t pix = (size_t)b * plane + (size_t)y * n + x;
         finish_pixel<SPLIT, FUSE>(
             tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value, lp.bias,
-            in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
+            net_scale<SPLIT>(n), in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
             Bs + B_BYTES + (warp - 2) * STG_WARP, lane);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -761,10 +791,12 @@ const CUtensorMap* act_map(const void* ptr, int n, int nimg, int cw) {
 }
 
 // last layer from the fused partial sums: h[p] = s (b4 + sum_tap g[tap][p + off(tap)])
-// with zero padding outside the image
+// with zero padding outside the image; fp16 split form (g carries the
+// network scale sigma): h = (s / sigma) (sigma b4 + sum_tap g), bscale = sigma
 __global__ void __launch_bounds__(256)
 k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ hout,
-              float bias0, const double* __restrict__ snorm, const int* __restrict__ active) {
+              float bias0, float bscale, const double* __restrict__ snorm,
+              const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
   const double s = snorm[b];
@@ -773,7 +805,7 @@ k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ 
     float acc = 0.f;
     if (s != 0.0) {
       const int y = p / n, x = p % n;
-      acc = bias0;
+      acc = bscale * bias0;
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
@@ -781,6 +813,7 @@ k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ 
           acc += g[t * gstride + (size_t)b * plane + (size_t)yy * n + xx];
       }
       acc *= (float)s;
+      acc *= 1.f / bscale;  // a power of two: exact
     }
     hout[(size_t)b * plane + p] = acc;
   }
@@ -792,6 +825,19 @@ uint16_t bf16_bits(float f) {
   std::memcpy(&u, &f, 4);
   u += 0x7FFFu + ((u >> 16) & 1u);
   return (uint16_t)(u >> 16);
+}
+
+// host fp16 round-to-nearest (CUDA's conversion) and its value
+uint16_t f16_bits(float f) {
+  const __half h = __float2half_rn(f);
+  uint16_t b;
+  std::memcpy(&b, &h, 2);
+  return b;
+}
+float f16_value(uint16_t b) {
+  __half h;
+  std::memcpy(&h, &b, 2);
+  return __half2float(h);
 }
 
 int g_num_sms = 0;
@@ -873,7 +919,7 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   if (L4.bias_host_valid) bias0 = L4.bias0;
   pi_ = log.begin(K_CNN_LAST, st);
   k_last_gather<<<dim3(ceil_div(n * n, 256) < 64 ? ceil_div(n * n, 256) : 64, B), 256, 0, st>>>(
-      n, map_imgs, reinterpret_cast<const float*>(nxt), h, bias0, s, active);
+      n, map_imgs, reinterpret_cast<const float*>(nxt), h, bias0, net_scale<SPLIT>(n), s, active);
   log.end(pi_, st, units);
 }
 
@@ -883,7 +929,7 @@ std::vector<std::pair<const void*, Bf16Pack>> g_headers;
 
 // Build the device weight pack of one smoother level from PyTorch-layout
 // fp64 weights (width 32, 3x3, at least 3 layers).  split = 1: the split
-// bf16 form; 0: plain bf16.  Returns one device allocation holding packed
+// bf16 form; 2: the split fp16 form; 0: plain bf16.  Returns one device allocation holding packed
 // weights and biases; the per-layer device pointers are kept in a host
 // table keyed by it.
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
@@ -903,8 +949,8 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
       std::vector<float> f(WIDTH * 9, 0.f);
       for (int c = 0; c < WIDTH; ++c)
         for (int t = 0; t < 9; ++t) f[c * 9 + t] = (float)w[c * 9 + t];
-      wl[li].resize(f.size() * sizeof(float));
-      std::memcpy(wl[li].data(), f.data(), wl[li].size());
+      wl[li].assign(reinterpret_cast<const unsigned char*>(f.data()),
+                    reinterpret_cast<const unsigned char*>(f.data() + f.size()));
       continue;
     }
     const int N = split ? 2 * WIDTH : WIDTH;
@@ -913,14 +959,21 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
       for (int ci = 0; ci < cin; ++ci)
         for (int tap = 0; tap < 9; ++tap) {
           const double v = w[((size_t)co * cin + ci) * 9 + tap];
-          const uint16_t hb = bf16_bits((float)v);
-          uint32_t u = (uint32_t)hb << 16;
+          uint16_t hb;
           float hf;
-          std::memcpy(&hf, &u, 4);
+          if (split == 2) {
+            hb = f16_bits((float)v);
+            hf = f16_value(hb);
+          } else {
+            hb = bf16_bits((float)v);
+            uint32_t u = (uint32_t)hb << 16;
+            std::memcpy(&hf, &u, 4);
+          }
           const size_t row = ((size_t)tap * 4 + ci / 8) * N;
           p[(row + co) * 8 + ci % 8] = hb;
           if (split) {
-            const uint16_t lb = bf16_bits((float)(v - (double)hf));
+            const float rest = (float)(v - (double)hf);
+            const uint16_t lb = split == 2 ? f16_bits(rest) : bf16_bits(rest);
             p[(row + WIDTH + co) * 8 + ci % 8] = lb;
             if (lb != 0 && lb != 0x8000) has_lo[li] = 1;
           }
@@ -982,7 +1035,9 @@ void bf16_cnn_launch(int n, int B, int map_imgs, int layers, const void* pack, c
   if (!P) return;
   __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(act0);
   __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(act1);
-  if (P->split)
+  if (P->split == 2)
+    run_layers<2>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
+  else if (P->split)
     run_layers<1>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
   else
     run_layers<0>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);

@@ -6,6 +6,10 @@ fp32 outer residual, fp64 update) against the FP64 oracle.
   iterate bar is 1e-3 (norm-wise relative), also for trained smoothers on
   the first cycle from zero, where the smoother's large filtered-out
   near-constant output makes single-rounding bf16 fail.
+* fp16_refine (split operands in fp16, power-of-two-scaled network): the
+  smoother against FP64 at 1e-5 (hi + lo fp16 carries 2^-22 relative; the
+  scaling is exact), one refinement step and the first trained cycles at
+  1e-4.
 * bf16fast_refine (one bf16 per operand): compared with a CPU evaluation of
   the same network that rounds to bf16 exactly where the kernels store bf16
   (hidden activations, hidden-layer weights) and accumulates in fp64: the
@@ -102,7 +106,10 @@ def test_fast_smoother_matches_bf16_emulation(ctx):
         assert rel(h, emulated_fast(W[l], b32)) < 1e-3, l
 
 
-@pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine"])
+SPLIT_TOL = {"bf16_refine": 1e-4, "fp16_refine": 1e-5}
+
+
+@pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine", "fp16_refine"])
 def test_smoother_small_level_and_zero_rhs(ctx, prec):
     """An 8x8 level (smaller than the 16x16 tile) and a zero right-hand side."""
     H, G, W = make(ctx, prec, n=64, levels=5, sigma=1.0)
@@ -113,21 +120,26 @@ def test_smoother_small_level_and_zero_rhs(ctx, prec):
     if prec == "bf16fast_refine":
         assert rel(h[:1], emulated_fast(W[3], b32[:1])) < 1e-3
     else:
-        assert rel(h[:1], O.smoother(W[3], b32[:1])) < 1e-4
+        assert rel(h[:1], O.smoother(W[3], b32[:1])) < SPLIT_TOL[prec]
 
 
-def test_split_smoother_matches_fp64(ctx):
-    H, G, W = make(ctx, "bf16_refine")
+@pytest.mark.parametrize("prec", ["bf16_refine", "fp16_refine"])
+def test_split_smoother_matches_fp64(ctx, prec):
+    H, G, W = make(ctx, prec)
     rng = np.random.default_rng(3)
     for l in range(H.levels - 1):
         m = H.size(l)
         b = rng.standard_normal((3, m, m)) * np.array([1.0, 1e-4, 30.0])[:, None, None]
         b32, h = smooth_gpu(G, l, b)
-        assert rel(h, O.smoother(W[l], b32)) < 1e-4, l
+        assert rel(h, O.smoother(W[l], b32)) < SPLIT_TOL[prec], l
 
 
-def test_refine_step_matches_fp64_cycle(ctx):
-    H, G, W = make(ctx, "bf16_refine")
+CYCLE_TOL = {"bf16_refine": 1e-3, "fp16_refine": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["bf16_refine", "fp16_refine"])
+def test_refine_step_matches_fp64_cycle(ctx, prec):
+    H, G, W = make(ctx, prec)
     rng = np.random.default_rng(4)
     f = rng.standard_normal((4, 64, 64))
     u0 = 0.05 * rng.standard_normal((4, 64, 64))
@@ -137,7 +149,7 @@ def test_refine_step_matches_fp64_cycle(ctx):
     ud = torch.tensor(u0, dtype=torch.float64, device="cuda")
     G.cycle(fd, ud)
     torch.cuda.synchronize()
-    assert rel(ud.cpu().numpy(), O.nmgf(H, W, 0, u0, f32)) < 1e-3
+    assert rel(ud.cpu().numpy(), O.nmgf(H, W, 0, u0, f32)) < CYCLE_TOL[prec]
 
 
 @pytest.fixture(scope="module")
@@ -147,11 +159,12 @@ def c2w():
     return nmg.load_weights(C2W)
 
 
-def test_trained_first_cycles_match_fp64(ctx, c2w):
+@pytest.mark.parametrize("prec", ["bf16_refine", "fp16_refine"])
+def test_trained_first_cycles_match_fp64(ctx, c2w, prec):
     """Per-cycle iterate parity with trained smoothers on the 128x128 operator:
     cycles 1..4 from the GPU's own previous iterate, each against one oracle
     cycle from the same state."""
-    H, G, _ = make(ctx, "bf16_refine", n=128, levels=5, weights=c2w)
+    H, G, _ = make(ctx, prec, n=128, levels=5, weights=c2w)
     f, _ = I.rhs_2d_ellipses_grf(128, 3, seed=5, sigma=2.0)
     fd = torch.tensor(f, dtype=torch.float32, device="cuda")
     f32 = fd.double().cpu().numpy()
@@ -160,10 +173,10 @@ def test_trained_first_cycles_match_fp64(ctx, c2w):
         up = ud.cpu().numpy().copy()
         G.cycle(fd, ud)
         torch.cuda.synchronize()
-        assert rel(ud.cpu().numpy(), O.nmgf(H, c2w, 0, up, f32)) < 1e-3
+        assert rel(ud.cpu().numpy(), O.nmgf(H, c2w, 0, up, f32)) < CYCLE_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine"])
+@pytest.mark.parametrize("prec", ["bf16_refine", "bf16fast_refine", "fp16_refine"])
 def test_refine_solve_trained_c2_reaches_tolerance(ctx, c2w, prec):
     H, G, _ = make(ctx, prec, n=128, levels=5, sigma=2.0, alpha=1e-2, weights=c2w)
     f, _ = I.rhs_2d_ellipses_grf(128, 8, seed=77, sigma=2.0)

@@ -10,8 +10,9 @@ sides are checked against the FP64 oracle one by one.
   of the batch whose sampled results meet 1e-6 under the oracle's own apply.
 * 2D BTTB 512x512, sigma 4 px, 7 levels, 64 right-hand sides, alpha in
   {1e-1, 1e-2, 1e-3, 1e-4}: one cycle of the whole batch (autotuned launch
-  shapes) against the oracle for sampled items; full solves for the alphas
-  whose trained CNN smoothers converge (1e-1, 1e-2).
+  shapes) in the bf16 and fp16 split refinement forms against the oracle
+  for sampled items; full solves for the alphas whose trained CNN smoothers
+  converge (1e-1, 1e-2).
 """
 import os
 
@@ -125,7 +126,9 @@ _A3 = pytest.mark.xfail(reason="hi+lo bf16 activations: 1.04e-3 at alpha 1e-3", 
 
 @pytest.mark.parametrize("alpha,prec,tol", [(1e-1, "bf16_refine", 1e-3), (1e-2, "bf16_refine", 1e-3),
                                             pytest.param(1e-3, "bf16_refine", 1e-3, marks=_A3),
-                                            (1e-4, "bf16_refine", 1e-3), (1e-2, "fp32", 1e-4)])
+                                            (1e-4, "bf16_refine", 1e-3), (1e-2, "fp32", 1e-4),
+                                            (1e-1, "fp16_refine", 1e-3), (1e-2, "fp16_refine", 1e-3),
+                                            (1e-3, "fp16_refine", 1e-3), (1e-4, "fp16_refine", 1e-3)])
 def test_512_full_batch_one_cycle_sampled(ctx, c3f, alpha, prec, tol):
     W = nmg.load_weights(os.path.join(WDIR, f"c3_2d_n512_s4_a{alpha:.0e}".replace("e-0", "e-") + ".npz"))
     taps = I.gaussian_taps(4.0)
