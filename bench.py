@@ -234,6 +234,8 @@ def run_ours(args, wl, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     ctx = nmg.Context(local, stream=stream.cuda_stream)
+    if args.no_graphs:
+        ctx.set_graphs(False)
     W = nmg.load_weights(os.path.join(WEIGHTS, wl["weights"]))
     taps = I.gaussian_taps(wl["sigma"])
     prec = args.precision
@@ -429,6 +431,9 @@ def main():
     ap.add_argument("--ncu", action="store_true", help="a single solve, nothing else (profiling)")
     ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel eagerly instead of replaying captured iterations "
+                         "(profiler launch lists)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     wl = WORKLOADS[args.workload]
