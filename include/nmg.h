@@ -21,6 +21,8 @@
  *    work is ordered on the context's stream.  Functions that report values
  *    to the host (nmg_solve's info, norms) synchronise that stream before
  *    they return; the others are asynchronous.
+ *  - A batch holds 0 .. NMG_MAX_BATCH right-hand sides (larger batches:
+ *    NMG_ERR_ARG).
  *  - The caller owns every pointer it passes.  The library owns contexts,
  *    hierarchies and their workspaces until the matching destroy call.
  *  - Layouts are row-major: a batch of 2D grids is [batch][n][n], a batch
@@ -59,6 +61,9 @@ typedef enum {
   NMG_ERR_WEIGHTS = -6,    /* smoother weights inconsistent with the desc */
   NMG_ERR_UNSUPPORTED = -7 /* valid request this build does not implement */
 } nmg_status;
+
+/* largest batch of one call (one grid row of blocks per right-hand side) */
+#define NMG_MAX_BATCH 65535
 
 /* per right-hand-side outcome, in nmg_solve_info.status */
 enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };

@@ -64,6 +64,8 @@ struct DevLevel {
   double *Kd_d = nullptr, *Md_d = nullptr;
   float *Kd_f = nullptr, *Md_f = nullptr;
   float *Kd_lo = nullptr, *Md_lo = nullptr;  // fp32 residual of the fp64 coefficients
+  StencilHost<double> st_d;  // stencil form of Kd/Md (2D), if the level has one
+  StencilHost<float> st_f;
   double* A_d = nullptr;
   float* A_f = nullptr;
   double* tw_d = nullptr;
@@ -281,6 +283,9 @@ template <typename T> const T* Md(const DevLevel& d);
 template <> const double* Md<double>(const DevLevel& d) { return d.Md_d; }
 template <> const float* Md<float>(const DevLevel& d) { return d.Md_f; }
 template <typename T> const T* Ad(const DevLevel& d);
+template <typename T> const StencilHost<T>* St(const DevLevel& d);
+template <> const StencilHost<double>* St<double>(const DevLevel& d) { return &d.st_d; }
+template <> const StencilHost<float>* St<float>(const DevLevel& d) { return &d.st_f; }
 template <> const double* Ad<double>(const DevLevel& d) { return d.A_d; }
 template <> const float* Ad<float>(const DevLevel& d) { return d.A_f; }
 template <typename T> const T* Tw(const DevLevel& d);
@@ -290,7 +295,7 @@ template <> const float* Tw<float>(const DevLevel& d) { return d.tw_f; }
 template <typename T>
 Band2D<T> band(const nmg_hier* h, int l) {
   const DevLevel& d = h->lv[l];
-  return Band2D<T>{d.n, d.wK, d.wM, Kd<T>(d), Md<T>(d), (T)h->alpha};
+  return Band2D<T>{d.n, d.wK, d.wM, Kd<T>(d), Md<T>(d), (T)h->alpha, St<T>(d)};
 }
 
 template <typename T>
@@ -768,6 +773,7 @@ nmg_status check_common(nmg_ctx* ctx, const nmg_hier* h, int batch) {
   if (!ctx || !h) return fail(ctx, NMG_ERR_ARG, "null context or hierarchy");
   if (h->ctx != ctx) return fail(ctx, NMG_ERR_ARG, "hierarchy belongs to another context");
   if (batch < 0) return fail(ctx, NMG_ERR_ARG, "batch < 0");
+  if (batch > NMG_MAX_BATCH) return fail(ctx, NMG_ERR_ARG, "batch > NMG_MAX_BATCH");
   return NMG_OK;
 }
 
@@ -885,6 +891,26 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
       d.Md_f = upload(ctx, h->allocs, to_f(hl.Md), &st);
       d.Kd_lo = upload(ctx, h->allocs, lo_f(hl.Kd), &st);
       d.Md_lo = upload(ctx, h->allocs, lo_f(hl.Md), &st);
+      std::vector<double> sK, cK, sM, cM;
+      int nbK = 0, nbM = 0;
+      if (hl.wK <= kStencilMaxW && hl.wM <= 1 && stencil_form(hl.Kd, hl.n, hl.wK, sK, nbK, cK) &&
+          stencil_form(hl.Md, hl.n, hl.wM, sM, nbM, cM)) {
+        auto fill = [&](auto& S, auto conv) {
+          S.valid = 1;
+          S.wK = hl.wK;
+          S.wM = hl.wM;
+          S.nbK = nbK;
+          S.nbM = nbM;
+          for (size_t k = 0; k < sK.size(); ++k) S.sK[k] = conv(sK[k]);
+          for (size_t k = 0; k < sM.size(); ++k) S.sM[k] = conv(sM[k]);
+        };
+        fill(d.st_d, [](double v) { return v; });
+        fill(d.st_f, [](double v) { return (float)v; });
+        d.st_d.cK = upload(ctx, h->allocs, cK, &st);
+        d.st_d.cM = upload(ctx, h->allocs, cM, &st);
+        d.st_f.cK = upload(ctx, h->allocs, to_f(cK), &st);
+        d.st_f.cM = upload(ctx, h->allocs, to_f(cM), &st);
+      }
     } else {
       d.A_d = upload(ctx, h->allocs, hl.A, &st);
       d.A_f = upload(ctx, h->allocs, to_f(hl.A), &st);
@@ -1615,7 +1641,8 @@ void nmg_server_destroy(nmg_server* s) {
 }
 
 nmg_status nmg_server_add_operator(nmg_server* s, nmg_hier* h, int slots, int* op_id) {
-  if (!s || !h || slots < 1 || !op_id) return fail(s ? s->ctx : nullptr, NMG_ERR_ARG, "bad operator");
+  if (!s || !h || slots < 1 || slots > NMG_MAX_BATCH || !op_id)
+    return fail(s ? s->ctx : nullptr, NMG_ERR_ARG, "bad operator");
   nmg_ctx* ctx = s->ctx;
   if (h->ctx != ctx) return fail(ctx, NMG_ERR_ARG, "hierarchy belongs to another context");
   for (const SrvOp& o : s->ops)

@@ -7,6 +7,7 @@
 // M_{l+1} = R M_l P, K_{l+1} = R K_l P.  P and R have three nonzeros per
 // column/row, so each coarse entry is a 3x3 weighted sum of fine entries and
 // the band half-width grows as w -> floor(w/2) + 1.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -181,6 +182,35 @@ std::vector<double> filter_circulant_1d(int n) {
     c[d] = acc / n;
   }
   return c;
+}
+
+bool stencil_form(const std::vector<double>& dia, int n, int w, std::vector<double>& s, int& nb,
+                  std::vector<double>& corr) {
+  const int nk = 2 * w + 1;
+  const int ref = n / 2;  // an interior row: all of its band lies in the grid
+  if (ref - w < 0 || ref + w >= n) return false;
+  s.assign(dia.begin() + (size_t)ref * nk, dia.begin() + (size_t)(ref + 1) * nk);
+  double smax = 0.0;
+  for (double v : s) smax = std::max(smax, std::fabs(v));
+  const double tol = 1e-14 * smax;
+  auto differs = [&](int g) {
+    for (int k = 0; k < nk; ++k) {
+      const int j = g + k - w;
+      if (j >= 0 && j < n && std::fabs(dia[(size_t)g * nk + k] - s[k]) > tol) return true;
+    }
+    return false;
+  };
+  nb = 0;
+  for (int g = 0; g < n; ++g)
+    if (differs(g)) nb = g + 1;
+  if (nb > w) return false;  // only the first w rows may differ
+  corr.assign((size_t)nb * nk, 0.0);
+  for (int g = 0; g < nb; ++g)
+    for (int k = 0; k < nk; ++k) {
+      const int j = g + k - w;
+      if (j >= 0 && j < n) corr[(size_t)g * nk + k] = dia[(size_t)g * nk + k] - s[k];
+    }
+  return true;
 }
 
 std::vector<double> fft_twiddles(int n) {

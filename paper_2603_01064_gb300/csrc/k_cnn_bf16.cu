@@ -19,8 +19,9 @@
 // issues TMA tensor copies of the input tiles (the halo outside the image is
 // zero-filled by the copy engine) into a ring of shared-memory stages, one
 // warp issues the MMAs of a tile into one of two tensor-memory accumulators
-// as soon as its stage is full, and four warps drain the other accumulator
-// (tensor memory -> registers -> bias, ReLU -> bf16 -> global).  Stages and
+// as soon as its stage is full, and four (fast form) or eight (split forms)
+// warps drain the other accumulator (tensor memory -> registers -> bias,
+// ReLU -> 16-bit values -> global).  Stages and
 // accumulators are handed over with mbarriers (full/empty, acc_full/
 // acc_empty).  Smaller levels use a single-role version that stages with
 // cp.async and overlaps one tile ahead.  Every mbarrier wait is bounded; on
@@ -474,20 +475,20 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   const uint32_t a_base0 = smem_u32(smem), b_base = smem_u32(Bs);
   const int tiles_x = (n + TILE - 1) / TILE;
   const int per_img = tiles_x * tiles_x;
-  const long long total = (long long)nimg * per_img;
+  const int total = nimg * per_img;  // the launcher checks it fits
   const size_t plane = (size_t)n * n;
 
-  auto valid = [&](long long t) {
-    const int b = (int)(t / per_img);
+  auto valid = [&](int t) {
+    const int b = t / per_img;
     return active[b] != 0 && snorm[b] != 0.0;
   };
-  auto advance = [&](long long t) {
+  auto advance = [&](int t) {
     t += gridDim.x;
     while (t < total && !valid(t)) t += gridDim.x;
     return t;
   };
-  auto stage = [&](long long t, int buf) {
-    const int b = (int)(t / per_img), tt = (int)(t % per_img);
+  auto stage = [&](int t, int buf) {
+    const int b = t / per_img, tt = t - b * per_img;
     const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
     const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
     const uint32_t base = a_base0 + buf * ABUF;
@@ -507,8 +508,8 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       abort_flag = 1;
     }
   };
-  auto epilogue = [&](long long t, int acc) {
-    const int b = (int)(t / per_img), tt = (int)(t % per_img);
+  auto epilogue = [&](int t, int acc) {
+    const int b = t / per_img, tt = t - b * per_img;
     const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
     for (int mt = 0; mt < NT; ++mt) {
       const int m = warp * 32 + lane;
@@ -522,9 +523,9 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
     }
   };
 
-  long long cur = blockIdx.x;
+  int cur = blockIdx.x;
   while (cur < total && !valid(cur)) cur += gridDim.x;
-  long long prev = -1;
+  int prev = -1;
   uint32_t parity[2] = {0u, 0u};
   int k = 0;
   if (cur < total) stage(cur, 0);
@@ -539,7 +540,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       issue_tile_mmas<SPLIT, CH_BYTES>(a_base0 + sb * ABUF, b_base, tmem + sb * NACC);
       mma_commit(smem_u32(&mbar[sb]));
     }
-    const long long nxt = advance(cur);
+    const int nxt = advance(cur);
     if (prev >= 0) {
       // MMAs of the previous tile are done: its operand buffer is free and its
       // accumulator can be read
@@ -578,7 +579,12 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
 // hidden layer, warp-specialised: TMA producer / MMA issuer / 4 epilogue warps
 // ---------------------------------------------------------------------------
 constexpr int CH_PITCH = 5248;       // chunk stride in shared memory (128-byte multiple)
-constexpr int WS_THREADS = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: 8 in the split forms (two
+// per SM sub-partition, one per tensor-memory lane quarter and M tile: the
+// epilogue converts twice the accumulator columns and is latency-bound with
+// one warp per sub-partition), 4 in the fast form (which runs 2 CTAs per SM)
+template <int SPLIT> struct EPI { static constexpr int value = SPLIT ? 8 : 4; };
+template <int SPLIT> struct WST { static constexpr int value = 64 + 32 * EPI<SPLIT>::value; };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
@@ -597,7 +603,7 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 }
 
 template <int SPLIT, int STAGES, int FUSE>
-__global__ void __launch_bounds__(WS_THREADS)
+__global__ void __launch_bounds__(WST<SPLIT>::value)
 k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
             const float* __restrict__ w4, const double* __restrict__ snorm,
@@ -622,9 +628,9 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
-    for (int i = tid; i < B_BYTES / 16; i += WS_THREADS) dst[i] = src[i];
+    for (int i = tid; i < B_BYTES / 16; i += WST<SPLIT>::value) dst[i] = src[i];
     if (FUSE)
-      for (int i = tid; i < 9 * 32; i += WS_THREADS) w4s[i] = w4[(i % 32) * 9 + i / 32];
+      for (int i = tid; i < 9 * 32; i += WST<SPLIT>::value) w4s[i] = w4[(i % 32) * 9 + i / 32];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -639,7 +645,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     }
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_full[i])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])), "r"(4));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
+                   "r"(EPI<SPLIT>::value));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
@@ -651,18 +658,18 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   const uint32_t tmem = tmem_slot;
   const int tiles_x = (n + TILE - 1) / TILE;
   const int per_img = tiles_x * tiles_x;
-  const long long total = (long long)nimg * per_img;
+  const int total = nimg * per_img;  // the launcher checks it fits
   const size_t plane = (size_t)n * n;
-  auto valid = [&](long long t) {
-    const int b = (int)(t / per_img);
+  auto valid = [&](int t) {
+    const int b = t / per_img;
     return active[b] != 0 && snorm[b] != 0.0;
   };
   auto first = [&]() {
-    long long t = blockIdx.x;
+    int t = blockIdx.x;
     while (t < total && !valid(t)) t += gridDim.x;
     return t;
   };
-  auto advance = [&](long long t) {
+  auto advance = [&](int t) {
     t += gridDim.x;
     while (t < total && !valid(t)) t += gridDim.x;
     return t;
@@ -685,10 +692,10 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     // ---- TMA producer
     if (lane == 0) {
       int i = 0;
-      for (long long t = first(); t < total; t = advance(t), ++i) {
+      for (int t = first(); t < total; t = advance(t), ++i) {
         const int s = i % STAGES;
         if (i >= STAGES && !wait(&empty[s], (uint32_t)((i / STAGES - 1) & 1))) break;
-        const int b = (int)(t / per_img), tt = (int)(t % per_img);
+        const int b = t / per_img, tt = t - b * per_img;
         const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, TX);
@@ -701,7 +708,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     if (lane == 0) {
       const uint32_t b_base = smem_u32(Bs);
       int i = 0;
-      for (long long t = first(); t < total; t = advance(t), ++i) {
+      for (int t = first(); t < total; t = advance(t), ++i) {
         const int s = i % STAGES, a = i & 1;
         if (!wait(&full[s], (uint32_t)((i / STAGES) & 1))) break;
         if (i >= 2 && !wait(&acc_empty[a], (uint32_t)((i / 2 - 1) & 1))) break;
@@ -712,18 +719,21 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
       }
     }
   } else {
-    // ---- epilogue warps 2..5: lane quarter q = warp % 4 of tensor memory
+    // ---- epilogue warps: lane quarter q = warp % 4 of tensor memory; with 8
+    // warps, warps 2-5 take M tile 0 and warps 6-9 M tile 1
+    constexpr int MTW = NT * 4 / EPI<SPLIT>::value;  // M tiles per epilogue warp
     const int q = warp & 3;
+    const int mt0 = ((warp - 2) >> 2) * MTW;
     int i = 0;
-    for (long long t = first(); t < total; t = advance(t), ++i) {
+    for (int t = first(); t < total; t = advance(t), ++i) {
       const int a = i & 1;
       if (!wait(&acc_full[a], (uint32_t)((i / 2) & 1))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int b = (int)(t / per_img), tt = (int)(t % per_img);
+      const int b = t / per_img, tt = t - b * per_img;
       const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
       const int m = q * 32 + lane;
       const int y = y0 + (m >> 3);
-      for (int mt = 0; mt < NT; ++mt) {
+      for (int mt = mt0; mt < mt0 + MTW; ++mt) {
         const int x = x0 + mt * 8 + (m & 7);
         const bool in = y < n && x < n;
         const size_t pix = (size_t)b * plane + (size_t)y * n + x;
@@ -861,7 +871,7 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
     constexpr int STAGES = 3;
     constexpr int ACHs = SPLIT ? 8 : 4;
     constexpr int B_BYTESs = SPLIT ? 2 * B_HALF : B_HALF;
-    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + 4 * STG_WARP + 1024;
+    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + EPI<SPLIT>::value * STG_WARP + 1024;
     const int tiles_x = (n + TILE - 1) / TILE;
     long long total = (long long)nimg * tiles_x * tiles_x;
     long long grid = (long long)num_sms() * (SPLIT ? 1 : 2);
@@ -869,7 +879,7 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
     if (grid < 1) grid = 1;
     cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int pi_ = log.begin(K_CNN_HIDDEN, st);
-    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WS_THREADS, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, s, active, err);
+    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WST<SPLIT>::value, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, s, active, err);
     log.end(pi_, st, (double)n * n * log.active_hint);
     return;
   }

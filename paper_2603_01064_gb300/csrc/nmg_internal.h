@@ -51,12 +51,39 @@ std::vector<double> fft_twiddles(int n);
 // ---------------------------------------------------------------------------
 
 template <typename T>
+struct StencilHost;
+
+template <typename T>
 struct Band2D {
   int n, wK, wM;
   const T* Kd;
   const T* Md;
   T alpha;
+  const StencilHost<T>* st = nullptr;  // stencil form of Kd/Md (host), if any
 };
+
+// Stencil form of a level's banded factors, found on the host at setup: the
+// rows g >= nbK of K_l are one stencil sK (offsets -wK..wK), the first nbK
+// rows differ from it by the correction rows cK[g][0..2wK] (device), and
+// likewise for M_l (wM <= 1).  With x zero outside the grid this reproduces
+// K_l x exactly.  The fine level is Toeplitz (nb = 0); Galerkin levels
+// differ from their stencil only in the first rows (the coarse node J sits
+// on fine node 2J, so only the low boundary sees the zero phantom).
+constexpr int kStencilMaxW = 32;
+template <typename T>
+struct StencilHost {
+  int valid = 0;
+  int wK = 0, wM = 0, nbK = 0, nbM = 0;
+  T sK[2 * kStencilMaxW + 1] = {};
+  T sM[3] = {};
+  const T* cK = nullptr;
+  const T* cM = nullptr;
+};
+// stencil form of a DIA factor (n rows, half-width w): stencil s[2w+1], the
+// number nb of leading rows that differ and their corrections corr[nb][2w+1];
+// false if another row differs or there is no interior row
+bool stencil_form(const std::vector<double>& dia, int n, int w, std::vector<double>& s, int& nb,
+                  std::vector<double>& corr);
 
 // weights of one 2D conv layer: w[(ci*9 + tap)*cout + co], bias[co]
 template <typename T>
