@@ -125,7 +125,8 @@ struct nmg_hier {
   int layers = 0, width = 0, ksize = 0;
   HostHierarchy host;
   std::vector<DevLevel> lv;
-  double* chol = nullptr;
+  double* chol = nullptr;           // Cholesky factor L of the coarsest operator
+  double *chol_inv = nullptr, *chol_invT = nullptr;  // L^{-1} and L^{-T}
   std::vector<void*> allocs;
   Work w;
 };
@@ -389,7 +390,8 @@ void op_filter(nmg_hier* h, int l, int B, const T* xstar, const T* hv, T* x, con
 
 template <typename T>
 void op_coarse(nmg_hier* h, int B, const T* y, T* x, const int* active) {
-  launch_coarse_solve<T>(h->nc, h->chol, B, y, x, active, h->ctx->stream, h->ctx->log);
+  launch_coarse_solve<T>(h->nc, h->chol_inv, h->chol_invT, B, y, x, active, h->ctx->stream,
+                         h->ctx->log);
 }
 
 template <typename T>
@@ -1001,6 +1003,17 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
       else if (hflag) st = fail(ctx, NMG_ERR_NOT_SPD, "coarsest Galerkin operator is not SPD");
       cudaFree(flag);
     }
+    if (st == NMG_OK) {
+      const std::vector<double> zeros((size_t)h->nc * h->nc, 0.0);
+      h->chol_inv = upload(ctx, h->allocs, zeros, &st);
+      h->chol_invT = upload(ctx, h->allocs, zeros, &st);
+      if (st == NMG_OK) {
+        launch_chol_inverse(h->nc, A, h->chol_inv, h->chol_invT, ctx->stream, ctx->log);
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "cholesky inverse");
+      }
+    }
     if (st != NMG_OK) {
       for (void* p : h->allocs) cudaFree(p);
       return st;
@@ -1341,7 +1354,7 @@ nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_
       d.rst_tile = keep;
       best = 1e30f;
       int keepm = -1;
-      for (int m : {0, 1}) {
+      for (int m : {0, 1, 2}) {
         d.filt_mode = m;
         float ms = timeit([&]() {
           if (dbl) op_filter<double>(h, l, batch, (double*)w.x[l], (double*)w.h[l], (double*)w.x[l], w.active);

@@ -1,6 +1,7 @@
 // Coarsest-level exact solve x_L = (A^(L))^{-1} y_L (Algorithms 3 and 4)
-// in fp64: a one-block right-looking Cholesky factorisation at setup and
-// batched forward/back substitution per cycle.
+// in fp64: a one-block right-looking Cholesky factorisation A = L L^T and
+// the inverse factor L^{-1} at setup, then per cycle the two triangular
+// products x = L^{-T} (L^{-1} y) for the whole batch.
 #include "nmg_internal.h"
 
 namespace nmg {
@@ -37,31 +38,82 @@ __global__ void k_cholesky(int nc, double* A, int* flag) {
   if (threadIdx.x == 0) *flag = bad;
 }
 
-// One block per right-hand side: z = L^{-1} y, x = L^{-T} z in fp64.
+// Inverse of the Cholesky factor, once at setup: block j solves L z = e_j
+// by forward substitution and writes column j of L^{-1} (and row j of its
+// transpose), so that every cycle's coarsest solve is two dense triangular
+// products instead of 2 nc sequential substitution steps.
+__global__ void k_chol_inverse(int nc, const double* __restrict__ L, double* __restrict__ Li,
+                               double* __restrict__ LiT) {
+  const int j = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* z = reinterpret_cast<double*>(smem_raw);
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) z[i] = i == j ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = j; k < nc; ++k) {
+    const double zk = z[k] / L[(size_t)k * nc + k];
+    __syncthreads();
+    if (threadIdx.x == 0) z[k] = zk;
+    for (int i = k + 1 + threadIdx.x; i < nc; i += blockDim.x) z[i] -= L[(size_t)i * nc + k] * zk;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    Li[(size_t)i * nc + j] = z[i];
+    LiT[(size_t)j * nc + i] = z[i];
+  }
+}
+
+// x = L^{-T} (L^{-1} y) in fp64, one block per right-hand side.  Each warp
+// forms 8 rows of a triangular product at a time (lanes along the row, the
+// 8 rows' loads in flight together, then interleaved warp reductions), so
+// the factors are read coalesced and load latency is paid once per 8 rows.
+template <bool UPPER>
+__device__ __forceinline__ void tri_rows(int nc, const double* __restrict__ F, const double* in,
+                                         double* out, int lane, int warp, int nw) {
+  constexpr int R = 8;
+  for (int i0 = warp * R; i0 < nc; i0 += nw * R) {
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      acc[r] = 0.0;
+      const int i = i0 + r;
+      if (i < nc) {
+        const double* row = F + (size_t)i * nc;
+        if (UPPER) {
+          for (int c = i + lane; c < nc; c += 32) acc[r] += row[c] * in[c];
+        } else {
+          for (int c = lane; c <= i; c += 32) acc[r] += row[c] * in[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (i0 + r < nc) out[i0 + r] = acc[r];
+    }
+  }
+}
+
 template <typename T>
-__global__ void k_coarse_solve(int nc, const double* __restrict__ L, const T* __restrict__ y,
-                               T* __restrict__ x, const int* __restrict__ active) {
+__global__ void __launch_bounds__(256)
+k_coarse_apply(int nc, const double* __restrict__ Li, const double* __restrict__ LiT,
+               const T* __restrict__ y, T* __restrict__ x, const int* __restrict__ active) {
   const int b = blockIdx.x;
   if (!active[b]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* z = reinterpret_cast<double*>(smem_raw);
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) z[i] = (double)y[(size_t)b * nc + i];
+  double* v = reinterpret_cast<double*>(smem_raw);
+  double* z = v + nc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) v[i] = (double)y[(size_t)b * nc + i];
   __syncthreads();
-  for (int j = 0; j < nc; ++j) {
-    double zj = z[j] / L[(size_t)j * nc + j];
-    __syncthreads();
-    if (threadIdx.x == 0) z[j] = zj;
-    for (int i = j + 1 + threadIdx.x; i < nc; i += blockDim.x) z[i] -= L[(size_t)i * nc + j] * zj;
-    __syncthreads();
-  }
-  for (int j = nc - 1; j >= 0; --j) {
-    double xj = z[j] / L[(size_t)j * nc + j];
-    __syncthreads();
-    if (threadIdx.x == 0) z[j] = xj;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) z[i] -= L[(size_t)j * nc + i] * xj;
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) x[(size_t)b * nc + i] = (T)z[i];
+  tri_rows<false>(nc, Li, v, z, lane, warp, nw);  // z = L^{-1} v
+  __syncthreads();
+  tri_rows<true>(nc, LiT, z, v, lane, warp, nw);  // v = L^{-T} z
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) x[(size_t)b * nc + i] = (T)v[i];
 }
 
 }  // namespace
@@ -72,18 +124,26 @@ void launch_cholesky(int nc, double* A, int* flag, cudaStream_t st, LaunchLog& l
   log.end(pi_, st, 0.0);
 }
 
+void launch_chol_inverse(int nc, const double* L, double* Li, double* LiT, cudaStream_t st,
+                         LaunchLog& log) {
+  const int threads = nc < 64 ? 32 : (nc < 256 ? 64 : 256);
+  int pi_ = log.begin(K_OTHER, st);
+  k_chol_inverse<<<nc, threads, nc * sizeof(double), st>>>(nc, L, Li, LiT);
+  log.end(pi_, st, 0.0);
+}
+
 template <typename T>
-void launch_coarse_solve(int nc, const double* L, int B, const T* y, T* x, const int* active,
-                         cudaStream_t st, LaunchLog& log) {
-  int threads = nc < 64 ? 32 : (nc < 256 ? 64 : 256);
+void launch_coarse_solve(int nc, const double* Li, const double* LiT, int B, const T* y, T* x,
+                         const int* active, cudaStream_t st, LaunchLog& log) {
+  const int threads = nc <= 64 ? 64 : (nc <= 128 ? 128 : 256);
   int pi_ = log.begin(K_COARSE, st);
-  k_coarse_solve<T><<<B, threads, nc * sizeof(double), st>>>(nc, L, y, x, active);
+  k_coarse_apply<T><<<B, threads, 2 * nc * sizeof(double), st>>>(nc, Li, LiT, y, x, active);
   log.end(pi_, st, (double)nc * log.active_hint);
 }
 
-template void launch_coarse_solve<float>(int, const double*, int, const float*, float*,
-                                         const int*, cudaStream_t, LaunchLog&);
-template void launch_coarse_solve<double>(int, const double*, int, const double*, double*,
-                                          const int*, cudaStream_t, LaunchLog&);
+template void launch_coarse_solve<float>(int, const double*, const double*, int, const float*,
+                                         float*, const int*, cudaStream_t, LaunchLog&);
+template void launch_coarse_solve<double>(int, const double*, const double*, int, const double*,
+                                          double*, const int*, cudaStream_t, LaunchLog&);
 
 }  // namespace nmg

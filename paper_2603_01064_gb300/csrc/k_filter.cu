@@ -397,6 +397,227 @@ k_filter_fused(int n, int logn, const T* xstar, const T* __restrict__ h, T* x,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-level form of the fused filter for n = 64 and 128: the same
+// half-spectrum layout, but every row and column transform is done by one
+// warp in registers (M = length / 32 values per lane, radix-2 stages within
+// a lane's registers for spans >= 32 and across lanes with shuffles below),
+// so the block synchronises only between the row, column and row phases.
+// Forward transforms are decimation in frequency (natural order in, bit-
+// reversed out) and inverse ones decimation in time (bit-reversed in,
+// natural out), so the column spectra are masked in bit-reversed order and
+// no permutation pass is needed.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cmulc(Cx<T> a, Cx<T> b) {  // a * conj(b)
+  return Cx<T>{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_cx(Cx<T> v, int mask) {
+  return Cx<T>{__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask)};
+}
+
+// length-L DIF FFT (L = 32 M), natural order in, slot s = lane + 32 m holds
+// the spectrum at bitrev_L(s) on return; tw: exp(-2 pi i k / N), k < N / 2
+template <typename T, int L, int N>
+__device__ __forceinline__ void warp_dif(Cx<T> (&v)[L / 32], const Cx<T>* tw, int lane) {
+  constexpr int M = L / 32;
+#pragma unroll
+  for (int span = L / 2; span >= 32; span >>= 1) {
+    const int ms = span / 32;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      if (m & ms) continue;
+      const int j = lane + 32 * (m & (2 * ms - 1));  // position in the sub-transform
+      const Cx<T> a = v[m], b = v[m + ms];
+      v[m] = Cx<T>{a.x + b.x, a.y + b.y};
+      v[m + ms] = cmul(Cx<T>{a.x - b.x, a.y - b.y}, tw[j * (N / (2 * span))]);
+    }
+  }
+#pragma unroll
+  for (int span = (L / 2 < 16 ? L / 2 : 16); span >= 1; span >>= 1) {
+    const bool upper = lane & span;
+    const Cx<T> w = tw[((lane & (2 * span - 1)) - (upper ? span : 0)) * (N / (2 * span))];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const Cx<T> o = shfl_cx(v[m], span);
+      v[m] = upper ? cmul(Cx<T>{o.x - v[m].x, o.y - v[m].y}, w) : Cx<T>{v[m].x + o.x, v[m].y + o.y};
+    }
+  }
+}
+
+// length-L inverse DIT FFT (unnormalised), slot s holds the input at
+// bitrev_L(s), natural order out
+template <typename T, int L, int N>
+__device__ __forceinline__ void warp_dit_inv(Cx<T> (&v)[L / 32], const Cx<T>* tw, int lane) {
+  constexpr int M = L / 32;
+#pragma unroll
+  for (int span = 1; span <= (L / 2 < 16 ? L / 2 : 16); span <<= 1) {
+    const bool upper = lane & span;
+    const Cx<T> w = tw[((lane & (2 * span - 1)) - (upper ? span : 0)) * (N / (2 * span))];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const Cx<T> o = shfl_cx(v[m], span);
+      // lower: a + b w with a = mine, b = partner; upper: a - b w, a = partner
+      v[m] = upper ? Cx<T>{o.x - cmulc(v[m], w).x, o.y - cmulc(v[m], w).y}
+                   : Cx<T>{v[m].x + cmulc(o, w).x, v[m].y + cmulc(o, w).y};
+    }
+  }
+#pragma unroll
+  for (int span = 32; span <= L / 2; span <<= 1) {
+    const int ms = span / 32;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      if (m & ms) continue;
+      const int j = lane + 32 * (m & (2 * ms - 1));
+      const Cx<T> a = v[m], t = cmulc(v[m + ms], tw[j * (N / (2 * span))]);
+      v[m] = Cx<T>{a.x + t.x, a.y + t.y};
+      v[m + ms] = Cx<T>{a.x - t.x, a.y - t.y};
+    }
+  }
+}
+
+template <int L>
+__device__ __forceinline__ int brev_len(int s) { return __brev(s) >> (32 - (L == 32 ? 5 : L == 64 ? 6 : 7)); }
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256)
+k_filter_warp(const T* xstar, const T* __restrict__ h, T* x, const Cx<T>* __restrict__ twg,
+              const double* __restrict__ mtab, const int* __restrict__ active) {
+  constexpr int HN = N / 2, MR = N / 32, MC = HN / 32, P = N + 1;  // odd pitch
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<T>* tw = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* q = tw + HN;     // scratch of the packed column pair (N values)
+  T* mt = reinterpret_cast<T*>(q + N);  // mask table, HN + 1 values
+  Cx<T>* buf = reinterpret_cast<Cx<T>*>(mt + ((HN + 1 + 1) & ~1));  // [HN][P]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = threadIdx.x; k < HN; k += blockDim.x) tw[k] = twg[k];
+  for (int k = threadIdx.x; k <= HN; k += blockDim.x) mt[k] = (T)mtab[k];
+  __syncthreads();
+  const size_t base = (size_t)b * N * N;
+  // ---- rows: z_k = h[2k] + i h[2k+1], FFT, split into the row-pair layout
+  for (int k = warp; k < HN; k += nw) {
+    Cx<T> v[MR];
+    const T* h0 = h + base + (size_t)(2 * k) * N;
+#pragma unroll
+    for (int m = 0; m < MR; ++m) v[m] = Cx<T>{h0[lane + 32 * m], h0[N + lane + 32 * m]};
+    warp_dif<T, N, N>(v, tw, lane);
+    Cx<T>* row = buf + k * P;
+#pragma unroll
+    for (int m = 0; m < MR; ++m) row[brev_len<N>(lane + 32 * m)] = v[m];
+    __syncwarp();
+    for (int t = lane; t < HN; t += 32) {
+      if (t == 0) {
+        const Cx<T> a = row[0], c = row[HN];
+        row[0] = Cx<T>{a.x, c.x};
+        row[HN] = Cx<T>{a.y, c.y};
+      } else {
+        const Cx<T> za = row[t], zb = row[N - t];
+        row[t] = Cx<T>{T(0.5) * (za.x + zb.x), T(0.5) * (za.y - zb.y)};
+        row[N - t] = Cx<T>{T(0.5) * (za.y + zb.y), T(0.5) * (zb.x - za.x)};
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- column pairs: even rows in column p, odd rows in its partner
+  for (int p = warp; p < HN; p += nw) {
+    const int ce = p, co = p == 0 ? HN : N - p;
+    Cx<T> e[MC], o[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      e[m] = buf[(lane + 32 * m) * P + ce];
+      o[m] = buf[(lane + 32 * m) * P + co];
+    }
+    warp_dif<T, HN, N>(e, tw, lane);
+    warp_dif<T, HN, N>(o, tw, lane);
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      const int k1 = brev_len<HN>(lane + 32 * m);
+      const Cx<T> w = tw[k1], wo = cmul(o[m], w);
+      Cx<T> y0{e[m].x + wo.x, e[m].y + wo.y}, y1{e[m].x - wo.x, e[m].y - wo.y};
+      if (p == 0) {  // packed pair: separated below
+        q[k1] = y0;
+        q[k1 + HN] = y1;
+        continue;
+      }
+      const T m0 = mt[k1 > p ? k1 : p], m1 = mt[HN - k1 > p ? HN - k1 : p];
+      y0.x *= m0; y0.y *= m0;
+      y1.x *= m1; y1.y *= m1;
+      e[m] = Cx<T>{y0.x + y1.x, y0.y + y1.y};
+      o[m] = cmulc(Cx<T>{y0.x - y1.x, y0.y - y1.y}, w);
+    }
+    if (p == 0) {
+      __syncwarp();
+      const T mb = mt[HN];
+      for (int K = lane; K <= HN; K += 32) {
+        const int Kp = K == 0 ? 0 : N - K;
+        const T ma = mt[K], c1 = T(0.5) * (ma + mb), c2 = T(0.5) * (ma - mb);
+        const Cx<T> qa = q[K], qb = q[Kp];
+        q[K] = Cx<T>{c1 * qa.x + c2 * qb.x, c1 * qa.y - c2 * qb.y};
+        if (Kp != K) q[Kp] = Cx<T>{c1 * qb.x + c2 * qa.x, c1 * qb.y - c2 * qa.y};
+      }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < MC; ++m) {
+        const int k1 = brev_len<HN>(lane + 32 * m);
+        const Cx<T> y0 = q[k1], y1 = q[k1 + HN];
+        e[m] = Cx<T>{y0.x + y1.x, y0.y + y1.y};
+        o[m] = cmulc(Cx<T>{y0.x - y1.x, y0.y - y1.y}, tw[k1]);
+      }
+    }
+    warp_dit_inv<T, HN, N>(e, tw, lane);
+    warp_dit_inv<T, HN, N>(o, tw, lane);
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      buf[(lane + 32 * m) * P + ce] = e[m];
+      buf[(lane + 32 * m) * P + co] = o[m];
+    }
+  }
+  __syncthreads();
+  // ---- rows: rebuild z_k's spectrum, inverse FFT, x = x* + z / N^2
+  const T scale = T(1.0 / ((double)N * (double)N));
+  for (int k = warp; k < HN; k += nw) {
+    Cx<T>* row = buf + k * P;
+    for (int t = lane; t < HN; t += 32) {
+      if (t == 0) {
+        const Cx<T> a = row[0], c = row[HN];
+        row[0] = Cx<T>{a.x, c.x};
+        row[HN] = Cx<T>{a.y, c.y};
+      } else {
+        const Cx<T> xa = row[t], xb = row[N - t];
+        row[t] = Cx<T>{xa.x - xb.y, xa.y + xb.x};
+        row[N - t] = Cx<T>{xa.x + xb.y, xb.x - xa.y};
+      }
+    }
+    __syncwarp();
+    Cx<T> v[MR];
+#pragma unroll
+    for (int m = 0; m < MR; ++m) v[m] = row[brev_len<N>(lane + 32 * m)];
+    warp_dit_inv<T, N, N>(v, tw, lane);
+    const size_t g0 = base + (size_t)(2 * k) * N;
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+      const size_t g = g0 + lane + 32 * m;
+      x[g] = (xstar ? xstar[g] : T(0)) + v[m].x * scale;
+      x[g + N] = (xstar ? xstar[g + N] : T(0)) + v[m].y * scale;
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N>
+size_t filter_warp_smem() {
+  return (size_t)(N / 2 + N) * sizeof(Cx<T>) + (size_t)((N / 2 + 2) & ~1) * sizeof(T) +
+         (size_t)(N / 2) * (N + 1) * sizeof(Cx<T>);
+}
+
 // 1D: x[b][i] = x*[b][i] + sum_k c[(i - k) mod n] h[b][k]; one warp per output
 template <typename T>
 __global__ void k_filter1d(int n, const T* xs, const T* __restrict__ h, T* x, const double* __restrict__ circ,
@@ -430,6 +651,18 @@ void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
   Cx<T>* C = reinterpret_cast<Cx<T>*>(cbuf);
   const Cx<T>* tw = reinterpret_cast<const Cx<T>*>(twiddles);
   const double units = (double)n * n * log.active_hint;
+  // warp-level form (default where it applies; autotuner mode 2)
+  if ((n == 64 || n == 128) && (mode == 2 || mode < 0)) {
+    const size_t sm = n == 64 ? filter_warp_smem<T, 64>() : filter_warp_smem<T, 128>();
+    if (sm <= 200 * 1024) {
+      auto kern = n == 64 ? k_filter_warp<T, 64> : k_filter_warp<T, 128>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      int pi_ = log.begin(K_FILTER, st);
+      kern<<<B, 256, sm, st>>>(xstar, h, x, tw, mask_tab, active);
+      log.end(pi_, st, units);
+      return;
+    }
+  }
   const size_t fused_sm = (size_t)(halfn + (size_t)n * halfn) * sizeof(Cx<T>);
   if (fused_sm <= 160 * 1024 && mode != 0) {
     cudaFuncSetAttribute(k_filter_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_sm);

@@ -221,9 +221,13 @@ void launch_axpy_update(long long len, int B, const T* xstar, const T* h, T* x,
 // coarse: in-place Cholesky of an nc x nc fp64 matrix (device); flag set to
 // 1 if a pivot is not positive
 void launch_cholesky(int nc, double* A, int* flag, cudaStream_t st, LaunchLog& log);
+// L^{-1} and its transpose from the Cholesky factor (setup)
+void launch_chol_inverse(int nc, const double* L, double* Li, double* LiT, cudaStream_t st,
+                         LaunchLog& log);
+// x = L^{-T} L^{-1} y for B right-hand sides (fp64 arithmetic)
 template <typename T>
-void launch_coarse_solve(int nc, const double* L, int B, const T* y, T* x, const int* active,
-                         cudaStream_t st, LaunchLog& log);
+void launch_coarse_solve(int nc, const double* Li, const double* LiT, int B, const T* y, T* x,
+                         const int* active, cudaStream_t st, LaunchLog& log);
 
 // active[b] = 1 where newmask[b] (serving admission)
 void launch_admit(int B, const int* newmask, int* active, cudaStream_t st, LaunchLog& log);

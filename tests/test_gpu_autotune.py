@@ -41,7 +41,7 @@ def test_autotune_choices_and_results(ctx, prec, tmp_path):
         t = G.tuning(l)
         assert t["res_tile"] in (16, 32, 64)
         if l < 4:
-            assert t["rst_tile"] in (8, 16, 32) and t["filt_mode"] in (0, 1)
+            assert t["rst_tile"] in (8, 16, 32) and t["filt_mode"] in (0, 1, 2)
     u = u0.clone()
     for _ in range(3):
         G.cycle(fd, u)
