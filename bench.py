@@ -395,6 +395,12 @@ def run_ours(args, wl, world, rank, local):
     e2e = {"value": B * world * args.steps / e2e_s, "unit": "RHS/s",
            "h2d_bytes_per_step": int(fh.nbytes + uh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)}
 
+    # ---- serving: a Poisson stream of mixed-size requests through the
+    # continuous-batching server (p50/p99 latency beside throughput)
+    serving = None
+    if not args.no_serving:
+        serving = serving_leg(ctx, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, _, _ = oracle_solve_rate(wl, 2, wl["rhs_seed"])
@@ -415,8 +421,42 @@ def run_ours(args, wl, world, rank, local):
                            "parallelism": f"replicas x{world}"},
                 "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
                 "compare": compare, "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+                "serving": serving}
         print(json.dumps(line), flush=True)
+
+
+SERVING = dict(requests=800, rate=400.0, seed=4242,
+               ops=[  # (n, levels, sigma px, alpha, weights, slots)
+                   (128, 5, 2.0, 1e-2, "c2_2d_n128_s2_a1e-2.npz", 128),
+                   (512, 7, 4.0, 1e-2, "c3_2d_n512_s4_a1e-2.npz", 16)])
+
+
+def serving_leg(ctx, rank):
+    """Requests drawn uniformly from two resident operators (128x128 sigma 2
+    px and 512x512 sigma 4 px, both alpha 1e-2, bf16 split refinement),
+    arriving as a seeded Poisson stream in real time; every request runs to
+    1e-6.  Latency = completion - submission (host clock)."""
+    import paper_2603_01064_gb300 as nmg
+    from paper_2603_01064_gb300 import serve
+    ops = [serve.Operator(n, L, sig, a, nmg.load_weights(os.path.join(WEIGHTS, w)), "bf16_refine",
+                          slots) for (n, L, sig, a, w, slots) in SERVING["ops"]]
+    srv, hs, ids = serve.build_server(ctx, ops, budget_bytes=48 << 30)
+    for G in hs:
+        G.autotune(16)
+    reqs = serve.poisson_stream(ops, SERVING["requests"], SERVING["rate"],
+                                SERVING["seed"] + 7919 * rank, rhs_batch=8)
+    elapsed, done = serve.run_stream(srv, ids, reqs, time_limit_s=60.0)
+    lat = serve.latency_stats(done)
+    out = {"requests": len(reqs), "completed": len(done), "rate_rps": SERVING["rate"],
+           "sizes": [o.n for o in ops], "slots": [o.slots for o in ops],
+           "precision": "bf16_refine", "wall_s": elapsed,
+           "throughput_rhs_s": len(done) / elapsed if elapsed > 0 else None,
+           "converged": all(r.info and r.info[1] == 0 for r in done), **lat}
+    srv.close()
+    for G in hs:
+        G.close()
+    return out
 
 
 def main():
@@ -431,6 +471,7 @@ def main():
     ap.add_argument("--ncu", action="store_true", help="a single solve, nothing else (profiling)")
     ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured iterations "
                          "(profiler launch lists)")

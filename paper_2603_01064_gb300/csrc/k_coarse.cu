@@ -73,16 +73,19 @@ __device__ __forceinline__ void tri_rows(int nc, const double* __restrict__ F, c
   for (int i0 = warp * R; i0 < nc; i0 += nw * R) {
     double acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      acc[r] = 0.0;
-      const int i = i0 + r;
-      if (i < nc) {
-        const double* row = F + (size_t)i * nc;
-        if (UPPER) {
-          for (int c = i + lane; c < nc; c += 32) acc[r] += row[c] * in[c];
-        } else {
-          for (int c = lane; c <= i; c += 32) acc[r] += row[c] * in[c];
-        }
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    // column chunks outer, rows inner: the R rows' loads of a chunk are
+    // independent and in flight together (entries outside the triangle are
+    // zero in F, so only the row bounds are tested)
+    const int c_lo = UPPER ? (i0 & ~31) : 0;
+    const int c_hi = UPPER ? nc : (i0 + R < nc ? i0 + R : nc);
+    for (int cb = c_lo; cb < c_hi; cb += 32) {
+      const int c = cb + lane;
+      const double vin = c < nc ? in[c] : 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = i0 + r;
+        if (i < nc && c < nc) acc[r] += F[(size_t)i * nc + c] * vin;
       }
     }
 #pragma unroll
@@ -135,7 +138,7 @@ void launch_chol_inverse(int nc, const double* L, double* Li, double* LiT, cudaS
 template <typename T>
 void launch_coarse_solve(int nc, const double* Li, const double* LiT, int B, const T* y, T* x,
                          const int* active, cudaStream_t st, LaunchLog& log) {
-  const int threads = nc <= 64 ? 64 : (nc <= 128 ? 128 : 256);
+  const int threads = nc <= 64 ? 128 : 256;
   int pi_ = log.begin(K_COARSE, st);
   k_coarse_apply<T><<<B, threads, 2 * nc * sizeof(double), st>>>(nc, Li, LiT, y, x, active);
   log.end(pi_, st, (double)nc * log.active_hint);
