@@ -32,9 +32,9 @@ void bf16_cnn_forget(const void* pack);
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::vector<const double*>& bias,
                     int split);
 void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
-                       double alpha, int B, const double* u, const float* f, float* r,
-                       double* partials, int* ntiles, const int* active, cudaStream_t st,
-                       LaunchLog& log, int tile_req);
+                       const StencilHost<double>* stencil, double alpha, int B, const double* u,
+                       const float* f, float* r, double* partials, int* ntiles,
+                       const int* active, cudaStream_t st, LaunchLog& log, int tile_req);
 }  // namespace nmg
 
 using namespace nmg;
@@ -1890,7 +1890,8 @@ void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const 
                                      float* r, double* part, int* nt, const int* active) {
   const DevLevel& d = h->lv[0];
   Band2D<float> hi{d.n, d.wK, d.wM, d.Kd_f, d.Md_f, (float)h->alpha};
-  refine_residual2d(hi, d.Kd_lo, d.Md_lo, h->alpha, B, u, f, r, part, nt, active, h->ctx->stream,
+  refine_residual2d(hi, d.Kd_lo, d.Md_lo, &d.st_d, h->alpha, B, u, f, r, part, nt, active,
+                    h->ctx->stream,
                     h->ctx->log, d.ref_tile);
 }
 }  // namespace

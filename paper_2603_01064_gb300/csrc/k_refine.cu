@@ -145,12 +145,301 @@ k_refine_residual2d(Band2D<float> op, const float* __restrict__ Klo, const float
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stencil form for a Toeplitz fine level with M = I (every fine level built
+// from taps): r = f - (alpha u + K U K^T) with the stencil's double-float
+// pairs in kernel parameters.  Persistent blocks prefetch the next tile's u
+// (fp64, with halo) and f with cp.async into a double buffer; u is split
+// into float pairs once per staged value with integer operations (fp64
+// arithmetic runs at 1/64 of the fp32 rate on this GPU); each pass keeps a
+// register window of S + 2 WK pairs for S outputs.
+// ---------------------------------------------------------------------------
+template <int WK>
+struct RefineArgs {
+  int n;
+  float ah, al;  // alpha as a float pair
+  float sKh[2 * WK + 1], sKl[2 * WK + 1];
+};
+
+template <int WK> struct RSeg { static constexpr int value = WK <= 8 ? 8 : 4; };
+
+struct RefineGeom {
+  int XH, XW, XPD, XPF, YP, TKH, TP, words;  // words of 4 bytes
+  __host__ __device__ RefineGeom(int tile, int WK, int S) {
+    XH = tile + 2 * WK;
+    XW = tile + 2 * WK;
+    XPD = (1 + XW + 1) / 2 * 2;                       // doubles per staged row (offset <= 1)
+    const int reach = (tile + S - 1) / S * S + 2 * WK;  // window reach of the row pass
+    XPF = (reach + 3) / 4 * 4;
+    if (((XPF / 4) & 1) == 0) XPF += 4;               // odd number of 16-byte chunks
+    YP = (3 + tile + 3) / 4 * 4;
+    TKH = (tile + S - 1) / S * S + 2 * WK;
+    TP = ((tile + S - 1) / S * S) | 1;
+    words = 2 * 2 * XH * XPD + 2 * tile * YP + 2 * XH * XPF + 2 * TKH * TP;
+  }
+};
+
+__device__ __forceinline__ void cp_async_16r(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 16u : 0u)
+               : "memory");
+}
+
+// v = hi + lo with hi = v truncated to 24 significant bits (exact in fp32)
+// and lo the rest rounded to fp32 (~2^-47 relative), by integer operations;
+// values below 2^-74 in magnitude split to (0, 0), values beyond the fp32
+// range to (+-inf, 0).
+__device__ __forceinline__ void split_double(double v, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  if (e < 949) {  // also zero
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  if (e > 1150) {  // beyond fp32 range: an infinite residual (reported as diverged)
+    hi = __uint_as_float(sign | 0x7F800000u);
+    lo = 0.f;
+    return;
+  }
+  const unsigned m_hi = (unsigned)((u >> 29) & 0x7FFFFFu);
+  const unsigned m_lo = (unsigned)(u & 0x1FFFFFFFu);
+  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | m_hi);
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+  lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn(m_lo) * scale));
+}
+
+template <int WK>
+__global__ void __launch_bounds__(256)
+k_refine_pipe(RefineArgs<WK> op, int B, const double* __restrict__ u, const float* __restrict__ f,
+              float* __restrict__ r, double* __restrict__ partials,
+              const int* __restrict__ active, int tile, int tiles_x) {
+  constexpr int S = RSeg<WK>::value, NW = S + 2 * WK;
+  const RefineGeom g(tile, WK, S);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  double* ubuf = reinterpret_cast<double*>(smem_raw);  // [2][XH][XPD]
+  float* fbuf = reinterpret_cast<float*>(ubuf + 2 * g.XH * g.XPD);  // [2][tile][YP]
+  float* xh = fbuf + 2 * tile * g.YP;                  // [XH][XPF]
+  float* xl = xh + g.XH * g.XPF;
+  float* tkh = xl + g.XH * g.XPF;                      // [TKH][TP]
+  float* tkl = tkh + g.TKH * g.TP;
+  const int n = op.n;
+  const int per_img = tiles_x * tiles_x;
+  const int total = B * per_img;
+  const size_t plane = (size_t)n * n;
+  auto next_valid = [&](int t) {
+    while (t < total && !active[t / per_img]) t += gridDim.x;
+    return t;
+  };
+  auto origin = [&](int t, int& b, int& ty, int& tx, int& r0, int& c0, int& RH, int& RW) {
+    b = t / per_img;
+    const int tt = t - b * per_img;
+    ty = tt / tiles_x;
+    tx = tt - ty * tiles_x;
+    r0 = ty * tile;
+    c0 = tx * tile;
+    RH = min(tile, n - r0);
+    RW = min(tile, n - c0);
+  };
+  auto prefetch = [&](int t, int buf) {
+    if (t < total) {
+      int b, ty, tx, r0, c0, RH, RW;
+      origin(t, b, ty, tx, r0, c0, RH, RW);
+      const double* ub = u + (size_t)b * plane;
+      const int cs = (c0 - WK) & ~1;
+      const int uch = g.XPD / 2;
+      double* ud = ubuf + buf * g.XH * g.XPD;
+      for (int i = threadIdx.x; i < g.XH * uch; i += blockDim.x) {
+        const int a = i / uch, ch = i - a * uch;
+        const int gr = r0 - WK + a, gc = cs + 2 * ch;
+        const bool in = gr >= 0 && gr < n && gc >= 0 && gc < n;
+        cp_async_16r(ud + a * g.XPD + 2 * ch, in ? ub + (size_t)gr * n + gc : ub, in);
+      }
+      const float* fb = f + (size_t)b * plane;
+      const int cy = c0 & ~3;
+      const int fch = g.YP / 4;
+      float* fd = fbuf + buf * tile * g.YP;
+      for (int i = threadIdx.x; i < RH * fch; i += blockDim.x) {
+        const int a = i / fch, ch = i - a * fch;
+        const int gr = r0 + a, gc = cy + 4 * ch;
+        const bool in = gr < n && gc < n;
+        cp_async_16r(fd + a * g.YP + 4 * ch, in ? fb + (size_t)gr * n + gc : fb, in);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  int cur = next_valid(blockIdx.x);
+  int nxt = cur < total ? next_valid(cur + gridDim.x) : total;
+  prefetch(cur, 0);
+  prefetch(nxt, 1);
+  for (int k = 0; cur < total; ++k) {
+    const int buf = k & 1;
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();
+    int b, ty, tx, r0, c0, RH, RW;
+    origin(cur, b, ty, tx, r0, c0, RH, RW);
+    const int XH = RH + 2 * WK, XW = RW + 2 * WK;
+    const int ofs = (c0 - WK) - ((c0 - WK) & ~1);
+    const int oy = c0 - (c0 & ~3);
+    const double* us = ubuf + buf * g.XH * g.XPD;
+    const float* fs = fbuf + buf * tile * g.YP;
+    // split the staged u into float pairs (logical column c at physical c)
+    for (int i = threadIdx.x; i < XH * XW; i += blockDim.x) {
+      const int a = i / XW, c = i - a * XW;
+      float h, l;
+      split_double(us[a * g.XPD + c + ofs], h, l);
+      xh[a * g.XPF + c] = h;
+      xl[a * g.XPF + c] = l;
+    }
+    __syncthreads();
+    // row pass: t[a][j] = sum_d K[d] u[a][j + d] (double-float)
+    const int nseg_r = (RW + S - 1) / S;
+    for (int item = threadIdx.x; item < XH * nseg_r; item += blockDim.x) {
+      const int a = item % XH, P = (item / XH) * S;
+      float wh[NW], wl[NW];
+      const float* rh = xh + a * g.XPF + P;
+      const float* rl = xl + a * g.XPF + P;
+#pragma unroll
+      for (int q = 0; q < NW / 4; ++q) {
+        const float4 vh = *reinterpret_cast<const float4*>(rh + 4 * q);
+        const float4 vl = *reinterpret_cast<const float4*>(rl + 4 * q);
+        wh[4 * q] = vh.x; wh[4 * q + 1] = vh.y; wh[4 * q + 2] = vh.z; wh[4 * q + 3] = vh.w;
+        wl[4 * q] = vl.x; wl[4 * q + 1] = vl.y; wl[4 * q + 2] = vl.z; wl[4 * q + 3] = vl.w;
+      }
+      DF acc[S];
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) acc[s2] = DF{0.f, 0.f};
+#pragma unroll
+      for (int d = 0; d < 2 * WK + 1; ++d)
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) df_fma(acc[s2], op.sKh[d], op.sKl[d], wh[s2 + d], wl[s2 + d]);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) {
+        const DF t = df_norm(acc[s2]);
+        tkh[a * g.TP + P + s2] = t.h;
+        tkl[a * g.TP + P + s2] = t.l;
+      }
+    }
+    __syncthreads();
+    // column pass, alpha u, residual
+    const int nseg_c = (RH + S - 1) / S;
+    float ss = 0.f;
+    for (int item = threadIdx.x; item < RW * nseg_c; item += blockDim.x) {
+      const int j = item % RW, i0 = (item / RW) * S;
+      float th[NW], tl[NW];
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        th[q] = tkh[(i0 + q) * g.TP + j];
+        tl[q] = tkl[(i0 + q) * g.TP + j];
+      }
+      DF z[S];
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) z[s2] = DF{0.f, 0.f};
+#pragma unroll
+      for (int d = 0; d < 2 * WK + 1; ++d)
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) df_fma(z[s2], op.sKh[d], op.sKl[d], th[s2 + d], tl[s2 + d]);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) {
+        const int i = i0 + s2;
+        if (i >= RH) break;
+        // A u = alpha u + K U K^T, then r = f - A u (double-float, rounded once)
+        const int xc = (i + WK) * g.XPF + j + WK;
+        df_fma(z[s2], op.ah, op.al, xh[xc], xl[xc]);
+        const DF az = df_norm(z[s2]);
+        float s, e;
+        two_sum(fs[i * g.YP + j + oy], -az.h, s, e);
+        const float rv = s + (e - az.l);
+        r[(size_t)b * plane + (size_t)(r0 + i) * n + (c0 + j)] = rv;
+        ss = fmaf(rv, rv, ss);
+      }
+    }
+    if (partials) {
+      double v = (double)ss;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        partials[(size_t)b * per_img + ty * tiles_x + tx] = sum;
+      }
+    }
+    __syncthreads();  // the buffer, the split tile and red[] are free
+    const int after = nxt < total ? next_valid(nxt + gridDim.x) : total;
+    prefetch(after, buf);
+    cur = nxt;
+    nxt = after;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+int num_sms_refine() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+template <int WK>
+bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
+                        const float* f, float* r, double* partials, const int* active, int tile,
+                        int tx, cudaStream_t st) {
+  const RefineGeom g(tile, WK, RSeg<WK>::value);
+  const size_t sm = (size_t)g.words * 4;
+  if (sm > 200 * 1024) return false;
+  RefineArgs<WK> a{};
+  a.n = n;
+  a.ah = (float)alpha;
+  a.al = (float)(alpha - (double)a.ah);
+  for (int d = 0; d <= 2 * sd.wK; ++d) {
+    const double v = sd.sK[d];
+    a.sKh[WK - sd.wK + d] = (float)v;
+    a.sKl[WK - sd.wK + d] = (float)(v - (double)(float)v);
+  }
+  auto kern = k_refine_pipe<WK>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
+  long long grid = (long long)num_sms_refine() * (per_sm > 0 ? per_sm : 1);
+  const long long total = (long long)B * tx * tx;
+  if (grid > total) grid = total;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, 256, sm, st>>>(a, B, u, f, r, partials, active, tile, tx);
+  return true;
+}
+
+// the stencil kernel when the level qualifies (Toeplitz K, M = I, aligned
+// buffers, n a multiple of 4), else false
+bool try_refine_pipe(const StencilHost<double>* sd, double alpha, int n, int B, const double* u,
+                     const float* f, float* r, double* partials, const int* active, int tile,
+                     int tx, cudaStream_t st) {
+  if (!sd || !sd->valid || sd->nbK != 0 || sd->wM != 0 || sd->sM[0] != 1.0 || n % 4 != 0 ||
+      (reinterpret_cast<uintptr_t>(u) & 15) || (reinterpret_cast<uintptr_t>(f) & 15))
+    return false;
+  const int w = sd->wK;
+  if (w <= 2) return launch_refine_pipe<2>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
+  if (w <= 4) return launch_refine_pipe<4>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
+  if (w <= 8) return launch_refine_pipe<8>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
+  if (w <= 16) return launch_refine_pipe<16>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
+  if (w <= 32) return launch_refine_pipe<32>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
+  return false;
+}
+
 }  // namespace
 
 void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float* Md_lo,
-                       double alpha, int B, const double* u, const float* f, float* r,
-                       double* partials, int* ntiles, const int* active, cudaStream_t st,
-                       LaunchLog& log, int tile_req) {
+                       const StencilHost<double>* stencil, double alpha, int B, const double* u,
+                       const float* f, float* r, double* partials, int* ntiles,
+                       const int* active, cudaStream_t st, LaunchLog& log, int tile_req) {
   const int W = hi.wK > hi.wM ? hi.wK : hi.wM;
   int tile = tile_req > 0 ? tile_req : 32;
   if (tile > hi.n) tile = hi.n;
@@ -162,12 +451,13 @@ void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float*
   while (tile > 4 && smem(tile) > 200 * 1024) tile /= 2;
   while (tile < hi.n && (long long)ceil_div(hi.n, tile) * ceil_div(hi.n, tile) > 4096) tile *= 2;
   int tx = ceil_div(hi.n, tile);
-  size_t sm = smem(tile);
-  cudaFuncSetAttribute(k_refine_residual2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  dim3 grid(tx * tx, B);
   int pi_ = log.begin(K_REFINE_RESIDUAL, st);
-  k_refine_residual2d<0><<<grid, 256, sm, st>>>(hi, Kd_lo, Md_lo, alpha, u, f, r, partials, active,
-                                                tile, tx);
+  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, st)) {
+    size_t sm = smem(tile);
+    cudaFuncSetAttribute(k_refine_residual2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_refine_residual2d<0><<<dim3(tx * tx, B), 256, sm, st>>>(hi, Kd_lo, Md_lo, alpha, u, f, r,
+                                                              partials, active, tile, tx);
+  }
   if (ntiles) *ntiles = tx * tx;
   log.end(pi_, st, (double)hi.n * hi.n * log.active_hint);
 }
