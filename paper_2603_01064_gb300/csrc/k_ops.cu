@@ -123,7 +123,7 @@ k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
   }
   __syncthreads();
   // column pass and residual
-  double ss = 0.0;
+  T ss = T(0);
   {
     for (int idx = threadIdx.x; idx < RH * RW; idx += blockDim.x) {
       int i = idx / RW, j = idx % RW;
@@ -139,7 +139,7 @@ k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
         r = yv - (op.alpha * zm + zk);
         if (!RESTRICT) {
           out[(size_t)b * plane + (size_t)gi * n + gj] = r;
-          ss += (double)r * (double)r;
+          ss += r * r;
         }
       }
       if (RESTRICT) rs[idx] = r;
@@ -157,11 +157,11 @@ k_residual2d(Band2D<T> op, const T* __restrict__ x, const T* __restrict__ y,
             T(0.5) * (T(0.25) * c[-1] + T(0.5) * c[0] + T(0.25) * c[1]) +
             T(0.25) * (T(0.25) * c[RW - 1] + T(0.5) * c[RW] + T(0.25) * c[RW + 1]);
       out[(size_t)b * cplane + (size_t)(I0 + ci) * nc + (J0 + cj)] = v;
-      ss += (double)v * (double)v;
+      ss += v * v;
     }
   }
   if (partials) {
-    double s = block_sum<T>(ss, red);
+    double s = block_sum<T>((double)ss, red);
     if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = s;
   }
 }
@@ -383,7 +383,7 @@ k_res2d_pipe(StencilArgs<T, WK> op, int B, const T* __restrict__ x, const T* __r
     __syncthreads();
     // column pass and residual: item -> (column j, segment of S rows)
     const int nseg_c = (RH + S - 1) / S;
-    double ss = 0.0;
+    T ss = T(0);  // this thread's sum of squares (T: no fp64 arithmetic per point in fp32)
     for (int item = threadIdx.x; item < RW * nseg_c; item += blockDim.x) {
       const int j = item % RW, i0 = (item / RW) * S;
       T wk[NW], wm[S + 2];
@@ -433,7 +433,7 @@ k_res2d_pipe(StencilArgs<T, WK> op, int B, const T* __restrict__ x, const T* __r
           r = yv - (op.alpha * zm[s2] + zk[s2]);
           if (!RESTRICT) {
             out[(size_t)b * plane + (size_t)gi * n + gj] = r;
-            ss += (double)r * (double)r;
+            ss = fma_t(r, r, ss);
           }
         }
         if (RESTRICT) rs[i * g.TP + j] = r;
@@ -450,11 +450,11 @@ k_res2d_pipe(StencilArgs<T, WK> op, int B, const T* __restrict__ x, const T* __r
                     T(0.5) * (T(0.25) * c[-1] + T(0.5) * c[0] + T(0.25) * c[1]) +
                     T(0.25) * (T(0.25) * c[g.TP - 1] + T(0.5) * c[g.TP] + T(0.25) * c[g.TP + 1]);
         out[(size_t)b * cplane + (size_t)(I0 + ci) * nc + (J0 + cj)] = v;
-        ss += (double)v * (double)v;
+        ss = fma_t(v, v, ss);
       }
     }
     if (partials) {
-      const double s = block_sum<T>(ss, red);
+      const double s = block_sum<T>((double)ss, red);
       if (threadIdx.x == 0) partials[(size_t)b * per_img + (ty * tiles_x + tx)] = s;
     }
     __syncthreads();  // everyone is done with this buffer and with red[]

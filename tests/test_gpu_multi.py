@@ -28,7 +28,9 @@ def ctx():
 def items_spec():
     W = nmg.load_weights(os.path.join(WDIR, "c2_2d_n128_s2_a1e-2.npz"))
     # (n, levels, sigma, alpha, precision, batch); smoothers trained on the
-    # sigma-2 operator serve every grid size (per-level operators coincide)
+    # sigma-2 operator serve every grid size (per-level operators coincide);
+    # on the sigma-1 operator they diverge, which must also be reproduced
+    # bit for bit
     return W, [(128, 5, 2.0, 1e-2, "bf16_refine", 6), (64, 4, 2.0, 1e-2, "bf16_refine", 9),
                (64, 4, 2.0, 1e-2, "fp32", 5), (32, 3, 1.0, 1e-2, "bf16fast_refine", 4)]
 
@@ -62,7 +64,8 @@ def test_multi_equals_alone(ctx, graphs):
     for (Ga, fa, ua, _), (Gm, fm, um, _), ra, rm in zip(alone, together, res_alone, res_multi):
         assert np.array_equal(ra[0], rm[0])                       # cycles
         assert np.array_equal(ra[1], rm[1])                       # status
-        assert torch.equal(ua, um)                                # iterates, bitwise
+        iv = torch.int64 if ua.dtype == torch.float64 else torch.int32
+        assert torch.equal(ua.view(iv), um.view(iv))              # iterates, bitwise (NaN-safe)
     # the sigma-2 items converge to 1e-6, checked with the oracle's own apply
     for (G, f, u, taps), (n, L, sg, al, prec, B), r in zip(together, spec, res_multi):
         if sg == 2.0:
