@@ -65,6 +65,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x fp32 lanes x FMA x ma
 FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_last": 2 * 9 * 32}
 # tensor-core MMA flops per pixel actually issued by the hidden layers, per bf16 form
 # (the roofline's "achieved" uses the algorithmic flops above)
+# DRAM bytes per output pixel of the hidden convs, mean of the two hidden
+# layers, from one ncu capture of this kernel version (128x128, 64 RHS,
+# level 0; summarised under profiles/); None where no capture exists
+HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 177.3}
 MMA_FLOPS_PER_PX = {
     # split form: two A operands (hi, lo) x N = 64 ([w_hi | w_lo]) per tap and K half
     "bf16_refine": {"cnn_hidden": 2 * 2 * 9 * 32 * 64},
@@ -318,9 +322,14 @@ def run_ours(args, wl, world, rank, local):
         achieved = fl * d["units"] / (d["ms"] / 1e3) / 1e12
         issued = MMA_FLOPS_PER_PX[prec][dom] * d["units"] / (d["ms"] / 1e3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
+        bpu = HIDDEN_DRAM_B_PER_UNIT.get(prec) if dom == "cnn_hidden" else None
+        traffic = bpu * d["units"] / d["launches"] if bpu else None
         roof = {"kernel": f"{dom} (tcgen05 bf16 3x3 conv)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "traffic": traffic, "traffic_bytes_per_unit": bpu,
+                "traffic_source": "ncu dram__bytes_read+write of the 128x128 level at 64 RHS, "
+                                  "scaled to this launch's units" if bpu else None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flop_per_unit": fl, "unit_def": "output pixel x active right-hand side",
                 "mma_issued_tflops": issued,
                 "mma_issued_flop_per_unit": MMA_FLOPS_PER_PX[prec][dom],
