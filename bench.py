@@ -68,12 +68,12 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # DRAM bytes per output pixel of the hidden convs, mean of the two hidden
 # layers, from one ncu capture of this kernel version (128x128, 64 RHS,
 # level 0; summarised under profiles/); None where no capture exists
-HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 177.3}
+HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": None}
 MMA_FLOPS_PER_PX = {
-    # split form: two A operands (hi, lo) x N = 64 ([w_hi | w_lo]) per tap and K half
-    "bf16_refine": {"cnn_hidden": 2 * 2 * 9 * 32 * 64},
+    # split form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
+    "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
     "bf16fast_refine": {"cnn_hidden": 2 * 9 * 32 * 32},
-    "fp16_refine": {"cnn_hidden": 2 * 2 * 9 * 32 * 64},
+    "fp16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
 }
 
 

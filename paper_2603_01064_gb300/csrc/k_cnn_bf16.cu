@@ -31,8 +31,8 @@
 // Split form (SPLIT = 1, the default bf16 form): the smoother's output is
 // dominated by near-constant content that the output filter removes, so a
 // single bf16 rounding of the activations (2^-9 relative) is amplified far
-// beyond the useful filtered part.  Activations are stored as [hi 32 | lo 32]
-// bf16 (v = hi + lo, |lo| <= 2^-9 |v|) and each product is formed from bf16
+// beyond the useful filtered part.  Activations are stored as hi + lo bf16
+// pairs (v = hi + lo, |lo| <= 2^-9 |v|; hi channels in chunks 0-3, lo in 4-7) and each product is formed from bf16
 // MMAs a_hi*w_hi + a_lo*w_hi (+ a_hi*w_lo when the weights are not
 // bf16-exact), accumulated in fp32.  The SIMT layers read and write the
 // pairs and compute in fp32.
@@ -67,7 +67,8 @@ constexpr int CH_BYTES = RH * RW * 16;  // one 8-channel chunk of the staged til
 constexpr int WIDTH = 32;
 constexpr int THREADS = 128;
 // MMA N: fast form 32 output channels; split form 64 = [w_hi | w_lo] so that
-// one MMA per A operand forms both a*w_hi and a*w_lo (summed in the epilogue)
+// the hi A operand's MMA forms both a_hi*w_hi and a_hi*w_lo (summed in the
+// epilogue); the lo A operand's MMA uses N = 32 (w_hi only)
 template <int SPLIT> struct NB { static constexpr int value = SPLIT ? 64 : 32; };
 template <int SPLIT> struct TMC { static constexpr int value = SPLIT ? 256 : 128; };  // TMEM columns
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bound of every mbarrier wait
@@ -183,63 +184,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// write 32 channel values (>= 0: post-ReLU) of one pixel as 16-bit values:
-// bf16 (SPLIT 0, 1) or fp16 (SPLIT 2); split forms: hi block then lo block
+// Activations live in a chunk-planar layout: [image][chunk][y][x][8]
+// (16-bit values; chunk c holds channels 8c .. 8c+7, chunks 0-3 the hi parts
+// and 4-7 the lo parts in the split forms), so that one 16-byte chunk of a
+// pixel row is contiguous in its plane: a TMA tile copy of one chunk moves
+// whole 18-pixel rows, and a warp storing chunk c of its 32 pixels writes
+// contiguous runs.  px0: the pixel's chunk-0 address (nullptr: not stored),
+// cstride: elements between chunk planes.
 template <int SPLIT>
-__device__ __forceinline__ void store_channels(__nv_bfloat16* dst_px, const float* a) {
-  uint32_t pk[16], pl[16];
+__device__ __forceinline__ void store_pixel_planar(const float* a, __nv_bfloat16* px0,
+                                                   size_t cstride) {
+  if (!px0) return;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    if (SPLIT == 2) {
-      const float a0 = fminf(a[2 * c], 65504.f), a1 = fminf(a[2 * c + 1], 65504.f);
-      __half2 h2 = __floats2half2_rn(a0, a1);
-      pk[c] = *reinterpret_cast<uint32_t*>(&h2);
-      __half2 l2 = __floats2half2_rn(a0 - __low2float(h2), a1 - __high2float(h2));
-      pl[c] = *reinterpret_cast<uint32_t*>(&l2);
-      continue;
+  for (int q = 0; q < 4; ++q) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float a0 = a[8 * q + 2 * c], a1 = a[8 * q + 2 * c + 1];
+      if (SPLIT == 2) {
+        const float c0 = fminf(a0, 65504.f), c1 = fminf(a1, 65504.f);
+        __half2 h2 = __floats2half2_rn(c0, c1);
+        __half2 l2 = __floats2half2_rn(c0 - __low2float(h2), c1 - __high2float(h2));
+        hi[c] = *reinterpret_cast<uint32_t*>(&h2);
+        lo[c] = *reinterpret_cast<uint32_t*>(&l2);
+      } else {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+        hi[c] = *reinterpret_cast<uint32_t*>(&h2);
+        if (SPLIT) {
+          __nv_bfloat162 l2 = __floats2bfloat162_rn(a0 - __low2float(h2), a1 - __high2float(h2));
+          lo[c] = *reinterpret_cast<uint32_t*>(&l2);
+        }
+      }
     }
-    __nv_bfloat162 h2 = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
-    pk[c] = *reinterpret_cast<uint32_t*>(&h2);
-    if (SPLIT) {
-      __nv_bfloat162 l2 = __floats2bfloat162_rn(a[2 * c] - __low2float(h2),
-                                                a[2 * c + 1] - __high2float(h2));
-      pl[c] = *reinterpret_cast<uint32_t*>(&l2);
-    }
+    *reinterpret_cast<uint4*>(px0 + q * cstride) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    if (SPLIT)
+      *reinterpret_cast<uint4*>(px0 + (4 + q) * cstride) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
-  uint4* d = reinterpret_cast<uint4*>(dst_px);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) d[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-  if (SPLIT) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      d[4 + q] = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
-  }
-}
-
-// Warp-collective store of 32 pixels' channels: every lane converts its
-// pixel into the warp's shared staging area (144-byte pitch: conflict-free
-// 16-byte accesses), then the warp writes 16-byte pieces so that each store
-// instruction covers consecutive bytes of consecutive pixels.  dst: this
-// lane's pixel in global memory, or nullptr if the pixel is not stored.
-constexpr int STG_PITCH = 144;
-constexpr int STG_WARP = 32 * STG_PITCH;
-template <int SPLIT>
-__device__ __forceinline__ void warp_store_pixels(unsigned char* stg, int lane, const float* a,
-                                                  __nv_bfloat16* dst) {
-  constexpr int Q = SPLIT ? 8 : 4;  // 16-byte pieces per pixel
-  if (dst) store_channels<SPLIT>(reinterpret_cast<__nv_bfloat16*>(stg + lane * STG_PITCH), a);
-  __syncwarp();
-  const unsigned long long mine = reinterpret_cast<unsigned long long>(dst);
-#pragma unroll
-  for (int it = 0; it < Q; ++it) {
-    const int chunk = it * 32 + lane, px = chunk / Q, part = chunk % Q;
-    const unsigned long long d = __shfl_sync(0xffffffffu, mine, px);
-    if (d) {
-      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(d) + part * 16) =
-          *reinterpret_cast<const uint4*>(stg + px * STG_PITCH + part * 16);
-    }
-  }
-  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -251,7 +231,7 @@ __global__ void __launch_bounds__(256)
 k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ aout,
              LayerPack lp, const double* __restrict__ snorm, const int* __restrict__ active,
              int tiles_x) {
-  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
+  constexpr int ACHN = SPLIT ? 8 : 4;  // chunk planes per image
   const int b = blockIdx.y;
   if (!active[b]) return;
   const double s = snorm[b];
@@ -287,72 +267,8 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
     for (int t = 0; t < 9; ++t) acc = fmaf(ws[c * 9 + t], v[t], acc);
     a[c] = fmaxf(acc, 0.f);
   }
-  extern __shared__ __align__(16) unsigned char stg_first[];
-  warp_store_pixels<SPLIT>(stg_first + (tid >> 5) * STG_WARP, tid & 31, a,
-                           in ? aout + ((size_t)b * plane + (size_t)y * n + x) * CW : nullptr);
-}
-
-// ---------------------------------------------------------------------------
-// last layer 32 -> 1 (fp32 SIMT): h = s * (b4 + W4 * a)
-// ---------------------------------------------------------------------------
-template <int SPLIT>
-__global__ void __launch_bounds__(256)
-k_last_simt(int n, const __nv_bfloat16* __restrict__ ain, float* __restrict__ hout, LayerPack lp,
-            const double* __restrict__ snorm, const int* __restrict__ active, int tiles_x) {
-  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
-  constexpr int PXB = CW * 2 + 16;  // padded bytes per staged pixel (bank-conflict free)
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const double s = snorm[b];
-  const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
-  const size_t plane = (size_t)n * n;
-  const int tid = threadIdx.x;
-  if (s == 0.0) {
-    const int y = y0 + tid / TILE, x = x0 + tid % TILE;
-    if (y < n && x < n) hout[(size_t)b * plane + (size_t)y * n + x] = 0.f;
-    return;
-  }
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* ws = reinterpret_cast<float*>(smem);            // [c][tap]
-  unsigned char* ts = smem + WIDTH * 9 * sizeof(float);  // [ry][rx] x PXB bytes
-  for (int i = tid; i < WIDTH * 9; i += 256) ws[i] = lp.wf[i];
-  const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
-  constexpr int Q = CW / 8;  // 16-byte pieces per pixel
-  for (int i = tid; i < RH * RW * Q; i += 256) {
-    int q = i % Q, p = i / Q;
-    int ry = p / RW, rx = p % RW;
-    int y = y0 + ry - 1, x = x0 + rx - 1;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (y >= 0 && y < n && x >= 0 && x < n)
-      v = *reinterpret_cast<const uint4*>(ab + ((size_t)y * n + x) * CW + q * 8);
-    *reinterpret_cast<uint4*>(ts + p * PXB + q * 16) = v;
-  }
-  __syncthreads();
-  const int ry = tid / TILE, rx = tid % TILE;
-  const int y = y0 + ry, x = x0 + rx;
-  if (y >= n || x >= n) return;
-  float acc = lp.bias[0];
-#pragma unroll 1
-  for (int t = 0; t < 9; ++t) {
-    const unsigned char* px = ts + ((ry + t / 3) * RW + (rx + t % 3)) * PXB;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint4 hv = *reinterpret_cast<const uint4*>(px + q * 16);
-      const __nv_bfloat16* hh = reinterpret_cast<const __nv_bfloat16*>(&hv);
-      float a[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) a[e] = __bfloat162float(hh[e]);
-      if (SPLIT) {
-        uint4 lv = *reinterpret_cast<const uint4*>(px + 64 + q * 16);
-        const __nv_bfloat16* ll = reinterpret_cast<const __nv_bfloat16*>(&lv);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) a[e] += __bfloat162float(ll[e]);
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) acc = fmaf(ws[(q * 8 + e) * 9 + t], a[e], acc);
-    }
-  }
-  hout[(size_t)b * plane + (size_t)y * n + x] = (float)s * acc;
+  store_pixel_planar<SPLIT>(
+      a, in ? aout + ((size_t)b * ACHN * plane + (size_t)y * n + x) * 8 : nullptr, plane * 8);
 }
 
 // All MMAs of one block tile: for each M tile (8-column half), 9 taps x 2 K
@@ -363,19 +279,31 @@ template <int SPLIT, int PITCH>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base, uint32_t d0) {
   constexpr int N = NB<SPLIT>::value;
   constexpr uint32_t idesc = make_idesc(128, N, SPLIT == 2);
+  // lo A operand: N = 32 (w_hi only, the first 32 rows of B) accumulating
+  // into the hi columns; a_lo * w_lo (~2^-32 relative) is not formed
+  constexpr uint32_t idesc_lo = make_idesc(128, 32, SPLIT == 2);
   const uint64_t ad0 = make_desc(a_base, PITCH, RW * 16);
   const uint64_t bd0 = make_desc(b_base, N * 16, 128);
+  // the M tiles' accumulation chains are interleaved (consecutive MMAs write
+  // different accumulators)
 #pragma unroll
-  for (int mt = 0; mt < NT; ++mt) {
-    const uint32_t d = d0 + mt * N;
+  for (int tap = 0; tap < 9; ++tap) {
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
+    for (int kh = 0; kh < 2; ++kh) {
+      const uint32_t boff = ((tap * 4 + 2 * kh) * N * 16) >> 4;
 #pragma unroll
-      for (int kh = 0; kh < 2; ++kh) {
+      for (int mt = 0; mt < NT; ++mt) {
+        const uint32_t d = d0 + mt * N;
         const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
-        const uint32_t boff = ((tap * 4 + 2 * kh) * N * 16) >> 4;
         mma_bf16(d, ad0 + aoff, bd0 + boff, idesc, (tap | kh) ? 1u : 0u);
-        if (SPLIT) mma_bf16(d, ad0 + aoff + ((4 * PITCH) >> 4), bd0 + boff, idesc, 1u);
+      }
+      if (SPLIT) {
+#pragma unroll
+        for (int mt = 0; mt < NT; ++mt) {
+          const uint32_t d = d0 + mt * N;
+          const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
+          mma_bf16(d, ad0 + aoff + ((4 * PITCH) >> 4), bd0 + boff, idesc_lo, 1u);
+        }
       }
     }
   }
@@ -388,9 +316,9 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
 // written as fp32 planes g[tap][pixel] (plane stride gstride).
 template <int SPLIT, int FUSE>
 __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bias,
-                                             float bscale, __nv_bfloat16* dst, float* gdst,
-                                             size_t gstride, const float* __restrict__ w4,
-                                             bool store, unsigned char* stg, int lane) {
+                                             float bscale, __nv_bfloat16* dst, size_t cstride,
+                                             float* gdst, size_t gstride,
+                                             const float* __restrict__ w4, bool store) {
   float v[32];
   tmem_ld32(taddr, v);
   if (SPLIT) {
@@ -402,7 +330,7 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
 #pragma unroll
   for (int c = 0; c < 32; ++c) v[c] = fmaxf(fmaf(bscale, bias[c], v[c]), 0.f);
   if (!FUSE) {
-    warp_store_pixels<SPLIT>(stg, lane, v, store ? dst : nullptr);  // warp-collective
+    store_pixel_planar<SPLIT>(v, store ? dst : nullptr, cstride);
     return;
   }
   if (!store) return;
@@ -439,7 +367,6 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
   constexpr int TMEM_COLS = TMC<SPLIT>::value;
   constexpr int NACC = NT * NB<SPLIT>::value;  // columns of one accumulator
-  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* Bs = smem + 2 * ABUF;
   __shared__ __align__(8) uint64_t mbar[2];
@@ -490,14 +417,14 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   auto stage = [&](int t, int buf) {
     const int b = t / per_img, tt = t - b * per_img;
     const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
-    const __nv_bfloat16* ab = ain + (size_t)b * plane * CW;
+    const __nv_bfloat16* ab = ain + (size_t)b * ACH * plane * 8;
     const uint32_t base = a_base0 + buf * ABUF;
     for (int i = tid; i < RH * RW * ACH; i += THREADS) {
       const int c = i % ACH, p = i / ACH;
       const int ry = p / RW, rx = p % RW;
       const int y = y0 + ry - 1, x = x0 + rx - 1;
       const bool in = y >= 0 && y < n && x >= 0 && x < n;
-      const __nv_bfloat16* src = in ? ab + ((size_t)y * n + x) * CW + c * 8 : ain;
+      const __nv_bfloat16* src = in ? ab + ((size_t)c * plane + (size_t)y * n + x) * 8 : ain;
       cp_async16(base + c * CH_BYTES + (ry * RW + rx) * 16, src, in ? 16u : 0u);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -518,8 +445,8 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       const size_t pix = (size_t)b * plane + (size_t)y * n + x;
       finish_pixel<SPLIT, FUSE>(
           tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, lp.bias,
-          net_scale<SPLIT>(n), in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
-          Bs + B_BYTES + warp * STG_WARP, lane);
+          net_scale<SPLIT>(n), aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8, plane * 8,
+          in ? gout + pix : gout, (size_t)nimg * plane, w4s, in);
     }
   };
 
@@ -593,12 +520,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint32_t mbar) {
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, int c4, uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(mbar)
       : "memory");
 }
 
@@ -612,7 +540,6 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   constexpr int SBYTES = ACH * CH_PITCH;           // one stage
   constexpr uint32_t TX = ACH * RH * RW * 16;      // bytes the copies of one stage write
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
-  constexpr int CW = SPLIT ? 2 * WIDTH : WIDTH;
   constexpr int TMEM_COLS = TMC<SPLIT>::value;
   constexpr int NACC = NT * NB<SPLIT>::value;
   extern __shared__ __align__(16) unsigned char smem_raw_ws[];
@@ -700,7 +627,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, TX);
         const uint32_t dst = smem_u32(smem + s * SBYTES);
-        for (int c = 0; c < ACH; ++c) tma_load_4d(dst + c * CH_PITCH, &amap, c * 8, x0 - 1, y0 - 1, b, fb);
+        for (int c = 0; c < ACH; ++c) tma_load_5d(dst + c * CH_PITCH, &amap, 0, x0 - 1, y0 - 1, c, b, fb);
       }
     }
   } else if (warp == 1) {
@@ -739,8 +666,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const size_t pix = (size_t)b * plane + (size_t)y * n + x;
         finish_pixel<SPLIT, FUSE>(
             tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value, lp.bias,
-            net_scale<SPLIT>(n), in ? aout + pix * CW : aout, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in,
-            Bs + B_BYTES + (warp - 2) * STG_WARP, lane);
+            net_scale<SPLIT>(n), aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8,
+            plane * 8, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -754,7 +681,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-// tensor maps over the NHWC activation buffers, created on first use
+// tensor maps over the chunk-planar activation buffers, created on first use
 struct MapEntry {
   const void* ptr;
   int n, nimg, cw;
@@ -788,11 +715,14 @@ const CUtensorMap* act_map(const void* ptr, int n, int nimg, int cw) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return nullptr;
   MapEntry e{ptr, n, nimg, cw, {}};
-  cuuint64_t dims[4] = {(cuuint64_t)cw, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nimg};
-  cuuint64_t strides[3] = {(cuuint64_t)cw * 2, (cuuint64_t)n * cw * 2, (cuuint64_t)n * n * cw * 2};
-  cuuint32_t box[4] = {8, (cuuint32_t)RW, (cuuint32_t)RH, 1};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = fn(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims,
+  // chunk-planar activations [image][chunk][y][x][8]: one 16-byte chunk per
+  // pixel and plane; the box is one chunk of an 18 x 18 pixel tile
+  const cuuint64_t ch = (cuuint64_t)cw / 8;
+  cuuint64_t dims[5] = {8, (cuuint64_t)n, (cuuint64_t)n, ch, (cuuint64_t)nimg};
+  cuuint64_t strides[4] = {16, (cuuint64_t)n * 16, (cuuint64_t)n * n * 16, ch * n * n * 16};
+  cuuint32_t box[5] = {8, (cuuint32_t)RW, (cuuint32_t)RH, 1, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(ptr), dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return nullptr;
@@ -871,7 +801,7 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
     constexpr int STAGES = 3;
     constexpr int ACHs = SPLIT ? 8 : 4;
     constexpr int B_BYTESs = SPLIT ? 2 * B_HALF : B_HALF;
-    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + EPI<SPLIT>::value * STG_WARP + 1024;
+    const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + 1024;
     const int tiles_x = (n + TILE - 1) / TILE;
     long long total = (long long)nimg * tiles_x * tiles_x;
     long long grid = (long long)num_sms() * (SPLIT ? 1 : 2);
@@ -885,7 +815,7 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
   }
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
-  const size_t sm = 2 * ACH * CH_BYTES + B_BYTES + 4 * STG_WARP;
+  const size_t sm = 2 * ACH * CH_BYTES + B_BYTES;
   const int tiles_x = (n + TILE - 1) / TILE;
   long long total = (long long)nimg * tiles_x * tiles_x;
   long long grid = (long long)num_sms() * (SPLIT ? 1 : 3);
@@ -905,9 +835,7 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   dim3 grid(tiles_x * tiles_x, B);
   const double units = (double)n * n * log.active_hint;
   int pi_ = log.begin(K_CNN_FIRST, st);
-  const size_t smf = 8 * STG_WARP;
-  cudaFuncSetAttribute(k_first_simt<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-  k_first_simt<SPLIT><<<grid, 256, smf, st>>>(n, b, a0, P.l[0], s, active, tiles_x);
+  k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.l[0], s, active, tiles_x);
   log.end(pi_, st, units);
   __nv_bfloat16* cur = a0;
   __nv_bfloat16* nxt = a1;
@@ -1032,10 +960,10 @@ void bf16_cnn_forget(const void* pack) {
     }
 }
 
-// h = s N(b / s) for `B` images of side n; act0/act1 hold NHWC bf16
-// activations (B * n * n * 32 elements, x2 in the split form), described to
-// the copy engine as map_imgs >= B images so one tensor map serves every
-// chunk; err: device error word of the bounded waits.
+// h = s N(b / s) for `B` images of side n; act0/act1 hold chunk-planar
+// 16-bit activations (B * n * n * 32 elements, x2 in the split forms),
+// described to the copy engine as map_imgs >= B images so one tensor map
+// serves every chunk; err: device error word of the bounded waits.
 void bf16_cnn_launch(int n, int B, int map_imgs, int layers, const void* pack, const float* b,
                      const double* s, float* act0, float* act1, float* h, const int* active,
                      int* err, cudaStream_t st, LaunchLog& log) {
