@@ -28,14 +28,13 @@
 // timeout the block records an error code, stops and releases its tensor
 // memory.
 //
-// Split form (SPLIT = 1, the default bf16 form): the smoother's output is
-// dominated by near-constant content that the output filter removes, so a
-// single bf16 rounding of the activations (2^-9 relative) is amplified far
-// beyond the useful filtered part.  Activations are stored as hi + lo bf16
-// pairs (v = hi + lo, |lo| <= 2^-9 |v|; hi channels in chunks 0-3, lo in 4-7) and each product is formed from bf16
-// MMAs a_hi*w_hi + a_lo*w_hi (+ a_hi*w_lo when the weights are not
-// bf16-exact), accumulated in fp32.  The SIMT layers read and write the
-// pairs and compute in fp32.
+// Split form (SPLIT = 1, the default bf16 form): the trained smoothers
+// amplify rounding of their hidden activations (large, cancelling weights),
+// so a single bf16 rounding (2^-9 relative) moves a cycle's iterate by
+// percents.  Activations are stored as hi + lo bf16 pairs (v = hi + lo,
+// |lo| <= 2^-9 |v|; hi channels in chunks 0-3, lo in chunks 4-7) and each
+// product is formed from bf16 MMAs a_hi*w_hi + a_hi*w_lo + a_lo*w_hi,
+// accumulated in fp32.  The SIMT layers compute in fp32.
 //
 // fp16 split form (SPLIT = 2): the same [hi | lo] pairs and MMAs with fp16
 // operands (11-bit significands: hi + lo carries 2^-22 instead of 2^-16).
