@@ -511,6 +511,7 @@ constexpr int CH_PITCH = 5248;       // chunk stride in shared memory (128-byte 
 // one warp per sub-partition), 4 in the fast form (which runs 2 CTAs per SM)
 template <int SPLIT> struct EPI { static constexpr int value = SPLIT ? 8 : 4; };
 template <int SPLIT> struct WST { static constexpr int value = 64 + 32 * EPI<SPLIT>::value; };
+constexpr int kMaskImgs = 32768;  // images whose validity bits a block keeps in shared memory
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
@@ -550,6 +551,10 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   __shared__ int abort_flag;
 
   __shared__ __align__(16) float w4s[FUSE ? 9 * 32 : 4];
+  // one bit per image: active and with a nonzero norm.  Every role walks the
+  // tile sequence; reading these from global memory per tile would put an L2
+  // round trip between consecutive tiles of the MMA issuer.
+  __shared__ uint32_t vmask[kMaskImgs / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
@@ -557,6 +562,12 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     for (int i = tid; i < B_BYTES / 16; i += WST<SPLIT>::value) dst[i] = src[i];
     if (FUSE)
       for (int i = tid; i < 9 * 32; i += WST<SPLIT>::value) w4s[i] = w4[(i % 32) * 9 + i / 32];
+    if (nimg <= kMaskImgs)
+      for (int b0 = warp * 32; b0 < nimg; b0 += WST<SPLIT>::value) {  // warp-uniform loop
+        const int b = b0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, b < nimg && active[b] != 0 && snorm[b] != 0.0);
+        if (lane == 0) vmask[b0 >> 5] = m;
+      }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -588,6 +599,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   const size_t plane = (size_t)n * n;
   auto valid = [&](int t) {
     const int b = t / per_img;
+    if (nimg <= kMaskImgs) return ((vmask[b >> 5] >> (b & 31)) & 1u) != 0;
     return active[b] != 0 && snorm[b] != 0.0;
   };
   auto first = [&]() {
