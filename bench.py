@@ -250,7 +250,11 @@ def run_ours(args, wl, world, rank, local):
 
     G = hier(prec)
     B = args.batch or wl["batch"]
-    G.autotune(B)  # launch shapes per level, timed on this GPU (outside the timed region)
+    # launch shapes per level, timed on this GPU (outside the timed region);
+    # with --tune-cache the choices are read from / appended to that file, so
+    # that a profiled run (whose timings ncu distorts) launches the shapes the
+    # plain run chose
+    G.autotune(B, args.tune_cache)
     f_np = make_rhs(wl, B, rank_seed(wl, rank))
     refine = prec != "fp32"
     udt = torch.float64 if refine else torch.float32
@@ -478,6 +482,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling runs)")
     ap.add_argument("--ncu", action="store_true", help="a single solve, nothing else (profiling)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="launch-shape choices file (read if present, else written)")
     ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")

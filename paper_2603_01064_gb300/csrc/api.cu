@@ -1975,7 +1975,7 @@ extern "C" nmg_status nmg_residual_noalloc(nmg_ctx* ctx, nmg_hier* h, int level,
   quiet.active_hint = batch;
   k_noalloc_ones<<<ceil_div(batch, 256), 256, 0, ctx->stream>>>(active, batch);
   ++quiet.launches;
-  int launched_nt = 0;  // equals nt: both come from the launchers' tile choice
+  int launched_nt = 0;  // partial sums written per item (<= nt, the sizing bound)
   if (h->dim == 2) {
     if (f64)
       launch_residual2d<double>(band<double>(h, level), batch, (const double*)x, (const double*)y,
@@ -1995,7 +1995,7 @@ extern "C" nmg_status nmg_residual_noalloc(nmg_ctx* ctx, nmg_hier* h, int level,
                                (const float*)y, (float*)r, part, &launched_nt, active, ctx->stream,
                                quiet);
   }
-  if (norms) launch_norms(part, nt, batch, nrm, active, ctx->stream, quiet);
+  if (norms) launch_norms(part, launched_nt, batch, nrm, active, ctx->stream, quiet);
   ctx->log.launches += quiet.launches;
   CK(cudaGetLastError());
   if (norms) {

@@ -18,8 +18,9 @@
 // Levels with n >= 32 use a warp-specialised persistent kernel: one warp
 // issues TMA tensor copies of the input tiles (the halo outside the image is
 // zero-filled by the copy engine) into a ring of shared-memory stages, one
-// warp issues the MMAs of a tile into one of two tensor-memory accumulators
-// as soon as its stage is full, and four (fast form) or eight (split forms)
+// warp (fast form) or one warp per M tile (split forms) issues the MMAs of a
+// tile into one of two tensor-memory accumulators as soon as its stage is
+// full, and four (fast form) or eight (split forms)
 // warps drain the other accumulator (tensor memory -> registers -> bias,
 // ReLU -> 16-bit values -> global).  Stages and
 // accumulators are handed over with mbarriers (full/empty, acc_full/
@@ -233,18 +234,24 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   constexpr int ACHN = SPLIT ? 8 : 4;  // chunk planes per image
   const int b = blockIdx.y;
   if (!active[b]) return;
-  const double s = snorm[b];
-  if (s == 0.0) return;  // h = 0 is written by the last layer
+  // ||b|| = 0 (tested on the bits: fp64 arithmetic runs at 1/64 of the fp32
+  // rate, so one thread forms sigma / ||b|| for the block): h = 0 is written
+  // by the last layer
+  const long long sbits = __double_as_longlong(snorm[b]);
+  if ((sbits << 1) == 0) return;
   __shared__ float xs[RH][RW + 1];
   __shared__ float ws[WIDTH * 9];
   __shared__ float bs[WIDTH];
+  __shared__ float inv_s;
   const int tid = threadIdx.x;
   for (int i = tid; i < WIDTH * 9; i += 256) ws[i] = lp.wf[i];
   const float sig = net_scale<SPLIT>(n);
   if (tid < WIDTH) bs[tid] = sig * lp.bias[tid];
+  if (tid == 0) inv_s = (float)((double)sig / __longlong_as_double(sbits));
   const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
   const size_t plane = (size_t)n * n;
-  const float inv = (float)((double)sig / s);
+  __syncthreads();
+  const float inv = inv_s;
   const float* bb = bsrc + (size_t)b * plane;
   for (int i = tid; i < RH * RW; i += 256) {
     int ry = i / RW, rx = i % RW;
@@ -274,7 +281,7 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
 // halves, one MMA per A operand (hi, and lo in the split form).  Descriptors
 // are built once; per MMA only a compile-time offset is added to their
 // start-address field.
-template <int SPLIT, int PITCH>
+template <int SPLIT, int PITCH, int MT0 = 0, int MTN = NT>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base, uint32_t d0) {
   constexpr int N = NB<SPLIT>::value;
   constexpr uint32_t idesc = make_idesc(128, N, SPLIT == 2);
@@ -291,14 +298,14 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
     for (int kh = 0; kh < 2; ++kh) {
       const uint32_t boff = ((tap * 4 + 2 * kh) * N * 16) >> 4;
 #pragma unroll
-      for (int mt = 0; mt < NT; ++mt) {
+      for (int mt = MT0; mt < MT0 + MTN; ++mt) {
         const uint32_t d = d0 + mt * N;
         const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
         mma_bf16(d, ad0 + aoff, bd0 + boff, idesc, (tap | kh) ? 1u : 0u);
       }
       if (SPLIT) {
 #pragma unroll
-        for (int mt = 0; mt < NT; ++mt) {
+        for (int mt = MT0; mt < MT0 + MTN; ++mt) {
           const uint32_t d = d0 + mt * N;
           const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
           mma_bf16(d, ad0 + aoff + ((4 * PITCH) >> 4), bd0 + boff, idesc_lo, 1u);
@@ -502,15 +509,21 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
 }
 
 // ---------------------------------------------------------------------------
-// hidden layer, warp-specialised: TMA producer / MMA issuer / 4 epilogue warps
+// hidden layer, warp-specialised: TMA producer / MMA issuer(s) / epilogue warps
 // ---------------------------------------------------------------------------
 constexpr int CH_PITCH = 5248;       // chunk stride in shared memory (128-byte multiple)
-// warp 0 TMA, warp 1 MMA, then the epilogue warps: 8 in the split forms (two
-// per SM sub-partition, one per tensor-memory lane quarter and M tile: the
-// epilogue converts twice the accumulator columns and is latency-bound with
-// one warp per sub-partition), 4 in the fast form (which runs 2 CTAs per SM)
-template <int SPLIT> struct EPI { static constexpr int value = SPLIT ? 8 : 4; };
-template <int SPLIT> struct WST { static constexpr int value = 64 + 32 * EPI<SPLIT>::value; };
+// warp 0 TMA, then the MMA issuer(s), then the epilogue warps in groups of
+// four (one per tensor-memory lane quarter): the fast form has one group for
+// both M tiles (it runs 2 CTAs per SM), the split forms one group per M tile
+// (the epilogue converts twice the accumulator columns and is latency-bound
+// with one warp per sub-partition)
+template <int SPLIT, int FUSE> struct EPI { static constexpr int value = SPLIT ? 8 : 4; };
+// MMA issuers: one per M tile in the split forms (a single issuing thread
+// does not keep the tensor pipe fed with the split form's 72 MMAs per tile)
+template <int SPLIT> struct ISS { static constexpr int value = SPLIT ? NT : 1; };
+template <int SPLIT, int FUSE> struct WST {
+  static constexpr int value = 32 * (1 + ISS<SPLIT>::value + EPI<SPLIT, FUSE>::value);
+};
 constexpr int kMaskImgs = 32768;  // images whose validity bits a block keeps in shared memory
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -531,7 +544,7 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
 }
 
 template <int SPLIT, int STAGES, int FUSE>
-__global__ void __launch_bounds__(WST<SPLIT>::value)
+__global__ void __launch_bounds__(WST<SPLIT, FUSE>::value)
 k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
             const float* __restrict__ w4, const double* __restrict__ snorm,
@@ -559,11 +572,11 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
-    for (int i = tid; i < B_BYTES / 16; i += WST<SPLIT>::value) dst[i] = src[i];
+    for (int i = tid; i < B_BYTES / 16; i += WST<SPLIT, FUSE>::value) dst[i] = src[i];
     if (FUSE)
-      for (int i = tid; i < 9 * 32; i += WST<SPLIT>::value) w4s[i] = w4[(i % 32) * 9 + i / 32];
+      for (int i = tid; i < 9 * 32; i += WST<SPLIT, FUSE>::value) w4s[i] = w4[(i % 32) * 9 + i / 32];
     if (nimg <= kMaskImgs)
-      for (int b0 = warp * 32; b0 < nimg; b0 += WST<SPLIT>::value) {  // warp-uniform loop
+      for (int b0 = warp * 32; b0 < nimg; b0 += WST<SPLIT, FUSE>::value) {  // warp-uniform loop
         const int b = b0 + lane;
         const unsigned m = __ballot_sync(0xffffffffu, b < nimg && active[b] != 0 && snorm[b] != 0.0);
         if (lane == 0) vmask[b0 >> 5] = m;
@@ -578,12 +591,14 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   if (tid == 32) {
     for (int i = 0; i < STAGES; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])),
+                   "r"(ISS<SPLIT>::value));
     }
     for (int i = 0; i < 2; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_full[i])),
+                   "r"(ISS<SPLIT>::value));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
-                   "r"(EPI<SPLIT>::value));
+                   "r"(EPI<SPLIT, FUSE>::value));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
@@ -641,8 +656,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         for (int c = 0; c < ACH; ++c) tma_load_5d(dst + c * CH_PITCH, &amap, 0, x0 - 1, y0 - 1, c, b, fb);
       }
     }
-  } else if (warp == 1) {
-    // ---- MMA issuer
+  } else if (warp <= ISS<SPLIT>::value) {
+    // ---- MMA issuer(s): all M tiles, or M tile warp - 1
     if (lane == 0) {
       const uint32_t b_base = smem_u32(Bs);
       int i = 0;
@@ -651,17 +666,24 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         if (!wait(&full[s], (uint32_t)((i / STAGES) & 1))) break;
         if (i >= 2 && !wait(&acc_empty[a], (uint32_t)((i / 2 - 1) & 1))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        issue_tile_mmas<SPLIT, CH_PITCH>(smem_u32(smem + s * SBYTES), b_base, tmem + a * NACC);
+        const uint32_t sa = smem_u32(smem + s * SBYTES), d0 = tmem + a * NACC;
+        if (ISS<SPLIT>::value == 1)
+          issue_tile_mmas<SPLIT, CH_PITCH>(sa, b_base, d0);
+        else if (warp == 1)
+          issue_tile_mmas<SPLIT, CH_PITCH, 0, 1>(sa, b_base, d0);
+        else
+          issue_tile_mmas<SPLIT, CH_PITCH, 1, 1>(sa, b_base, d0);
         mma_commit(smem_u32(&empty[s]));
         mma_commit(smem_u32(&acc_full[a]));
       }
     }
   } else {
-    // ---- epilogue warps: lane quarter q = warp % 4 of tensor memory; with 8
-    // warps, warps 2-5 take M tile 0 and warps 6-9 M tile 1
-    constexpr int MTW = NT * 4 / EPI<SPLIT>::value;  // M tiles per epilogue warp
+    // ---- epilogue warps: lane quarter q = warp % 4 of tensor memory; group
+    // g of four consecutive warps takes M tile g (both with one group)
+    constexpr int GROUPS = EPI<SPLIT, FUSE>::value / 4;
+    constexpr int MTW = GROUPS >= NT ? 1 : NT;  // M tiles per epilogue warp
     const int q = warp & 3;
-    const int mt0 = ((warp - 2) >> 2) * MTW;
+    const int mt0 = GROUPS >= NT ? (warp - 1 - ISS<SPLIT>::value) >> 2 : 0;
     int i = 0;
     for (int t = first(); t < total; t = advance(t), ++i) {
       const int a = i & 1;
@@ -675,10 +697,11 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const int x = x0 + mt * 8 + (m & 7);
         const bool in = y < n && x < n;
         const size_t pix = (size_t)b * plane + (size_t)y * n + x;
-        finish_pixel<SPLIT, FUSE>(
-            tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value, lp.bias,
-            net_scale<SPLIT>(n), aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8,
-            plane * 8, in ? gout + pix : gout, (size_t)nimg * plane, w4s, in);
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value;
+        __nv_bfloat16* dst = aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8;
+        float* gd = in ? gout + pix : gout;
+        finish_pixel<SPLIT, FUSE>(ta, lp.bias, net_scale<SPLIT>(n), dst, plane * 8, gd,
+                                  (size_t)nimg * plane, w4s, in);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -750,11 +773,18 @@ k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ 
               const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
-  const double s = snorm[b];
+  // ||b|| as fp32, formed once per block (fp64 conversions run at 1/64 of
+  // the fp32 rate); zero tested on the fp64 bits
+  __shared__ float s_sh;
+  const long long sbits = __double_as_longlong(snorm[b]);
+  if (threadIdx.x == 0) s_sh = (float)__longlong_as_double(sbits);
+  __syncthreads();
+  const float sf = s_sh;
+  const bool nz = (sbits << 1) != 0;
   const size_t plane = (size_t)n * n, gstride = (size_t)nimg * plane;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)plane; p += gridDim.x * blockDim.x) {
     float acc = 0.f;
-    if (s != 0.0) {
+    if (nz) {
       const int y = p / n, x = p % n;
       acc = bscale * bias0;
 #pragma unroll
@@ -763,7 +793,7 @@ k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ 
         if (yy >= 0 && yy < n && xx >= 0 && xx < n)
           acc += g[t * gstride + (size_t)b * plane + (size_t)yy * n + xx];
       }
-      acc *= (float)s;
+      acc *= sf;
       acc *= 1.f / bscale;  // a power of two: exact
     }
     hout[(size_t)b * plane + p] = acc;
@@ -820,7 +850,7 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
     if (grid < 1) grid = 1;
     cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int pi_ = log.begin(K_CNN_HIDDEN, st);
-    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WST<SPLIT>::value, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, s, active, err);
+    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WST<SPLIT, FUSE>::value, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, s, active, err);
     log.end(pi_, st, (double)n * n * log.active_hint);
     return;
   }

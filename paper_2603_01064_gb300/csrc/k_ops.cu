@@ -399,22 +399,26 @@ void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
   int tile = pick_tile<T>(op.n, op.wK, op.wM, false, tile_req);
   int tx = ceil_div(op.n, tile);
   int pi_ = log.begin(K_RESIDUAL, st);
-  if (!launch_stencil_residual<T, false>(op, B, x, y, r, partials, active, tile, tx, st)) {
+  int nparts = tx * tx;
+  if (!launch_stencil_residual<T, false>(op, B, x, y, r, partials, active, tile, tx, st, &nparts)) {
+    nparts = tx * tx;
     size_t sm = residual_smem<T>(tile, tile, op.wK, op.wM, false);
     auto kern = k_residual2d<T, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<dim3(tx * tx, B), kThreads, sm, st>>>(op, x, y, r, partials, active, tile, tx);
   }
-  if (ntiles) *ntiles = tx * tx;
+  if (ntiles) *ntiles = nparts;
   log.end(pi_, st, (double)op.n * op.n * log.active_hint);
 }
 
-// Partial sums launch_residual2d writes per right-hand side (one per tile),
-// for a caller that has to size their buffer before the launch.
+// Upper bound of the partial sums launch_residual2d writes per right-hand
+// side (one per tile or strip unit), for a caller that has to size their
+// buffer before the launch (the launch reports the exact count).
 template <typename T>
 int residual2d_tiles(const Band2D<T>& op, int tile_req) {
   const int tx = ceil_div(op.n, pick_tile<T>(op.n, op.wK, op.wM, false, tile_req));
-  return tx * tx;
+  const int strip = stencil_strip_parts<T>(op);
+  return tx * tx > strip ? tx * tx : strip;
 }
 
 template <typename T>
@@ -425,13 +429,15 @@ void launch_residual_restrict2d(const Band2D<T>& op, int B, const T* x, const T*
   int nc = op.n / 2;
   int tx = ceil_div(nc, tile);
   int pi_ = log.begin(K_RESTRICT, st);
-  if (!launch_stencil_residual<T, true>(op, B, x, y, yc, partials, active, tile, tx, st)) {
+  int nparts = tx * tx;
+  if (!launch_stencil_residual<T, true>(op, B, x, y, yc, partials, active, tile, tx, st, &nparts)) {
+    nparts = tx * tx;
     size_t sm = residual_smem<T>(2 * tile + 1, 2 * tile + 1, op.wK, op.wM, true);
     auto kern = k_residual2d<T, true>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<dim3(tx * tx, B), kThreads, sm, st>>>(op, x, y, yc, partials, active, tile, tx);
   }
-  if (ntiles) *ntiles = tx * tx;
+  if (ntiles) *ntiles = nparts;
   log.end(pi_, st, (double)op.n * op.n * log.active_hint);
 }
 

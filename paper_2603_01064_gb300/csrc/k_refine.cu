@@ -219,7 +219,7 @@ k_refine_pipe(RefineArgs<WK> op, int B, const double* __restrict__ u, const floa
   constexpr int S = RSeg<WK>::value, NW = S + 2 * WK;
   const RefineGeom g(tile, WK, S);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ float red[32];
   double* ubuf = reinterpret_cast<double*>(smem_raw);  // [2][XH][XPD]
   float* fbuf = reinterpret_cast<float*>(ubuf + 2 * g.XH * g.XPD);  // [2][tile][YP]
   float* xh = fbuf + 2 * tile * g.YP;                  // [XH][XPF]
@@ -359,14 +359,16 @@ k_refine_pipe(RefineArgs<WK> op, int B, const double* __restrict__ u, const floa
       }
     }
     if (partials) {
-      double v = (double)ss;
+      // fp32 tree over the tile (fp64 adds run at 1/64 of the fp32 rate and
+      // stalled the whole block on this reduction); fp64 across tiles
+      float v = ss;
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
       __syncthreads();
       if (threadIdx.x == 0) {
-        double sum = 0.0;
+        float sum = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
-        partials[(size_t)b * per_img + ty * tiles_x + tx] = sum;
+        partials[(size_t)b * per_img + ty * tiles_x + tx] = (double)sum;
       }
     }
     __syncthreads();  // the buffer, the split tile and red[] are free
@@ -390,12 +392,7 @@ int num_sms_refine() {
 }
 
 template <int WK>
-bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
-                        const float* f, float* r, double* partials, const int* active, int tile,
-                        int tx, cudaStream_t st) {
-  const RefineGeom g(tile, WK, RSeg<WK>::value);
-  const size_t sm = (size_t)g.words * 4;
-  if (sm > 200 * 1024) return false;
+RefineArgs<WK> refine_args(const StencilHost<double>& sd, double alpha, int n) {
   RefineArgs<WK> a{};
   a.n = n;
   a.ah = (float)alpha;
@@ -405,6 +402,17 @@ bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int 
     a.sKh[WK - sd.wK + d] = (float)v;
     a.sKl[WK - sd.wK + d] = (float)(v - (double)(float)v);
   }
+  return a;
+}
+
+template <int WK>
+bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
+                        const float* f, float* r, double* partials, const int* active, int tile,
+                        int tx, cudaStream_t st) {
+  const RefineGeom g(tile, WK, RSeg<WK>::value);
+  const size_t sm = (size_t)g.words * 4;
+  if (sm > 200 * 1024) return false;
+  const RefineArgs<WK> a = refine_args<WK>(sd, alpha, n);
   auto kern = k_refine_pipe<WK>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int per_sm = 0;

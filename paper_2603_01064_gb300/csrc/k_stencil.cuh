@@ -53,19 +53,23 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return d;
 }
 
-// block-wide sum (warp shuffles, then one value per warp in shared memory,
-// added in a fixed order: deterministic); the result is valid in thread 0
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// block-wide sum in the level type T (warp shuffles, then one value per
+// warp in shared memory, added in a fixed order: deterministic); the result
+// is valid in thread 0.  fp32 levels stay in fp32: fp64 adds run at 1/64 of
+// the fp32 rate, and a tree of them held every warp of the block at the next
+// barrier.
+template <typename T>
+__device__ __forceinline__ double block_sum(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   if (threadIdx.x == 0) {
     const int nw = (blockDim.x + 31) >> 5;
     for (int i = 0; i < nw; ++i) s += red[i];
   }
-  return s;
+  return (double)s;
 }
 
 template <typename T, int WK>
@@ -154,7 +158,7 @@ k_res2d_pipe(StencilArgs<T, WK> op, int B, const T* __restrict__ x, const T* __r
   constexpr bool PACK = std::is_same<T, float>::value;
   const G g(tile);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ T red[32];
   T* xbuf = reinterpret_cast<T*>(smem_raw);  // [2][XH][XP]
   T* ybuf = xbuf + 2 * g.XH * g.XP;          // [2][RH][YP]
   T* tk = ybuf + 2 * g.RH * g.YP + G::TOFF;  // [TKH][TP], column j at j + TOFF
@@ -391,7 +395,7 @@ k_res2d_pipe(StencilArgs<T, WK> op, int B, const T* __restrict__ x, const T* __r
       }
     }
     if (partials) {
-      const double s = block_sum((double)ss, red);
+      const double s = block_sum<T>(ss, red);
       if (threadIdx.x == 0) partials[(size_t)b * per_img + (ty * tiles_x + tx)] = s;
     }
     __syncthreads();  // everyone is done with this buffer and with red[]
@@ -460,16 +464,289 @@ bool launch_st_m(const Band2D<T>& op, int B, const T* x, const T* y, T* out, dou
              : launch_st<T, RESTRICT, WK, false>(op, B, x, y, out, partials, active, tile, ntx, st);
 }
 
+// ---------------------------------------------------------------------------
+// Fine-level strip form: M = I (alpha X + K X K^T), K one Toeplitz stencil
+// of half-width <= 8 with no correction rows, n = 32 C with C in {2, 4}.
+// One warp computes the residual (RESTRICT: and its full-weighting
+// restriction) of kStripH consecutive rows of one right-hand side over the
+// whole row width, lane j owning columns C j .. C j + C - 1.  Input rows
+// stream through a warp-private shared-memory ring (cp.async, kStripPF rows
+// ahead); the row-pass outputs t of the last 2 WK + 1 rows stay in registers
+// (a ring of register rows indexed at compile time: the row loop is unrolled
+// by 2 WK + 1), so the column pass reads no shared memory and no warp waits
+// on another.  Column pairs of a lane form the packed fp32 FMA operands.
+// ---------------------------------------------------------------------------
+constexpr int kStripH = 16;     // fine output rows per warp unit
+constexpr int kStripWarps = 4;  // warps per block
+constexpr int kStripPF = 6;     // rows staged ahead
+constexpr int kStripRing = 16;  // staged rows per warp: > kStripPF + max WK
+constexpr int kStripHalo = 8;   // staged halo columns per side (>= WK)
+
+template <int WK>
+struct StripArgs {
+  int n;
+  float alpha;
+  float sK[2 * WK + 1];  // stencil padded to WK: entry WK + o is offset o
+};
+
+template <int C>
+__host__ __device__ constexpr int strip_words() {
+  return kStripRing * ((32 * C + 2 * kStripHalo) + 32 * C);
+}
+
+template <bool RESTRICT, int WK, int C>
+__global__ void __launch_bounds__(32 * kStripWarps, 3)
+k_res_strip(StripArgs<WK> op, int B, const float* __restrict__ x, const float* __restrict__ y,
+            float* __restrict__ out, double* __restrict__ partials,
+            const int* __restrict__ active) {
+  static_assert(C == 2 || C == 4, "two or four columns per lane");
+  static_assert(WK <= kStripHalo && kStripRing > kStripPF + WK, "ring too short");
+  constexpr int SW = 32 * C;               // columns per unit: the whole row
+  constexpr int XW = SW + 2 * kStripHalo;  // staged x row (staged index k = column k - halo)
+  constexpr int P = 2 * WK + 1;
+  constexpr int CC = C / 2;                // column pairs (and coarse columns) per lane
+  extern __shared__ __align__(16) float strip_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* xring = strip_smem + wib * strip_words<C>();  // [ring][XW]
+  float* yring = xring + kStripRing * XW;              // [ring][SW]
+  const int n = op.n;                                  // == SW
+  const int upi = n / kStripH;                         // units per right-hand side
+  const int total = B * upi;
+  const size_t plane = (size_t)n * n;
+  float cf[P];
+#pragma unroll
+  for (int d = 0; d < P; ++d) cf[d] = op.sK[d];
+  const float alpha = op.alpha;
+
+  for (int u = blockIdx.x * kStripWarps + wib; u < total; u += gridDim.x * kStripWarps) {
+    const int b = u / upi;
+    if (!active[b]) continue;  // warp-uniform
+    const int i0 = (u - b * upi) * kStripH;
+    const int olo = RESTRICT ? i0 - 1 : i0, ohi = i0 + kStripH;  // fine output rows
+    const int alo = olo - WK, ahi = ohi + WK;                     // input rows
+    const float* xb = x + (size_t)b * plane;
+    const float* yb = y ? y + (size_t)b * plane : nullptr;
+    // stage input row a (x with halo; y for output rows) into ring slot
+    // (a - alo) mod ring; one commit group per row (empty past the end)
+    auto stage = [&](int a) {
+      if (a < ahi) {
+        const int slot = (a - alo) % kStripRing;
+        const bool rin = a >= 0 && a < n;
+        float* xd = xring + slot * XW;
+        for (int ch = lane; ch < XW / 4; ch += 32) {
+          const int gc = ch * 4 - kStripHalo;
+          const bool in = rin && gc >= 0 && gc < n;
+          cp_async_16(xd + ch * 4, in ? xb + (size_t)a * n + gc : xb, in);
+        }
+        if (yb && a >= olo && a < ohi) {
+          float* yd = yring + slot * SW;
+          for (int ch = lane; ch < SW / 4; ch += 32)
+            cp_async_16(yd + ch * 4, rin ? yb + (size_t)a * n + ch * 4 : yb, rin);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int k = 0; k < kStripPF; ++k) stage(alo + k);
+
+    float2 tw[P][CC];  // row-pass outputs of the last P input rows (column pairs)
+    float hm1[CC], hm2[CC];  // horizontally restricted residual rows i-1, i-2
+#pragma unroll
+    for (int q = 0; q < CC; ++q) hm1[q] = hm2[q] = 0.f;
+    float ss = 0.f;
+    for (int a0 = alo; a0 < ahi; a0 += P) {
+#pragma unroll
+      for (int ph = 0; ph < P; ++ph) {
+        const int a = a0 + ph;  // input row; its t goes to register row ph
+        if (a < ahi) {
+          asm volatile("cp.async.wait_group %0;" ::"n"(kStripPF - 1) : "memory");
+          __syncwarp();
+          stage(a + kStripPF);
+          // row pass: t[c] = sum_d sK[d] x[a][C lane + c + d - WK]
+          const float* xs = xring + ((a - alo) % kStripRing) * XW + C * lane;
+          float w[C + 2 * kStripHalo];
+          if (C == 4) {
+#pragma unroll
+            for (int k4 = 0; k4 < (C + 2 * kStripHalo) / 4; ++k4) {
+              const float4 v = *reinterpret_cast<const float4*>(xs + 4 * k4);
+              w[4 * k4] = v.x; w[4 * k4 + 1] = v.y; w[4 * k4 + 2] = v.z; w[4 * k4 + 3] = v.w;
+            }
+          } else {
+#pragma unroll
+            for (int k2 = 0; k2 < (C + 2 * kStripHalo) / 2; ++k2) {
+              const float2 v = *reinterpret_cast<const float2*>(xs + 2 * k2);
+              w[2 * k2] = v.x; w[2 * k2 + 1] = v.y;
+            }
+          }
+          float t[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) t[c] = 0.f;
+#pragma unroll
+          for (int d = 0; d < P; ++d)
+#pragma unroll
+            for (int c = 0; c < C; ++c) t[c] = fmaf(cf[d], w[c + kStripHalo - WK + d], t[c]);
+#pragma unroll
+          for (int q = 0; q < CC; ++q) tw[ph][q] = make_float2(t[2 * q], t[2 * q + 1]);
+          if (a >= olo + WK) {
+            // column pass for output row i = a - WK: rows i - WK + d sit in
+            // register rows (ph + 1 + d) mod P
+            const int i = a - WK;
+            float2 z[CC];
+#pragma unroll
+            for (int q = 0; q < CC; ++q) z[q] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int d = 0; d < P; ++d) {
+              const float2 c2 = make_float2(cf[d], cf[d]);
+#pragma unroll
+              for (int q = 0; q < CC; ++q) z[q] = ffma2(c2, tw[(ph + 1 + d) % P][q], z[q]);
+            }
+            const int slot = (i - alo) % kStripRing;
+            const float* xc = xring + slot * XW + kStripHalo + C * lane;
+            const float* yc = yring + slot * SW + C * lane;
+            const bool rin = i >= 0 && i < n;
+            float r[C];
+#pragma unroll
+            for (int q = 0; q < CC; ++q) {
+              const float2 xv = *reinterpret_cast<const float2*>(xc + 2 * q);
+              const float2 yv = yb ? *reinterpret_cast<const float2*>(yc + 2 * q) : make_float2(0.f, 0.f);
+              r[2 * q] = rin ? yv.x - fmaf(alpha, xv.x, z[q].x) : 0.f;
+              r[2 * q + 1] = rin ? yv.y - fmaf(alpha, xv.y, z[q].y) : 0.f;
+            }
+            if (!RESTRICT) {
+              if (rin) {
+                float* o = out + (size_t)b * plane + (size_t)i * n + C * lane;
+                if (C == 4)
+                  *reinterpret_cast<float4*>(o) = make_float4(r[0], r[1], r[2], r[3]);
+                else
+                  *reinterpret_cast<float2*>(o) = make_float2(r[0], r[1]);
+#pragma unroll
+                for (int c = 0; c < C; ++c) ss = fmaf(r[c], r[c], ss);
+              }
+            } else {
+              // [1 2 1] / 4 along the row: coarse column CC lane + q is
+              // centred on fine column C lane + 2q; fine column C lane - 1
+              // comes from the left lane (zero left of the grid)
+              float left = __shfl_up_sync(0xffffffffu, r[C - 1], 1);
+              if (lane == 0) left = 0.f;
+              float h[CC];
+#pragma unroll
+              for (int q = 0; q < CC; ++q)
+                h[q] = 0.25f * (q == 0 ? left : r[2 * q - 1]) + 0.5f * r[2 * q] + 0.25f * r[2 * q + 1];
+              // [1 2 1] / 4 down the column: coarse row I = (i - 1) / 2 once
+              // its bottom fine row i = 2I + 1 is done
+              if ((i & 1) && i >= olo + 2) {
+                const int I = (i - 1) >> 1;
+                float v[CC];
+#pragma unroll
+                for (int q = 0; q < CC; ++q) {
+                  v[q] = 0.25f * hm2[q] + 0.5f * hm1[q] + 0.25f * h[q];
+                  ss = fmaf(v[q], v[q], ss);
+                }
+                float* o = out + (size_t)b * (plane / 4) + (size_t)I * (n / 2) + CC * lane;
+                if (CC == 2)
+                  *reinterpret_cast<float2*>(o) = make_float2(v[0], v[CC - 1]);
+                else
+                  o[0] = v[0];
+              }
+#pragma unroll
+              for (int q = 0; q < CC; ++q) {
+                hm2[q] = hm1[q];
+                hm1[q] = h[q];
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();  // every lane is done with the ring before the next unit restages it
+    if (partials) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) partials[(size_t)b * upi + (u - b * upi)] = (double)ss;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// the strip form applies: fp32 fine level (M = I, Toeplitz K, WK <= 8),
+// n = 64 or 128, 16-byte aligned vectors
+template <typename T>
+bool strip_applies(const Band2D<T>& op, const T* x, const T* y) {
+  if (!std::is_same<T, float>::value || !op.st || !op.st->valid) return false;
+  const StencilHost<T>& h = *op.st;
+  if (h.wM != 0 || h.nbM != 0 || h.nbK != 0 || h.sM[0] != T(1) || h.wK > kStripHalo) return false;
+  if (op.n != 64 && op.n != 128) return false;
+  return !((reinterpret_cast<uintptr_t>(x) & 15) || (y && (reinterpret_cast<uintptr_t>(y) & 15)));
+}
+
+template <bool RESTRICT, int WK, int C>
+void launch_strip(const Band2D<float>& op, int B, const float* x, const float* y, float* out,
+                  double* partials, const int* active, cudaStream_t st) {
+  StripArgs<WK> a{};
+  a.n = op.n;
+  a.alpha = op.alpha;
+  const StencilHost<float>& h = *op.st;
+  for (int d = 0; d <= 2 * h.wK; ++d) a.sK[WK - h.wK + d] = h.sK[d];
+  const size_t sm = (size_t)kStripWarps * strip_words<C>() * sizeof(float);
+  auto kern = k_res_strip<RESTRICT, WK, C>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kStripWarps, sm);
+  if (per_sm < 1) per_sm = 1;
+  const long long units = (long long)B * (op.n / kStripH);
+  long long grid = (units + kStripWarps - 1) / kStripWarps;
+  const long long cap = (long long)num_sms() * per_sm;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, 32 * kStripWarps, sm, st>>>(a, B, x, y, out, partials, active);
+}
+
+template <typename T, bool RESTRICT>
+bool launch_strip_any(const Band2D<T>& op, int B, const T* x, const T* y, T* out,
+                      double* partials, const int* active, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    const int w = op.st->wK;
+    if (op.n == 128) {
+      if (w <= 2) launch_strip<RESTRICT, 2, 4>(op, B, x, y, out, partials, active, st);
+      else if (w <= 4) launch_strip<RESTRICT, 4, 4>(op, B, x, y, out, partials, active, st);
+      else launch_strip<RESTRICT, 8, 4>(op, B, x, y, out, partials, active, st);
+    } else {
+      if (w <= 2) launch_strip<RESTRICT, 2, 2>(op, B, x, y, out, partials, active, st);
+      else if (w <= 4) launch_strip<RESTRICT, 4, 2>(op, B, x, y, out, partials, active, st);
+      else launch_strip<RESTRICT, 8, 2>(op, B, x, y, out, partials, active, st);
+    }
+    return true;
+  }
+  return false;
+}
+
 }  // namespace stencil
 
-// the stencil kernel for this level, or false (generic kernel) if the level
-// has no stencil form or a half-width above kStencilMaxW
+// partial sums per right-hand side the strip form writes (0: not used)
+template <typename T>
+int stencil_strip_parts(const Band2D<T>& op) {
+  if (!std::is_same<T, float>::value || !op.st || !op.st->valid) return 0;
+  const StencilHost<T>& h = *op.st;
+  if (h.wM != 0 || h.nbM != 0 || h.nbK != 0 || h.sM[0] != T(1) || h.wK > stencil::kStripHalo)
+    return 0;
+  return (op.n == 64 || op.n == 128) ? op.n / stencil::kStripH : 0;
+}
+
+// the stencil kernel for this level (the strip form on an fp32 fine level,
+// else the tiled pipeline), or false (generic kernel) if the level has no
+// stencil form or a half-width above kStencilMaxW; *nparts: partial sums
+// written per right-hand side
 template <typename T, bool RESTRICT>
 bool launch_stencil_residual(const Band2D<T>& op, int B, const T* x, const T* y, T* out,
                              double* partials, const int* active, int tile, int ntx,
-                             cudaStream_t st) {
+                             cudaStream_t st, int* nparts) {
   using namespace stencil;
   if (!op.st || !op.st->valid || op.st->wM > 1) return false;
+  if (strip_applies<T>(op, x, y) && launch_strip_any<T, RESTRICT>(op, B, x, y, out, partials, active, st)) {
+    *nparts = op.n / kStripH;
+    return true;
+  }
+  *nparts = ntx * ntx;
   // 16-byte chunks of x and y must not straddle the image edge
   constexpr int E = 16 / (int)sizeof(T);
   if (op.n % E != 0 || (reinterpret_cast<uintptr_t>(x) & 15) ||

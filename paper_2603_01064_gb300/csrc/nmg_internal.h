@@ -146,13 +146,18 @@ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 // skipped (their outputs are left untouched).
 // ---------------------------------------------------------------------------
 
-// stencil form of the level residual (and residual + restriction) in one
-// persistent pipelined kernel; false if the level has no stencil form or is
-// not staged that way (the caller then launches the generic kernel)
+// stencil form of the level residual (and residual + restriction): the
+// fine-level strip kernel or the persistent pipelined tile kernel; false if
+// the level has no stencil form or is not staged that way (the caller then
+// launches the generic kernel).  *nparts: partial sums per right-hand side.
 template <typename T, bool RESTRICT>
 bool launch_stencil_residual(const Band2D<T>& op, int B, const T* x, const T* y, T* out,
                              double* partials, const int* active, int tile, int ntx,
-                             cudaStream_t st);
+                             cudaStream_t st, int* nparts);
+// partial sums per right-hand side of the fine-level strip form (0 if the
+// level does not use it)
+template <typename T>
+int stencil_strip_parts(const Band2D<T>& op);
 
 // r = y - A x on a 2D level (+ per-tile partial sums of r^2 if partials)
 // tile_req: requested tile side (0 = default), see pick_tile
