@@ -68,7 +68,7 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # DRAM bytes per output pixel of the hidden convs, mean of the two hidden
 # layers, from one ncu capture of this kernel version (128x128, 64 RHS,
 # level 0; summarised under profiles/); None where no capture exists
-HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": None}
+HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 177.9}
 MMA_FLOPS_PER_PX = {
     # split form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
     "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
@@ -355,6 +355,20 @@ def run_ours(args, wl, world, rank, local):
                 "launch_ms": d["ms"] / d["launches"]}
     breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "share": v["ms"] / prof_total} for k, v in kern.items()}
+    # the memory-bound classes against the measured HBM copy bandwidth:
+    # algorithmic bytes per unit (fine grid point x active right-hand side,
+    # every level of the class together) / class time
+    act_b = {"bf16_refine": 128, "fp16_refine": 128, "bf16fast_refine": 64, "fp32": 128}[prec]
+    hbm_bpu = {"restrict": 9, "refine_residual": 16,
+               "prolong": 9, "filter": 8, "cnn_first": 4 + act_b, "cnn_last": 40}
+    if prec == "fp32":
+        hbm_bpu.pop("cnn_first")
+        hbm_bpu.pop("cnn_last")
+    for k, bpu_k in hbm_bpu.items():
+        if k in kern and kern[k]["ms"] > 0:
+            gbs = bpu_k * kern[k]["units"] / (kern[k]["ms"] / 1e3) / 1e9
+            breakdown[k].update({"bytes_per_unit": bpu_k, "achieved_gbs": gbs,
+                                 "hbm_frac": gbs / peaks["hbm_gbs"]})
 
     # ---- the comparison forms on the same GPU and right-hand sides
     compare = {}

@@ -86,10 +86,18 @@ struct LayerPack {
   float bias0;          // host copy of the output layer's bias
   int bias_host_valid;
 };
+// first layer's weights [cout][tap] and biases, passed by value as kernel
+// parameters: every multiply-add of the layer reads its weight straight from
+// the constant bank
+struct FirstW {
+  float w[WIDTH * 9];
+  float b[WIDTH];
+};
 struct Bf16Pack {
   int layers;
   int split;
   LayerPack l[8];
+  FirstW first;  // host copy of layer 0
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -229,8 +237,8 @@ __device__ __forceinline__ void store_pixel_planar(const float* a, __nv_bfloat16
 template <int SPLIT>
 __global__ void __launch_bounds__(256)
 k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ aout,
-             LayerPack lp, const double* __restrict__ snorm, const int* __restrict__ active,
-             int tiles_x) {
+             const __grid_constant__ FirstW fw, const double* __restrict__ snorm,
+             const int* __restrict__ active, int tiles_x) {
   constexpr int ACHN = SPLIT ? 8 : 4;  // chunk planes per image
   const int b = blockIdx.y;
   if (!active[b]) return;
@@ -240,13 +248,9 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   const long long sbits = __double_as_longlong(snorm[b]);
   if ((sbits << 1) == 0) return;
   __shared__ float xs[RH][RW + 1];
-  __shared__ float ws[WIDTH * 9];
-  __shared__ float bs[WIDTH];
   __shared__ float inv_s;
   const int tid = threadIdx.x;
-  for (int i = tid; i < WIDTH * 9; i += 256) ws[i] = lp.wf[i];
   const float sig = net_scale<SPLIT>(n);
-  if (tid < WIDTH) bs[tid] = sig * lp.bias[tid];
   if (tid == 0) inv_s = (float)((double)sig / __longlong_as_double(sbits));
   const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
   const size_t plane = (size_t)n * n;
@@ -268,9 +272,9 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   float a[WIDTH];
 #pragma unroll
   for (int c = 0; c < WIDTH; ++c) {
-    float acc = bs[c];
+    float acc = sig * fw.b[c];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc = fmaf(ws[c * 9 + t], v[t], acc);
+    for (int t = 0; t < 9; ++t) acc = fmaf(fw.w[c * 9 + t], v[t], acc);
     a[c] = fmaxf(acc, 0.f);
   }
   store_pixel_planar<SPLIT>(
@@ -876,7 +880,7 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   dim3 grid(tiles_x * tiles_x, B);
   const double units = (double)n * n * log.active_hint;
   int pi_ = log.begin(K_CNN_FIRST, st);
-  k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.l[0], s, active, tiles_x);
+  k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.first, s, active, tiles_x);
   log.end(pi_, st, units);
   __nv_bfloat16* cur = a0;
   __nv_bfloat16* nxt = a1;
@@ -916,6 +920,7 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
   if (layers < 3 || layers > 8) return nullptr;
   std::vector<std::vector<unsigned char>> wl(layers), bl(layers);
   std::vector<int> has_lo(layers, 0);
+  FirstW first{};
   for (int li = 0; li < layers; ++li) {
     const int cin = li == 0 ? 1 : WIDTH, cout = li == layers - 1 ? 1 : WIDTH;
     const double* w = W[li];
@@ -928,6 +933,10 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
       std::vector<float> f(WIDTH * 9, 0.f);
       for (int c = 0; c < WIDTH; ++c)
         for (int t = 0; t < 9; ++t) f[c * 9 + t] = (float)w[c * 9 + t];
+      if (li == 0) {
+        std::memcpy(first.w, f.data(), sizeof(first.w));
+        std::memcpy(first.b, bb.data(), sizeof(first.b));
+      }
       wl[li].assign(reinterpret_cast<const unsigned char*>(f.data()),
                     reinterpret_cast<const unsigned char*>(f.data() + f.size()));
       continue;
@@ -974,6 +983,7 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
   Bf16Pack hdr{};
   hdr.layers = layers;
   hdr.split = split;
+  hdr.first = first;
   for (int li = 0; li < layers; ++li) {
     std::memcpy(host.data() + woff[li], wl[li].data(), wl[li].size());
     std::memcpy(host.data() + boff[li], bl[li].data(), bl[li].size());

@@ -405,6 +405,171 @@ RefineArgs<WK> refine_args(const StencilHost<double>& sd, double alpha, int n) {
   return a;
 }
 
+// ---------------------------------------------------------------------------
+// Strip form of the same residual for stencils of half-width <= 8 and n a
+// multiple of 64: one warp computes kRsH consecutive rows of a 64-column
+// strip of one right-hand side, lane j owning columns 2j and 2j + 1.  Input
+// rows stream through a warp-private ring (cp.async, kRsPF rows ahead); each
+// staged row of u is split into float pairs once, into a one-row buffer the
+// lanes' windows read; the double-float row-pass outputs of the last 2 WK + 1
+// rows stay in registers, shifted down by one row per input row (one loop
+// body: the double-float column pass is too long to specialise per ring
+// phase), so no warp waits on another.
+// ---------------------------------------------------------------------------
+constexpr int kRsH = 32;      // output rows per warp unit
+constexpr int kRsWarps = 4;   // warps per block
+constexpr int kRsPF = 6;      // rows staged ahead
+constexpr int kRsRing = 16;   // staged rows per warp: > kRsPF + max WK
+constexpr int kRsHalo = 8;    // staged halo columns per side (>= WK)
+constexpr int kRsSW = 64;     // columns per strip
+constexpr int kRsXW = kRsSW + 2 * kRsHalo;  // staged u row (doubles)
+// per-warp shared memory in 4-byte words: u ring, split row (hi, lo), f ring
+constexpr int kRsWords = kRsRing * kRsXW * 2 + 2 * kRsXW + kRsRing * kRsSW;
+
+template <int WK>
+__global__ void __launch_bounds__(32 * kRsWarps, 3)
+k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
+               const float* __restrict__ f, float* __restrict__ r,
+               double* __restrict__ partials, const int* __restrict__ active) {
+  static_assert(WK <= kRsHalo && kRsRing > kRsPF + WK, "ring too short");
+  constexpr int P = 2 * WK + 1;
+  extern __shared__ __align__(16) float rs_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* uring = reinterpret_cast<double*>(rs_smem + wib * kRsWords);  // [ring][XW]
+  float* xh = reinterpret_cast<float*>(uring + kRsRing * kRsXW);         // [XW]
+  float* xl = xh + kRsXW;                                                // [XW]
+  float* fring = xl + kRsXW;                                             // [ring][SW]
+  const int n = op.n;
+  const int ns = n / kRsSW, upi = ns * (n / kRsH);
+  const int total = B * upi;
+  const size_t plane = (size_t)n * n;
+
+  for (int unit = blockIdx.x * kRsWarps + wib; unit < total; unit += gridDim.x * kRsWarps) {
+    const int b = unit / upi;
+    if (!active[b]) continue;  // warp-uniform
+    const int rem = unit - b * upi;
+    const int c0 = (rem % ns) * kRsSW, i0 = (rem / ns) * kRsH;
+    const int alo = i0 - WK, ahi = i0 + kRsH + WK;  // input rows
+    const double* ub = u + (size_t)b * plane;
+    const float* fb = f + (size_t)b * plane;
+    auto stage = [&](int a) {
+      if (a < ahi) {
+        const int slot = (a - alo) % kRsRing;
+        const bool rin = a >= 0 && a < n;
+        double* ud = uring + slot * kRsXW;
+        for (int ch = lane; ch < kRsXW / 2; ch += 32) {
+          const int gc = c0 - kRsHalo + 2 * ch;
+          const bool in = rin && gc >= 0 && gc < n;
+          cp_async_16r(ud + 2 * ch, in ? ub + (size_t)a * n + gc : ub, in);
+        }
+        if (a >= i0 && a < i0 + kRsH) {
+          float* fd = fring + slot * kRsSW;
+          for (int ch = lane; ch < kRsSW / 4; ch += 32)
+            cp_async_16r(fd + 4 * ch, fb + (size_t)a * n + c0 + 4 * ch, true);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int k = 0; k < kRsPF; ++k) stage(alo + k);
+
+    DF tw[P][2];  // row-pass outputs of input rows a - 2 WK .. a
+#pragma unroll
+    for (int k = 0; k < P; ++k) tw[k][0] = tw[k][1] = DF{0.f, 0.f};
+    float ss = 0.f;
+#pragma unroll 1
+    for (int a = alo; a < ahi; ++a) {
+      asm volatile("cp.async.wait_group %0;" ::"n"(kRsPF - 1) : "memory");
+      __syncwarp();
+      stage(a + kRsPF);
+      // split the staged row once (the previous row's window reads are
+      // ordered before this by the barrier above)
+      const double* us = uring + ((a - alo) % kRsRing) * kRsXW;
+      for (int k = lane; k < kRsXW; k += 32) {
+        float h, l;
+        split_double(us[k], h, l);
+        xh[k] = h;
+        xl[k] = l;
+      }
+      __syncwarp();
+      // row pass: t[c] = sum_d K[d] u[a][c0 + 2 lane + c + d - WK]
+      float wh[2 + 2 * kRsHalo], wl[2 + 2 * kRsHalo];
+#pragma unroll
+      for (int k2 = 0; k2 < 1 + kRsHalo; ++k2) {
+        const float2 vh = *reinterpret_cast<const float2*>(xh + 2 * lane + 2 * k2);
+        const float2 vl = *reinterpret_cast<const float2*>(xl + 2 * lane + 2 * k2);
+        wh[2 * k2] = vh.x; wh[2 * k2 + 1] = vh.y;
+        wl[2 * k2] = vl.x; wl[2 * k2 + 1] = vl.y;
+      }
+      DF acc[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+#pragma unroll
+      for (int d = 0; d < P; ++d)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          df_fma(acc[c], op.sKh[d], op.sKl[d], wh[c + kRsHalo - WK + d], wl[c + kRsHalo - WK + d]);
+#pragma unroll
+      for (int k = 0; k + 1 < P; ++k) {
+        tw[k][0] = tw[k + 1][0];
+        tw[k][1] = tw[k + 1][1];
+      }
+      tw[P - 1][0] = df_norm(acc[0]);
+      tw[P - 1][1] = df_norm(acc[1]);
+      if (a >= i0 + WK) {
+        // column pass for output row i = a - WK, alpha u, r = f - A u
+        const int i = a - WK;
+        DF z[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+#pragma unroll
+        for (int d = 0; d < P; ++d)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) df_fma(z[c], op.sKh[d], op.sKl[d], tw[d][c].h, tw[d][c].l);
+        const int slot = (i - alo) % kRsRing;
+        const double2 uc = *reinterpret_cast<const double2*>(uring + slot * kRsXW + kRsHalo + 2 * lane);
+        const float2 fv = *reinterpret_cast<const float2*>(fring + slot * kRsSW + 2 * lane);
+        float rv[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float h, l;
+          split_double(c ? uc.y : uc.x, h, l);
+          df_fma(z[c], op.ah, op.al, h, l);
+          const DF az = df_norm(z[c]);
+          float s2, e;
+          two_sum(c ? fv.y : fv.x, -az.h, s2, e);
+          rv[c] = s2 + (e - az.l);
+          ss = fmaf(rv[c], rv[c], ss);
+        }
+        *reinterpret_cast<float2*>(r + (size_t)b * plane + (size_t)i * n + c0 + 2 * lane) =
+            make_float2(rv[0], rv[1]);
+      }
+    }
+    __syncwarp();  // every lane is done with the ring before the next unit restages it
+    if (partials) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) partials[(size_t)b * upi + rem] = (double)ss;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int WK>
+void launch_refine_strip(const StencilHost<double>& sd, double alpha, int n, int B,
+                         const double* u, const float* f, float* r, double* partials,
+                         const int* active, cudaStream_t st) {
+  const size_t sm = (size_t)kRsWarps * kRsWords * 4;
+  auto kern = k_refine_strip<WK>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kRsWarps, sm);
+  if (per_sm < 1) per_sm = 1;
+  const long long units = (long long)B * (n / kRsSW) * (n / kRsH);
+  long long grid = (units + kRsWarps - 1) / kRsWarps;
+  const long long cap = (long long)num_sms_refine() * per_sm;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, 32 * kRsWarps, sm, st>>>(refine_args<WK>(sd, alpha, n), B, u, f, r, partials,
+                                             active);
+}
+
 template <int WK>
 bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
                         const float* f, float* r, double* partials, const int* active, int tile,
@@ -425,15 +590,25 @@ bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int 
   return true;
 }
 
-// the stencil kernel when the level qualifies (Toeplitz K, M = I, aligned
-// buffers, n a multiple of 4), else false
+// the stencil kernels when the level qualifies (Toeplitz K, M = I, aligned
+// buffers, n a multiple of 4): the strip form for half-widths <= 8 and n a
+// multiple of 64, else the tiled pipeline; false otherwise.  *nparts:
+// partial sums written per right-hand side.
 bool try_refine_pipe(const StencilHost<double>* sd, double alpha, int n, int B, const double* u,
                      const float* f, float* r, double* partials, const int* active, int tile,
-                     int tx, cudaStream_t st) {
+                     int tx, cudaStream_t st, int* nparts) {
   if (!sd || !sd->valid || sd->nbK != 0 || sd->wM != 0 || sd->sM[0] != 1.0 || n % 4 != 0 ||
       (reinterpret_cast<uintptr_t>(u) & 15) || (reinterpret_cast<uintptr_t>(f) & 15))
     return false;
   const int w = sd->wK;
+  if (w <= kRsHalo && n % kRsSW == 0) {
+    if (w <= 2) launch_refine_strip<2>(*sd, alpha, n, B, u, f, r, partials, active, st);
+    else if (w <= 4) launch_refine_strip<4>(*sd, alpha, n, B, u, f, r, partials, active, st);
+    else launch_refine_strip<8>(*sd, alpha, n, B, u, f, r, partials, active, st);
+    *nparts = (n / kRsSW) * (n / kRsH);
+    return true;
+  }
+  *nparts = tx * tx;
   if (w <= 2) return launch_refine_pipe<2>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
   if (w <= 4) return launch_refine_pipe<4>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
   if (w <= 8) return launch_refine_pipe<8>(*sd, alpha, n, B, u, f, r, partials, active, tile, tx, st);
@@ -460,13 +635,15 @@ void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float*
   while (tile < hi.n && (long long)ceil_div(hi.n, tile) * ceil_div(hi.n, tile) > 4096) tile *= 2;
   int tx = ceil_div(hi.n, tile);
   int pi_ = log.begin(K_REFINE_RESIDUAL, st);
-  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, st)) {
+  int nparts = tx * tx;
+  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, st, &nparts)) {
+    nparts = tx * tx;
     size_t sm = smem(tile);
     cudaFuncSetAttribute(k_refine_residual2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_refine_residual2d<0><<<dim3(tx * tx, B), 256, sm, st>>>(hi, Kd_lo, Md_lo, alpha, u, f, r,
                                                               partials, active, tile, tx);
   }
-  if (ntiles) *ntiles = tx * tx;
+  if (ntiles) *ntiles = nparts;
   log.end(pi_, st, (double)hi.n * hi.n * log.active_hint);
 }
 
