@@ -114,6 +114,13 @@ typedef enum {
  *   precision  nmg_precision
  *   filter   1: NMGF with the output filter F'_l (Algorithms 3/4);
  *            0: no filter (Algorithm 2, x = x* + h)
+ *   reg, nreg  dim 1 only, optional (NULL, 0: D = I, the Tikhonov term):
+ *            the regularisation matrix D of the anisotropic case of
+ *            Section 4.1 (A = alpha D + K), symmetric tridiagonal, given as
+ *            its n diagonal entries followed by its n-1 off-diagonal
+ *            entries (nreg == 2n-1), host, copied at setup;
+ *            A_1 = Toeplitz(t) + alpha D.  NMG_ERR_ARG if given in 2D or
+ *            with another length.
  * Coarse operators are Galerkin products A_{l+1} = R A_l P with linear
  * interpolation P (coarse node J at fine 2J) and full weighting R = P^T/2
  * per axis.
@@ -127,6 +134,8 @@ typedef struct {
   const double* taps;
   int precision;
   int filter;
+  const double* reg;
+  int nreg;
 } nmg_operator_desc;
 
 /*

@@ -58,6 +58,26 @@ def kernel_column_1d(n: int, width: float = 0.05) -> np.ndarray:
     return h * np.exp(-(d * d) / (2.0 * width * width))
 
 
+def aniso_coefficient(z: np.ndarray) -> np.ndarray:
+    """Coefficient a(z) = 1 + 0.5 sin(2 pi z) of the anisotropic
+    regularisation of Section 4.1 (R(u) = -(a u')')."""
+    return 1.0 + 0.5 * np.sin(2.0 * np.pi * z)
+
+
+def aniso_regularisation_1d(n: int, a=aniso_coefficient):
+    """Tridiagonal D of the anisotropic regularisation (Section 4.1, A = alpha
+    D + K), as (diag, off): the conservative three-point form of -(a u')' on
+    the n midpoint cells of [0, 1] with u = 0 outside, coefficients at the
+    cell faces z = i h:
+        (D u)_i = (a(ih) (u_i - u_{i-1}) - a((i+1)h) (u_{i+1} - u_i)) / h^2.
+    diag has n entries, off the n - 1 sub/super-diagonal entries."""
+    h = 1.0 / n
+    faces = a(np.arange(n + 1, dtype=np.float64) * h)  # a(0), a(h), ..., a(1)
+    diag = (faces[:-1] + faces[1:]) / (h * h)
+    off = -faces[1:-1] / (h * h)
+    return diag, off
+
+
 def blur_1d(u: np.ndarray, col: np.ndarray) -> np.ndarray:
     """Data model of the 1D problem: the discrete blur (hK) u, u of shape [B, n]."""
     n = u.shape[-1]

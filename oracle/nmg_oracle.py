@@ -111,12 +111,19 @@ class Hierarchy:
         return self.n >> l
 
 
-def build_hierarchy_1d(col: np.ndarray, alpha: float, levels: int) -> Hierarchy:
+def build_hierarchy_1d(col: np.ndarray, alpha: float, levels: int, reg=None) -> Hierarchy:
     """1D: A_1 = hK + alpha I (Eq. (10) with the kernel column given by the
-    midpoint rule), A_{l+1} = R A_l P (Algorithm 3, Galerkin)."""
+    midpoint rule), A_{l+1} = R A_l P (Algorithm 3, Galerkin).  With reg =
+    (diag, off), the anisotropic case of Section 4.1: A_1 = hK + alpha D with
+    D the symmetric tridiagonal matrix of those diagonals."""
     n = len(col)
     assert n % (1 << (levels - 1)) == 0
-    A = toeplitz_from_column(col) + alpha * np.eye(n)
+    if reg is None:
+        D = np.eye(n)
+    else:
+        diag, off = reg
+        D = np.diag(np.asarray(diag, dtype=np.float64)) + np.diag(off, 1) + np.diag(off, -1)
+    A = toeplitz_from_column(col) + alpha * D
     ops = [A]
     for _ in range(levels - 1):
         nf = A.shape[0]

@@ -45,7 +45,8 @@ class _OpDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("ntaps", ctypes.c_int),
                 ("taps", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int),
-                ("filter", ctypes.c_int)]
+                ("filter", ctypes.c_int), ("reg", ctypes.POINTER(ctypes.c_double)),
+                ("nreg", ctypes.c_int)]
 
 
 class _SmDesc(ctypes.Structure):
@@ -208,15 +209,24 @@ class Hierarchy:
 
     def __init__(self, ctx: Context, *, dim: int, n: int, levels: int, alpha: float,
                  taps, precision="fp32", filter: bool = True, weights=None,
-                 layers=None, width=None, ksize=None):
+                 layers=None, width=None, ksize=None, reg=None):
+        """reg: None (D = I) or (diag, off) of the tridiagonal regularisation
+        matrix D of the anisotropic 1D case (A = alpha D + K)."""
         L = lib()
         self.ctx = ctx
         self.dim, self.n, self.levels, self.alpha = dim, n, levels, alpha
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self._taps = np.ascontiguousarray(taps, dtype=np.float64)
+        self._reg = None
+        if reg is not None:
+            self._reg = np.ascontiguousarray(np.concatenate([np.asarray(reg[0], np.float64),
+                                                             np.asarray(reg[1], np.float64)]))
         op = _OpDesc(dim, n, levels, alpha, len(self._taps),
                      self._taps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                     self.precision, 1 if filter else 0)
+                     self.precision, 1 if filter else 0,
+                     self._reg.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                     if self._reg is not None else None,
+                     0 if self._reg is None else self._reg.size)
         smp = None
         if weights is not None:
             if layers is None:

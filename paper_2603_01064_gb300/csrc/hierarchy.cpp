@@ -106,12 +106,24 @@ bool build_host_hierarchy(const nmg_operator_desc& op, HostHierarchy& H, std::st
   int ncoarse = op.n >> (op.levels - 1);
   H.nc = op.dim == 1 ? ncoarse : ncoarse * ncoarse;
   if (H.nc > 1024) { err = "coarsest level has more than 1024 unknowns"; return false; }
+  if (op.reg && op.dim != 1) { err = "reg (tridiagonal D) is 1D only"; return false; }
+  if (op.reg && op.nreg != 2 * op.n - 1) { err = "reg must hold 2n-1 values (diagonal, off-diagonal)"; return false; }
   if (op.dim == 1) {
     if (op.ntaps != op.n) { err = "1D: ntaps must equal n (first Toeplitz column)"; return false; }
     int n = op.n;
     std::vector<double> A((size_t)n * n);
     for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = op.taps[std::abs(i - j)] + (i == j ? op.alpha : 0.0);
+      for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = op.taps[std::abs(i - j)] + (i == j && !op.reg ? op.alpha : 0.0);
+    if (op.reg) {
+      // A = Toeplitz(t) + alpha D, D symmetric tridiagonal (Section 4.1)
+      for (int i = 0; i < n; ++i) {
+        A[(size_t)i * n + i] += op.alpha * op.reg[i];
+        if (i + 1 < n) {
+          A[(size_t)i * n + i + 1] += op.alpha * op.reg[n + i];
+          A[(size_t)(i + 1) * n + i] += op.alpha * op.reg[n + i];
+        }
+      }
+    }
     H.lv[0].n = n;
     H.lv[0].A = A;
     for (int l = 1; l < op.levels; ++l) {

@@ -94,7 +94,7 @@ def _prolong_np(nc):
 
 class Problem:
     def __init__(self, dim, n, levels, alpha, taps=None, col=None, device="cpu",
-                 dtype=torch.float32):
+                 dtype=torch.float32, reg=None):
         self.dim, self.n, self.L, self.alpha = dim, n, levels, alpha
         self.device, self.dtype = device, dtype
         T = lambda a: torch.tensor(a, dtype=dtype, device=device)  # noqa: E731
@@ -105,7 +105,11 @@ class Problem:
             self.R.append(T(P.T / 2.0))
         if dim == 1:
             i = np.arange(n)
-            A = col[np.abs(i[:, None] - i[None, :])] + alpha * np.eye(n)
+            # A = hK + alpha D: D = I (Tikhonov) or the anisotropic
+            # tridiagonal of Section 4.1, given as (diag, off)
+            D = np.eye(n) if reg is None else (np.diag(reg[0]) + np.diag(reg[1], 1) +
+                                               np.diag(reg[1], -1))
+            A = col[np.abs(i[:, None] - i[None, :])] + alpha * D
             ops = [A]
             for l in range(levels - 1):
                 P = _prolong_np((n >> l) // 2)
@@ -324,6 +328,9 @@ def nets_from_npz(path, dim, layers, width, ksize, device="cpu", gains=None):
 PRESETS = {
     # dim, n, levels, alpha, kernel, batch, epochs
     "c1": dict(dim=1, n=256, levels=3, alpha=1e-3, width_t=0.05, layers=3, width=16, ksize=5),
+    # the anisotropic regularisation of Section 4.1 (A = alpha D + hK)
+    "c1a": dict(dim=1, n=256, levels=3, alpha=1e-5, width_t=0.05, layers=3, width=16, ksize=5,
+                reg="aniso"),
     "c2": dict(dim=2, n=128, levels=5, alpha=1e-2, sigma=2.0, layers=4, width=32, ksize=3),
     "c3": dict(dim=2, n=512, levels=7, alpha=1e-3, sigma=4.0, layers=4, width=32, ksize=3,
                rhs="waves"),
@@ -360,7 +367,9 @@ def main(argv=None):
     dim = cfg["dim"]
     if dim == 1:
         col = nmg_inputs.kernel_column_1d(cfg["n"], cfg["width_t"])
-        prob = Problem(1, cfg["n"], cfg["levels"], cfg["alpha"], col=col, device=a.device)
+        reg = nmg_inputs.aniso_regularisation_1d(cfg["n"]) if cfg.get("reg") == "aniso" else None
+        prob = Problem(1, cfg["n"], cfg["levels"], cfg["alpha"], col=col, device=a.device,
+                       reg=reg)
     else:
         taps = nmg_inputs.gaussian_taps(cfg["sigma"])
         prob = Problem(2, cfg["n"], cfg["levels"], cfg["alpha"], taps=taps, device=a.device)

@@ -428,3 +428,67 @@ def test_full_solve_1d_converges_to_lu_solution():
     kappa = np.linalg.cond(H.ops[0])
     err = np.linalg.norm(u - ulu, axis=1) / np.linalg.norm(ulu, axis=1)
     assert np.all(err <= kappa * 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# anisotropic regularisation (Section 4.1: A = alpha D + K, D tridiagonal)
+# ---------------------------------------------------------------------------
+
+def test_aniso_constant_coefficient_is_dirichlet_laplacian():
+    """a = 1 reduces the flux form of -(a u')' to the textbook three-point
+    Dirichlet Laplacian tridiag(-1, 2, -1) / h^2."""
+    n = 16
+    diag, off = I.aniso_regularisation_1d(n, a=lambda z: np.ones_like(z))
+    assert np.allclose(diag, 2.0 * n * n, rtol=0, atol=1e-12)
+    assert np.allclose(off, -1.0 * n * n, rtol=0, atol=1e-12)
+
+
+def test_aniso_energy_identity():
+    """u^T D u equals the discrete energy sum over the n + 1 cell faces of
+    a(face) (u_right - u_left)^2 / h^2, with u = 0 outside the grid: the
+    defining property of the conservative form, checked on random u."""
+    n = 32
+    h = 1.0 / n
+    diag, off = I.aniso_regularisation_1d(n)
+    D = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        u = rng.standard_normal(n)
+        up = np.concatenate([[0.0], u, [0.0]])
+        faces = 1.0 + 0.5 * np.sin(2 * np.pi * np.arange(n + 1) * h)
+        energy = np.sum(faces * np.diff(up) ** 2) / (h * h)
+        assert abs(u @ D @ u - energy) <= 1e-12 * energy
+
+
+def test_aniso_hierarchy_spd_and_galerkin():
+    """A_1 = hK + alpha D is the dense sum of its parts; every Galerkin level
+    R A P is symmetric positive definite."""
+    n, alpha = 64, 1e-5
+    col = I.kernel_column_1d(n)
+    reg = I.aniso_regularisation_1d(n)
+    H = O.build_hierarchy_1d(col, alpha, 3, reg=reg)
+    i = np.arange(n)
+    T = col[np.abs(i[:, None] - i[None, :])]
+    D = np.diag(reg[0]) + np.diag(reg[1], 1) + np.diag(reg[1], -1)
+    assert np.abs(H.ops[0] - (T + alpha * D)).max() <= 1e-15 * np.abs(H.ops[0]).max()
+    for A in H.ops:
+        assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+        assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_full_solve_1d_aniso_converges_to_lu_solution():
+    path = os.path.join(os.path.dirname(os.path.dirname(__file__)),
+                        "paper_2603_01064_gb300", "weights", "c1a_1d_n256_aniso_a1e-5.npz")
+    if not os.path.exists(path):
+        pytest.skip("trained anisotropic weights not present")
+    z = np.load(path)
+    W = [[(z[f"l{l}_w{i}"], z[f"l{l}_b{i}"]) for i in range(3)] for l in range(2)]
+    col = I.kernel_column_1d(256)
+    H = O.build_hierarchy_1d(col, 1e-5, 3, reg=I.aniso_regularisation_1d(256))
+    f, _ = I.rhs_1d_sines_steps(256, 4, seed=1011)
+    u, cyc, rr = O.solve(H, W, f, rtol=1e-6, max_cycles=60)
+    assert np.all(rr <= 1e-6), (cyc, rr)
+    ulu = sla.lu_solve(sla.lu_factor(H.ops[0]), f.T).T
+    kappa = np.linalg.cond(H.ops[0])
+    err = np.linalg.norm(u - ulu, axis=1) / np.linalg.norm(ulu, axis=1)
+    assert np.all(err <= kappa * 1e-6)
