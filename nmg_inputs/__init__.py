@@ -237,3 +237,27 @@ CONFIGS = {
     "c3_2d_bf16": dict(dim=2, n=512, levels=7, alphas=(1e-4, 1e-3, 1e-2, 1e-1), sigma=4.0,
                        batch=64, precision="bf16_refine", rhs_seed=1003),
 }
+
+
+def random_fno_weights(nlevels: int, seed: int, width: int = 8, layers: int = 2,
+                       modes: int = 4, ksize: int = 3):
+    """Seeded random weights of the 2D FNO smoother (Appendix A: lift 1 -> c,
+    `layers` Fourier layers with a ksize x ksize W term and complex R on
+    `modes` modes per axis, projection c -> 1), one dict per level:
+    dict(lift=(Wl [c], bl [c]), layers=[(W [c, c, k, k], b [c],
+    R [2, c, c, m, m] complex)], proj=(Wp [c], bp [1])).  He-style scales
+    keep the activations O(1)."""
+    rng = np.random.default_rng(seed)
+    c, m, k = width, modes, ksize
+    out = []
+    for _ in range(nlevels):
+        lift = (rng.standard_normal(c), 0.1 * rng.standard_normal(c))
+        lay = []
+        for _ in range(layers):
+            W = rng.standard_normal((c, c, k, k)) * math.sqrt(1.0 / (c * k * k))
+            b = 0.1 * rng.standard_normal(c)
+            R = (rng.standard_normal((2, c, c, m, m)) + 1j * rng.standard_normal((2, c, c, m, m)))
+            lay.append((W, b, R * math.sqrt(1.0 / c)))
+        proj = (rng.standard_normal(c) * math.sqrt(1.0 / c), 0.1 * rng.standard_normal(1))
+        out.append(dict(lift=lift, layers=lay, proj=proj))
+    return out

@@ -12,7 +12,8 @@ Everything is plain float64 numpy, written to follow the paper step by step:
 * coarse operators are the Galerkin products R A P (Algorithm 1, step
   A^(l+1) <- I_l^{l+1} A^(l) I_{l+1}^l);
 * the coarsest system is solved with a hand-written dense Cholesky;
-* the smoother is the CNN applied by a direct convolution sum;
+* the smoother is the CNN applied by a direct convolution sum, or the FNO of
+  Appendix A (spectral part by numpy's real FFTs);
 * the output filter is Re(IDFT(m' . DFT(h))) (Sections 3.2 and 3.3) using
   numpy's FFT as a library primitive;
 * the cycle is NMGF1d / NMGF2d exactly as Algorithms 3 and 4 list it, and the
@@ -31,6 +32,10 @@ design notes of the repository):
   R4  ||b|| = 0 gives h = 0.
   R5  smoothers sit on levels 1..L-1 and the coarsest level L has the
       exact solve.
+  R13 FNO: the retained modes are the half spectrum of the real 2D DFT with
+      k1 in [0, m) and [n - m, n), k2 in [0, m) (the FNO the paper cites);
+      sigma = ReLU after every Fourier layer; the lift and projection are
+      pointwise affine maps.
 """
 from __future__ import annotations
 
@@ -39,7 +44,8 @@ import numpy as np
 __all__ = [
     "prolongation", "restriction", "toeplitz_from_column", "banded_toeplitz",
     "Hierarchy", "build_hierarchy_1d", "build_hierarchy_2d",
-    "cholesky", "cholesky_solve", "apply_level", "cnn_forward", "smoother",
+    "cholesky", "cholesky_solve", "apply_level", "cnn_forward", "fno_spectral", "fno_forward",
+    "smoother",
     "filter_mask", "spectral_filter", "restrict", "prolong", "nmgf", "relres", "solve",
 ]
 
@@ -253,6 +259,42 @@ def cnn_forward(weights, x: np.ndarray) -> np.ndarray:
     return z[:, 0]
 
 
+# ---------------------------------------------------------------------------
+# FNO smoother (Section 3.1, Appendix A): lift, Fourier layers, projection
+# ---------------------------------------------------------------------------
+
+def fno_spectral(z: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """DFT^{-1}(R . DFT(z)) of one Fourier layer (Appendix A): R acts only on
+    the first m low-frequency modes per axis (reading R13: the half spectrum
+    of a real 2D signal, k1 in [0, m) and [n - m, n), k2 in [0, m)) and the
+    other modes are zeroed.  z is [B, c, n, n] real, R is [2, c_in, c_out, m,
+    m] complex (block 0: k1 = 0..m-1, block 1: k1 = n-m..n-1).  The DFTs are
+    numpy's real FFTs (a library primitive)."""
+    B, c, n, _ = z.shape
+    m = R.shape[-1]
+    Z = np.fft.rfft2(z)  # [B, c, n, n/2 + 1]
+    Y = np.zeros((B, R.shape[2], n, n // 2 + 1), dtype=np.complex128)
+    Y[:, :, :m, :m] = np.einsum("bixy,ioxy->boxy", Z[:, :, :m, :m], R[0])
+    Y[:, :, n - m:, :m] = np.einsum("bixy,ioxy->boxy", Z[:, :, n - m:, :m], R[1])
+    return np.fft.irfft2(Y, s=(n, n))
+
+
+def fno_forward(weights, x: np.ndarray) -> np.ndarray:
+    """N_theta(x) of the FNO of Appendix A on [B, n, n]: a pointwise lift
+    1 -> c, L Fourier layers z <- sigma(DFT^{-1}(R . DFT(z)) + W z + B) with
+    W a 'same' convolution and sigma = ReLU (reading R13), then a pointwise
+    projection c -> 1.  weights = dict(lift=(Wl [c], bl [c]),
+    layers=[(W [c, c, k, k], b [c], R [2, c, c, m, m] complex), ...],
+    proj=(Wp [c], bp [1]))."""
+    Wl, bl = (np.asarray(a, np.float64) for a in weights["lift"])
+    z = Wl[None, :, None, None] * x[:, None] + bl[None, :, None, None]
+    for W, b, R in weights["layers"]:
+        z = np.maximum(_conv_same(z, np.asarray(W, np.float64), np.asarray(b, np.float64)) +
+                       fno_spectral(z, np.asarray(R, np.complex128)), 0.0)
+    Wp, bp = (np.asarray(a, np.float64) for a in weights["proj"])
+    return np.einsum("c,bcij->bij", Wp, z) + bp[0]
+
+
 def _norms(v: np.ndarray) -> np.ndarray:
     return np.sqrt(np.sum(v.reshape(v.shape[0], -1) ** 2, axis=1))
 
@@ -263,7 +305,8 @@ def smoother(weights, b: np.ndarray) -> np.ndarray:
     s = _norms(b)
     shape = (-1,) + (1,) * (b.ndim - 1)
     safe = np.where(s > 0, s, 1.0).reshape(shape)
-    h = cnn_forward(weights, b / safe) * safe
+    net = fno_forward if isinstance(weights, dict) else cnn_forward
+    h = net(weights, b / safe) * safe
     return np.where(s.reshape(shape) > 0, h, 0.0)
 
 

@@ -492,3 +492,91 @@ def test_full_solve_1d_aniso_converges_to_lu_solution():
     kappa = np.linalg.cond(H.ops[0])
     err = np.linalg.norm(u - ulu, axis=1) / np.linalg.norm(ulu, axis=1)
     assert np.all(err <= kappa * 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# FNO smoother (Section 3.1, Appendix A; reading R13)
+# ---------------------------------------------------------------------------
+
+def _fno_full_mask(n, m):
+    """The real-output spectral layer with identity R, written on the full
+    (complex) DFT grid: modes k1 in [-m, m-1], k2 in (0, m) and their mirror
+    images carry weight 1; on the k2 = 0 column (whose imaginary part the
+    real inverse discards) k1 and -k1 each carry half of the retained set."""
+    M = np.zeros((n, n))
+    kept = lambda k1: (k1 % n) < m or (k1 % n) >= n - m  # noqa: E731
+    for k1 in range(n):
+        for k2 in range(n):
+            if 0 < k2 < m and kept(k1):
+                M[k1, k2] += 1.0
+            if 0 < (-k2) % n < m and kept(-k1):
+                M[k1, k2] += 1.0
+            if k2 == 0:
+                M[k1, 0] = 0.5 * (kept(k1) + kept(-k1))
+    return M
+
+
+def test_fno_spectral_identity_R_is_full_dft_projection():
+    """With R the identity on every retained mode, the spectral layer is the
+    projection Re(IDFT(M . DFT(z))) with the full-grid mask above, computed
+    here with numpy's complex 2D FFT (the oracle uses the real FFTs)."""
+    n, m, c = 16, 3, 2
+    rng = np.random.default_rng(11)
+    z = rng.standard_normal((2, c, n, n))
+    R = np.zeros((2, c, c, m, m), np.complex128)
+    for i in range(c):
+        R[:, i, i] = 1.0
+    got = O.fno_spectral(z, R)
+    ref = np.real(np.fft.ifft2(_fno_full_mask(n, m) * np.fft.fft2(z)))
+    assert np.abs(got - ref).max() < 1e-13
+
+
+def test_fno_spectral_single_mode_closed_form():
+    """One retained mode (k1, k2) = (1, 2) with R = r (c = 1) maps a cosine of
+    that frequency to Re(r) cos - Im(r) sin of the same frequency (the DFT of a
+    pure wave is a single pair of spikes), and removes a wave of frequency
+    (0, m) along the half-spectrum axis, outside the retained set (while
+    (m, 0) keeps half its amplitude: -m is retained on that axis, +m is not)."""
+    n, m = 16, 3
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    th = 2 * np.pi * (1 * y + 2 * x) / n
+    r = 0.7 - 0.4j
+    R = np.zeros((2, 1, 1, m, m), np.complex128)
+    R[0, 0, 0, 1, 2] = r      # k1 = 1
+    R[1, 0, 0, m - 1, 2] = r  # k1 = n - 1 (the mirror row, same weight)
+    z = np.cos(th)[None, None]
+    got = O.fno_spectral(z, R)[0, 0]
+    assert np.abs(got - (r.real * np.cos(th) - r.imag * np.sin(th))).max() < 1e-13
+    R2 = np.ones((2, 1, 1, m, m), np.complex128)
+    far = np.cos(2 * np.pi * m * x / n)[None, None]
+    assert np.abs(O.fno_spectral(far, R2)).max() < 1e-13
+    edge = np.cos(2 * np.pi * m * y / n)[None, None]
+    assert np.abs(O.fno_spectral(edge, R2) - 0.5 * edge).max() < 1e-13
+
+
+def test_fno_without_spectral_part_matches_torch():
+    """R = 0: the FNO is lift (1x1 conv) -> [conv + bias, ReLU] x L -> 1x1
+    projection, checked against torch.nn.functional.conv2d."""
+    torch = pytest.importorskip("torch")
+    W = I.random_fno_weights(1, 21, width=4, layers=2, modes=2, ksize=3)[0]
+    W["layers"] = [(w, b, 0 * R) for (w, b, R) in W["layers"]]
+    x = np.random.default_rng(4).standard_normal((2, 12, 12))
+    got = O.fno_forward(W, x)
+    F = torch.nn.functional
+    t = torch.tensor(x[:, None])
+    Wl, bl = W["lift"]
+    t = F.conv2d(t, torch.tensor(Wl).view(-1, 1, 1, 1), torch.tensor(bl))
+    for w, b, _ in W["layers"]:
+        t = torch.relu(F.conv2d(t, torch.tensor(w), torch.tensor(b), padding=1))
+    Wp, bp = W["proj"]
+    t = F.conv2d(t, torch.tensor(Wp).view(1, -1, 1, 1), torch.tensor(bp))
+    assert np.abs(got - t[:, 0].numpy()).max() < 1e-12
+
+
+def test_fno_smoother_is_positively_homogeneous_in_b():
+    """h = N(b / ||b||) ||b||: scaling b by s > 0 scales h by s."""
+    W = I.random_fno_weights(1, 5, width=4, layers=2, modes=2)[0]
+    b = np.random.default_rng(2).standard_normal((3, 16, 16))
+    h1 = O.smoother(W, b)
+    h2 = O.smoother(W, 3.5 * b)
+    assert np.abs(h2 - 3.5 * h1).max() <= 1e-12 * np.abs(h2).max()
