@@ -138,10 +138,14 @@ typedef struct {
   int nreg;
 } nmg_operator_desc;
 
+/* smoother architectures (nmg_smoother_desc.arch) */
+#define NMG_SMOOTHER_CNN 0
+#define NMG_SMOOTHER_FNO 1
+
 /*
  * Smoother description: a CNN per smoother level (the paper's smoothers
  * are neural operators, Section 3.1; here conv -> ReLU -> ... -> conv with
- * zero 'same' padding and a bias on every layer).
+ * zero 'same' padding and a bias on every layer), or the FNO of Appendix A.
  *   layers   number of conv layers (>= 2); channels 1 -> width ->...-> 1
  *   width    hidden channels (2D: 32; 1D: 16 in this build)
  *   ksize    kernel size (2D: 3; 1D: 5 in this build)
@@ -152,6 +156,18 @@ typedef struct {
  *            layer: W in PyTorch Conv layout [Cout][Cin][k] (1D) or
  *            [Cout][Cin][k][k] (2D), then bias [Cout].
  *   nweights total number of doubles in `weights` (checked).
+ *   arch     NMG_SMOOTHER_CNN (0, the above) or NMG_SMOOTHER_FNO (1).
+ *   modes    FNO only: m, the retained modes per axis (the half spectrum of
+ *            the real 2D DFT with k1 in [0, m) and [n-m, n), k2 in [0, m);
+ *            1 <= m <= 32 and 2m <= the smallest smoother level's side).
+ * FNO (2D, precisions NMG_FP64 / NMG_FP32): a pointwise lift 1 -> width,
+ * `layers` Fourier layers z <- ReLU(W * z + B + DFT^-1(R . DFT(z))) with W a
+ * ksize x ksize 'same' convolution (odd ksize <= 7), and a pointwise
+ * projection width -> 1 (width <= 64).  Weights per level, in this order:
+ * lift W [width], lift b [width]; per layer W [width][width][ksize][ksize],
+ * b [width], Re R [2][width][width][m][m], Im R [2][width][width][m][m]
+ * ([block][in][out][k1][k2], block 0: k1 = 0..m-1, block 1: k1 =
+ * n-m..n-1); projection W [width], b [1].
  */
 typedef struct {
   int layers;
@@ -160,6 +176,8 @@ typedef struct {
   int nlevels;
   const double* weights;
   size_t nweights;
+  int arch;
+  int modes;
 } nmg_smoother_desc;
 
 typedef struct {

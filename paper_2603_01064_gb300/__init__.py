@@ -52,7 +52,9 @@ class _OpDesc(ctypes.Structure):
 class _SmDesc(ctypes.Structure):
     _fields_ = [("layers", ctypes.c_int), ("width", ctypes.c_int), ("ksize", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("weights", ctypes.POINTER(ctypes.c_double)),
-                ("nweights", ctypes.c_size_t)]
+                ("nweights", ctypes.c_size_t), ("arch", ctypes.c_int), ("modes", ctypes.c_int)]
+
+SMOOTHER_CNN, SMOOTHER_FNO = 0, 1
 
 
 class SolveInfo(ctypes.Structure):
@@ -145,6 +147,21 @@ def pack_weights(levels: Sequence[Sequence[tuple]]) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate(parts)) if parts else np.zeros(0)
 
 
+def pack_fno_weights(levels) -> np.ndarray:
+    """Flatten per-level FNO weights dict(lift=(W, b), layers=[(W, b, R)],
+    proj=(W, b)) into the ABI order: lift W, b; per layer W (PyTorch Conv2d
+    layout), b, Re R, Im R (R as [2][in][out][m][m]); projection W, b."""
+    parts = []
+    for lv in levels:
+        parts += [np.asarray(a, np.float64).ravel() for a in lv["lift"]]
+        for W, b, R in lv["layers"]:
+            R = np.asarray(R, np.complex128)
+            parts += [np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64).ravel(),
+                      R.real.ravel(), R.imag.ravel()]
+        parts += [np.asarray(a, np.float64).ravel() for a in lv["proj"]]
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
 def load_weights(path: str):
     """Read a trained smoother file (npz: l{level}_w{layer}, l{level}_b{layer})."""
     z = np.load(path)
@@ -228,13 +245,24 @@ class Hierarchy:
                      if self._reg is not None else None,
                      0 if self._reg is None else self._reg.size)
         smp = None
-        if weights is not None:
+        if weights is not None and isinstance(weights[0], dict):
+            # FNO smoother (Appendix A): dims from the first level's arrays
+            lv0 = weights[0]
+            W1, _, R1 = lv0["layers"][0]
+            layers, width, ksize = len(lv0["layers"]), np.asarray(W1).shape[0], np.asarray(W1).shape[-1]
+            self._w = pack_fno_weights(weights)
+            sm = _SmDesc(layers, width, ksize, len(weights),
+                         self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._w.size,
+                         SMOOTHER_FNO, np.asarray(R1).shape[-1])
+            smp = ctypes.byref(sm)
+        elif weights is not None:
             if layers is None:
                 W0 = np.asarray(weights[0][0][0])  # first layer: [width, 1, k(, k)]
                 layers, width, ksize = len(weights[0]), W0.shape[0], W0.shape[-1]
             self._w = pack_weights(weights)
             sm = _SmDesc(layers, width, ksize, len(weights),
-                         self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._w.size)
+                         self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._w.size,
+                         SMOOTHER_CNN, 0)
             smp = ctypes.byref(sm)
         self._h = ctypes.c_void_p()
         ctx.check(L.nmg_setup(ctx._h, ctypes.byref(op), smp, ctypes.byref(self._h)))

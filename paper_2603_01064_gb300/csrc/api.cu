@@ -78,6 +78,10 @@ struct DevLevel {
   double* wp_d = nullptr;  // 1D packed
   float* wp_f = nullptr;
   void* bf16_pack = nullptr;  // bf16 tensor-core weight pack (2D)
+  double* fno_d = nullptr;    // FNO weights (nmg_smoother_desc layout)
+  float* fno_f = nullptr;
+  double* ftw_d = nullptr;    // e^{-2 pi i j / n}, j < n, (re, im) pairs
+  float* ftw_f = nullptr;
   // launch choices (0 / -1 = built-in defaults), set by nmg_autotune
   int res_tile = 0, rst_tile = 0, ref_tile = 0, filt_mode = -1;
 };
@@ -99,6 +103,8 @@ struct Work {
   void* act0 = nullptr;
   void* act1 = nullptr;
   void* cbuf = nullptr;
+  void* fno_a = nullptr;  // FNO spectral scratch: [cap][width][n][m] complex
+  void* fno_b = nullptr;  // 2 x [cap][width][2m][m] complex
   float* r32 = nullptr;   // refinement residual (inner rhs)
   float* d32 = nullptr;   // refinement correction
   void* fdev = nullptr;   // nmg_solve_host staging
@@ -123,6 +129,7 @@ struct nmg_hier {
   double alpha = 0;
   int nc = 0;
   int layers = 0, width = 0, ksize = 0;
+  int arch = NMG_SMOOTHER_CNN, modes = 0;
   HostHierarchy host;
   std::vector<DevLevel> lv;
   double* chol = nullptr;           // Cholesky factor L of the coarsest operator
@@ -252,6 +259,11 @@ nmg_status ensure_work(nmg_hier* h, int B) {
     AL(actb, w.act0);
     AL(actb, w.act1);
     AL(n0 * B * 2 * es, w.cbuf);
+    if (h->arch == NMG_SMOOTHER_FNO) {
+      const size_t m = (size_t)h->modes, c = (size_t)h->width;
+      AL((size_t)B * c * h->n * m * 2 * es, w.fno_a);
+      AL(2 * (size_t)B * c * 2 * m * m * 2 * es, w.fno_b);
+    }
   }
   if (is_refine(h->precision)) {
     AL(plane(h, 0) * B * sizeof(float), w.r32);
@@ -341,6 +353,13 @@ void op_smooth<double>(nmg_hier* h, int l, int B, const double* b, const double*
                        const int* active) {
   nmg_ctx* c = h->ctx;
   const DevLevel& d = h->lv[l];
+  if (h->arch == NMG_SMOOTHER_FNO) {
+    launch_fno2d<double>(FnoDims{h->width, h->layers, h->ksize, h->modes}, d.n, B, d.fno_d,
+                         d.ftw_d, b, s, reinterpret_cast<double*>(h->w.act0),
+                         reinterpret_cast<double*>(h->w.act1), reinterpret_cast<double*>(h->w.fno_a),
+                         reinterpret_cast<double*>(h->w.fno_b), out, active, c->stream, c->log);
+    return;
+  }
   if (h->dim == 2) {
     std::vector<ConvW<double>> cw(h->layers);
     for (int i = 0; i < h->layers; ++i) cw[i] = ConvW<double>{d.Wd[i], d.bd[i]};
@@ -358,6 +377,13 @@ void op_smooth<float>(nmg_hier* h, int l, int B, const float* b, const double* s
                       const int* active) {
   nmg_ctx* c = h->ctx;
   const DevLevel& d = h->lv[l];
+  if (h->arch == NMG_SMOOTHER_FNO) {
+    launch_fno2d<float>(FnoDims{h->width, h->layers, h->ksize, h->modes}, d.n, B, d.fno_f,
+                        d.ftw_f, b, s, reinterpret_cast<float*>(h->w.act0),
+                        reinterpret_cast<float*>(h->w.act1), reinterpret_cast<float*>(h->w.fno_a),
+                        reinterpret_cast<float*>(h->w.fno_b), out, active, c->stream, c->log);
+    return;
+  }
   if (h->dim == 2) {
     if (is_refine(h->precision)) {
       launch_cnn2d_bf16_dispatch(h, l, B, b, s, out, active);
@@ -856,6 +882,34 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
   if (L > 1) {
     if (!sm || !sm->weights) return fail(ctx, NMG_ERR_WEIGHTS, "smoother weights required for levels > 1");
     if (sm->nlevels < L - 1) return fail(ctx, NMG_ERR_WEIGHTS, "fewer smoother levels than levels-1");
+    if (sm->arch != NMG_SMOOTHER_CNN && sm->arch != NMG_SMOOTHER_FNO)
+      return fail(ctx, NMG_ERR_ARG, "unknown smoother arch");
+  }
+  if (L > 1 && sm->arch == NMG_SMOOTHER_FNO) {
+    // ---- FNO smoother checks (Appendix A)
+    if (op->dim != 2) return fail(ctx, NMG_ERR_UNSUPPORTED, "the FNO smoother is 2D only");
+    if (op->precision != NMG_FP64 && op->precision != NMG_FP32)
+      return fail(ctx, NMG_ERR_UNSUPPORTED, "the FNO smoother runs in fp64 or fp32");
+    if (sm->layers < 1 || sm->width < 1 || sm->width > 64 || sm->ksize < 1 || sm->ksize > 7 ||
+        sm->ksize % 2 == 0)
+      return fail(ctx, NMG_ERR_UNSUPPORTED, "FNO: layers >= 1, width <= 64, odd ksize <= 7");
+    const int nmin = op->n >> (L - 2);  // smallest smoother level
+    if (sm->modes < 1 || sm->modes > 32 || 2 * sm->modes > nmin)
+      return fail(ctx, NMG_ERR_UNSUPPORTED, "FNO: 1 <= modes <= 32 and 2 modes <= every smoother level's side");
+    const int sw = 16 + sm->ksize - 1;
+    if ((size_t)sm->width * sw * sw * elem_size(op->precision) > 200 * 1024)
+      return fail(ctx, NMG_ERR_UNSUPPORTED, "FNO: width x (ksize + 15)^2 input tile exceeds shared memory");
+    if (sm->nweights != fno_weights_per_level(sm->width, sm->layers, sm->ksize, sm->modes) *
+                            (size_t)sm->nlevels)
+      return fail(ctx, NMG_ERR_WEIGHTS, "nweights does not match the FNO dimensions");
+    for (size_t i = 0; i < sm->nweights; ++i)
+      if (!std::isfinite(sm->weights[i])) return fail(ctx, NMG_ERR_WEIGHTS, "non-finite weight");
+    h->arch = NMG_SMOOTHER_FNO;
+    h->modes = sm->modes;
+    h->layers = sm->layers;
+    h->width = sm->width;
+    h->ksize = sm->ksize;
+  } else if (L > 1) {
     if (sm->layers < 2) return fail(ctx, NMG_ERR_WEIGHTS, "smoother needs at least 2 layers");
     if (op->dim == 2 && (sm->width != 32 || sm->ksize != 3))
       return fail(ctx, NMG_ERR_UNSUPPORTED, "2D smoother must be width 32, 3x3");
@@ -930,7 +984,27 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
     }
   }
   // ---- weights
-  if (L > 1) {
+  if (L > 1 && h->arch == NMG_SMOOTHER_FNO) {
+    const size_t per_level = fno_weights_per_level(h->width, h->layers, h->ksize, h->modes);
+    for (int l = 0; l < L - 1 && st == NMG_OK; ++l) {
+      DevLevel& d = h->lv[l];
+      std::vector<double> v(sm->weights + per_level * l, sm->weights + per_level * (l + 1));
+      d.fno_d = upload(ctx, h->allocs, v, &st);
+      d.fno_f = upload(ctx, h->allocs, to_f(v), &st);
+      std::vector<double> tw(2 * (size_t)d.n);
+      for (int j = 0; j < d.n; ++j) {
+        const double a = -2.0 * M_PI * j / d.n;
+        tw[2 * j] = std::cos(a);
+        tw[2 * j + 1] = std::sin(a);
+      }
+      d.ftw_d = upload(ctx, h->allocs, tw, &st);
+      d.ftw_f = upload(ctx, h->allocs, to_f(tw), &st);
+    }
+    if (st != NMG_OK) {
+      for (void* p : h->allocs) cudaFree(p);
+      return st;
+    }
+  } else if (L > 1) {
     size_t off = 0;
     const size_t kk = op->dim == 1 ? (size_t)h->ksize : (size_t)h->ksize * h->ksize;
     size_t per_level = 0;

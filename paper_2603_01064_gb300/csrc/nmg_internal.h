@@ -205,6 +205,20 @@ void launch_converge(const double* s, const double* fn, double rtol, int B, int*
                      LaunchLog& log);
 
 // CNN smoother (SIMT), 2D: h = s * N(b / s)
+// FNO smoother (k_fno.cu): dimensions shared by every smoother level
+struct FnoDims {
+  int width, layers, ksize, modes;
+};
+size_t fno_weights_per_level(int c, int layers, int ks, int m);
+// h = N_FNO(b / s) s on an n x n level; wts: the level's weights in the
+// nmg_smoother_desc layout (type T); tw: e^{-2 pi i j / n}, j < n, as (re, im)
+// pairs; z0, z1: [B][width][n][n]; cA: [B][width][n][modes] complex;
+// cB: 2 x [B][width][2 modes][modes] complex
+template <typename T>
+void launch_fno2d(const FnoDims& dm, int n, int B, const T* wts, const T* tw, const T* b,
+                  const double* s, T* z0, T* z1, T* cA, T* cB, T* h, const int* active,
+                  cudaStream_t st, LaunchLog& log);
+
 template <typename T>
 void launch_cnn2d_simt(int n, int B, int layers, int width, const ConvW<T>* layers_w,
                        const T* b, const double* s, T* act0, T* act1, T* h, const int* active,
