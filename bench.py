@@ -427,6 +427,9 @@ def run_ours(args, wl, world, rank, local):
     serving = None
     if not args.no_serving:
         serving = serving_leg(ctx, rank)
+    fno = None
+    if not args.no_fno:
+        fno = fno_leg(ctx, wl, B, taps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -449,7 +452,7 @@ def run_ours(args, wl, world, rank, local):
                 "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
                 "compare": compare, "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "serving": serving}
+                "serving": serving, "fno_smoother": fno}
         print(json.dumps(line), flush=True)
 
 
@@ -457,6 +460,49 @@ SERVING = dict(requests=800, rate=400.0, seed=4242,
                ops=[  # (n, levels, sigma px, alpha, weights, slots)
                    (128, 5, 2.0, 1e-2, "c2_2d_n128_s2_a1e-2.npz", 128),
                    (512, 7, 4.0, 1e-2, "c3_2d_n512_s4_a1e-2.npz", 16)])
+
+
+FNO = dict(width=64, layers=4, modes=8, ksize=3, seed=0, reps=5)
+
+
+def fno_leg(ctx, wl, B, taps):
+    """The FNO smoother of Appendix A (the paper's 2D hyperparameters at
+    h = 1/128: 64 channels, 4 Fourier layers, 3x3 W term; 8 retained modes
+    per axis, the most a 16x16 coarsest smoother level holds) applied once to
+    the fine level of the workload's whole batch in fp32, with seeded random
+    weights (its cost does not depend on the weights).  CUDA events around
+    `reps` applications after one warm-up; flops counted per output pixel:
+    lift and projection 4c, per layer 2 c^2 k^2 (W term) + 8 c m (the
+    truncated DFTs' row passes) + the smaller column passes and mode mixing."""
+    import torch
+    import paper_2603_01064_gb300 as nmg
+    n, L = wl["n"], wl["levels"]
+    c, nl, m, k = FNO["width"], FNO["layers"], FNO["modes"], FNO["ksize"]
+    W = I.random_fno_weights(L - 1, FNO["seed"], width=c, layers=nl, modes=m, ksize=k)
+    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=wl["alpha"], taps=taps, precision="fp32",
+                      weights=W)
+    b = torch.tensor(make_rhs(wl, B, 99), dtype=torch.float32, device="cuda")
+    h = torch.empty_like(b)
+    G.smooth(0, b, h)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(FNO["reps"]):
+        G.smooth(0, b, h)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / FNO["reps"]
+    G.close()
+    per_px = (4 * c + nl * (2 * c * c * k * k + 8 * c * m) +
+              nl * (32 * m * m * c / n + 16 * m * m * c * c / (n * n)))
+    tflops = per_px * n * n * B / (ms / 1e3) / 1e12
+    return {"config": {"n": n, "batch": B, "width": c, "layers": nl, "modes": m, "ksize": k,
+                       "precision": "fp32", "weights": "seeded random"},
+            "ms_per_application": ms, "flop_per_pixel": per_px, "achieved_tflops": tflops,
+            "bound": "alu", "peak_tflops": FP32_PEAK_TFLOPS,
+            "frac": tflops / FP32_PEAK_TFLOPS,
+            "peak_source": "152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz (derived)"}
 
 
 def serving_leg(ctx, rank):
@@ -501,6 +547,7 @@ def main():
     ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-fno", action="store_true", help="skip the FNO smoother timing")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured iterations "
                          "(profiler launch lists)")

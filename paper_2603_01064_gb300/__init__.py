@@ -163,9 +163,17 @@ def pack_fno_weights(levels) -> np.ndarray:
 
 
 def load_weights(path: str):
-    """Read a trained smoother file (npz: l{level}_w{layer}, l{level}_b{layer})."""
+    """Read a trained smoother file: CNN (npz: l{level}_w{layer},
+    l{level}_b{layer}) or FNO (meta_arch = "fno": per level a dict of lift,
+    layers (W, b, R) and proj, see pack_fno_weights)."""
     z = np.load(path)
     nl = int(z["meta_smoother_levels"])
+    if "meta_arch" in z.files and str(z["meta_arch"]) == "fno":
+        nk = len([k for k in z.files if k.startswith("l0_k") and k.endswith("_w")])
+        return [dict(lift=(z[f"l{l}_lift_w"], z[f"l{l}_lift_b"]),
+                     layers=[(z[f"l{l}_k{i}_w"], z[f"l{l}_k{i}_b"],
+                              z[f"l{l}_k{i}_rre"] + 1j * z[f"l{l}_k{i}_rim"]) for i in range(nk)],
+                     proj=(z[f"l{l}_proj_w"], z[f"l{l}_proj_b"])) for l in range(nl)]
     nlayers = len([k for k in z.files if k.startswith("l0_w")])
     return [[(z[f"l{l}_w{i}"], z[f"l{l}_b{i}"]) for i in range(nlayers)] for l in range(nl)]
 

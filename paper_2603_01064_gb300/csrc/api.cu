@@ -896,9 +896,6 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
     const int nmin = op->n >> (L - 2);  // smallest smoother level
     if (sm->modes < 1 || sm->modes > 32 || 2 * sm->modes > nmin)
       return fail(ctx, NMG_ERR_UNSUPPORTED, "FNO: 1 <= modes <= 32 and 2 modes <= every smoother level's side");
-    const int sw = 16 + sm->ksize - 1;
-    if ((size_t)sm->width * sw * sw * elem_size(op->precision) > 200 * 1024)
-      return fail(ctx, NMG_ERR_UNSUPPORTED, "FNO: width x (ksize + 15)^2 input tile exceeds shared memory");
     if (sm->nweights != fno_weights_per_level(sm->width, sm->layers, sm->ksize, sm->modes) *
                             (size_t)sm->nlevels)
       return fail(ctx, NMG_ERR_WEIGHTS, "nweights does not match the FNO dimensions");

@@ -151,65 +151,99 @@ __global__ void k_fno_idft_cols(int n, int m, int c, const C2<T>* __restrict__ y
   }
 }
 
-constexpr int FT = 16;      // output tile side of the W-term convolution
-constexpr int FOC = 8;      // output channels per block
+constexpr int FTW = 16;  // W-term tile: 16 columns
+constexpr int FTH = 32;  // x 32 rows (two pixels per thread, rows ty and ty + 16)
+constexpr int FOC = 16;  // output channels per block
+
+// input channels staged per pass (the tile with halo, and the block's
+// weights for them)
+template <typename T> struct FnoCC { static constexpr int value = sizeof(T) == 4 ? 16 : 8; };
+
+template <typename T>
+size_t fno_wconv_smem(int ks) {
+  constexpr int CC = FnoCC<T>::value;
+  return ((size_t)CC * (FTH + ks - 1) * (FTW + ks - 1) + (size_t)CC * ks * ks * FOC) * sizeof(T);
+}
 
 // z_out[img][o][p] = ReLU(b[o] + sum_{i,t} W[o][i][t] z_in[img][i][p + t] + S[o][p]),
-// S the last (row) pass of the inverse DFT from U; one block per 16x16 tile,
-// 8 output channels and image; the input tile (all channels, with halo) is
-// staged in shared memory
+// S the last (row) pass of the inverse DFT from U.  One block per 16 x 32
+// tile, 16 output channels and image; input channels pass through shared
+// memory CC at a time together with their weights, laid out [i][tap][16
+// outputs] so that a thread reads the 16 weights of a (channel, tap) with
+// vector loads and applies them to its two pixels.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_fno_wconv(int n, int m, int c, int ks, const T* __restrict__ zin, const C2<T>* __restrict__ u,
             const C2<T>* __restrict__ tw, const T* __restrict__ W, const T* __restrict__ bias,
             T* __restrict__ zout, const int* __restrict__ active, int tiles_x) {
+  constexpr int CC = FnoCC<T>::value;
   const int img = blockIdx.z;
   if (!active[img]) return;
   extern __shared__ __align__(16) unsigned char fno_smem[];
-  T* xs = reinterpret_cast<T*>(fno_smem);  // [c][FT + ks - 1][FT + ks - 1]
-  const int hw = ks / 2, SW = FT + ks - 1;
-  const int y0 = (blockIdx.x / tiles_x) * FT, x0 = (blockIdx.x % tiles_x) * FT;
+  const int hw = ks / 2, SW = FTW + ks - 1, SH = FTH + ks - 1, KK = ks * ks;
+  T* ws = reinterpret_cast<T*>(fno_smem);  // [CC][KK][FOC]
+  T* xs = ws + (size_t)CC * KK * FOC;      // [CC][SH][SW]
+  const int y0 = (blockIdx.x / tiles_x) * FTH, x0 = (blockIdx.x % tiles_x) * FTW;
   const int o0 = blockIdx.y * FOC;
   const size_t plane = (size_t)n * n;
   const T* zb = zin + (size_t)img * c * plane;
-  for (int i = threadIdx.x; i < c * SW * SW; i += blockDim.x) {
-    const int ch = i / (SW * SW), r = i - ch * SW * SW;
-    const int yy = y0 - hw + r / SW, xx = x0 - hw + r % SW;
-    xs[i] = (yy >= 0 && yy < n && xx >= 0 && xx < n) ? zb[(size_t)ch * plane + (size_t)yy * n + xx]
-                                                     : T(0);
-  }
-  __syncthreads();
-  const int ty = threadIdx.x / FT, tx = threadIdx.x % FT;
-  const int y = y0 + ty, x = x0 + tx;
-  if (y >= n || x >= n) return;
-  T acc[FOC];
+  const int tx = threadIdx.x % FTW, ty = threadIdx.x / FTW;  // ty < 16
+  T acc0[FOC], acc1[FOC];
 #pragma unroll
-  for (int q = 0; q < FOC; ++q) acc[q] = (o0 + q < c) ? bias[o0 + q] : T(0);
-  for (int ch = 0; ch < c; ++ch) {
-    const T* xc = xs + (size_t)ch * SW * SW + ty * SW + tx;
-    for (int dy = 0; dy < ks; ++dy)
-      for (int dx = 0; dx < ks; ++dx) {
-        const T v = xc[dy * SW + dx];
+  for (int q = 0; q < FOC; ++q) acc0[q] = acc1[q] = T(0);
+  for (int ch0 = 0; ch0 < c; ch0 += CC) {
+    __syncthreads();  // the previous pass is done with xs and ws
+    for (int i = threadIdx.x; i < CC * SH * SW; i += blockDim.x) {
+      const int cc = i / (SH * SW), r = i - cc * SH * SW;
+      const int yy = y0 - hw + r / SW, xx = x0 - hw + r % SW;
+      const bool in = ch0 + cc < c && yy >= 0 && yy < n && xx >= 0 && xx < n;
+      xs[i] = in ? zb[(size_t)(ch0 + cc) * plane + (size_t)yy * n + xx] : T(0);
+    }
+    for (int i = threadIdx.x; i < CC * KK * FOC; i += blockDim.x) {
+      const int cc = i / (KK * FOC), r = i - cc * KK * FOC, t = r / FOC, q = r - t * FOC;
+      const bool in = ch0 + cc < c && o0 + q < c;
+      ws[i] = in ? W[((size_t)(o0 + q) * c + ch0 + cc) * KK + t] : T(0);
+    }
+    __syncthreads();
+    for (int cc = 0; cc < CC; ++cc) {
+      const T* xc = xs + (size_t)cc * SH * SW + ty * SW + tx;
+      const T* wc = ws + (size_t)cc * KK * FOC;
+      for (int dy = 0; dy < ks; ++dy)
+        for (int dx = 0; dx < ks; ++dx) {
+          const T v0 = xc[dy * SW + dx], v1 = xc[(dy + 16) * SW + dx];
+          const T* wt = wc + (dy * ks + dx) * FOC;
 #pragma unroll
-        for (int q = 0; q < FOC; ++q)
-          if (o0 + q < c) acc[q] += W[(((size_t)(o0 + q) * c + ch) * ks + dy) * ks + dx] * v;
-      }
+          for (int q = 0; q < FOC; ++q) {
+            const T wq = wt[q];
+            acc0[q] += wq * v0;
+            acc1[q] += wq * v1;
+          }
+        }
+    }
   }
   const T inv_n = T(1) / T(n);
+  const int x = x0 + tx;
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    const int y = y0 + ty + 16 * half;
+    if (y >= n || x >= n) continue;
 #pragma unroll
-  for (int q = 0; q < FOC; ++q) {
-    const int o = o0 + q;
-    if (o >= c) break;
-    // row pass of the inverse DFT at (y, x): row y of U, column x
-    const C2<T>* ur = u + (((size_t)img * c + o) * n + y) * m;
-    T s = ur[0].x;
-    int idx = x % n;
-    for (int k2 = 1; k2 < m; ++k2, idx = (idx + x) % n) {
-      // e^{+2 pi i k2 x / n} = conj(tw[(k2 x) mod n])
-      s += T(2) * (ur[k2].x * tw[idx].x + ur[k2].y * tw[idx].y);
+    for (int q = 0; q < FOC; ++q) {
+      const int o = o0 + q;
+      if (o >= c) break;
+      // row pass of the inverse DFT at (y, x): row y of U, column x
+      const C2<T>* ur = u + (((size_t)img * c + o) * n + y) * m;
+      T sp = ur[0].x;
+      int idx = x;
+      for (int k2 = 1; k2 < m; ++k2) {
+        // e^{+2 pi i k2 x / n} = conj(tw[(k2 x) mod n])
+        sp += T(2) * (ur[k2].x * tw[idx].x + ur[k2].y * tw[idx].y);
+        idx += x;
+        if (idx >= n) idx -= n;
+      }
+      const T v = (half ? acc1[q] : acc0[q]) + bias[o] + sp * inv_n;
+      zout[((size_t)img * c + o) * plane + (size_t)y * n + x] = v > T(0) ? v : T(0);
     }
-    const T v = acc[q] + s * inv_n;
-    zout[((size_t)img * c + o) * plane + (size_t)y * n + x] = v > T(0) ? v : T(0);
   }
 }
 
@@ -257,9 +291,8 @@ void launch_fno2d(const FnoDims& dm, int n, int B, const T* wts, const T* tw, co
   k_fno_lift<T><<<gp, 256, 0, st>>>(n, c, b, s, wts, z0, active);
   log.end(pi_, st, units);
   const size_t per_layer = (size_t)c * c * ks * ks + c + 4 * (size_t)c * c * m * m;
-  const int tiles_x = (n + FT - 1) / FT;
-  const int SW = FT + ks - 1;
-  const size_t sm = (size_t)c * SW * SW * sizeof(T);
+  const int tiles_x = (n + FTW - 1) / FTW, tiles_y = (n + FTH - 1) / FTH;
+  const size_t sm = fno_wconv_smem<T>(ks);
   cudaFuncSetAttribute(k_fno_wconv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   T* zi = z0;
   T* zo = z1;
@@ -275,7 +308,7 @@ void launch_fno2d(const FnoDims& dm, int n, int B, const T* wts, const T* tw, co
     k_fno_mix<T><<<dim3((unsigned)std::min(64, (c * 2 * m * m + 255) / 256), (unsigned)B), 256, 0,
                    st>>>(m, c, zh, rre, rim, yh, active);
     k_fno_idft_cols<T><<<B * c, 256, 0, st>>>(n, m, c, yh, twc, t1, active);
-    k_fno_wconv<T><<<dim3(tiles_x * tiles_x, (c + FOC - 1) / FOC, B), FT * FT, sm, st>>>(
+    k_fno_wconv<T><<<dim3(tiles_x * tiles_y, (c + FOC - 1) / FOC, B), FTW * 16, sm, st>>>(
         n, m, c, ks, zi, t1, twc, Wl, bl, zo, active, tiles_x);
     log.launches += 4;
     log.end(pi_, st, units);

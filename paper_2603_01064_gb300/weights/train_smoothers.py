@@ -78,6 +78,43 @@ class CNN(nn.Module):
         return self.gain * z.squeeze(1)
 
 
+class FNO(nn.Module):
+    """2D FNO smoother of Appendix A: pointwise lift 1 -> width, `layers`
+    Fourier layers z <- ReLU(W * z + B + DFT^-1(R . DFT(z))) with R on the
+    modes k1 in [0, m) and [n - m, n), k2 in [0, m) of the real 2D DFT, and a
+    pointwise projection width -> 1 (times the training gain, folded into the
+    projection on export)."""
+
+    def __init__(self, layers, width, ksize, modes, gain=1.0):
+        super().__init__()
+        self.m = modes
+        self.lift = nn.Conv2d(1, width, 1)
+        self.w = nn.ModuleList(nn.Conv2d(width, width, ksize, padding=ksize // 2)
+                               for _ in range(layers))
+        scale = 1.0 / width
+        self.r = nn.ParameterList(
+            nn.Parameter(scale * torch.randn(2, width, width, modes, modes, dtype=torch.cfloat))
+            for _ in range(layers))
+        self.proj = nn.Conv2d(width, 1, 1)
+        self.gain = gain
+        nn.init.zeros_(self.proj.weight)
+        nn.init.zeros_(self.proj.bias)
+
+    def spectral(self, z, R):
+        n, m = z.shape[-1], self.m
+        Z = torch.fft.rfft2(z)
+        Y = torch.zeros(z.shape[0], R.shape[2], n, n // 2 + 1, dtype=Z.dtype, device=z.device)
+        Y[:, :, :m, :m] = torch.einsum("bixy,ioxy->boxy", Z[:, :, :m, :m], R[0])
+        Y[:, :, n - m:, :m] = torch.einsum("bixy,ioxy->boxy", Z[:, :, n - m:, :m], R[1])
+        return torch.fft.irfft2(Y, s=(n, n))
+
+    def forward(self, x):
+        z = self.lift(x.unsqueeze(1))
+        for W, R in zip(self.w, self.r):
+            z = F.relu(W(z) + self.spectral(z, R))
+        return self.gain * self.proj(z).squeeze(1)
+
+
 # ---------------------------------------------------------------------------
 # dense hierarchy (same definitions as the solve path; written independently)
 # ---------------------------------------------------------------------------
@@ -309,6 +346,29 @@ def nets_to_npz(nets, path, meta):
     np.savez(path, **arrs)
 
 
+def fno_to_npz(nets, path, meta):
+    """Export FNO smoothers: l{l}_lift_w [c], l{l}_lift_b [c], l{l}_k{i}_w
+    [c, c, k, k], l{l}_k{i}_b [c], l{l}_k{i}_rre / _rim [2, c, c, m, m],
+    l{l}_proj_w [c], l{l}_proj_b [1] (gain folded in; the projection's bias
+    exported as zero for the reason given in nets_to_npz)."""
+    arrs = {}
+    np_ = lambda t: t.detach().cpu().numpy()  # noqa: E731
+    for l, net in enumerate(nets):
+        arrs[f"l{l}_lift_w"] = np_(net.lift.weight).reshape(-1).astype(np.float64)
+        arrs[f"l{l}_lift_b"] = np_(net.lift.bias).astype(np.float64)
+        for i, (W, R) in enumerate(zip(net.w, net.r)):
+            arrs[f"l{l}_k{i}_w"] = np_(W.weight).astype(np.float64)
+            arrs[f"l{l}_k{i}_b"] = np_(W.bias).astype(np.float64)
+            arrs[f"l{l}_k{i}_rre"] = np_(R.real).astype(np.float64)
+            arrs[f"l{l}_k{i}_rim"] = np_(R.imag).astype(np.float64)
+        arrs[f"l{l}_proj_w"] = net.gain * np_(net.proj.weight).reshape(-1).astype(np.float64)
+        arrs[f"l{l}_proj_b"] = np.zeros(1)
+    for k, v in meta.items():
+        arrs["meta_" + k] = np.array(v)
+    arrs["meta_arch"] = np.array("fno")
+    np.savez(path, **arrs)
+
+
 def nets_from_npz(path, dim, layers, width, ksize, device="cpu", gains=None):
     z = np.load(path)
     nl = int(z["meta_smoother_levels"])
@@ -334,6 +394,10 @@ PRESETS = {
     "c2": dict(dim=2, n=128, levels=5, alpha=1e-2, sigma=2.0, layers=4, width=32, ksize=3),
     "c3": dict(dim=2, n=512, levels=7, alpha=1e-3, sigma=4.0, layers=4, width=32, ksize=3,
                rhs="waves"),
+    # the FNO smoother of Appendix A on the 128x128 operator (8 modes: the
+    # most the 16x16 coarsest smoother level holds)
+    "c2f": dict(dim=2, n=128, levels=5, alpha=1e-2, sigma=2.0, layers=4, width=32, ksize=3,
+                arch="fno", modes=8),
 }
 
 
@@ -375,7 +439,10 @@ def main(argv=None):
         prob = Problem(2, cfg["n"], cfg["levels"], cfg["alpha"], taps=taps, device=a.device)
     gains = [prob.top_gain(l) for l in range(cfg["levels"] - 1)]
     print("output gains", ["%.3g" % g for g in gains])
-    if a.init:
+    if cfg.get("arch") == "fno":
+        nets = [FNO(cfg["layers"], cfg["width"], cfg["ksize"], cfg["modes"], gain=g).to(a.device)
+                for g in gains]
+    elif a.init:
         nets = nets_from_npz(a.init, dim, cfg["layers"], cfg["width"], cfg["ksize"], a.device, gains)
     else:
         nets = [CNN(dim, cfg["layers"], cfg["width"], cfg["ksize"], gain=g).to(a.device)
@@ -412,7 +479,7 @@ def main(argv=None):
                 best = score
                 meta = dict(cfg, epochs=ep, bs=a.bs, K=a.K, lr=a.lr, seed=a.seed,
                             smoother_levels=cfg["levels"] - 1, eval_cycles=score)
-                nets_to_npz(nets, a.out, meta)
+                (fno_to_npz if cfg.get("arch") == "fno" else nets_to_npz)(nets, a.out, meta)
                 print(f"   saved (mean cycles {score:.2f})", flush=True)
     print("done", a.out, f"{time.time() - t0:.0f}s")
 
