@@ -46,7 +46,7 @@ WORKLOADS = {
     # 5 levels, 256 right-hand sides (ellipses + Gaussian random field, blurred, 1% noise)
     "c2": dict(name="2d_bttb_128x128_sigma2_alpha1e-2_L5_batch256", n=128, levels=5, alpha=1e-2,
                sigma=2.0, batch=256, rhs="ellipses_grf", rhs_seed=1002,
-               weights="c2_2d_n128_s2_a1e-2.npz"),
+               weights="c2_2d_n128_s2_a1e-2.npz", fno_weights="c2f_2d_n128_s2_a1e-2_fno.npz"),
 }
 PRECISION_TEXT = {
     "bf16_refine": "bf16 tensor-core smoother with split hi+lo bf16 operands and fp32 accumulation, "
@@ -389,6 +389,23 @@ def run_ours(args, wl, world, rank, local):
                 "mean_cycles": float(np.mean([r[0].mean() for r in rp])),
                 "max_relres": float(max(r[2].max() for r in rp))}
             Gp.close()
+        # the FNO smoother of Appendix A (fp32 SIMT), where trained FNO
+        # weights for this operator exist
+        fno_w = os.path.join(WEIGHTS, wl.get("fno_weights", ""))
+        if wl.get("fno_weights") and os.path.exists(fno_w):
+            Gf = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"],
+                               taps=taps, precision="fp32", weights=nmg.load_weights(fno_w))
+            uf = torch.zeros(f.shape, dtype=torch.float32, device="cuda")
+            step_f = (lambda Gf=Gf, uf=uf: step(Gf, f, uf))
+            step_f()
+            tf_, rf = timed(step_f, 1)
+            compare["fno_fp32_batched"] = {
+                "value": B * len(tf_) / (sum(tf_) / 1e3), "unit": "RHS/s", "batch": B,
+                "smoother": "FNO (Appendix A), trained, " + wl["fno_weights"],
+                "mean_cycles": float(np.mean([r[0].mean() for r in rf])),
+                "max_relres": float(max(r[2].max() for r in rf)),
+                "converged": bool(all((r[1] == 0).all() for r in rf))}
+            Gf.close()
         # plain fp32 single-RHS cycle: one right-hand side per solve call
         Gs = hier("fp32")
         nsingle = min(16, B)

@@ -91,7 +91,9 @@ class FNO(nn.Module):
         self.lift = nn.Conv2d(1, width, 1)
         self.w = nn.ModuleList(nn.Conv2d(width, width, ksize, padding=ksize // 2)
                                for _ in range(layers))
-        scale = 1.0 / width
+        # R starts near zero: the untrained layer is its local W term, and
+        # the spectral part grows from there
+        scale = 0.01 / width
         self.r = nn.ParameterList(
             nn.Parameter(scale * torch.randn(2, width, width, modes, modes, dtype=torch.cfloat))
             for _ in range(layers))
@@ -350,19 +352,20 @@ def fno_to_npz(nets, path, meta):
     """Export FNO smoothers: l{l}_lift_w [c], l{l}_lift_b [c], l{l}_k{i}_w
     [c, c, k, k], l{l}_k{i}_b [c], l{l}_k{i}_rre / _rim [2, c, c, m, m],
     l{l}_proj_w [c], l{l}_proj_b [1] (gain folded in; the projection's bias
-    exported as zero for the reason given in nets_to_npz)."""
+    exported as zero for the reason given in nets_to_npz).  Stored as fp32,
+    the precision the net was trained in."""
     arrs = {}
-    np_ = lambda t: t.detach().cpu().numpy()  # noqa: E731
+    np_ = lambda t: t.detach().cpu().numpy().astype(np.float32)  # noqa: E731
     for l, net in enumerate(nets):
-        arrs[f"l{l}_lift_w"] = np_(net.lift.weight).reshape(-1).astype(np.float64)
-        arrs[f"l{l}_lift_b"] = np_(net.lift.bias).astype(np.float64)
+        arrs[f"l{l}_lift_w"] = np_(net.lift.weight).reshape(-1)
+        arrs[f"l{l}_lift_b"] = np_(net.lift.bias)
         for i, (W, R) in enumerate(zip(net.w, net.r)):
-            arrs[f"l{l}_k{i}_w"] = np_(W.weight).astype(np.float64)
-            arrs[f"l{l}_k{i}_b"] = np_(W.bias).astype(np.float64)
-            arrs[f"l{l}_k{i}_rre"] = np_(R.real).astype(np.float64)
-            arrs[f"l{l}_k{i}_rim"] = np_(R.imag).astype(np.float64)
-        arrs[f"l{l}_proj_w"] = net.gain * np_(net.proj.weight).reshape(-1).astype(np.float64)
-        arrs[f"l{l}_proj_b"] = np.zeros(1)
+            arrs[f"l{l}_k{i}_w"] = np_(W.weight)
+            arrs[f"l{l}_k{i}_b"] = np_(W.bias)
+            arrs[f"l{l}_k{i}_rre"] = np_(R.real)
+            arrs[f"l{l}_k{i}_rim"] = np_(R.imag)
+        arrs[f"l{l}_proj_w"] = (net.gain * np_(net.proj.weight)).reshape(-1)
+        arrs[f"l{l}_proj_b"] = np.zeros(1, np.float32)
     for k, v in meta.items():
         arrs["meta_" + k] = np.array(v)
     arrs["meta_arch"] = np.array("fno")

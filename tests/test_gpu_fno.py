@@ -7,8 +7,12 @@ oracle, on seeded random FNO weights (width 8, 2 Fourier layers, 4 modes,
   path's parity tests);
 * a ragged batch with an all-zero right-hand side (h = 0 there);
 * setup rejects modes beyond the coarsest smoother level, the 16-bit forms
-  and a weight count that does not match.
+  and a weight count that does not match;
+* the trained FNO smoothers of the 128x128 operator (sigma 2 px, alpha
+  1e-2, 5 levels): one fp32 cycle against the oracle, and a solve to 1e-6.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -93,3 +97,34 @@ def test_fno_setup_rejects(ctx, setup):
     with pytest.raises(nmg.NMGError):  # one smoother level too few
         nmg.Hierarchy(ctx, dim=2, n=N, levels=L + 1, alpha=ALPHA, taps=taps, precision="fp32",
                       weights=W)
+
+
+# ---------------------------------------------------------------------------
+# trained FNO smoothers (128x128, sigma 2 px, alpha 1e-2, 5 levels)
+# ---------------------------------------------------------------------------
+
+FNO_W = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                     "paper_2603_01064_gb300", "weights", "c2f_2d_n128_s2_a1e-2_fno.npz")
+
+
+def test_fno_trained_cycle_and_solve(ctx):
+    """The trained FNO smoothers: one fp32 cycle of 2 sampled right-hand sides
+    against the oracle's cycle (1e-4: trained smoothers amplify fp32
+    rounding), and the whole 32-RHS batch solved to 1e-6 with the oracle's
+    own apply confirming the residual."""
+    W = nmg.load_weights(FNO_W)
+    taps = I.gaussian_taps(2.0)
+    H = O.build_hierarchy_2d(taps, 128, 1e-2, 5)
+    f, _ = I.rhs_2d_ellipses_grf(128, 32, seed=1002, sigma=2.0)
+    G = nmg.Hierarchy(ctx, dim=2, n=128, levels=5, alpha=1e-2, taps=taps, precision="fp32",
+                      weights=W)
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    ud = torch.zeros_like(fd)
+    G.cycle(fd, ud)
+    torch.cuda.synchronize()
+    ref = O.nmgf(H, W, 0, None, f[:2])
+    assert np.max(rel(ud[:2].double().cpu().numpy(), ref)) < 1e-4
+    ud.zero_()
+    cyc, st, rr = G.solve(fd, ud, rtol=1e-6, max_cycles=100)
+    assert np.all(st == 0) and np.all(rr <= 1e-6)
+    assert np.all(O.relres(H, f[[0, 31]], ud[[0, 31]].double().cpu().numpy()) <= 1.5e-6)
