@@ -484,8 +484,13 @@ __device__ __forceinline__ void warp_dit_inv(Cx<T> (&v)[L / 32], const Cx<T>* tw
 template <int L>
 __device__ __forceinline__ int brev_len(int s) { return __brev(s) >> (32 - (L == 32 ? 5 : L == 64 ? 6 : 7)); }
 
+// threads of the warp-level filter: one warp per row / column pair at a
+// time; 16 warps for 128 x 128 (a block holds one image, so more warps
+// shorten the per-image chain of row and column passes)
+template <int N> struct FWThreads { static constexpr int value = N == 128 ? 512 : 256; };
+
 template <typename T, int N>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(FWThreads<N>::value)
 k_filter_warp(const T* xstar, const T* __restrict__ h, T* x, const Cx<T>* __restrict__ twg,
               const double* __restrict__ mtab, const int* __restrict__ active) {
   constexpr int HN = N / 2, MR = N / 32, MC = HN / 32, P = N + 1;  // odd pitch
@@ -656,9 +661,10 @@ void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
     const size_t sm = n == 64 ? filter_warp_smem<T, 64>() : filter_warp_smem<T, 128>();
     if (sm <= 200 * 1024) {
       auto kern = n == 64 ? k_filter_warp<T, 64> : k_filter_warp<T, 128>;
+      const int threads = n == 64 ? FWThreads<64>::value : FWThreads<128>::value;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       int pi_ = log.begin(K_FILTER, st);
-      kern<<<B, 256, sm, st>>>(xstar, h, x, tw, mask_tab, active);
+      kern<<<B, threads, sm, st>>>(xstar, h, x, tw, mask_tab, active);
       log.end(pi_, st, units);
       return;
     }
