@@ -371,14 +371,16 @@ __global__ void __launch_bounds__(THREADS)
 k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
             const float* __restrict__ w4, const double* __restrict__ snorm,
-            const int* __restrict__ active, int* __restrict__ err) {
+            const int* __restrict__ active, int* __restrict__ err, int nbuf) {
   constexpr int ACH = SPLIT ? 8 : 4;  // 8-channel chunks per staged pixel
   constexpr int ABUF = ACH * CH_BYTES;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
   constexpr int TMEM_COLS = TMC<SPLIT>::value;
   constexpr int NACC = NT * NB<SPLIT>::value;  // columns of one accumulator
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* Bs = smem + 2 * ABUF;
+  // nbuf operand buffers (1 when the grid covers every tile: no tile is
+  // staged ahead, and two CTAs fit on an SM), then the weights
+  unsigned char* Bs = smem + nbuf * ABUF;
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -860,15 +862,20 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
   }
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
-  const size_t sm = 2 * ACH * CH_BYTES + B_BYTES;
   const int tiles_x = (n + TILE - 1) / TILE;
   long long total = (long long)nimg * tiles_x * tiles_x;
   long long grid = (long long)num_sms() * (SPLIT ? 1 : 3);
+  // few tiles (the 16 x 16 level): one tile per CTA with a single operand
+  // buffer, two CTAs per SM
+  const int nbuf = total <= 2LL * num_sms() ? 1 : 2;
+  if (nbuf == 1) grid = total;
+  const size_t sm = (size_t)nbuf * ACH * CH_BYTES + B_BYTES;
   if (grid > total) grid = total;
   if (grid < 1) grid = 1;
   cudaFuncSetAttribute(k_hidden_tc<SPLIT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int pi_ = log.begin(K_CNN_HIDDEN, st);
-  k_hidden_tc<SPLIT, FUSE><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, gout, lp, w4, s, active, err);
+  k_hidden_tc<SPLIT, FUSE><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, gout, lp, w4, s, active, err,
+                                                           nbuf);
   log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
