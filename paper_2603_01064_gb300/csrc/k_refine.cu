@@ -159,6 +159,8 @@ struct RefineArgs {
   int n;
   float ah, al;  // alpha as a float pair
   float sKh[2 * WK + 1], sKl[2 * WK + 1];
+  // the same as two-lane pairs (c, c) for the packed strip kernel; nKh = -sKh
+  float2 kh2[2 * WK + 1], nkh2[2 * WK + 1], kl2[2 * WK + 1];
 };
 
 template <int WK> struct RSeg { static constexpr int value = WK <= 8 ? 8 : 4; };
@@ -402,7 +404,62 @@ RefineArgs<WK> refine_args(const StencilHost<double>& sd, double alpha, int n) {
     a.sKh[WK - sd.wK + d] = (float)v;
     a.sKl[WK - sd.wK + d] = (float)(v - (double)(float)v);
   }
+  for (int d = 0; d <= 2 * WK; ++d) {
+    a.kh2[d] = make_float2(a.sKh[d], a.sKh[d]);
+    a.nkh2[d] = make_float2(-a.sKh[d], -a.sKh[d]);
+    a.kl2[d] = make_float2(a.sKl[d], a.sKl[d]);
+  }
   return a;
+}
+
+// two-lane fp32 arithmetic (add/sub/mul/fma.rn.f32x2): each lane of the
+// strip kernel owns two adjacent columns, whose double-float operations are
+// independent and run as one packed instruction each
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+  return *reinterpret_cast<unsigned long long*>(&v);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long v) {
+  return *reinterpret_cast<float2*>(&v);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+  return u2f(d);
+}
+// (h, l) += (ah + al)(xh + xl) on two lanes: the operations of df_fma with
+// p kept negated (pn = -ah xh, exact in sign), so that TwoProduct's error
+// term is fma(ah, xh, pn) and TwoSum subtracts pn; bitwise the same results
+__device__ __forceinline__ void df_fma2(float2& h, float2& l, float2 ah, float2 nah, float2 al,
+                                        float2 xh, float2 xl) {
+  const float2 pn = mul2(nah, xh);
+  float2 pe = fma2(ah, xh, pn);
+  pe = fma2(ah, xl, pe);
+  pe = fma2(al, xh, pe);
+  const float2 s = sub2(h, pn);
+  const float2 bb = sub2(s, h);
+  const float2 e = sub2(sub2(h, sub2(s, bb)), add2(pn, bb));
+  h = s;
+  l = add2(l, add2(e, pe));
+}
+__device__ __forceinline__ void df_norm2(float2& h, float2& l) {
+  const float2 s = add2(h, l);
+  l = sub2(l, sub2(s, h));
+  h = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -427,7 +484,7 @@ constexpr int kRsXW = kRsSW + 2 * kRsHalo;  // staged u row (doubles)
 constexpr int kRsWords = kRsRing * kRsXW * 2 + 2 * kRsXW + kRsRing * kRsSW;
 
 template <int WK>
-__global__ void __launch_bounds__(32 * kRsWarps, 3)
+__global__ void __launch_bounds__(32 * kRsWarps, 2)
 k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
                const float* __restrict__ f, float* __restrict__ r,
                double* __restrict__ partials, const int* __restrict__ active) {
@@ -473,9 +530,11 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
 #pragma unroll
     for (int k = 0; k < kRsPF; ++k) stage(alo + k);
 
-    DF tw[P][2];  // row-pass outputs of input rows a - 2 WK .. a
+    // row-pass outputs of input rows a - 2 WK .. a, double-float, the lane's
+    // two columns as pairs
+    float2 twh[P], twl[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) tw[k][0] = tw[k][1] = DF{0.f, 0.f};
+    for (int k = 0; k < P; ++k) twh[k] = twl[k] = make_float2(0.f, 0.f);
     float ss = 0.f;
 #pragma unroll 1
     for (int a = alo; a < ahi; ++a) {
@@ -501,27 +560,29 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
         wh[2 * k2] = vh.x; wh[2 * k2 + 1] = vh.y;
         wl[2 * k2] = vl.x; wl[2 * k2 + 1] = vl.y;
       }
-      DF acc[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+      float2 ah2 = make_float2(0.f, 0.f), al2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int d = 0; d < P; ++d)
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-          df_fma(acc[c], op.sKh[d], op.sKl[d], wh[c + kRsHalo - WK + d], wl[c + kRsHalo - WK + d]);
+      for (int d = 0; d < P; ++d) {
+        const int j = kRsHalo - WK + d;
+        df_fma2(ah2, al2, op.kh2[d], op.nkh2[d], op.kl2[d], make_float2(wh[j], wh[j + 1]),
+                make_float2(wl[j], wl[j + 1]));
+      }
+      df_norm2(ah2, al2);
 #pragma unroll
       for (int k = 0; k + 1 < P; ++k) {
-        tw[k][0] = tw[k + 1][0];
-        tw[k][1] = tw[k + 1][1];
+        twh[k] = twh[k + 1];
+        twl[k] = twl[k + 1];
       }
-      tw[P - 1][0] = df_norm(acc[0]);
-      tw[P - 1][1] = df_norm(acc[1]);
+      twh[P - 1] = ah2;
+      twl[P - 1] = al2;
       if (a >= i0 + WK) {
         // column pass for output row i = a - WK, alpha u, r = f - A u
         const int i = a - WK;
-        DF z[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+        float2 zh2 = make_float2(0.f, 0.f), zl2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int d = 0; d < P; ++d)
-#pragma unroll
-          for (int c = 0; c < 2; ++c) df_fma(z[c], op.sKh[d], op.sKl[d], tw[d][c].h, tw[d][c].l);
+          df_fma2(zh2, zl2, op.kh2[d], op.nkh2[d], op.kl2[d], twh[d], twl[d]);
+        DF z[2] = {DF{zh2.x, zl2.x}, DF{zh2.y, zl2.y}};
         const int slot = (i - alo) % kRsRing;
         const double2 uc = *reinterpret_cast<const double2*>(uring + slot * kRsXW + kRsHalo + 2 * lane);
         const float2 fv = *reinterpret_cast<const float2*>(fring + slot * kRsSW + 2 * lane);
