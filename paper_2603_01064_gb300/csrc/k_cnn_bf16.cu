@@ -92,6 +92,7 @@ struct LayerPack {
 struct FirstW {
   float w[WIDTH * 9];
   float b[WIDTH];
+  float2 w2[9][WIDTH / 2];  // w2[t][p] = (w[2p][t], w[2p + 1][t]): channel pairs
 };
 struct Bf16Pack {
   int layers;
@@ -269,13 +270,27 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   float v[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) v[t] = xs[ry + t / 3][rx + t % 3];
+  // channel pairs as packed two-lane FMAs (fma.rn.f32x2)
+  float2 v2[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) v2[t] = make_float2(v[t], v[t]);
   float a[WIDTH];
 #pragma unroll
-  for (int c = 0; c < WIDTH; ++c) {
-    float acc = sig * fw.b[c];
+  for (int p = 0; p < WIDTH / 2; ++p) {
+    float2 acc = make_float2(sig * fw.b[2 * p], sig * fw.b[2 * p + 1]);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc = fmaf(fw.w[c * 9 + t], v[t], acc);
-    a[c] = fmaxf(acc, 0.f);
+    for (int t = 0; t < 9; ++t) {
+      unsigned long long d;
+      const float2 w = fw.w2[t][p];
+      asm("fma.rn.f32x2 %0, %1, %2, %3;"
+          : "=l"(d)
+          : "l"(*reinterpret_cast<const unsigned long long*>(&w)),
+            "l"(*reinterpret_cast<const unsigned long long*>(&v2[t])),
+            "l"(*reinterpret_cast<const unsigned long long*>(&acc)));
+      acc = *reinterpret_cast<float2*>(&d);
+    }
+    a[2 * p] = fmaxf(acc.x, 0.f);
+    a[2 * p + 1] = fmaxf(acc.y, 0.f);
   }
   store_pixel_planar<SPLIT>(
       a, in ? aout + ((size_t)b * ACHN * plane + (size_t)y * n + x) * 8 : nullptr, plane * 8);
@@ -943,6 +958,9 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
       if (li == 0) {
         std::memcpy(first.w, f.data(), sizeof(first.w));
         std::memcpy(first.b, bb.data(), sizeof(first.b));
+        for (int t = 0; t < 9; ++t)
+          for (int p2 = 0; p2 < WIDTH / 2; ++p2)
+            first.w2[t][p2] = make_float2(f[(2 * p2) * 9 + t], f[(2 * p2 + 1) * 9 + t]);
       }
       wl[li].assign(reinterpret_cast<const unsigned char*>(f.data()),
                     reinterpret_cast<const unsigned char*>(f.data() + f.size()));
