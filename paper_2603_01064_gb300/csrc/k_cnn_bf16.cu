@@ -340,8 +340,8 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
 // the 32 -> 1 output layer's weights w4[c][tap] into 9 per-tap partial sums
 // written as fp32 planes g[tap][pixel] (plane stride gstride).
 template <int SPLIT, int FUSE>
-__device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bias,
-                                             float bscale, __nv_bfloat16* dst, size_t cstride,
+__device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bsc,
+                                             __nv_bfloat16* dst, size_t cstride,
                                              float* gdst, size_t gstride,
                                              const float* __restrict__ w4, bool store) {
   float v[32];
@@ -350,30 +350,47 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
     float w[32];
     tmem_ld32(taddr + 32, w);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] += w[c];
+    for (int c = 0; c < 32; c += 2) {  // packed fp32x2 adds
+      unsigned long long* vp = reinterpret_cast<unsigned long long*>(&v[c]);
+      asm("add.rn.f32x2 %0, %0, %1;" : "+l"(*vp) : "l"(*reinterpret_cast<const unsigned long long*>(&w[c])));
+    }
   }
 #pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = fmaxf(fmaf(bscale, bias[c], v[c]), 0.f);
+  for (int c = 0; c < 32; c += 2) {
+    unsigned long long* vp = reinterpret_cast<unsigned long long*>(&v[c]);
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(*vp) : "l"(*reinterpret_cast<const unsigned long long*>(&bsc[c])));
+    v[c] = fmaxf(v[c], 0.f);
+    v[c + 1] = fmaxf(v[c + 1], 0.f);
+  }
   if (!FUSE) {
     store_pixel_planar<SPLIT>(v, store ? dst : nullptr, cstride);
     return;
   }
   if (!store) return;
   {
-    // w4 is staged in shared memory as [tap][32 channels]
+    // w4 is staged in shared memory as [tap][32 channels]; even and odd
+    // channels accumulate in the two lanes of packed fp32x2 FMAs
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
       const float4* wt = reinterpret_cast<const float4*>(w4 + t * 32);
-      float g = 0.f;
+      unsigned long long g2 = 0ull;  // (0.f, 0.f)
 #pragma unroll
       for (int c4 = 0; c4 < 8; ++c4) {
         const float4 w = wt[c4];
-        g = fmaf(w.x, v[4 * c4], g);
-        g = fmaf(w.y, v[4 * c4 + 1], g);
-        g = fmaf(w.z, v[4 * c4 + 2], g);
-        g = fmaf(w.w, v[4 * c4 + 3], g);
+        const float2 wa = make_float2(w.x, w.y), wb = make_float2(w.z, w.w);
+        const float2 va = make_float2(v[4 * c4], v[4 * c4 + 1]);
+        const float2 vb = make_float2(v[4 * c4 + 2], v[4 * c4 + 3]);
+        asm("fma.rn.f32x2 %0, %1, %2, %0;"
+            : "+l"(g2)
+            : "l"(*reinterpret_cast<const unsigned long long*>(&wa)),
+              "l"(*reinterpret_cast<const unsigned long long*>(&va)));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;"
+            : "+l"(g2)
+            : "l"(*reinterpret_cast<const unsigned long long*>(&wb)),
+              "l"(*reinterpret_cast<const unsigned long long*>(&vb)));
       }
-      gdst[t * gstride] = g;
+      const float2 g = *reinterpret_cast<const float2*>(&g2);
+      gdst[t * gstride] = g.x + g.y;
     }
   }
 }
@@ -401,6 +418,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   __shared__ int abort_flag;
 
   __shared__ __align__(16) float w4s[FUSE ? 9 * 32 : 4];
+  __shared__ __align__(16) float bsc[32];  // the layer's bias times the network scale
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
@@ -408,6 +426,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
     for (int i = tid; i < B_BYTES / 16; i += THREADS) dst[i] = src[i];
     if (FUSE)
       for (int i = tid; i < 9 * 32; i += THREADS) w4s[i] = w4[(i % 32) * 9 + i / 32];
+    if (tid < 32) bsc[tid] = net_scale<SPLIT>(n) * lp.bias[tid];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -471,8 +490,8 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       const bool in = y < n && x < n;
       const size_t pix = (size_t)b * plane + (size_t)y * n + x;
       finish_pixel<SPLIT, FUSE>(
-          tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, lp.bias,
-          net_scale<SPLIT>(n), aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8, plane * 8,
+          tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, bsc,
+          aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8, plane * 8,
           in ? gout + pix : gout, (size_t)nimg * plane, w4s, in);
     }
   };
@@ -565,7 +584,7 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
 }
 
 template <int SPLIT, int STAGES, int FUSE>
-__global__ void __launch_bounds__(WST<SPLIT, FUSE>::value)
+__global__ void __launch_bounds__(WST<SPLIT, FUSE>::value, SPLIT ? 1 : 2)
 k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
             const float* __restrict__ w4, const double* __restrict__ snorm,
@@ -585,6 +604,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   __shared__ int abort_flag;
 
   __shared__ __align__(16) float w4s[FUSE ? 9 * 32 : 4];
+  __shared__ __align__(16) float bsc[32];  // the layer's bias times the network scale
   // one bit per image: active and with a nonzero norm.  Every role walks the
   // tile sequence; reading these from global memory per tile would put an L2
   // round trip between consecutive tiles of the MMA issuer.
@@ -596,6 +616,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     for (int i = tid; i < B_BYTES / 16; i += WST<SPLIT, FUSE>::value) dst[i] = src[i];
     if (FUSE)
       for (int i = tid; i < 9 * 32; i += WST<SPLIT, FUSE>::value) w4s[i] = w4[(i % 32) * 9 + i / 32];
+    if (tid < 32) bsc[tid] = net_scale<SPLIT>(n) * lp.bias[tid];
     if (nimg <= kMaskImgs)
       for (int b0 = warp * 32; b0 < nimg; b0 += WST<SPLIT, FUSE>::value) {  // warp-uniform loop
         const int b = b0 + lane;
@@ -721,8 +742,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value;
         __nv_bfloat16* dst = aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8;
         float* gd = in ? gout + pix : gout;
-        finish_pixel<SPLIT, FUSE>(ta, lp.bias, net_scale<SPLIT>(n), dst, plane * 8, gd,
-                                  (size_t)nimg * plane, w4s, in);
+        finish_pixel<SPLIT, FUSE>(ta, bsc, dst, plane * 8, gd, (size_t)nimg * plane, w4s, in);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
