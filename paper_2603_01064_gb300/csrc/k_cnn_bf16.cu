@@ -341,6 +341,7 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
 // written as fp32 planes g[tap][pixel] (plane stride gstride).
 template <int SPLIT, int FUSE>
 __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __restrict__ bsc,
+                                             const float* __restrict__ bias_g,
                                              __nv_bfloat16* dst, size_t cstride,
                                              float* gdst, size_t gstride,
                                              const float* __restrict__ w4, bool store) {
@@ -355,12 +356,20 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
       asm("add.rn.f32x2 %0, %0, %1;" : "+l"(*vp) : "l"(*reinterpret_cast<const unsigned long long*>(&w[c])));
     }
   }
+  if (SPLIT) {
 #pragma unroll
-  for (int c = 0; c < 32; c += 2) {
-    unsigned long long* vp = reinterpret_cast<unsigned long long*>(&v[c]);
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(*vp) : "l"(*reinterpret_cast<const unsigned long long*>(&bsc[c])));
-    v[c] = fmaxf(v[c], 0.f);
-    v[c + 1] = fmaxf(v[c + 1], 0.f);
+    for (int c = 0; c < 32; c += 2) {
+      unsigned long long* vp = reinterpret_cast<unsigned long long*>(&v[c]);
+      asm("add.rn.f32x2 %0, %0, %1;" : "+l"(*vp) : "l"(*reinterpret_cast<const unsigned long long*>(&bsc[c])));
+      v[c] = fmaxf(v[c], 0.f);
+      v[c + 1] = fmaxf(v[c + 1], 0.f);
+    }
+  } else {
+    // single-bf16 form (network scale 1): the bias from global memory (its
+    // epilogue warps hold two M tiles; loads hoisted from shared memory
+    // would cost the registers of a second CTA per SM)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias_g[c], 0.f);
   }
   if (!FUSE) {
     store_pixel_planar<SPLIT>(v, store ? dst : nullptr, cstride);
@@ -368,8 +377,27 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
   }
   if (!store) return;
   {
-    // w4 is staged in shared memory as [tap][32 channels]; even and odd
-    // channels accumulate in the two lanes of packed fp32x2 FMAs
+    // w4 is staged in shared memory as [tap][32 channels]; in the split
+    // forms even and odd channels accumulate in the two lanes of packed
+    // fp32x2 FMAs (the single-bf16 form keeps scalar FMAs: its epilogue
+    // warps hold two M tiles and run out of registers otherwise)
+    if (!SPLIT) {
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const float4* wt = reinterpret_cast<const float4*>(w4 + t * 32);
+        float g = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < 8; ++c4) {
+          const float4 w = wt[c4];
+          g = fmaf(w.x, v[4 * c4], g);
+          g = fmaf(w.y, v[4 * c4 + 1], g);
+          g = fmaf(w.z, v[4 * c4 + 2], g);
+          g = fmaf(w.w, v[4 * c4 + 3], g);
+        }
+        gdst[t * gstride] = g;
+      }
+      return;
+    }
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
       const float4* wt = reinterpret_cast<const float4*>(w4 + t * 32);
@@ -490,7 +518,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       const bool in = y < n && x < n;
       const size_t pix = (size_t)b * plane + (size_t)y * n + x;
       finish_pixel<SPLIT, FUSE>(
-          tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, bsc,
+          tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, bsc, lp.bias,
           aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8, plane * 8,
           in ? gout + pix : gout, (size_t)nimg * plane, w4s, in);
     }
@@ -742,7 +770,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * NACC + mt * NB<SPLIT>::value;
         __nv_bfloat16* dst = aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8;
         float* gd = in ? gout + pix : gout;
-        finish_pixel<SPLIT, FUSE>(ta, bsc, dst, plane * 8, gd, (size_t)nimg * plane, w4s, in);
+        finish_pixel<SPLIT, FUSE>(ta, bsc, lp.bias, dst, plane * 8, gd, (size_t)nimg * plane, w4s,
+                                  in);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
