@@ -68,7 +68,7 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # DRAM bytes per output pixel of the hidden convs, mean of the two hidden
 # layers, from one ncu capture of this kernel version (128x128, 64 RHS,
 # level 0; summarised under profiles/); None where no capture exists
-HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 177.9}
+HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 178.2}
 MMA_FLOPS_PER_PX = {
     # split form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
     "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
