@@ -836,7 +836,10 @@ const CUtensorMap* act_map(const void* ptr, int n, int nimg, int cw) {
 
 // last layer from the fused partial sums: h[p] = s (b4 + sum_tap g[tap][p + off(tap)])
 // with zero padding outside the image; fp16 split form (g carries the
-// network scale sigma): h = (s / sigma) (sigma b4 + sum_tap g), bscale = sigma
+// network scale sigma): h = (s / sigma) (sigma b4 + sum_tap g), bscale = sigma.
+// Four pixels of a row per thread (n % 4 == 0): each tap reads one aligned
+// 16-byte run of its plane's row and takes the column shifted by -1 / +1 from
+// the neighbouring lanes' runs (zero past the row ends).
 __global__ void __launch_bounds__(256)
 k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ hout,
               float bias0, float bscale, const double* __restrict__ snorm,
@@ -852,21 +855,67 @@ k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ 
   const float sf = s_sh;
   const bool nz = (sbits << 1) != 0;
   const size_t plane = (size_t)n * n, gstride = (size_t)nimg * plane;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)plane; p += gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    if (nz) {
-      const int y = p / n, x = p % n;
-      acc = bscale * bias0;
+  const int quads = (int)(plane / 4);
+  // every lane of a warp takes part in the shuffles: the loop runs to a
+  // multiple of the warp size
+  const int span = (quads + 31) / 32 * 32;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q - (int)(threadIdx.x & 31) < span;
+       q += gridDim.x * blockDim.x) {
+    const bool live = q < quads;
+    const int lane = threadIdx.x & 31;
+    const int p = 4 * (live ? q : 0);
+    const int y = p / n, x = p % n;
+    float acc[4];
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        if (yy >= 0 && yy < n && xx >= 0 && xx < n)
-          acc += g[t * gstride + (size_t)b * plane + (size_t)yy * n + xx];
+    for (int k = 0; k < 4; ++k) acc[k] = bscale * bias0;
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty) {
+      const int yy = y + ty - 1;
+      const bool rin = live && yy >= 0 && yy < n;
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx) {
+        const float* grow = g + (ty * 3 + tx) * gstride + (size_t)b * plane + (size_t)yy * n;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rin) v = *reinterpret_cast<const float4*>(grow + x);
+        if (tx == 1) {
+          acc[0] += v.x;
+          acc[1] += v.y;
+          acc[2] += v.z;
+          acc[3] += v.w;
+        } else if (tx == 0) {
+          // columns x - 1 .. x + 2: x - 1 is the left lane's last value (read
+          // directly by lane 0, whose left quad belongs to another warp)
+          float l = __shfl_up_sync(0xffffffffu, v.w, 1);
+          if (lane == 0) l = (rin && x > 0) ? grow[x - 1] : 0.f;
+          else if (x == 0) l = 0.f;
+          acc[0] += l;
+          acc[1] += v.x;
+          acc[2] += v.y;
+          acc[3] += v.z;
+        } else {
+          // columns x + 1 .. x + 4: x + 4 is the right lane's first value
+          float r = __shfl_down_sync(0xffffffffu, v.x, 1);
+          if (lane == 31) r = (rin && x + 4 < n) ? grow[x + 4] : 0.f;
+          else if (x + 4 >= n) r = 0.f;
+          acc[0] += v.y;
+          acc[1] += v.z;
+          acc[2] += v.w;
+          acc[3] += r;
+        }
       }
-      acc *= sf;
-      acc *= 1.f / bscale;  // a power of two: exact
     }
-    hout[(size_t)b * plane + p] = acc;
+    if (live) {
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (nz) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[k] *= sf;
+          acc[k] *= 1.f / bscale;  // a power of two: exact
+        }
+        o = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      }
+      *reinterpret_cast<float4*>(hout + (size_t)b * plane + p) = o;
+    }
   }
 }
 
@@ -972,7 +1021,7 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   float bias0 = 0.f;
   if (L4.bias_host_valid) bias0 = L4.bias0;
   pi_ = log.begin(K_CNN_LAST, st);
-  k_last_gather<<<dim3(ceil_div(n * n, 256) < 64 ? ceil_div(n * n, 256) : 64, B), 256, 0, st>>>(
+  k_last_gather<<<dim3(ceil_div(n * n / 4, 256) < 64 ? ceil_div(n * n / 4, 256) : 64, B), 256, 0, st>>>(
       n, map_imgs, reinterpret_cast<const float*>(nxt), h, bias0, net_scale<SPLIT>(n), s, active);
   log.end(pi_, st, units);
 }
