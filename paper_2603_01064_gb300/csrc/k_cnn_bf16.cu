@@ -94,11 +94,18 @@ struct FirstW {
   float b[WIDTH];
   float2 w2[9][WIDTH / 2];  // w2[t][p] = (w[2p][t], w[2p + 1][t]): channel pairs
 };
+// the 32 -> 1 output layer's weights as channel pairs per tap, passed by
+// value to the last hidden layer (its epilogue's packed FMAs read them from
+// the constant bank): w[t][p] = (w4[2p][t], w4[2p + 1][t])
+struct OutW {
+  float2 w[9][WIDTH / 2];
+};
 struct Bf16Pack {
   int layers;
   int split;
   LayerPack l[8];
   FirstW first;  // host copy of layer 0
+  OutW last;     // host copy of the output layer
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -344,7 +351,8 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
                                              const float* __restrict__ bias_g,
                                              __nv_bfloat16* dst, size_t cstride,
                                              float* gdst, size_t gstride,
-                                             const float* __restrict__ w4, bool store) {
+                                             const float* __restrict__ w4, const OutW& ow,
+                                             bool store) {
   float v[32];
   tmem_ld32(taddr, v);
   if (SPLIT) {
@@ -400,12 +408,10 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
     }
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const float4* wt = reinterpret_cast<const float4*>(w4 + t * 32);
       unsigned long long g2 = 0ull;  // (0.f, 0.f)
 #pragma unroll
       for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 w = wt[c4];
-        const float2 wa = make_float2(w.x, w.y), wb = make_float2(w.z, w.w);
+        const float2 wa = ow.w[t][2 * c4], wb = ow.w[t][2 * c4 + 1];
         const float2 va = make_float2(v[4 * c4], v[4 * c4 + 1]);
         const float2 vb = make_float2(v[4 * c4 + 2], v[4 * c4 + 3]);
         asm("fma.rn.f32x2 %0, %1, %2, %0;"
@@ -430,8 +436,9 @@ template <int SPLIT, int FUSE>
 __global__ void __launch_bounds__(THREADS)
 k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
-            const float* __restrict__ w4, const double* __restrict__ snorm,
-            const int* __restrict__ active, int* __restrict__ err, int nbuf) {
+            const float* __restrict__ w4, const __grid_constant__ OutW ow,
+            const double* __restrict__ snorm, const int* __restrict__ active,
+            int* __restrict__ err, int nbuf) {
   constexpr int ACH = SPLIT ? 8 : 4;  // 8-channel chunks per staged pixel
   constexpr int ABUF = ACH * CH_BYTES;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
@@ -520,7 +527,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
       finish_pixel<SPLIT, FUSE>(
           tmem + ((uint32_t)(warp * 32) << 16) + acc * NACC + mt * NB<SPLIT>::value, bsc, lp.bias,
           aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8, plane * 8,
-          in ? gout + pix : gout, (size_t)nimg * plane, w4s, in);
+          in ? gout + pix : gout, (size_t)nimg * plane, w4s, ow, in);
     }
   };
 
@@ -615,8 +622,9 @@ template <int SPLIT, int STAGES, int FUSE>
 __global__ void __launch_bounds__(WST<SPLIT, FUSE>::value, SPLIT ? 1 : 2)
 k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
-            const float* __restrict__ w4, const double* __restrict__ snorm,
-            const int* __restrict__ active, int* __restrict__ err) {
+            const float* __restrict__ w4, const __grid_constant__ OutW ow,
+            const double* __restrict__ snorm, const int* __restrict__ active,
+            int* __restrict__ err) {
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int SBYTES = ACH * CH_PITCH;           // one stage
   constexpr uint32_t TX = ACH * RH * RW * 16;      // bytes the copies of one stage write
@@ -771,7 +779,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         __nv_bfloat16* dst = aout + ((size_t)b * ACH * plane + (size_t)y * n + x) * 8;
         float* gd = in ? gout + pix : gout;
         finish_pixel<SPLIT, FUSE>(ta, bsc, lp.bias, dst, plane * 8, gd, (size_t)nimg * plane, w4s,
-                                  in);
+                                  ow, in);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -953,8 +961,9 @@ int num_sms() {
 
 template <int SPLIT, int FUSE>
 void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv_bfloat16* aout,
-                   float* gout, const LayerPack& lp, const float* w4, const double* s,
-                   const int* active, int* err, cudaStream_t st, LaunchLog& log) {
+                   float* gout, const LayerPack& lp, const float* w4, const OutW& ow,
+                   const double* s, const int* active, int* err, cudaStream_t st,
+                   LaunchLog& log) {
   constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
   const CUtensorMap* map = n >= 32 ? act_map(ain, n, map_imgs, CWs) : nullptr;
   if (map) {
@@ -969,7 +978,7 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
     if (grid < 1) grid = 1;
     cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int pi_ = log.begin(K_CNN_HIDDEN, st);
-    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WST<SPLIT, FUSE>::value, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, s, active, err);
+    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WST<SPLIT, FUSE>::value, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, ow, s, active, err);
     log.end(pi_, st, (double)n * n * log.active_hint);
     return;
   }
@@ -987,8 +996,8 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
   if (grid < 1) grid = 1;
   cudaFuncSetAttribute(k_hidden_tc<SPLIT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int pi_ = log.begin(K_CNN_HIDDEN, st);
-  k_hidden_tc<SPLIT, FUSE><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, gout, lp, w4, s, active, err,
-                                                           nbuf);
+  k_hidden_tc<SPLIT, FUSE><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, gout, lp, w4, ow, s, active,
+                                                           err, nbuf);
   log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
@@ -1009,13 +1018,14 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   const LayerPack& L4 = P.l[layers - 1];
   for (int li = 1; li < layers - 1; ++li) {
     if (li < layers - 2) {
-      launch_hidden<SPLIT, 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[li], nullptr, s, active, err, st, log);
+      launch_hidden<SPLIT, 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[li], nullptr, P.last, s, active, err,
+                              st, log);
       __nv_bfloat16* t = cur;
       cur = nxt;
       nxt = t;
     } else {
       launch_hidden<SPLIT, 1>(n, B, map_imgs, cur, nxt, reinterpret_cast<float*>(nxt), P.l[li],
-                              L4.wf, s, active, err, st, log);
+                              L4.wf, P.last, s, active, err, st, log);
     }
   }
   float bias0 = 0.f;
@@ -1041,6 +1051,7 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
   std::vector<std::vector<unsigned char>> wl(layers), bl(layers);
   std::vector<int> has_lo(layers, 0);
   FirstW first{};
+  OutW last{};
   for (int li = 0; li < layers; ++li) {
     const int cin = li == 0 ? 1 : WIDTH, cout = li == layers - 1 ? 1 : WIDTH;
     const double* w = W[li];
@@ -1053,6 +1064,10 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
       std::vector<float> f(WIDTH * 9, 0.f);
       for (int c = 0; c < WIDTH; ++c)
         for (int t = 0; t < 9; ++t) f[c * 9 + t] = (float)w[c * 9 + t];
+      if (li == layers - 1)
+        for (int t = 0; t < 9; ++t)
+          for (int p2 = 0; p2 < WIDTH / 2; ++p2)
+            last.w[t][p2] = make_float2(f[(2 * p2) * 9 + t], f[(2 * p2 + 1) * 9 + t]);
       if (li == 0) {
         std::memcpy(first.w, f.data(), sizeof(first.w));
         std::memcpy(first.b, bb.data(), sizeof(first.b));
@@ -1107,6 +1122,7 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
   hdr.layers = layers;
   hdr.split = split;
   hdr.first = first;
+  hdr.last = last;
   for (int li = 0; li < layers; ++li) {
     std::memcpy(host.data() + woff[li], wl[li].data(), wl[li].size());
     std::memcpy(host.data() + boff[li], bl[li].data(), bl[li].size());
