@@ -68,7 +68,7 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # DRAM bytes per output pixel of the hidden convs, mean of the two hidden
 # layers, from one ncu capture of this kernel version (128x128, 64 RHS,
 # level 0; summarised under profiles/); None where no capture exists
-HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 178.2}
+HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 109.9}
 MMA_FLOPS_PER_PX = {
     # split form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
     "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
@@ -447,6 +447,9 @@ def run_ours(args, wl, world, rank, local):
     fno = None
     if not args.no_fno:
         fno = fno_leg(ctx, wl, B, taps)
+    hbm = None
+    if not args.no_hbm_apply:
+        hbm = hbm_apply_leg(ctx, W, flush, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -469,7 +472,7 @@ def run_ours(args, wl, world, rank, local):
                 "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
                 "compare": compare, "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "serving": serving, "fno_smoother": fno}
+                "serving": serving, "fno_smoother": fno, "hbm_apply": hbm}
         print(json.dumps(line), flush=True)
 
 
@@ -522,6 +525,61 @@ def fno_leg(ctx, wl, B, taps):
             "peak_source": "152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz (derived)"}
 
 
+HBM_APPLY = dict(reps=5, ops=[  # (n, levels, sigma px, alpha, weights, batch)
+    (128, 5, 2.0, 1e-2, "c2_2d_n128_s2_a1e-2.npz", 2048),
+    (512, 7, 4.0, 1e-2, "c3_2d_n512_s4_a1e-2.npz", 128)])
+
+
+def hbm_apply_leg(ctx, W128, flush, stream):
+    """The fine-level operator kernels on vectors larger than L2 (134 MB per
+    fp32 vector; L2 written over before every launch): the residual
+    r = y - A x (12 B per grid point: x, y in, r out), the fused residual +
+    full-weighting restriction (9 B: x, y in, a quarter-size vector out) and
+    the prolongation + correction x += P e (9 B: x in and out, e a quarter).
+    CUDA events around each launch on the library's stream; GB/s from the
+    algorithmic bytes, against the measured HBM copy bandwidth."""
+    import torch
+    import paper_2603_01064_gb300 as nmg
+    peaks, src = load_peaks()
+    out = []
+    for n, L, sg, al, wname, B in HBM_APPLY["ops"]:
+        Wx = W128 if n == 128 else nmg.load_weights(os.path.join(WEIGHTS, wname))
+        G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=al, taps=I.gaussian_taps(sg),
+                          precision="fp32", weights=Wx)
+        G.autotune(B)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        x = torch.randn((B, n, n), device="cuda", generator=g)
+        y = torch.randn((B, n, n), device="cuda", generator=g)
+        r = torch.empty_like(x)
+        yc = torch.empty((B, n // 2, n // 2), device="cuda")
+        ops = {"residual": (lambda: G.residual(0, x, y, r), 12),
+               "residual_restrict": (lambda: G.residual_restrict(0, x, y, yc), 9),
+               "prolong_correct": (lambda: G.prolong_correct(0, yc, r), 9)}
+        row = {"operator": f"{n}x{n} sigma {sg:g} px alpha {al:g}", "batch": B,
+               "vector_mb": B * n * n * 4 / 1e6}
+        for name, (fn, bpp) in ops.items():
+            fn()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for k in range(HBM_APPLY["reps"]):
+                flush.fill_(k & 0xFF)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = tot / HBM_APPLY["reps"]
+            gbs = bpp * B * n * n / (ms / 1e3) / 1e9
+            row[name] = {"ms": ms, "bytes_per_unit": bpp, "achieved_gbs": gbs,
+                         "hbm_frac": gbs / peaks["hbm_gbs"]}
+        G.close()
+        del x, y, r, yc
+        out.append(row)
+    return {"peak_gbs": peaks["hbm_gbs"], "peak_source": src, "results": out}
+
+
 def serving_leg(ctx, rank):
     """Requests drawn uniformly from two resident operators (128x128 sigma 2
     px and 512x512 sigma 4 px, both alpha 1e-2, bf16 split refinement),
@@ -565,6 +623,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-fno", action="store_true", help="skip the FNO smoother timing")
+    ap.add_argument("--no-hbm-apply", action="store_true",
+                    help="skip the out-of-L2 operator apply timing")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured iterations "
                          "(profiler launch lists)")

@@ -250,16 +250,17 @@ k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ 
   constexpr int ACHN = SPLIT ? 8 : 4;  // chunk planes per image
   const int b = blockIdx.y;
   if (!active[b]) return;
-  // ||b|| = 0 (tested on the bits: fp64 arithmetic runs at 1/64 of the fp32
-  // rate, so one thread forms sigma / ||b|| for the block): h = 0 is written
-  // by the last layer
+  // ||b|| = 0 (tested on the bits): h = 0 is written by the last layer.
+  // sigma / ||b|| is formed in fp32 from ||b|| rounded to fp32, once per
+  // block (fp64 arithmetic runs at 1/64 of the fp32 rate); the first hidden
+  // layer's fused form computes the same value
   const long long sbits = __double_as_longlong(snorm[b]);
   if ((sbits << 1) == 0) return;
   __shared__ float xs[RH][RW + 1];
   __shared__ float inv_s;
   const int tid = threadIdx.x;
   const float sig = net_scale<SPLIT>(n);
-  if (tid == 0) inv_s = (float)((double)sig / __longlong_as_double(sbits));
+  if (tid == 0) inv_s = __fdiv_rn(sig, (float)__longlong_as_double(sbits));
   const int y0 = (blockIdx.x / tiles_x) * TILE, x0 = (blockIdx.x % tiles_x) * TILE;
   const size_t plane = (size_t)n * n;
   __syncthreads();
@@ -596,9 +597,15 @@ template <int SPLIT, int FUSE> struct EPI { static constexpr int value = SPLIT ?
 // MMA issuers: one per M tile in the split forms (a single issuing thread
 // does not keep the tensor pipe fed with the split form's 72 MMAs per tile)
 template <int SPLIT> struct ISS { static constexpr int value = SPLIT ? NT : 1; };
-template <int SPLIT, int FUSE> struct WST {
-  static constexpr int value = 32 * (1 + ISS<SPLIT>::value + EPI<SPLIT, FUSE>::value);
+// warps that compute the first layer into the operand stages (FIRST = 1)
+constexpr int kFirstWarps = 4;
+template <int SPLIT, int FUSE, int FIRST = 0> struct WST {
+  static constexpr int value =
+      32 * (1 + ISS<SPLIT>::value + EPI<SPLIT, FUSE>::value + (FIRST ? kFirstWarps : 0));
 };
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 constexpr int kMaskImgs = 32768;  // images whose validity bits a block keeps in shared memory
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -618,13 +625,24 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-template <int SPLIT, int STAGES, int FUSE>
-__global__ void __launch_bounds__(WST<SPLIT, FUSE>::value, SPLIT ? 1 : 2)
+// FIRST = 1 (first hidden layer of the split forms): the operand stages are
+// not copied from a first-layer output in global memory but computed in
+// place by kFirstWarps extra warps from the level's input b: the 20 x 20
+// input window of a tile (zero outside the image), then the 1 -> 32 layer
+// a = ReLU(sigma b1 + W1 * (sigma b / s)) on the 18 x 18 pixels of the
+// staged tile (zero outside the image, as the copy engine's fill), split
+// into hi + lo 16-bit values in the stage's chunk-planar layout.  The 128
+// bytes per pixel of the first layer's output never reach global memory.
+template <int SPLIT, int STAGES, int FUSE, int FIRST = 0>
+__global__ void __launch_bounds__(WST<SPLIT, FUSE, FIRST>::value, SPLIT ? 1 : 2)
 k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
             const float* __restrict__ w4, const __grid_constant__ OutW ow,
             const double* __restrict__ snorm, const int* __restrict__ active,
-            int* __restrict__ err) {
+            int* __restrict__ err, const float* __restrict__ bsrc,
+            const __grid_constant__ FirstW fw) {
+  constexpr int NTHR = WST<SPLIT, FUSE, FIRST>::value;
+  static_assert(!FIRST || (SPLIT && !FUSE), "the fused first layer serves the split forms' first hidden layer");
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int SBYTES = ACH * CH_PITCH;           // one stage
   constexpr uint32_t TX = ACH * RH * RW * 16;      // bytes the copies of one stage write
@@ -649,12 +667,12 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   {
     const uint4* src = reinterpret_cast<const uint4*>(lp.w);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
-    for (int i = tid; i < B_BYTES / 16; i += WST<SPLIT, FUSE>::value) dst[i] = src[i];
+    for (int i = tid; i < B_BYTES / 16; i += NTHR) dst[i] = src[i];
     if (FUSE)
-      for (int i = tid; i < 9 * 32; i += WST<SPLIT, FUSE>::value) w4s[i] = w4[(i % 32) * 9 + i / 32];
+      for (int i = tid; i < 9 * 32; i += NTHR) w4s[i] = w4[(i % 32) * 9 + i / 32];
     if (tid < 32) bsc[tid] = net_scale<SPLIT>(n) * lp.bias[tid];
     if (nimg <= kMaskImgs)
-      for (int b0 = warp * 32; b0 < nimg; b0 += WST<SPLIT, FUSE>::value) {  // warp-uniform loop
+      for (int b0 = warp * 32; b0 < nimg; b0 += NTHR) {  // warp-uniform loop
         const int b = b0 + lane;
         const unsigned m = __ballot_sync(0xffffffffu, b < nimg && active[b] != 0 && snorm[b] != 0.0);
         if (lane == 0) vmask[b0 >> 5] = m;
@@ -668,7 +686,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   }
   if (tid == 32) {
     for (int i = 0; i < STAGES; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])),
+                   "r"(FIRST ? 32 * kFirstWarps : 1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])),
                    "r"(ISS<SPLIT>::value));
     }
@@ -719,9 +738,97 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     }
   };
 
-  if (warp == 0) {
+  constexpr int FW0 = 1 + ISS<SPLIT>::value + EPI<SPLIT, FUSE>::value;  // first producer warp
+  if (FIRST && warp >= FW0) {
+    // ---- first-layer producers (FIRST = 1)
+    constexpr int PT = 32 * kFirstWarps;
+    constexpr int XW = TILE + 4;  // input window side
+    constexpr int XPT = (XW * XW + PT - 1) / PT;  // window values per thread
+    __shared__ float xs[2][XW * XW];
+    __shared__ int stop_sh[2];
+    const int pt = tid - 32 * FW0;
+    const float sig = net_scale<SPLIT>(n);
+    // the next tile's input window and ||b|| are loaded into registers one
+    // tile ahead, so their latency hides behind the current tile's layer
+    float pre[XPT];
+    float pre_s = 1.f;
+    auto fetch = [&](int t) {
+      const int b = t / per_img, tt = t - b * per_img;
+      const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
+      const float* bb = bsrc + (size_t)b * plane;
+#pragma unroll
+      for (int j = 0; j < XPT; ++j) {
+        const int k = pt + j * PT;
+        const int y = y0 + k / XW - 2, x = x0 + k % XW - 2;
+        pre[j] = (k < XW * XW && y >= 0 && y < n && x >= 0 && x < n) ? bb[(size_t)y * n + x] : 0.f;
+      }
+      pre_s = (float)snorm[b];
+    };
+    int i = 0;
+    int t = first();
+    if (t < total) fetch(t);
+    for (; t < total; ++i) {
+      const int s = i % STAGES, xb = i & 1;
+      const int b = t / per_img, tt = t - b * per_img;
+      const int y0 = (tt / tiles_x) * TILE, x0 = (tt % tiles_x) * TILE;
+#pragma unroll
+      for (int j = 0; j < XPT; ++j)
+        if (pt + j * PT < XW * XW) xs[xb][pt + j * PT] = pre[j];
+      // sigma / ||b|| in fp32 (fp64 arithmetic runs at 1/64 of the fp32
+      // rate); the same value k_first_simt forms
+      const float inv = __fdiv_rn(sig, pre_s);
+      const int tn = advance(t);
+      if (tn < total) fetch(tn);
+      // one thread waits for the stage to be free; the decision to stop
+      // reaches the other producers through the barrier
+      if (pt == 0)
+        stop_sh[xb] = (i >= STAGES && !wait(&empty[s], (uint32_t)((i / STAGES - 1) & 1))) ? 1 : 0;
+      named_bar_sync(1, PT);
+      if (stop_sh[xb]) break;
+      unsigned char* stage = smem + s * SBYTES;
+      for (int p = pt; p < RH * RW; p += PT) {
+        const int ry = p / RW, rx = p % RW;
+        const int y = y0 + ry - 1, x = x0 + rx - 1;
+        float a[WIDTH];
+        if (y >= 0 && y < n && x >= 0 && x < n) {
+          float2 v2[9];
+#pragma unroll
+          for (int tp = 0; tp < 9; ++tp) {
+            const float v = xs[xb][(ry + tp / 3) * XW + rx + tp % 3] * inv;
+            v2[tp] = make_float2(v, v);
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < WIDTH / 2; ++q2) {
+            float2 acc = make_float2(sig * fw.b[2 * q2], sig * fw.b[2 * q2 + 1]);
+#pragma unroll
+            for (int tp = 0; tp < 9; ++tp) {
+              unsigned long long d;
+              const float2 w = fw.w2[tp][q2];
+              asm("fma.rn.f32x2 %0, %1, %2, %3;"
+                  : "=l"(d)
+                  : "l"(*reinterpret_cast<const unsigned long long*>(&w)),
+                    "l"(*reinterpret_cast<const unsigned long long*>(&v2[tp])),
+                    "l"(*reinterpret_cast<const unsigned long long*>(&acc)));
+              acc = *reinterpret_cast<float2*>(&d);
+            }
+            a[2 * q2] = fmaxf(acc.x, 0.f);
+            a[2 * q2 + 1] = fmaxf(acc.y, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < WIDTH; ++c) a[c] = 0.f;
+        }
+        store_pixel_planar<SPLIT>(a, reinterpret_cast<__nv_bfloat16*>(stage + p * 16),
+                                  CH_PITCH / 2);
+      }
+      // generic-proxy writes made visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full[s]));
+      t = tn;
+    }
+  } else if (warp == 0) {
     // ---- TMA producer
-    if (lane == 0) {
+    if (lane == 0 && !FIRST) {
       int i = 0;
       for (int t = first(); t < total; t = advance(t), ++i) {
         const int s = i % STAGES;
@@ -959,11 +1066,13 @@ int num_sms() {
   return g_num_sms;
 }
 
-template <int SPLIT, int FUSE>
+// FIRST = 1: the first layer is computed inside the kernel from bsrc / fw
+// (persistent path only; ain then only names the tensor map's buffer)
+template <int SPLIT, int FUSE, int FIRST = 0>
 void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv_bfloat16* aout,
                    float* gout, const LayerPack& lp, const float* w4, const OutW& ow,
                    const double* s, const int* active, int* err, cudaStream_t st,
-                   LaunchLog& log) {
+                   LaunchLog& log, const float* bsrc = nullptr, const FirstW* fw = nullptr) {
   constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
   const CUtensorMap* map = n >= 32 ? act_map(ain, n, map_imgs, CWs) : nullptr;
   if (map) {
@@ -976,12 +1085,15 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
     long long grid = (long long)num_sms() * (SPLIT ? 1 : 2);
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
-    cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_hidden_ws<SPLIT, STAGES, FUSE, FIRST>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int pi_ = log.begin(K_CNN_HIDDEN, st);
-    k_hidden_ws<SPLIT, STAGES, FUSE><<<(int)grid, WST<SPLIT, FUSE>::value, sm, st>>>(*map, n, map_imgs, aout, gout, lp, w4, ow, s, active, err);
+    k_hidden_ws<SPLIT, STAGES, FUSE, FIRST><<<(int)grid, WST<SPLIT, FUSE, FIRST>::value, sm, st>>>(
+        *map, n, map_imgs, aout, gout, lp, w4, ow, s, active, err, bsrc, fw ? *fw : FirstW{});
     log.end(pi_, st, (double)n * n * log.active_hint);
     return;
   }
+  if (FIRST) return;  // not reached: run_layers takes FIRST only where a map exists
   constexpr int ACH = SPLIT ? 8 : 4;
   constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
   const int tiles_x = (n + TILE - 1) / TILE;
@@ -1008,15 +1120,28 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   const int tiles_x = (n + TILE - 1) / TILE;
   dim3 grid(tiles_x * tiles_x, B);
   const double units = (double)n * n * log.active_hint;
-  int pi_ = log.begin(K_CNN_FIRST, st);
-  k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.first, s, active, tiles_x);
-  log.end(pi_, st, units);
+  constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
+  // split forms with a first hidden layer that is not the last one, on the
+  // persistent path: the first layer runs inside that layer's kernel
+  const bool fused_first = SPLIT && layers >= 4 && n >= 32 && act_map(a0, n, map_imgs, CWs);
   __nv_bfloat16* cur = a0;
   __nv_bfloat16* nxt = a1;
+  int li0 = 1;
+  if (fused_first) {
+    launch_hidden<SPLIT, 0, SPLIT ? 1 : 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[1], nullptr, P.last,
+                                          s, active, err, st, log, b, &P.first);
+    cur = a1;
+    nxt = a0;
+    li0 = 2;
+  } else {
+    int pi_ = log.begin(K_CNN_FIRST, st);
+    k_first_simt<SPLIT><<<grid, 256, 0, st>>>(n, b, a0, P.first, s, active, tiles_x);
+    log.end(pi_, st, units);
+  }
   // hidden layers; the last one also applies the 32 -> 1 output layer's
   // weights in its epilogue and writes 9 per-tap partial-sum planes
   const LayerPack& L4 = P.l[layers - 1];
-  for (int li = 1; li < layers - 1; ++li) {
+  for (int li = li0; li < layers - 1; ++li) {
     if (li < layers - 2) {
       launch_hidden<SPLIT, 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[li], nullptr, P.last, s, active, err,
                               st, log);
@@ -1030,7 +1155,7 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   }
   float bias0 = 0.f;
   if (L4.bias_host_valid) bias0 = L4.bias0;
-  pi_ = log.begin(K_CNN_LAST, st);
+  int pi_ = log.begin(K_CNN_LAST, st);
   k_last_gather<<<dim3(ceil_div(n * n / 4, 256) < 64 ? ceil_div(n * n / 4, 256) : 64, B), 256, 0, st>>>(
       n, map_imgs, reinterpret_cast<const float*>(nxt), h, bias0, net_scale<SPLIT>(n), s, active);
   log.end(pi_, st, units);
