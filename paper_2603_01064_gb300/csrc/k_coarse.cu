@@ -119,54 +119,42 @@ k_coarse_apply(int nc, const double* __restrict__ Li, const double* __restrict__
   for (int i = threadIdx.x; i < nc; i += blockDim.x) x[(size_t)b * nc + i] = (T)v[i];
 }
 
-// nc <= 64: one warp (and block) per right-hand side, lane i owning rows i
-// and i + 32, two accumulation chains per row;
+// nc <= 64: one block of two warps per right-hand side, thread i owning
+// row i, two accumulation chains per row (fp64 runs at 1/64 of the fp32 rate
+// on this GPU: two warps per right-hand side spread the multiply-adds over
+// twice the SM sub-partitions of one warp owning two rows per lane);
 // both products read the stored transposes row by row, so the 32 lanes load
 // consecutive entries: z = L^{-1} v as z_i = sum_j (L^{-T})[j][i] v_j and
 // x = L^{-T} z as x_i = sum_j (L^{-1})[j][i] z_j
 template <typename T>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(64)
 k_coarse_apply_warp(int nc, const double* __restrict__ Li, const double* __restrict__ LiT, int B,
                     const T* __restrict__ y, T* __restrict__ x, const int* __restrict__ active) {
   __shared__ double v[64];
-  const int lane = threadIdx.x;
+  const int t = threadIdx.x;
   const int b = blockIdx.x;
   if (!active[b]) return;
-  for (int i = lane; i < nc; i += 32) v[i] = (double)y[(size_t)b * nc + i];
-  __syncwarp();
-  const bool r0 = lane < nc, r1 = lane + 32 < nc;
-  const int c0 = r0 ? lane : 0, c1 = r1 ? lane + 32 : 0;  // in-bounds columns
-  double z0a = 0.0, z0b = 0.0, z1a = 0.0, z1b = 0.0;
+  if (t < nc) v[t] = (double)y[(size_t)b * nc + t];
+  __syncthreads();
+  const bool in = t < nc;
+  const int c = in ? t : 0;  // in-bounds column
+  double za = 0.0, zb = 0.0;
   int j = 0;
   for (; j + 1 < nc; j += 2) {
-    const double va = v[j], vb = v[j + 1];
-    z0a = fma(LiT[(size_t)j * nc + c0], va, z0a);
-    z0b = fma(LiT[(size_t)(j + 1) * nc + c0], vb, z0b);
-    z1a = fma(LiT[(size_t)j * nc + c1], va, z1a);
-    z1b = fma(LiT[(size_t)(j + 1) * nc + c1], vb, z1b);
+    za = fma(LiT[(size_t)j * nc + c], v[j], za);
+    zb = fma(LiT[(size_t)(j + 1) * nc + c], v[j + 1], zb);
   }
-  if (j < nc) {
-    z0a = fma(LiT[(size_t)j * nc + c0], v[j], z0a);
-    z1a = fma(LiT[(size_t)j * nc + c1], v[j], z1a);
-  }
-  __syncwarp();
-  if (r0) v[lane] = z0a + z0b;
-  if (r1) v[lane + 32] = z1a + z1b;
-  __syncwarp();
-  double x0a = 0.0, x0b = 0.0, x1a = 0.0, x1b = 0.0;
+  if (j < nc) za = fma(LiT[(size_t)j * nc + c], v[j], za);
+  __syncthreads();
+  if (in) v[t] = za + zb;
+  __syncthreads();
+  double xa = 0.0, xb = 0.0;
   for (j = 0; j + 1 < nc; j += 2) {
-    const double za = v[j], zb = v[j + 1];
-    x0a = fma(Li[(size_t)j * nc + c0], za, x0a);
-    x0b = fma(Li[(size_t)(j + 1) * nc + c0], zb, x0b);
-    x1a = fma(Li[(size_t)j * nc + c1], za, x1a);
-    x1b = fma(Li[(size_t)(j + 1) * nc + c1], zb, x1b);
+    xa = fma(Li[(size_t)j * nc + c], v[j], xa);
+    xb = fma(Li[(size_t)(j + 1) * nc + c], v[j + 1], xb);
   }
-  if (j < nc) {
-    x0a = fma(Li[(size_t)j * nc + c0], v[j], x0a);
-    x1a = fma(Li[(size_t)j * nc + c1], v[j], x1a);
-  }
-  if (r0) x[(size_t)b * nc + lane] = (T)(x0a + x0b);
-  if (r1) x[(size_t)b * nc + lane + 32] = (T)(x1a + x1b);
+  if (j < nc) xa = fma(Li[(size_t)j * nc + c], v[j], xa);
+  if (in) x[(size_t)b * nc + t] = (T)(xa + xb);
 }
 
 }  // namespace
@@ -190,7 +178,7 @@ void launch_coarse_solve(int nc, const double* Li, const double* LiT, int B, con
                          const int* active, cudaStream_t st, LaunchLog& log) {
   int pi_ = log.begin(K_COARSE, st);
   if (nc <= 64) {
-    k_coarse_apply_warp<T><<<B, 32, 0, st>>>(nc, Li, LiT, B, y, x, active);
+    k_coarse_apply_warp<T><<<B, 64, 0, st>>>(nc, Li, LiT, B, y, x, active);
   } else {
     k_coarse_apply<T><<<B, 256, 2 * nc * sizeof(double), st>>>(nc, Li, LiT, y, x, active);
   }
