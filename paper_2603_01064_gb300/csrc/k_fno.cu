@@ -33,6 +33,17 @@ struct C2 {
   T x, y;
 };
 
+// acc += w * v, both lanes of the register pairs (fma.rn.f32x2)
+__device__ __forceinline__ void fma2_acc(float2& acc, float2 w, float2 v) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&w)),
+        "l"(*reinterpret_cast<const unsigned long long*>(&v)),
+        "l"(*reinterpret_cast<const unsigned long long*>(&acc)));
+  acc = *reinterpret_cast<const float2*>(&d);
+}
+
 template <typename T>
 __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
   return C2<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
@@ -191,6 +202,11 @@ k_fno_wconv(int n, int m, int c, int ks, const T* __restrict__ zin, const C2<T>*
   T acc0[FOC], acc1[FOC];
 #pragma unroll
   for (int q = 0; q < FOC; ++q) acc0[q] = acc1[q] = T(0);
+  // fp32: output-channel pairs accumulate in packed two-lane FMAs
+  // (fma.rn.f32x2), the pixel value duplicated into both lanes
+  float2 p0[FOC / 2], p1[FOC / 2];
+#pragma unroll
+  for (int q = 0; q < FOC / 2; ++q) p0[q] = p1[q] = make_float2(0.f, 0.f);
   for (int ch0 = 0; ch0 < c; ch0 += CC) {
     __syncthreads();  // the previous pass is done with xs and ws
     for (int i = threadIdx.x; i < CC * SH * SW; i += blockDim.x) {
@@ -205,20 +221,57 @@ k_fno_wconv(int n, int m, int c, int ks, const T* __restrict__ zin, const C2<T>*
       ws[i] = in ? W[((size_t)(o0 + q) * c + ch0 + cc) * KK + t] : T(0);
     }
     __syncthreads();
-    for (int cc = 0; cc < CC; ++cc) {
-      const T* xc = xs + (size_t)cc * SH * SW + ty * SW + tx;
-      const T* wc = ws + (size_t)cc * KK * FOC;
-      for (int dy = 0; dy < ks; ++dy)
-        for (int dx = 0; dx < ks; ++dx) {
-          const T v0 = xc[dy * SW + dx], v1 = xc[(dy + 16) * SW + dx];
-          const T* wt = wc + (dy * ks + dx) * FOC;
+    if constexpr (sizeof(T) == 4) {
+      for (int cc = 0; cc < CC; ++cc) {
+        const float* xc = reinterpret_cast<const float*>(xs) + (size_t)cc * SH * SW + ty * SW + tx;
+        const float* wc = reinterpret_cast<const float*>(ws) + (size_t)cc * KK * FOC;
+        auto tap = [&](int dy, int dx) {
+          const float v0 = xc[dy * SW + dx], v1 = xc[(dy + 16) * SW + dx];
+          const float2 d0 = make_float2(v0, v0), d1 = make_float2(v1, v1);
+          const float4* wt = reinterpret_cast<const float4*>(wc + (dy * ks + dx) * FOC);
 #pragma unroll
-          for (int q = 0; q < FOC; ++q) {
-            const T wq = wt[q];
-            acc0[q] += wq * v0;
-            acc1[q] += wq * v1;
+          for (int q4 = 0; q4 < FOC / 4; ++q4) {
+            const float4 w = wt[q4];
+            const float2 wa = make_float2(w.x, w.y), wb = make_float2(w.z, w.w);
+            fma2_acc(p0[2 * q4], wa, d0);
+            fma2_acc(p0[2 * q4 + 1], wb, d0);
+            fma2_acc(p1[2 * q4], wa, d1);
+            fma2_acc(p1[2 * q4 + 1], wb, d1);
           }
+        };
+        if (ks == 3) {
+#pragma unroll
+          for (int t = 0; t < 9; ++t) tap(t / 3, t % 3);
+        } else {
+          for (int dy = 0; dy < ks; ++dy)
+            for (int dx = 0; dx < ks; ++dx) tap(dy, dx);
         }
+      }
+    } else {
+      for (int cc = 0; cc < CC; ++cc) {
+        const T* xc = xs + (size_t)cc * SH * SW + ty * SW + tx;
+        const T* wc = ws + (size_t)cc * KK * FOC;
+        for (int dy = 0; dy < ks; ++dy)
+          for (int dx = 0; dx < ks; ++dx) {
+            const T v0 = xc[dy * SW + dx], v1 = xc[(dy + 16) * SW + dx];
+            const T* wt = wc + (dy * ks + dx) * FOC;
+#pragma unroll
+            for (int q = 0; q < FOC; ++q) {
+              const T wq = wt[q];
+              acc0[q] += wq * v0;
+              acc1[q] += wq * v1;
+            }
+          }
+      }
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < FOC / 2; ++q) {
+      acc0[2 * q] = p0[q].x;
+      acc0[2 * q + 1] = p0[q].y;
+      acc1[2 * q] = p1[q].x;
+      acc1[2 * q + 1] = p1[q].y;
     }
   }
   const T inv_n = T(1) / T(n);
