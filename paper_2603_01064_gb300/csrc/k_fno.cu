@@ -207,13 +207,30 @@ k_fno_wconv(int n, int m, int c, int ks, const T* __restrict__ zin, const C2<T>*
   float2 p0[FOC / 2], p1[FOC / 2];
 #pragma unroll
   for (int q = 0; q < FOC / 2; ++q) p0[q] = p1[q] = make_float2(0.f, 0.f);
+  const int st_c0 = threadIdx.x / (SH * SW), st_r0 = threadIdx.x - st_c0 * SH * SW;
+  const int st_y0 = st_r0 / SW, st_x0 = st_r0 - st_y0 * SW;
+  const int st_dy = blockDim.x / SW, st_dx = blockDim.x - st_dy * SW;
   for (int ch0 = 0; ch0 < c; ch0 += CC) {
     __syncthreads();  // the previous pass is done with xs and ws
-    for (int i = threadIdx.x; i < CC * SH * SW; i += blockDim.x) {
-      const int cc = i / (SH * SW), r = i - cc * SH * SW;
-      const int yy = y0 - hw + r / SW, xx = x0 - hw + r % SW;
-      const bool in = ch0 + cc < c && yy >= 0 && yy < n && xx >= 0 && xx < n;
-      xs[i] = in ? zb[(size_t)(ch0 + cc) * plane + (size_t)yy * n + xx] : T(0);
+    {
+      // (channel, row, column) of staged element i, stepped along with i
+      // (no integer division per element)
+      int cc = st_c0, ry = st_y0, rx = st_x0;
+      for (int i = threadIdx.x; i < CC * SH * SW; i += blockDim.x) {
+        const int yy = y0 - hw + ry, xx = x0 - hw + rx;
+        const bool in = ch0 + cc < c && yy >= 0 && yy < n && xx >= 0 && xx < n;
+        xs[i] = in ? zb[(size_t)(ch0 + cc) * plane + (size_t)yy * n + xx] : T(0);
+        rx += st_dx;
+        ry += st_dy;
+        if (rx >= SW) {
+          rx -= SW;
+          ++ry;
+        }
+        while (ry >= SH) {
+          ry -= SH;
+          ++cc;
+        }
+      }
     }
     for (int i = threadIdx.x; i < CC * KK * FOC; i += blockDim.x) {
       const int cc = i / (KK * FOC), r = i - cc * KK * FOC, t = r / FOC, q = r - t * FOC;
