@@ -134,6 +134,27 @@ def test_split_smoother_matches_fp64(ctx, prec):
         assert rel(h, O.smoother(W[l], b32)) < SPLIT_TOL[prec], l
 
 
+@pytest.mark.parametrize("prec", ["bf16_refine", "fp16_refine"])
+@pytest.mark.parametrize("layers", [3, 4, 5])
+def test_split_smoother_depths_and_zero_rhs(ctx, prec, layers):
+    """On levels of side >= 32 the split forms compute the first layer inside
+    the first hidden layer's kernel when another hidden layer follows (4 and
+    5 layers; 3 layers keep the separate first-layer kernel).  A zero
+    right-hand side between nonzero ones is skipped by the tile schedule
+    and gets h = 0; the others match the FP64 oracle."""
+    W = I.random_cnn_weights(2, 2, seed=40 + layers, layers=layers)
+    H, G, W = make(ctx, prec, n=64, levels=3, weights=W)
+    rng = np.random.default_rng(layers)
+    for l in range(2):
+        m = H.size(l)
+        b = rng.standard_normal((4, m, m)) * np.array([1.0, 1.0, 1e-3, 20.0])[:, None, None]
+        b[1] = 0.0
+        b32, h = smooth_gpu(G, l, b)
+        assert np.all(h[1] == 0.0)
+        keep = [0, 2, 3]
+        assert rel(h[keep], O.smoother(W[l], b32[keep])) < SPLIT_TOL[prec], (l, layers)
+
+
 CYCLE_TOL = {"bf16_refine": 1e-3, "fp16_refine": 1e-4}
 
 
