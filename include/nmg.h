@@ -231,6 +231,15 @@ nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_ho
                           void* u_host, double rtol, int max_cycles,
                           nmg_solve_info* info);
 
+/* nmg_solve_host from the zero initial guess x^0 = 0 of the outer loop
+ * (Section 3.3, Algorithms 3/4 run from zero): u_host is output only
+ * ([batch][n][n] (2D) or [batch][n], fp64 in the FP64 and refinement
+ * precisions, fp32 in FP32); it is not read, and only f is copied to the
+ * device.  Errors as nmg_solve_host.  Synchronous. */
+nmg_status nmg_solve_host_zero(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host,
+                               void* u_host, double rtol, int max_cycles,
+                               nmg_solve_info* info);
+
 /* Exactly one cycle u <- NMGF(u, f) at the finest level for every
  * right-hand side (no convergence test).  Asynchronous. */
 nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u);

@@ -87,6 +87,7 @@ def lib():
         "nmg_destroy_hier": (V, [P]),
         "nmg_solve": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
         "nmg_solve_host": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
+        "nmg_solve_host_zero": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
         "nmg_solve_multi": (I, [P, I, ctypes.POINTER(_SolveItem), D, I]),
         "nmg_server_create": (I, [P, ctypes.c_size_t, D, I, ctypes.POINTER(P)]),
         "nmg_server_destroy": (V, [P]),
@@ -293,15 +294,17 @@ class Hierarchy:
                                        int(max_cycles), info))
         return _unpack(info, B)
 
-    def solve_host(self, f: np.ndarray, u: np.ndarray, rtol=1e-6, max_cycles=100):
-        """Solve from host (numpy) buffers; u is updated in place."""
+    def solve_host(self, f: np.ndarray, u: np.ndarray, rtol=1e-6, max_cycles=100,
+                   zero_start: bool = False):
+        """Solve from host (numpy) buffers; u is updated in place.  With
+        zero_start the solve starts from u = 0 and u is output only (not
+        read or copied to the device)."""
         assert f.flags.c_contiguous and u.flags.c_contiguous
         B = f.shape[0]
         info = (SolveInfo * max(B, 1))()
-        self.ctx.check(lib().nmg_solve_host(self.ctx._h, self._h, B,
-                                            ctypes.c_void_p(f.ctypes.data),
-                                            ctypes.c_void_p(u.ctypes.data), float(rtol),
-                                            int(max_cycles), info))
+        fn = lib().nmg_solve_host_zero if zero_start else lib().nmg_solve_host
+        self.ctx.check(fn(self.ctx._h, self._h, B, ctypes.c_void_p(f.ctypes.data),
+                          ctypes.c_void_p(u.ctypes.data), float(rtol), int(max_cycles), info))
         return _unpack(info, B)
 
     def cycle(self, f, u):

@@ -1162,8 +1162,12 @@ nmg_status nmg_solve_multi(nmg_ctx* ctx, int nitems, const nmg_solve_item* items
   return run_outer_multi(ctx, its, key, rtol, max_cycles);
 }
 
-nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host, void* u_host,
-                          double rtol, int max_cycles, nmg_solve_info* info) {
+namespace {
+
+// host-buffer solve; zero_start: u_host is output only, the device iterate
+// starts from zero (no host-to-device copy of u)
+nmg_status solve_host_impl(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host, void* u_host,
+                           double rtol, int max_cycles, nmg_solve_info* info, bool zero_start) {
   nmg_status s = check_common(ctx, h, batch);
   if (s != NMG_OK) return s;
   if (batch == 0) return NMG_OK;
@@ -1185,12 +1189,27 @@ nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_ho
     w.all.push_back(w.udev);
   }
   CK(cudaMemcpyAsync(w.fdev, f_host, n * fes, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(w.udev, u_host, n * ues, cudaMemcpyHostToDevice, ctx->stream));
+  if (zero_start)
+    CK(cudaMemsetAsync(w.udev, 0, n * ues, ctx->stream));
+  else
+    CK(cudaMemcpyAsync(w.udev, u_host, n * ues, cudaMemcpyHostToDevice, ctx->stream));
   s = nmg_solve(ctx, h, batch, w.fdev, w.udev, rtol, max_cycles, info);
   if (s != NMG_OK) return s;
   CK(cudaMemcpyAsync(u_host, w.udev, n * ues, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return NMG_OK;
+}
+
+}  // namespace
+
+nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host, void* u_host,
+                          double rtol, int max_cycles, nmg_solve_info* info) {
+  return solve_host_impl(ctx, h, batch, f_host, u_host, rtol, max_cycles, info, false);
+}
+
+nmg_status nmg_solve_host_zero(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_host,
+                               void* u_host, double rtol, int max_cycles, nmg_solve_info* info) {
+  return solve_host_impl(ctx, h, batch, f_host, u_host, rtol, max_cycles, info, true);
 }
 
 nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u) {

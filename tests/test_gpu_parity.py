@@ -268,3 +268,28 @@ def test_batch_zero_is_noop(ctx):
     f = torch.zeros((0, 64, 64), dtype=torch.float32, device="cuda")
     cyc, st, rr = G.solve(f, f.clone())
     assert len(cyc) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_refine"])
+def test_host_buffer_solves_match_device_solve(ctx, prec):
+    """nmg_solve_host (f and u copied in, u copied back) and
+    nmg_solve_host_zero (zero initial guess; u is output only, here filled
+    with NaN beforehand) give bitwise the same iterate and per-RHS
+    information as nmg_solve on device buffers."""
+    H, G, W = make2d(ctx, prec)
+    f, _ = I.rhs_2d_ellipses_grf(64, 3, seed=77, sigma=2.0)
+    udt = np.float32 if prec == "fp32" else np.float64
+    fd = dev(f, "fp32")
+    ud = torch.zeros((3, 64, 64), dtype=torch.float32 if prec == "fp32" else torch.float64,
+                     device="cuda")
+    ref = G.solve(fd, ud, rtol=1e-12, max_cycles=4)
+    u_dev = host(ud)
+    fh = np.ascontiguousarray(f, dtype=np.float32)
+    u1 = np.zeros((3, 64, 64), dtype=udt)
+    got1 = G.solve_host(fh, u1, rtol=1e-12, max_cycles=4)
+    u2 = np.full((3, 64, 64), np.nan, dtype=udt)
+    got2 = G.solve_host(fh, u2, rtol=1e-12, max_cycles=4, zero_start=True)
+    for got, u in ((got1, u1), (got2, u2)):
+        for a, b in zip(got, ref):
+            assert np.array_equal(np.asarray(a), np.asarray(b))
+        assert np.array_equal(u.astype(np.float64), u_dev)
