@@ -17,7 +17,9 @@
 //               (thread: one column j, S consecutive rows)
 // Rows/columns g < nb add their correction rows (read from shared memory:
 // the register windows are only indexed at compile-time offsets).  WK >= wK
-// is the padded half-width (compile time); the M factor is padded to
+// is the padded half-width (compile time: 2, 4, 6, 8, 16, or the maximum;
+// even, so that the S + 2 WK window is whole 16-byte chunks of fp32 and
+// fp64); the M factor is padded to
 // half-width 1.  Staged tiles start on 16-byte-aligned global columns
 // (n % (16 / sizeof(T)) == 0): a 16-byte chunk is either inside the image or
 // outside it and then zero-filled.
@@ -155,6 +157,7 @@ k_res2d_pipe(StencilArgs<T, WK> op, int B, const T* __restrict__ x, const T* __r
              int tile, int tiles_x) {
   using G = PipeGeom<T, RESTRICT, WK, MID>;
   constexpr int E = G::E, S = G::S, NW = S + 2 * WK;
+  static_assert(NW % E == 0, "the row pass loads its window as whole 16-byte chunks");
   constexpr bool PACK = std::is_same<T, float>::value;
   const G g(tile);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -755,6 +758,7 @@ bool launch_stencil_residual(const Band2D<T>& op, int B, const T* x, const T* y,
   const int w = op.st->wK;
   if (w <= 2) return launch_st_m<T, RESTRICT, 2>(op, B, x, y, out, partials, active, tile, ntx, st);
   if (w <= 4) return launch_st_m<T, RESTRICT, 4>(op, B, x, y, out, partials, active, tile, ntx, st);
+  if (w <= 6) return launch_st_m<T, RESTRICT, 6>(op, B, x, y, out, partials, active, tile, ntx, st);
   if (w <= 8) return launch_st_m<T, RESTRICT, 8>(op, B, x, y, out, partials, active, tile, ntx, st);
   if (w <= 16) return launch_st_m<T, RESTRICT, 16>(op, B, x, y, out, partials, active, tile, ntx, st);
   if (w <= kStencilMaxW)
