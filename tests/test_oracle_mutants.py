@@ -1,0 +1,187 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in the FP64 oracle (on the CPU, by replacing
+one of its functions for the duration of the test) -- a dropped term, a
+wrong scale, sign or index, a flipped kernel, a missing normalisation -- and
+checks that the named pins of ``test_oracle_pins.py`` then fail.  The
+unmodified oracle passes the same pins in that file.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import nmg_oracle as NO
+import test_oracle_pins as P
+
+CAUGHT = (AssertionError, ValueError, np.linalg.LinAlgError)
+
+
+def _plant(monkeypatch, name, fn):
+    """Replace oracle function `name` in the module (its internal callers)
+    and in the package namespace (the pins' callers)."""
+    monkeypatch.setattr(NO, name, fn)
+    monkeypatch.setattr(O, name, fn, raising=False)
+
+
+_prolongation = NO.prolongation
+_restriction = NO.restriction
+_filter_mask = NO.filter_mask
+_conv_same = NO._conv_same
+_apply_level = NO.apply_level
+_fno_spectral = NO.fno_spectral
+
+
+def restriction_missing_half(nf):
+    return _prolongation(nf // 2).T  # P^T instead of P^T / 2
+
+
+def prolongation_copies_last_point(nc):
+    Pm = _prolongation(nc)
+    Pm[2 * nc - 1, nc - 1] = 1.0  # constant extension instead of the zero phantom
+    return Pm
+
+
+def mask_without_sqrt(n, dim):
+    return _filter_mask(n, dim) ** 2  # |omega| / pi instead of its square root
+
+
+def mask_min_instead_of_max(n, dim):
+    if dim == 1:
+        return _filter_mask(n, 1)
+    j = np.arange(n)
+    w = 2.0 * np.pi * np.minimum(j, n - j) / n
+    return np.sqrt(np.minimum(w[:, None], w[None, :]) / np.pi)
+
+
+def mask_on_unshifted_bins(n, dim):
+    # the symbol sampled at phi_k = (2k - n) pi / n but applied to DFT bin k
+    # without the shift that puts frequency 0 at bin 0
+    phi = np.abs((2 * np.arange(n) - n) * np.pi / n)
+    if dim == 1:
+        return np.sqrt(phi / np.pi)
+    return np.sqrt(np.maximum(phi[:, None], phi[None, :]) / np.pi)
+
+
+def conv_flipped_kernel(x, W, bias):
+    # true convolution instead of PyTorch's cross-correlation
+    return _conv_same(x, np.flip(W, axis=tuple(range(2, W.ndim))).copy(), bias)
+
+
+def cnn_relu_after_last_layer(weights, x):
+    z = x[:, None]
+    for W, b in weights:
+        z = np.maximum(_conv_same(z, np.asarray(W, np.float64), np.asarray(b, np.float64)), 0.0)
+    return z[:, 0]
+
+
+def smoother_without_normalisation(weights, b):
+    net = NO.fno_forward if isinstance(weights, dict) else NO.cnn_forward
+    return net(weights, b)  # N(b) instead of N(b / ||b||) ||b||
+
+
+def apply_without_alpha(H, l, x):
+    if H.dim == 1:
+        return _apply_level(H, l, x)
+    M, K = H.ops[l]
+    return K @ x @ K.T  # the alpha M X M^T term dropped
+
+
+def apply_negated(H, l, x):
+    return -_apply_level(H, l, x)  # b = y + A x*: residual sign flipped
+
+
+def cholesky_solve_wrong_back_substitution(L, y):
+    n = L.shape[0]
+    z = np.array(y, dtype=np.float64, copy=True)
+    for i in range(n):
+        z[i] = (z[i] - L[i, :i] @ z[:i]) / L[i, i]
+    x = z
+    for i in range(n - 1, -1, -1):
+        x[i] = (x[i] - L[i, i + 1:] @ x[i + 1:]) / L[i, i]  # row of L instead of column
+    return x
+
+
+def prolong_half_scale(H, l, e):
+    Pm = _prolongation(H.size(l + 1)) / 2.0
+    if H.dim == 1:
+        return e @ Pm.T
+    return Pm @ e @ Pm.T
+
+
+def fno_drops_negative_rows(z, R):
+    R2 = np.array(R, copy=True)
+    R2[1] = 0.0  # the k1 in [n - m, n) block never applied
+    return _fno_spectral(z, R2)
+
+
+def fno_block0_for_both(z, R):
+    R2 = np.array(R, copy=True)
+    R2[1] = R2[0]  # block 0's weights reused for the k1 in [n - m, n) rows
+    return _fno_spectral(z, R2)
+
+
+MUTANTS = {
+    # (a Galerkin cycle with a zero smoother is invariant to the scale of R:
+    # A_c = R A P and R y scale together, so only these pins can see it)
+    "restriction without the 1/2": (
+        "restriction", restriction_missing_half,
+        [P.test_restriction_is_scaled_transpose_and_full_weighting,
+         P.test_2d_transfer_is_kronecker,
+         P.test_galerkin_2d_equals_dense_RAP]),
+    "prolongation copies the last coarse value": (
+        "prolongation", prolongation_copies_last_point,
+        [P.test_prolongation_interpolates_linear_functions]),
+    "filter symbol without the square root": (
+        "filter_mask", mask_without_sqrt,
+        [lambda: P.test_filter_1d_cosine_eigenvectors(16),
+         P.test_filter_2d_cosine_products_and_special_vectors,
+         P.test_filter_matches_bruteforce_dft]),
+    "2D filter symbol with min instead of max": (
+        "filter_mask", mask_min_instead_of_max,
+        [P.test_filter_2d_cosine_products_and_special_vectors,
+         P.test_filter_matches_bruteforce_dft]),
+    "filter symbol on unshifted bins": (
+        "filter_mask", mask_on_unshifted_bins,
+        [lambda: P.test_filter_1d_cosine_eigenvectors(16),
+         P.test_filter_matches_bruteforce_dft]),
+    "convolution instead of cross-correlation": (
+        "_conv_same", conv_flipped_kernel,
+        [P.test_cnn_2d_matches_torch_conv, P.test_cnn_1d_matches_torch_conv]),
+    "ReLU after the output layer": (
+        "cnn_forward", cnn_relu_after_last_layer,
+        [P.test_cnn_2d_matches_torch_conv]),
+    "smoother without the norm scaling": (
+        "smoother", smoother_without_normalisation,
+        [P.test_smoother_is_positively_homogeneous_and_zero_safe,
+         P.test_cycle_positive_homogeneity]),
+    "operator apply without the alpha term": (
+        "apply_level", apply_without_alpha,
+        [lambda: P.test_2d_apply_matches_bruteforce_assembly(8, 1.0)]),
+    "residual sign flipped": (
+        "apply_level", apply_negated,
+        [lambda: P.test_2d_apply_matches_bruteforce_assembly(8, 1.0),
+         P.test_linear_jacobi_smoother_reproduces_classical_backslash_mg]),
+    "back substitution with L instead of L^T": (
+        "cholesky_solve", cholesky_solve_wrong_back_substitution,
+        [P.test_coarse_cholesky_vs_scipy, P.test_single_level_cycle_is_exact_solve]),
+    "prolongation of the correction at half scale": (
+        "prolong", prolong_half_scale,
+        [P.test_2d_transfer_is_kronecker,
+         P.test_cycle_with_zero_smoother_is_pure_coarse_correction]),
+    "FNO: negative-k1 block dropped": (
+        "fno_spectral", fno_drops_negative_rows,
+        [P.test_fno_spectral_identity_R_is_full_dft_projection,
+         P.test_fno_spectral_blocks_act_on_their_own_rows]),
+    "FNO: block 0 weights on both blocks": (
+        "fno_spectral", fno_block0_for_both,
+        [P.test_fno_spectral_blocks_act_on_their_own_rows]),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(monkeypatch, mutant):
+    name, fn, pins = MUTANTS[mutant]
+    _plant(monkeypatch, name, fn)
+    for pin in pins:
+        with pytest.raises(CAUGHT):
+            pin()

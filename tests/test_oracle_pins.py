@@ -580,3 +580,22 @@ def test_fno_smoother_is_positively_homogeneous_in_b():
     h1 = O.smoother(W, b)
     h2 = O.smoother(W, 3.5 * b)
     assert np.abs(h2 - 3.5 * h1).max() <= 1e-12 * np.abs(h2).max()
+
+
+def test_fno_spectral_blocks_act_on_their_own_rows():
+    """The two R blocks (k1 in [0, m) and k1 in [n - m, n)) act on their own
+    rows of the half spectrum: with R = 1 on block 0 and 0 on block 1, the
+    wave cos 2 pi (y + 2x) / n (half-spectrum spike at k1 = 1, k2 = 2) passes
+    unchanged and cos 2 pi (-y + 2x) / n (spike at k1 = n - 1) is removed;
+    swapping the blocks swaps the outcomes."""
+    n, m = 16, 3
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    plus = np.cos(2 * np.pi * (y + 2 * x) / n)[None, None]
+    minus = np.cos(2 * np.pi * (-y + 2 * x) / n)[None, None]
+    R = np.zeros((2, 1, 1, m, m), np.complex128)
+    R[0] = 1.0
+    assert np.abs(O.fno_spectral(plus, R) - plus).max() < 1e-13
+    assert np.abs(O.fno_spectral(minus, R)).max() < 1e-13
+    R = R[::-1].copy()
+    assert np.abs(O.fno_spectral(plus, R)).max() < 1e-13
+    assert np.abs(O.fno_spectral(minus, R) - minus).max() < 1e-13
