@@ -120,7 +120,38 @@ def fno_block0_for_both(z, R):
     return _fno_spectral(z, R2)
 
 
+def make_cycle(mistake):
+    """The cycle of Algorithms 3/4 as the oracle runs it, with one step done
+    wrongly: 'restrict_xstar' restricts y - A x* instead of y - A x (the
+    smoothed iterate), 'filter_x' filters x* + h instead of h, 'smooth_y'
+    smooths y instead of the defect b = y - A x*."""
+    def cycle(H, weights, l, xstar, y, filt=True, trace=None):
+        if l == H.levels - 1:
+            B = y.shape[0]
+            return NO.cholesky_solve(H.chol, y.reshape(B, -1).T).T.reshape(y.shape)
+        xs = np.zeros_like(y) if xstar is None else xstar
+        b = y - NO.apply_level(H, l, xs)
+        h = NO.smoother(weights[l], y if mistake == "smooth_y" else b)
+        if mistake == "filter_x":
+            x = NO.spectral_filter(xs + h, H.dim) if filt else xs + h
+        else:
+            x = xs + (NO.spectral_filter(h, H.dim) if filt else h)
+        xr = xs if mistake == "restrict_xstar" else x
+        yc = NO.restrict(H, l, y - NO.apply_level(H, l, xr))
+        return x + NO.prolong(H, l, NO.nmgf(H, weights, l + 1, None, yc, filt))
+    return cycle
+
+
 MUTANTS = {
+    "cycle restricts the residual of x* instead of x": (
+        "nmgf", make_cycle("restrict_xstar"),
+        [P.test_linear_jacobi_smoother_reproduces_classical_backslash_mg]),
+    "cycle filters x* + h instead of h": (
+        "nmgf", make_cycle("filter_x"),
+        [P.test_cycle_with_initial_guess_is_defect_correction]),
+    "cycle smooths y instead of the defect": (
+        "nmgf", make_cycle("smooth_y"),
+        [P.test_cycle_with_initial_guess_is_defect_correction]),
     # (a Galerkin cycle with a zero smoother is invariant to the scale of R:
     # A_c = R A P and R y scale together, so only these pins can see it)
     "restriction without the 1/2": (
@@ -185,3 +216,13 @@ def test_pins_catch_planted_mistake(monkeypatch, mutant):
     for pin in pins:
         with pytest.raises(CAUGHT):
             pin()
+
+
+def test_cycle_copy_without_mistake_passes_the_pins(monkeypatch):
+    """Control for the cycle mutants: the same copy of the cycle with no
+    mistake passes the pins they fail."""
+    _plant(monkeypatch, "nmgf", make_cycle(None))
+    P.test_linear_jacobi_smoother_reproduces_classical_backslash_mg()
+    P.test_cycle_with_initial_guess_is_defect_correction()
+    P.test_cycle_with_zero_smoother_is_pure_coarse_correction()
+    P.test_cycle_positive_homogeneity()
