@@ -351,6 +351,20 @@ nmg_status nmg_hier_info(const nmg_hier* h, int level, int* n, int* wK, int* wM,
  * 1D: A_l (n_l x n_l) into K (M unused). */
 nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double* M);
 
+/* The Galerkin hierarchy of an operator description built on the host only
+ * (no context, no device memory, no GPU needed): the same fp64 banded
+ * products nmg_setup uses (A_{l+1} = R A_l P with R = P^T / 2 per axis,
+ * Algorithms 3/4; 2D as K_{l+1} = R K_l P and M_{l+1} = R M_l P, Section
+ * 4.2).  Writes the side n_l of level `level` (0 = finest), the band
+ * half-widths of K_l and M_l (2D; -1 in 1D), and, where K is not NULL,
+ * the level's factors in dense row-major form exactly as
+ * nmg_hier_level_dense does (2D: K_l and M_l, n_l x n_l each, M may be
+ * NULL; 1D: A_l into K).  Host pointers; any of n, wK, wM may be NULL.
+ * NMG_ERR_ARG for an invalid description (the checks of nmg_setup on the
+ * operator) or a level outside [0, levels). */
+nmg_status nmg_host_level_dense(const nmg_operator_desc* op, int level, int* n, int* wK,
+                                int* wM, double* K, double* M);
+
 /* Number of kernels the library launched on this context so far. */
 long long nmg_launch_count(const nmg_ctx* ctx);
 

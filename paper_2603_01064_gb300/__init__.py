@@ -108,6 +108,8 @@ def lib():
         "nmg_hier_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I)]),
         "nmg_hier_level_dense": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "nmg_host_level_dense": (I, [ctypes.POINTER(_OpDesc), I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                     ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "nmg_launch_count": (ctypes.c_longlong, [P]),
         "nmg_profile_enable": (I, [P, I]),
         "nmg_set_graphs": (I, [P, I]),
@@ -135,6 +137,35 @@ def _ptr(t):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def host_level_dense(*, dim: int, n: int, levels: int, alpha: float, taps, level: int,
+                     reg=None):
+    """The Galerkin hierarchy built on the host by the library (no GPU):
+    level `level`'s factors in dense form, (K_l, M_l) in 2D or A_l in 1D,
+    exactly as a hierarchy set up from the same description holds them."""
+    L = lib()
+    t = np.ascontiguousarray(taps, dtype=np.float64)
+    r = None
+    if reg is not None:
+        r = np.ascontiguousarray(np.concatenate([np.asarray(reg[0], np.float64),
+                                                 np.asarray(reg[1], np.float64)]))
+    dp = ctypes.POINTER(ctypes.c_double)
+    op = _OpDesc(dim, n, levels, alpha, len(t), t.ctypes.data_as(dp), PRECISIONS["fp64"], 1,
+                 r.ctypes.data_as(dp) if r is not None else None, 0 if r is None else r.size)
+    nl, wk, wm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = L.nmg_host_level_dense(ctypes.byref(op), level, ctypes.byref(nl), ctypes.byref(wk),
+                                ctypes.byref(wm), None, None)
+    if rc != 0:
+        raise NMGError(rc, L.nmg_status_str(rc).decode())
+    m = nl.value
+    K = np.zeros((m, m))
+    M = np.zeros((m, m)) if dim == 2 else None
+    rc = L.nmg_host_level_dense(ctypes.byref(op), level, None, None, None, K.ctypes.data_as(dp),
+                                M.ctypes.data_as(dp) if M is not None else None)
+    if rc != 0:
+        raise NMGError(rc, L.nmg_status_str(rc).decode())
+    return (K, M) if dim == 2 else K
 
 
 def pack_weights(levels: Sequence[Sequence[tuple]]) -> np.ndarray:

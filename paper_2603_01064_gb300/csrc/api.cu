@@ -1525,13 +1525,14 @@ nmg_status nmg_hier_info(const nmg_hier* h, int level, int* n, int* wK, int* wM,
   return NMG_OK;
 }
 
-nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double* M) {
-  if (!h || level < 0 || level >= h->L || !K) return NMG_ERR_ARG;
-  const HostLevel& hl = h->host.lv[level];
+namespace {
+
+// dense copy of one host level: 2D K_l and M_l from their DIA rows, 1D A_l
+void host_level_dense(int dim, const HostLevel& hl, double* K, double* M) {
   const int n = hl.n;
-  if (h->dim == 1) {
+  if (dim == 1) {
     std::memcpy(K, hl.A.data(), (size_t)n * n * sizeof(double));
-    return NMG_OK;
+    return;
   }
   auto dense = [n](const std::vector<double>& dia, int w, double* out) {
     std::memset(out, 0, (size_t)n * n * sizeof(double));
@@ -1543,6 +1544,28 @@ nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double*
   };
   dense(hl.Kd, hl.wK, K);
   if (M) dense(hl.Md, hl.wM, M);
+}
+
+}  // namespace
+
+nmg_status nmg_hier_level_dense(const nmg_hier* h, int level, double* K, double* M) {
+  if (!h || level < 0 || level >= h->L || !K) return NMG_ERR_ARG;
+  host_level_dense(h->dim, h->host.lv[level], K, M);
+  return NMG_OK;
+}
+
+nmg_status nmg_host_level_dense(const nmg_operator_desc* op, int level, int* n, int* wK,
+                                int* wM, double* K, double* M) {
+  if (!op) return NMG_ERR_ARG;
+  HostHierarchy H;
+  std::string err;
+  if (!build_host_hierarchy(*op, H, err)) return NMG_ERR_ARG;
+  if (level < 0 || level >= H.levels) return NMG_ERR_ARG;
+  const HostLevel& hl = H.lv[level];
+  if (n) *n = hl.n;
+  if (wK) *wK = H.dim == 2 ? hl.wK : -1;
+  if (wM) *wM = H.dim == 2 ? hl.wM : -1;
+  if (K) host_level_dense(H.dim, hl, K, M);
   return NMG_OK;
 }
 
