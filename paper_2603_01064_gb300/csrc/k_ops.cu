@@ -299,7 +299,9 @@ __global__ void k_converge(const double* __restrict__ s, const double* __restric
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !active[b]) return;
   double f = fn[b];
-  double rr = f > 0.0 ? s[b] / f : 0.0;
+  // ||f|| = 0: converged (u = 0 solves it); ||f|| NaN (a NaN in f): rr stays
+  // NaN and the right-hand side is reported as diverged
+  double rr = f > 0.0 ? s[b] / f : (f == 0.0 ? 0.0 : f);
   relres[b] = rr;
   if (!(rr == rr) || rr > 1e30) {
     status[b] = NMG_DIVERGED;
