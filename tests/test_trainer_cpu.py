@@ -1,0 +1,106 @@
+"""The offline level-wise trainer (Algorithm 5) on the CPU, at toy sizes.
+
+* Its own cycle (a separate PyTorch implementation of Algorithms 3/4 with a
+  dense hierarchy) equals the FP64 oracle's cycle for the same weights, with
+  and without the exported zero output bias (F' removes constants, so the
+  filtered cycle does not depend on it).
+* DataGeneration returns pairs with y = A x and unit error norms.
+* A few Adam steps on the level-wise loss of level 0 lower it.
+* Export to npz and the library's loader round-trip the weights.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import nmg_inputs as I  # noqa: E402
+import oracle as O  # noqa: E402
+import paper_2603_01064_gb300 as nmg  # noqa: E402
+from paper_2603_01064_gb300.weights import train_smoothers as T  # noqa: E402
+
+N, L, ALPHA, SIGMA = 16, 3, 1e-2, 1.0
+
+
+def _nets(seed, dim=2, layers=4, width=8, ksize=3):
+    torch.manual_seed(seed)
+    nets = []
+    for _ in range(L - 1):
+        net = T.CNN(dim, layers, width, ksize).double()
+        with torch.no_grad():  # the trainer zero-initialises the output layer
+            net.convs[-1].weight.normal_(0.0, 0.3)
+            net.convs[-1].bias.normal_(0.0, 0.3)
+        nets.append(net)
+    return nets
+
+
+def _weights(nets, zero_out_bias):
+    W = []
+    for net in nets:
+        lv = [(c.weight.detach().numpy().copy(), c.bias.detach().numpy().copy()) for c in net.convs]
+        if zero_out_bias:
+            lv[-1] = (lv[-1][0], np.zeros_like(lv[-1][1]))
+        W.append(lv)
+    return W
+
+
+def _problem():
+    return T.Problem(2, N, L, ALPHA, taps=I.gaussian_taps(SIGMA), dtype=torch.float64)
+
+
+@pytest.mark.parametrize("zero_out_bias", [False, True])
+def test_trainer_cycle_equals_oracle_cycle(zero_out_bias):
+    nets = _nets(0)
+    prob = _problem()
+    y = np.random.default_rng(1).standard_normal((3, N, N))
+    with torch.no_grad():
+        xt = T.cycle(prob, nets, 0, torch.tensor(y)).numpy()
+    H = O.build_hierarchy_2d(I.gaussian_taps(SIGMA), N, ALPHA, L)
+    xo = O.nmgf(H, _weights(nets, zero_out_bias), 0, None, y)
+    assert np.max(np.abs(xt - xo)) <= 1e-11 * np.max(np.abs(xo))
+
+
+def test_data_generation_pairs():
+    nets = _nets(1)
+    prob = _problem()
+    gen = torch.Generator().manual_seed(2)
+    x, y = T.data_generation(prob, nets, 6, 3, gen)
+    assert torch.allclose(y, prob.apply(0, x), atol=1e-12)
+    assert torch.allclose(x.reshape(6, -1).norm(dim=1), torch.ones(6, dtype=torch.float64))
+
+
+def test_levelwise_loss_decreases_with_adam():
+    torch.manual_seed(3)
+    prob = T.Problem(2, N, L, ALPHA, taps=I.gaussian_taps(SIGMA))
+    nets = [T.CNN(2, 4, 8, 3, gain=prob.top_gain(l)) for l in range(L - 1)]
+    gen = torch.Generator().manual_seed(4)
+    x, y = T.data_generation(prob, nets, 16, 2, gen)
+    opt = torch.optim.Adam(nets[0].parameters(), lr=1e-3)  # the trainer's default rate
+    first = None
+    for _ in range(40):
+        loss = T.levelwise_losses(prob, nets, x, y)[0]
+        if first is None:
+            first = loss.item()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+    assert T.levelwise_losses(prob, nets, x, y)[0].item() < 0.85 * first
+
+
+def test_export_round_trip(tmp_path):
+    nets = [n.float() for n in _nets(5)]
+    for n_, g in zip(nets, (2.0, 3.0)):
+        n_.gain = g
+    path = os.path.join(tmp_path, "w.npz")
+    T.nets_to_npz(nets, path, {"smoother_levels": L - 1})
+    W = nmg.load_weights(path)
+    assert len(W) == L - 1 and all(len(lv) == 4 for lv in W)
+    for lv, net in zip(W, nets):
+        for i, (w, b) in enumerate(lv):
+            g = net.gain if i == 3 else 1.0
+            assert np.array_equal(w, g * net.convs[i].weight.detach().double().numpy())
+            if i < 3:
+                assert np.array_equal(b, net.convs[i].bias.detach().double().numpy())
+            else:
+                assert not np.any(b)  # output bias exported as zero
