@@ -232,7 +232,7 @@ nmg_status nmg_solve_host(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f_ho
                           nmg_solve_info* info);
 
 /* nmg_solve_host from the zero initial guess x^0 = 0 of the outer loop
- * (Section 3.3, Algorithms 3/4 run from zero): u_host is output only
+ * (Section 3.2: x^0 = 0, then Algorithms 3/4): u_host is output only
  * ([batch][n][n] (2D) or [batch][n], fp64 in the FP64 and refinement
  * precisions, fp32 in FP32); it is not read, and only f is copied to the
  * device.  Errors as nmg_solve_host.  Synchronous. */
