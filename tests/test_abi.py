@@ -63,3 +63,16 @@ def test_pack_weights_order():
     assert p[0] == W[0][0][0].ravel()[0]
     assert p[288] == W[0][0][1][0]          # bias after the first conv weights
     assert p[19105] == W[1][0][0].ravel()[0]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback path: without the built library every entry raises."""
+    import paper_2603_01064_gb300 as nmg
+    monkeypatch.setattr(nmg, "_lib", None)
+    monkeypatch.setattr(nmg, "_LIB_PATH", str(tmp_path / "libnmg.so"))
+    with pytest.raises(RuntimeError, match="no fallback"):
+        nmg.lib()
+    with pytest.raises(RuntimeError, match="no fallback"):
+        nmg.Context(0)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        nmg.host_level_dense(dim=2, n=16, levels=2, alpha=1e-2, taps=[1.0], level=0)
