@@ -104,3 +104,19 @@ def test_export_round_trip(tmp_path):
                 assert np.array_equal(b, net.convs[i].bias.detach().double().numpy())
             else:
                 assert not np.any(b)  # output bias exported as zero
+
+
+def test_trainer_command_line_writes_loadable_weights(tmp_path, capsys):
+    """The trainer's entry point at a toy size: two epochs, an evaluation,
+    and a weight file the library's loader reads (CNN, 2D and 1D)."""
+    for cfg, extra in (("c2", ["--n", "16", "--levels", "3"]),
+                       ("c1", ["--n", "32", "--levels", "2"])):
+        out = os.path.join(tmp_path, cfg + ".npz")
+        T.main(["--config", cfg, *extra, "--epochs", "2", "--bs", "2", "--K", "1",
+                "--eval-batch", "1", "--eval-every", "1", "--out", out])
+        W = nmg.load_weights(out)
+        levels = int(extra[-1])
+        assert len(W) == levels - 1
+        dim = 2 if cfg == "c2" else 1
+        assert all(np.asarray(w).ndim == 2 + dim for lv in W for (w, _) in lv)
+    assert "saved" in capsys.readouterr().out
