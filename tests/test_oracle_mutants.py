@@ -9,8 +9,10 @@ unmodified oracle passes the same pins in that file.
 import numpy as np
 import pytest
 
+import nmg_inputs as I
 import oracle as O
 from oracle import nmg_oracle as NO
+import test_inputs as TI
 import test_oracle_pins as P
 
 CAUGHT = (AssertionError, ValueError, np.linalg.LinAlgError)
@@ -207,6 +209,47 @@ MUTANTS = {
         "fno_spectral", fno_block0_for_both,
         [P.test_fno_spectral_blocks_act_on_their_own_rows]),
 }
+
+
+# problem data shared by the oracle and the CUDA path (nmg_inputs): mistakes
+# there would pass every parity test, so their own pins must catch them
+_aniso = I.aniso_regularisation_1d
+_taps = I.gaussian_taps
+
+
+def aniso_at_cell_centres(n, a=I.aniso_coefficient):
+    return _aniso(n, a=lambda z: a(z + 0.5 / n))  # a at cell centres, not faces
+
+
+def aniso_off_diagonal_sign(n, a=I.aniso_coefficient):
+    diag, off = _aniso(n, a)
+    return diag, -off
+
+
+def taps_not_normalised(sigma):
+    w = int(np.ceil(4.0 * sigma))
+    j = np.arange(0, w + 1, dtype=np.float64)
+    return np.exp(-(j * j) / (2.0 * sigma * sigma))
+
+
+INPUT_MUTANTS = {
+    "anisotropic coefficient at cell centres": (
+        "aniso_regularisation_1d", aniso_at_cell_centres, [P.test_aniso_energy_identity]),
+    "anisotropic off-diagonal sign": (
+        "aniso_regularisation_1d", aniso_off_diagonal_sign,
+        [P.test_aniso_constant_coefficient_is_dirichlet_laplacian, P.test_aniso_energy_identity]),
+    "PSF taps not normalised": (
+        "gaussian_taps", taps_not_normalised, [lambda: TI.test_gaussian_taps(2.0)]),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(INPUT_MUTANTS))
+def test_input_pins_catch_planted_mistake(monkeypatch, mutant):
+    name, fn, pins = INPUT_MUTANTS[mutant]
+    monkeypatch.setattr(I, name, fn)
+    for pin in pins:
+        with pytest.raises(CAUGHT):
+            pin()
 
 
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))
