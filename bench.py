@@ -1,6 +1,7 @@
 #!/usr/bin/env python
 """Throughput of the neural multigrid solve: right-hand sides solved per
-second to relative residual 1e-6.
+second to relative residual 1e-6, the bf16 refinement form batched against
+the plain fp32 cycle one right-hand side at a time on the same GPU.
 
 One step = one full solve of a batch of right-hand sides (every row of the
 cycle: residual, norms, smoother, output filter, fused residual+restriction,
@@ -10,12 +11,16 @@ right-hand side meets the tolerance.  Inputs are resident in HBM when the
 timed region starts; L2 is flushed (a 256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c3|c2]
                   [--precision bf16_refine|bf16fast_refine|fp16_refine|fp32]
 
-The headline is the bf16 refinement form solving the whole batch at once;
-the same run also times, on the same GPU and right-hand sides, the fp32
-form batched, the fp32 form one right-hand side per call (the plain fp32
-single-RHS cycle) and the other bf16 form ("compare").
+Default workload (c3): 2D BTTB deblurring on a 512 x 512 grid, Gaussian PSF
+sigma 4 px truncated at 4 sigma, alpha 1e-2, 7 levels, 64 right-hand sides
+(plane waves + rectangles, blurred, 1% noise).  The same run sweeps alpha
+over {1e-4, 1e-3, 1e-2, 1e-1} with that operator's trained smoothers
+("alpha_sweep"), times the fp32 form batched, the fp32 form one
+right-hand side per call (the plain fp32 single-RHS cycle) and the other
+16-bit forms ("compare"), and the smaller 128 x 128 problem ("secondary").
 
 Under torchrun each rank solves its own batch (different seeds, the same
 sizes): weak scaling with no data-path collective.
@@ -39,9 +44,17 @@ import numpy as np  # noqa: E402
 import nmg_inputs as I  # noqa: E402
 
 WEIGHTS = os.path.join(ROOT, "paper_2603_01064_gb300", "weights")
-METRIC = "RHS solved/s to 1e-6 rel. residual"
+METRIC = "RHS solved/s to 1e-6 rel. residual (BF16+refine vs FP32 plain); p50/p99 latency"
 
 WORKLOADS = {
+    # 2D BTTB deblurring, 512x512, PSF sigma 4 px (truncated at 4 sigma), 7 levels,
+    # 64 right-hand sides (8 plane waves + 2 rectangles, blurred, 1% noise);
+    # headline alpha 1e-2, the sweep over the four alphas reported beside it
+    "c3": dict(name="2d_bttb_512x512_sigma4_alpha1e-2_L7_batch64", n=512, levels=7, alpha=1e-2,
+               sigma=4.0, batch=64, rhs="waves_rects", rhs_seed=1003,
+               weights="c3_2d_n512_s4_a1e-2.npz",
+               sweep=[(1e-4, "c3_2d_n512_s4_a1e-4.npz"), (1e-3, "c3_2d_n512_s4_a1e-3.npz"),
+                      (1e-2, "c3_2d_n512_s4_a1e-2.npz"), (1e-1, "c3_2d_n512_s4_a1e-1.npz")]),
     # 2D BTTB deblurring, 128x128, PSF sigma 2 px (truncated at 4 sigma), alpha 1e-2,
     # 5 levels, 256 right-hand sides (ellipses + Gaussian random field, blurred, 1% noise)
     "c2": dict(name="2d_bttb_128x128_sigma2_alpha1e-2_L5_batch256", n=128, levels=5, alpha=1e-2,
@@ -68,7 +81,7 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # DRAM bytes per output pixel of the hidden convs, mean of the two hidden
 # layers, from one ncu capture of this kernel version (128x128, 64 RHS,
 # level 0; summarised under profiles/); None where no capture exists
-HIDDEN_DRAM_B_PER_UNIT = {"bf16_refine": 109.9}
+HIDDEN_DRAM_B_PER_UNIT = {("bf16_refine", 128): 109.9}
 MMA_FLOPS_PER_PX = {
     # split form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
     "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
@@ -187,39 +200,90 @@ def aggregate(batch_per_rank, world, steps, max_total_ms):
 # the CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_solve_rate(wl, nrhs, seed, reps=1):
-    """Time the FP64 oracle on `nrhs` right-hand sides of the workload."""
+def oracle_cycle_time(wl, seed, ncycles):
+    """Seconds per cycle of the FP64 oracle (Algorithm 4, one right-hand
+    side of the workload, from x^0 = 0 as in the outer iteration of Section
+    3.2), over `ncycles` cycles."""
     import oracle as O
     import paper_2603_01064_gb300 as nmg_pkg  # weights loader only (no library call)
     W = nmg_pkg.load_weights(os.path.join(WEIGHTS, wl["weights"]))
     H = O.build_hierarchy_2d(I.gaussian_taps(wl["sigma"]), wl["n"], wl["alpha"], wl["levels"])
-    f = make_rhs(wl, nrhs, seed)
+    f = make_rhs(wl, 1, seed)
+    x = None
     t0 = time.perf_counter()
-    for _ in range(reps):
-        u, cyc, rr = O.solve(H, W, f, rtol=1e-6, max_cycles=100)
-    dt = time.perf_counter() - t0
-    return nrhs * reps / dt, dt, cyc, rr
+    for _ in range(ncycles):
+        x = O.nmgf(H, W, 0, x, f)
+    return (time.perf_counter() - t0) / ncycles
+
+
+def oracle_cycles_to_converge(wl):
+    """Cycles the FP64 oracle takes to reach 1e-6 on the workload's first
+    right-hand side, as stored by tests/golden/make_oracle_cycles.py (a
+    script that runs only the oracle); None if not stored."""
+    p = os.path.join(ROOT, "tests", "golden", "oracle_cycles.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(wl["name"])
+    return None if e is None else int(e["cycles"])
+
+
+def oracle_rate_sample(wl, seed, ncycles, threads=None):
+    """Oracle right-hand sides per second on a bounded sample: `ncycles`
+    cycles of one right-hand side timed, scaled by the oracle's own cycle
+    count to 1e-6.  threads: run in a child process with every BLAS / OpenMP
+    pool limited to that many threads (None: this process, all cores)."""
+    if threads is None:
+        t_cyc = oracle_cycle_time(wl, seed, ncycles)
+    else:
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                  "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+            env[k] = str(threads)
+        env.pop("RANK", None)
+        env.pop("WORLD_SIZE", None)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-cycle-probe",
+                            str(ncycles), "--workload", wl["key"], "--probe-seed", str(seed)],
+                           capture_output=True, text=True, env=env, timeout=900)
+        if r.returncode != 0:
+            return None, None, None
+        t_cyc = float(json.loads(r.stdout.strip().splitlines()[-1])["s_per_cycle"])
+    cyc = oracle_cycles_to_converge(wl)
+    if not cyc:
+        return None, t_cyc, None
+    return 1.0 / (t_cyc * cyc), t_cyc, cyc
+
+
+REF_CYCLES_PER_STEP = 1
 
 
 def run_reference(args, wl, world, rank):
+    """The oracle timed on the host cores: each step is one cycle of one
+    right-hand side of the workload (a bounded sample; a whole 512 x 512
+    solve takes minutes on the CPU), and right-hand sides per second are
+    that cycle time times the oracle's own cycle count to 1e-6."""
     if rank != 0:
         return
-    nrhs = 1
     cores = os.cpu_count()
-    for _ in range(args.warmup):
-        oracle_solve_rate(wl, nrhs, wl["rhs_seed"])
+    cyc = oracle_cycles_to_converge(wl)
+    for k in range(args.warmup):
+        oracle_cycle_time(wl, wl["rhs_seed"], REF_CYCLES_PER_STEP)
     times = []
     for k in range(args.steps):
-        _, dt, cyc, rr = oracle_solve_rate(wl, nrhs, wl["rhs_seed"] + k)
-        times.append(dt)
-    value = nrhs * args.steps / sum(times)
-    sample = f"{nrhs} right-hand sides of the workload per step (FP64 numpy oracle)"
+        times.append(oracle_cycle_time(wl, wl["rhs_seed"], REF_CYCLES_PER_STEP)
+                     * REF_CYCLES_PER_STEP)
+    t_cyc = sum(times) / (args.steps * REF_CYCLES_PER_STEP)
+    value = 1.0 / (t_cyc * cyc) if cyc else None
+    sample = (f"{REF_CYCLES_PER_STEP} cycle of 1 right-hand side of the workload per step "
+              f"(FP64 numpy oracle, BLAS threads = all host cores); RHS/s = 1 / (seconds per "
+              f"cycle x {cyc} cycles, the oracle's own count to 1e-6 on this workload)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "n": wl["n"], "levels": wl["levels"],
-                       "batch": nrhs, "l2": "n/a (CPU)"},
+                       "batch": 1, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
@@ -230,6 +294,91 @@ def run_reference(args, wl, world, rank):
 # ---------------------------------------------------------------------------
 # our CUDA path
 # ---------------------------------------------------------------------------
+
+def timed_steps(stepfn, K, flush, stream):
+    """CUDA events on the library's stream around each of K steps, L2
+    written over (256 MiB) before each; returns (ms list, step results)."""
+    import torch
+    times, res = [], []
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res.append(stepfn())
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, res
+
+
+def solve_summary(B, tp, rp):
+    return {"value": B * len(tp) / (sum(tp) / 1e3), "unit": "RHS/s", "batch": B,
+            "mean_cycles": float(np.mean([r[0].mean() for r in rp])),
+            "max_cycles": int(max(r[0].max() for r in rp)),
+            "converged": int(min((r[1] == 0).sum() for r in rp)),
+            "max_relres": float(max(r[2].max() for r in rp))}
+
+
+def roofline_of(kern, prec, n, peaks, peak_src):
+    """Roofline of the dominant kernel class: algorithmic work per unit x
+    units / the class's summed CUDA-event time."""
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    refine = prec != "fp32"
+    if dom in FLOPS_PER_PX and refine:
+        fl = FLOPS_PER_PX[dom]
+        achieved = fl * d["units"] / (d["ms"] / 1e3) / 1e12
+        issued = MMA_FLOPS_PER_PX[prec][dom] * d["units"] / (d["ms"] / 1e3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        bpu = HIDDEN_DRAM_B_PER_UNIT.get((prec, n)) if dom == "cnn_hidden" else None
+        traffic = bpu * d["units"] / d["launches"] if bpu else None
+        return {"kernel": f"{dom} (tcgen05 bf16 3x3 conv)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "traffic_bytes_per_unit": bpu,
+                "traffic_source": (f"ncu dram__bytes_read+write of the {n}x{n} level, scaled to "
+                                   "this launch's units") if bpu else None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "flop_per_unit": fl, "unit_def": "output pixel x active right-hand side",
+                "mma_issued_tflops": issued,
+                "mma_issued_flop_per_unit": MMA_FLOPS_PER_PX[prec][dom],
+                "launch_ms": d["ms"] / d["launches"]}
+    if dom in FLOPS_PER_PX:
+        achieved = FLOPS_PER_PX[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
+        return {"kernel": f"{dom} (fp32 SIMT 3x3 conv)", "bound": "alu", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None,
+                "peak_source": "152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz (derived)",
+                "flop_per_unit": FLOPS_PER_PX[dom], "launch_ms": d["ms"] / d["launches"]}
+    bpu = {"residual": 12, "restrict": 9, "prolong": 9, "filter": 8,
+           "refine_residual": 16}.get(dom, 8)
+    achieved = bpu * d["units"] / (d["ms"] / 1e3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": peak_src, "bytes_per_unit": bpu,
+            "launch_ms": d["ms"] / d["launches"]}
+
+
+def kernel_breakdown(kern, prec, steps, peaks):
+    prof_total = sum(v["ms"] for v in kern.values())
+    breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps,
+                     "share": v["ms"] / prof_total} for k, v in kern.items()}
+    # the memory-bound classes against the measured HBM copy bandwidth:
+    # algorithmic bytes per unit (grid point x active right-hand side, every
+    # level of the class together) / class time
+    act_b = {"bf16_refine": 128, "fp16_refine": 128, "bf16fast_refine": 64, "fp32": 128}[prec]
+    hbm_bpu = {"restrict": 9, "refine_residual": 16,
+               "prolong": 9, "filter": 8, "cnn_first": 4 + act_b, "cnn_last": 40}
+    if prec == "fp32":
+        hbm_bpu.pop("cnn_first")
+        hbm_bpu.pop("cnn_last")
+    for k, bpu_k in hbm_bpu.items():
+        if k in kern and kern[k]["ms"] > 0:
+            gbs = bpu_k * kern[k]["units"] / (kern[k]["ms"] / 1e3) / 1e9
+            breakdown[k].update({"bytes_per_unit": bpu_k, "achieved_gbs": gbs,
+                                 "hbm_frac": gbs / peaks["hbm_gbs"]})
+    return breakdown
+
 
 def run_ours(args, wl, world, rank, local):
     import torch
@@ -244,9 +393,10 @@ def run_ours(args, wl, world, rank, local):
     taps = I.gaussian_taps(wl["sigma"])
     prec = args.precision
 
-    def hier(p):
-        return nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"],
-                             taps=taps, precision=p, weights=W)
+    def hier(p, alpha=None, Wx=None):
+        return nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"],
+                             alpha=wl["alpha"] if alpha is None else alpha,
+                             taps=taps, precision=p, weights=W if Wx is None else Wx)
 
     G = hier(prec)
     B = args.batch or wl["batch"]
@@ -262,9 +412,9 @@ def run_ours(args, wl, world, rank, local):
     u = torch.zeros(f.shape, dtype=udt, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def step(Gx=G, fx=f, ux=u):
+    def step(Gx=G, fx=f, ux=u, max_cycles=100):
         ux.zero_()
-        return Gx.solve(fx, ux, rtol=1e-6, max_cycles=100)
+        return Gx.solve(fx, ux, rtol=1e-6, max_cycles=max_cycles)
 
     if args.ncu:
         # one solve only: the command profiled by ncu
@@ -278,26 +428,13 @@ def run_ours(args, wl, world, rank, local):
         cyc, st, rr = step()
     torch.cuda.synchronize()
 
-    def timed(stepfn, K):
-        times, res = [], []
-        for k in range(K):
-            flush.fill_(k & 0xFF)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            res.append(stepfn())
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        return times, res
-
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     l0 = ctx.launches()
     barrier(world)
     torch.cuda.synchronize()
-    times, res = timed(step, args.steps)
+    times, res = timed_steps(step, args.steps, flush, stream)
     torch.cuda.synchronize()
     barrier(world)
     launches = ctx.launches() - l0
@@ -309,71 +446,22 @@ def run_ours(args, wl, world, rank, local):
     mean_cycles = float(np.mean([r[0].mean() for r in res]))
 
     # ---- per-kernel timing with CUDA events on the library's stream (same steps again)
+    ksteps = max(1, min(args.steps, 3))
     ctx.profile(True)
-    timed(step, args.steps)
+    timed_steps(step, ksteps, flush, stream)
     ctx.profile(False)
     kern = {}
     for kind, name in enumerate(nmg.KERNEL_CLASSES):
         c, ms, units = ctx.profile_read(kind)
         if c:
             kern[name] = {"launches": c, "ms": ms, "units": units}
-    prof_total = sum(v["ms"] for v in kern.values())
-    dom = max(kern, key=lambda k: kern[k]["ms"])
     peaks, peak_src = load_peaks()
-    d = kern[dom]
-    if dom in FLOPS_PER_PX and refine:
-        fl = FLOPS_PER_PX[dom]
-        achieved = fl * d["units"] / (d["ms"] / 1e3) / 1e12
-        issued = MMA_FLOPS_PER_PX[prec][dom] * d["units"] / (d["ms"] / 1e3) / 1e12
-        peak = peaks["bf16_tflops_sustained"]
-        bpu = HIDDEN_DRAM_B_PER_UNIT.get(prec) if dom == "cnn_hidden" else None
-        traffic = bpu * d["units"] / d["launches"] if bpu else None
-        roof = {"kernel": f"{dom} (tcgen05 bf16 3x3 conv)", "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_bytes_per_unit": bpu,
-                "traffic_source": "ncu dram__bytes_read+write of the 128x128 level at 64 RHS, "
-                                  "scaled to this launch's units" if bpu else None,
-                "peak_source": f"{peak_src} bf16_tflops_sustained",
-                "flop_per_unit": fl, "unit_def": "output pixel x active right-hand side",
-                "mma_issued_tflops": issued,
-                "mma_issued_flop_per_unit": MMA_FLOPS_PER_PX[prec][dom],
-                "launch_ms": d["ms"] / d["launches"]}
-    elif dom in FLOPS_PER_PX:
-        achieved = FLOPS_PER_PX[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
-        roof = {"kernel": f"{dom} (fp32 SIMT 3x3 conv)", "bound": "alu", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_source": "152 SMs x 128 fp32 lanes x 2 flop x 2070 MHz (derived)",
-                "flop_per_unit": FLOPS_PER_PX[dom], "launch_ms": d["ms"] / d["launches"]}
-    else:
-        bpu = {"residual": 12, "restrict": 9, "prolong": 9, "filter": 8,
-               "refine_residual": 16}.get(dom, 8)
-        achieved = bpu * d["units"] / (d["ms"] / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peak_src, "bytes_per_unit": bpu,
-                "launch_ms": d["ms"] / d["launches"]}
-    breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                     "share": v["ms"] / prof_total} for k, v in kern.items()}
-    # the memory-bound classes against the measured HBM copy bandwidth:
-    # algorithmic bytes per unit (fine grid point x active right-hand side,
-    # every level of the class together) / class time
-    act_b = {"bf16_refine": 128, "fp16_refine": 128, "bf16fast_refine": 64, "fp32": 128}[prec]
-    hbm_bpu = {"restrict": 9, "refine_residual": 16,
-               "prolong": 9, "filter": 8, "cnn_first": 4 + act_b, "cnn_last": 40}
-    if prec == "fp32":
-        hbm_bpu.pop("cnn_first")
-        hbm_bpu.pop("cnn_last")
-    for k, bpu_k in hbm_bpu.items():
-        if k in kern and kern[k]["ms"] > 0:
-            gbs = bpu_k * kern[k]["units"] / (kern[k]["ms"] / 1e3) / 1e9
-            breakdown[k].update({"bytes_per_unit": bpu_k, "achieved_gbs": gbs,
-                                 "hbm_frac": gbs / peaks["hbm_gbs"]})
+    roof = roofline_of(kern, prec, wl["n"], peaks, peak_src)
+    breakdown = kernel_breakdown(kern, prec, ksteps, peaks)
 
     # ---- the comparison forms on the same GPU and right-hand sides
     compare = {}
     if not args.no_compare:
-        f32 = torch.zeros(f.shape, dtype=torch.float32, device="cuda")
         for p in ["fp32", "bf16fast_refine", "bf16_refine", "fp16_refine"]:
             if p == prec:
                 continue
@@ -383,29 +471,10 @@ def run_ours(args, wl, world, rank, local):
                              device="cuda")
             step_p = (lambda Gp=Gp, up=up: step(Gp, f, up))
             step_p()
-            tp, rp = timed(step_p, max(1, min(args.steps, 2)))
-            compare[p + "_batched"] = {
-                "value": B * len(tp) / (sum(tp) / 1e3), "unit": "RHS/s", "batch": B,
-                "mean_cycles": float(np.mean([r[0].mean() for r in rp])),
-                "max_relres": float(max(r[2].max() for r in rp))}
+            tp, rp = timed_steps(step_p, max(1, min(args.steps, 2)), flush, stream)
+            compare[p + "_batched"] = solve_summary(B, tp, rp)
             Gp.close()
-        # the FNO smoother of Appendix A (fp32 SIMT), where trained FNO
-        # weights for this operator exist
-        fno_w = os.path.join(WEIGHTS, wl.get("fno_weights", ""))
-        if wl.get("fno_weights") and os.path.exists(fno_w):
-            Gf = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"],
-                               taps=taps, precision="fp32", weights=nmg.load_weights(fno_w))
-            uf = torch.zeros(f.shape, dtype=torch.float32, device="cuda")
-            step_f = (lambda Gf=Gf, uf=uf: step(Gf, f, uf))
-            step_f()
-            tf_, rf = timed(step_f, 1)
-            compare["fno_fp32_batched"] = {
-                "value": B * len(tf_) / (sum(tf_) / 1e3), "unit": "RHS/s", "batch": B,
-                "smoother": "FNO (Appendix A), trained, " + wl["fno_weights"],
-                "mean_cycles": float(np.mean([r[0].mean() for r in rf])),
-                "max_relres": float(max(r[2].max() for r in rf)),
-                "converged": bool(all((r[1] == 0).all() for r in rf))}
-            Gf.close()
+            del up
         # plain fp32 single-RHS cycle: one right-hand side per solve call
         Gs = hier("fp32")
         nsingle = min(16, B)
@@ -415,16 +484,24 @@ def run_ours(args, wl, world, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rr1 = []
+        rr1, cc1 = [], []
         for i in range(nsingle):
-            rr1.append(step(Gs, f[i:i + 1], us)[2][0])
+            r1 = step(Gs, f[i:i + 1], us)
+            rr1.append(r1[2][0])
+            cc1.append(r1[0][0])
         e1.record(stream)
         e1.synchronize()
         compare["fp32_single_rhs"] = {
             "value": nsingle / (e0.elapsed_time(e1) / 1e3), "unit": "RHS/s", "batch": 1,
-            "rhs_timed": nsingle, "max_relres": float(max(rr1))}
+            "rhs_timed": nsingle, "mean_cycles": float(np.mean(cc1)),
+            "max_relres": float(max(rr1))}
         Gs.close()
-        del f32
+        compare["headline_vs_fp32_single_rhs"] = value / world / compare["fp32_single_rhs"]["value"]
+
+    # ---- alpha sweep of the workload's operator (its own trained smoothers per alpha)
+    sweep = None
+    if wl.get("sweep") and not args.no_sweep:
+        sweep = sweep_leg(ctx, wl, f, taps, flush, stream, rank)
 
     # ---- end to end through the C ABI with host buffers (pinned): f copied
     # in, the solve from the zero initial guess, u copied back, every step
@@ -439,6 +516,13 @@ def run_ours(args, wl, world, rank, local):
     e2e = {"value": B * world * args.steps / e2e_s, "unit": "RHS/s",
            "h2d_bytes_per_step": int(fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes),
            "call": "nmg_solve_host_zero"}
+    G.close()
+    del u, f
+
+    # ---- the smaller 128x128 problem as a secondary line
+    secondary = None
+    if wl["key"] != "c2" and not args.no_secondary:
+        secondary = secondary_leg(ctx, WORKLOADS["c2"], prec, flush, stream, rank)
 
     # ---- serving: a Poisson stream of mixed-size requests through the
     # continuous-batching server (p50/p99 latency beside throughput)
@@ -447,17 +531,24 @@ def run_ours(args, wl, world, rank, local):
         serving = serving_leg(ctx, rank)
     fno = None
     if not args.no_fno:
-        fno = fno_leg(ctx, wl, B, taps)
+        fno = fno_leg(ctx, WORKLOADS["c2"])
     hbm = None
     if not args.no_hbm_apply:
-        hbm = hbm_apply_leg(ctx, W, flush, stream)
+        hbm = hbm_apply_leg(ctx, flush, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, _, _ = oracle_solve_rate(wl, 2, wl["rhs_seed"])
+        ncyc = 2
+        rate, t_cyc, ocyc = oracle_rate_sample(wl, wl["rhs_seed"], ncyc)
+        rate1, t_cyc1, _ = oracle_rate_sample(wl, wl["rhs_seed"], 1, threads=1)
         cpu = {"value": rate, "unit": "RHS/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"2 of the {B} right-hand sides, full solve to 1e-6 ({dt:.1f} s, "
-                         "numpy FP64, BLAS threads = all host cores)"}
+               "sample": (f"{ncyc} cycles of 1 right-hand side of the workload timed "
+                          f"({t_cyc:.2f} s per cycle, numpy FP64, BLAS threads = all host "
+                          f"cores), scaled by the oracle's own {ocyc} cycles to 1e-6"),
+               "one_core": {"value": rate1, "unit": "RHS/s", "cores": 1,
+                            "s_per_cycle": t_cyc1,
+                            "sample": "1 cycle of 1 right-hand side, every BLAS / OpenMP pool "
+                                      "limited to 1 thread, same scaling"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
@@ -466,15 +557,104 @@ def run_ours(args, wl, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
                 "data": "synthetic",
                 "config": {"workload": wl["name"], "n": wl["n"], "levels": wl["levels"],
+                           "sigma_px": wl["sigma"], "alpha": wl["alpha"],
                            "batch_per_gpu": B, "precision": prec,
                            "precision_detail": PRECISION_TEXT[prec],
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
-                "compare": compare, "roofline": roof, "kernels": breakdown, "cpu_baseline": cpu,
+                "compare": compare, "alpha_sweep": sweep, "roofline": roof,
+                "kernels": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "serving": serving, "fno_smoother": fno, "hbm_apply": hbm}
+                "secondary": secondary, "serving": serving, "fno_smoother": fno,
+                "hbm_apply": hbm}
         print(json.dumps(line), flush=True)
+
+
+SWEEP_ORACLE_SAMPLE = 1  # right-hand sides per alpha checked against the oracle's cycle
+
+
+def sweep_leg(ctx, wl, f, taps, flush, stream, rank):
+    """For each alpha of the workload's sweep, with that operator's trained
+    CNN smoothers: a bf16 split refinement solve of the whole batch to 1e-6
+    (at most 100 cycles), its cycles and residuals, the final residual of
+    sampled right-hand sides recomputed by the FP64 oracle's own apply, and
+    one cycle from zero of the whole batch against the oracle's cycle for a
+    sampled right-hand side (the per-cycle parity bar of the bf16 form is
+    1e-3, element-wise error reported beside the norm-wise one)."""
+    import torch
+    import oracle as O
+    import paper_2603_01064_gb300 as nmg
+    B = f.shape[0]
+    out = []
+    for alpha, wname in wl["sweep"]:
+        Wa = nmg.load_weights(os.path.join(WEIGHTS, wname))
+        G = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=alpha, taps=taps,
+                          precision="bf16_refine", weights=Wa)
+        G.autotune(B)
+        u = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
+        G.solve(f, u, rtol=1e-6, max_cycles=100)
+        tp, rp = timed_steps(lambda: (u.zero_(), G.solve(f, u, rtol=1e-6, max_cycles=100))[1],
+                             1, flush, stream)
+        row = {"alpha": alpha, "weights": wname, **solve_summary(B, tp, rp)}
+        if rank == 0:
+            H = O.build_hierarchy_2d(taps, wl["n"], alpha, wl["levels"])
+            idx = [0, B - 1][:max(1, min(2, B))]
+            fs = f[idx].double().cpu().numpy()
+            row["oracle_relres_sampled"] = [float(v) for v in
+                                            O.relres(H, fs, u[idx].cpu().numpy())]
+            u.zero_()
+            G.cycle(f, u)
+            torch.cuda.synchronize()
+            k = idx[:SWEEP_ORACLE_SAMPLE]
+            ref = O.nmgf(H, Wa, 0, None, f[k].double().cpu().numpy())
+            got = u[k].cpu().numpy()
+            d = (got - ref).reshape(len(k), -1)
+            rf = ref.reshape(len(k), -1)
+            row["one_cycle_vs_oracle"] = {
+                "rhs": k,
+                "normwise": float(np.max(np.linalg.norm(d, axis=1) / np.linalg.norm(rf, axis=1))),
+                "elementwise": float(np.max(np.abs(d).max(axis=1) / np.abs(rf).max(axis=1))),
+                "bar": 1e-3}
+        out.append(row)
+        G.close()
+        del u
+    return out
+
+
+def secondary_leg(ctx, wl, prec, flush, stream, rank):
+    """The 128 x 128 problem (sigma 2 px, alpha 1e-2, 5 levels, 256
+    right-hand sides): the same form batched and the plain fp32 cycle one
+    right-hand side per call."""
+    import torch
+    import paper_2603_01064_gb300 as nmg
+    W = nmg.load_weights(os.path.join(WEIGHTS, wl["weights"]))
+    taps = I.gaussian_taps(wl["sigma"])
+    B = wl["batch"]
+    f = torch.tensor(make_rhs(wl, B, rank_seed(wl, rank)), dtype=torch.float32, device="cuda")
+    out = {"workload": wl["name"]}
+    for p in [prec, "fp32"]:
+        G = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"],
+                          taps=taps, precision=p, weights=W)
+        G.autotune(B)
+        u = torch.zeros(f.shape, dtype=torch.float32 if p == "fp32" else torch.float64,
+                        device="cuda")
+        step = (lambda G=G, u=u: (u.zero_(), G.solve(f, u, rtol=1e-6, max_cycles=100))[1])
+        step()
+        tp, rp = timed_steps(step, 3, flush, stream)
+        out[p + "_batched"] = solve_summary(B, tp, rp)
+        if p == "fp32":
+            us = torch.zeros((1, wl["n"], wl["n"]), dtype=torch.float32, device="cuda")
+            G.solve(f[0:1], us)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(16):
+                us.zero_()
+                G.solve(f[i:i + 1], us)
+            out["fp32_single_rhs"] = {"value": 16 / (time.perf_counter() - t0), "unit": "RHS/s",
+                                      "batch": 1, "rhs_timed": 16}
+        G.close()
+    return out
 
 
 SERVING = dict(requests=800, rate=400.0, seed=4242,
@@ -486,7 +666,7 @@ SERVING = dict(requests=800, rate=400.0, seed=4242,
 FNO = dict(width=64, layers=4, modes=8, ksize=3, seed=0, reps=5)
 
 
-def fno_leg(ctx, wl, B, taps):
+def fno_leg(ctx, wl):
     """The FNO smoother of Appendix A (the paper's 2D hyperparameters at
     h = 1/128: 64 channels, 4 Fourier layers, 3x3 W term; 8 retained modes
     per axis, the most a 16x16 coarsest smoother level holds) applied once to
@@ -497,7 +677,8 @@ def fno_leg(ctx, wl, B, taps):
     truncated DFTs' row passes) + the smaller column passes and mode mixing."""
     import torch
     import paper_2603_01064_gb300 as nmg
-    n, L = wl["n"], wl["levels"]
+    n, L, B = wl["n"], wl["levels"], wl["batch"]
+    taps = I.gaussian_taps(wl["sigma"])
     c, nl, m, k = FNO["width"], FNO["layers"], FNO["modes"], FNO["ksize"]
     W = I.random_fno_weights(L - 1, FNO["seed"], width=c, layers=nl, modes=m, ksize=k)
     G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=wl["alpha"], taps=taps, precision="fp32",
@@ -531,7 +712,7 @@ HBM_APPLY = dict(reps=5, ops=[  # (n, levels, sigma px, alpha, weights, batch)
     (512, 7, 4.0, 1e-2, "c3_2d_n512_s4_a1e-2.npz", 128)])
 
 
-def hbm_apply_leg(ctx, W128, flush, stream):
+def hbm_apply_leg(ctx, flush, stream):
     """The fine-level operator kernels on vectors larger than L2 (134 MB per
     fp32 vector; L2 written over before every launch): the residual
     r = y - A x (12 B per grid point: x, y in, r out), the fused residual +
@@ -544,7 +725,7 @@ def hbm_apply_leg(ctx, W128, flush, stream):
     peaks, src = load_peaks()
     out = []
     for n, L, sg, al, wname, B in HBM_APPLY["ops"]:
-        Wx = W128 if n == 128 else nmg.load_weights(os.path.join(WEIGHTS, wname))
+        Wx = nmg.load_weights(os.path.join(WEIGHTS, wname))
         G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=al, taps=I.gaussian_taps(sg),
                           precision="fp32", weights=Wx)
         G.autotune(B)
@@ -614,7 +795,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling runs)")
     ap.add_argument("--ncu", action="store_true", help="a single solve, nothing else (profiling)")
@@ -622,6 +803,8 @@ def main():
                     help="launch-shape choices file (read if present, else written)")
     ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the alpha sweep")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 128x128 line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-fno", action="store_true", help="skip the FNO smoother timing")
     ap.add_argument("--no-hbm-apply", action="store_true",
@@ -629,9 +812,16 @@ def main():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured iterations "
                          "(profiler launch lists)")
+    ap.add_argument("--oracle-cycle-probe", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--probe-seed", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload], key=args.workload)
+    if args.oracle_cycle_probe:
+        # child process of the one-core CPU baseline (thread pools set by the parent)
+        t = oracle_cycle_time(wl, args.probe_seed, args.oracle_cycle_probe)
+        print(json.dumps({"s_per_cycle": t}))
+        return
     world, rank, local = dist_init()
-    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, world, rank)
     else:

@@ -1,7 +1,7 @@
 """The bench's reference arm (the FP64 oracle timed on the host cores) runs
 without a GPU: one JSON line with the contract's keys, on the same metric,
-unit and workload as the CUDA arm, and a cpu_baseline / e2e describing the
-run itself.  The CUDA arm's keys are checked on the GPU by running it."""
+unit and workload (512 x 512, sigma 4 px, alpha 1e-2) as the CUDA arm, and a
+cpu_baseline / e2e describing the run itself.  The CUDA arm's keys are checked on the GPU by running it."""
 import json
 import os
 import subprocess
@@ -20,7 +20,7 @@ def test_reference_arm_json_line():
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    wl = bench.WORKLOADS["c2"]
+    wl = bench.WORKLOADS["c3"]
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == "RHS/s"
     assert d["higher_is_better"] is True and d["scaling"] == "weak"
@@ -30,6 +30,10 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert cb["unit"] == d["unit"] and cb["sample"]
+    # the sample is one oracle cycle per step, scaled by the oracle's own
+    # cycle count to 1e-6, stored for this workload
+    assert wl["name"] in json.load(open(os.path.join(ROOT, "tests", "golden",
+                                                      "oracle_cycles.json")))
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

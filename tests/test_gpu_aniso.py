@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import nmg_inputs as I  # noqa: E402
 import oracle as O  # noqa: E402
+from parity_err import rel_both  # noqa: E402
 import paper_2603_01064_gb300 as nmg  # noqa: E402
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -25,7 +26,8 @@ N, L, ALPHA = 256, 3, 1e-5
 
 
 def rel(a, b):
-    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    """Per-RHS max(norm-wise, element-wise) relative error."""
+    return rel_both(a, b)
 
 
 @pytest.fixture(scope="module")

@@ -29,6 +29,7 @@ pytestmark = pytest.mark.gpu
 
 import nmg_inputs as I  # noqa: E402
 import oracle as O  # noqa: E402
+from parity_err import rel_both  # noqa: E402
 from oracle import nmg_oracle as ON  # noqa: E402
 import paper_2603_01064_gb300 as nmg  # noqa: E402
 
@@ -81,9 +82,8 @@ def make(ctx, prec="bf16_refine", n=64, levels=4, sigma=2.0, alpha=1e-2, seed=21
 
 
 def rel(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1))
+    """Largest per-RHS max(norm-wise, element-wise) relative error."""
+    return np.max(rel_both(a, b))
 
 
 def smooth_gpu(G, l, b):

@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 import nmg_inputs as I  # noqa: E402
 import oracle as O  # noqa: E402
+from parity_err import rel_both  # noqa: E402
 import paper_2603_01064_gb300 as nmg  # noqa: E402
 
 N, L, ALPHA, SIGMA = 64, 3, 1e-2, 2.0
@@ -30,9 +31,8 @@ TOL_CYCLE = {"fp64": 1e-10, "fp32": 1e-5}
 
 
 def rel(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+    """Per-RHS max(norm-wise, element-wise) relative error."""
+    return rel_both(a, b)
 
 
 @pytest.fixture(scope="module")

@@ -24,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 import nmg_inputs as I  # noqa: E402
 import oracle as O  # noqa: E402
+from parity_err import rel_both  # noqa: E402
 import paper_2603_01064_gb300 as nmg  # noqa: E402
 
 WDIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -32,9 +33,8 @@ SAMPLE = [0, 77, 190, 255]
 
 
 def rel(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    """Per-RHS max(norm-wise, element-wise) relative error."""
+    return rel_both(a, b)
 
 
 @pytest.fixture(scope="module")

@@ -13,6 +13,7 @@ pytestmark = pytest.mark.gpu
 
 import nmg_inputs as I  # noqa: E402
 import oracle as O  # noqa: E402
+from parity_err import rel_both  # noqa: E402
 import paper_2603_01064_gb300 as nmg  # noqa: E402
 
 TOL_STEP = {"fp64": 1e-12, "fp32": 2e-5}
@@ -21,9 +22,8 @@ DT = {"fp64": torch.float64, "fp32": torch.float32}
 
 
 def relerr(a, b):
-    a = np.asarray(a, np.float64).reshape(a.shape[0], -1)
-    b = np.asarray(b, np.float64).reshape(b.shape[0], -1)
-    return np.max(np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300))
+    """Largest per-RHS max(norm-wise, element-wise) relative error."""
+    return np.max(rel_both(a, b))
 
 
 @pytest.fixture(scope="module")
