@@ -62,8 +62,12 @@ WORKLOADS = {
                weights="c2_2d_n128_s2_a1e-2.npz", fno_weights="c2f_2d_n128_s2_a1e-2_fno.npz"),
 }
 PRECISION_TEXT = {
-    "bf16_refine": "bf16 tensor-core smoother with split hi+lo bf16 operands and fp32 accumulation, "
-                   "fp32 cycle vectors, compensated-fp32 outer residual, fp64 update and coarse solve",
+    "bf16_refine": "bf16 tensor-core smoother, every operand three bf16 terms (six products per "
+                   "product, fp32 accumulation), fp32 cycle vectors, compensated-fp32 outer "
+                   "residual, fp64 update and coarse solve",
+    "bf16x3_refine": "bf16 tensor-core smoother with hi+lo bf16 operand pairs (three products) and "
+                     "fp32 accumulation, fp32 cycle vectors, compensated-fp32 outer residual, fp64 "
+                     "update and coarse solve",
     "bf16fast_refine": "bf16 tensor-core smoother (one bf16 per operand, fp32 accumulation), fp32 "
                        "cycle vectors, compensated-fp32 outer residual, fp64 update and coarse solve",
     "fp16_refine": "fp16 tensor-core smoother with split hi+lo fp16 operands (power-of-two scaled "
@@ -71,7 +75,8 @@ PRECISION_TEXT = {
                    "residual, fp64 update and coarse solve",
     "fp32": "fp32 throughout (SIMT smoother), fp64 coarse solve",
 }
-DTYPE = {"bf16_refine": "bf16x2+f32+f64", "bf16fast_refine": "bf16+f32+f64",
+DTYPE = {"bf16_refine": "bf16x3+f32+f64", "bf16x3_refine": "bf16x2+f32+f64",
+         "bf16fast_refine": "bf16+f32+f64",
          "fp16_refine": "f16x2+f32+f64", "fp32": "f32"}
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x fp32 lanes x FMA x max clock
@@ -83,8 +88,10 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # level 0; summarised under profiles/); None where no capture exists
 HIDDEN_DRAM_B_PER_UNIT = {("bf16_refine", 128): 109.9}
 MMA_FLOPS_PER_PX = {
-    # split form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
-    "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
+    # three-term form per tap and K half: a1 x N = 96 ([w1 | w2 | w3]), a2 x N = 64, a3 x N = 32
+    "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (96 + 64 + 32)},
+    # pair form per tap and K half: hi A x N = 64 ([w_hi | w_lo]) and lo A x N = 32 (w_hi)
+    "bf16x3_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
     "bf16fast_refine": {"cnn_hidden": 2 * 9 * 32 * 32},
     "fp16_refine": {"cnn_hidden": 2 * 9 * 32 * (64 + 32)},
 }
@@ -366,7 +373,8 @@ def kernel_breakdown(kern, prec, steps, peaks):
     # the memory-bound classes against the measured HBM copy bandwidth:
     # algorithmic bytes per unit (grid point x active right-hand side, every
     # level of the class together) / class time
-    act_b = {"bf16_refine": 128, "fp16_refine": 128, "bf16fast_refine": 64, "fp32": 128}[prec]
+    act_b = {"bf16_refine": 192, "bf16x3_refine": 128, "fp16_refine": 128, "bf16fast_refine": 64,
+             "fp32": 128}[prec]
     hbm_bpu = {"restrict": 9, "refine_residual": 16,
                "prolong": 9, "filter": 8, "cnn_first": 4 + act_b, "cnn_last": 40}
     if prec == "fp32":
@@ -462,7 +470,7 @@ def run_ours(args, wl, world, rank, local):
     # ---- the comparison forms on the same GPU and right-hand sides
     compare = {}
     if not args.no_compare:
-        for p in ["fp32", "bf16fast_refine", "bf16_refine", "fp16_refine"]:
+        for p in ["fp32", "bf16fast_refine", "bf16x3_refine", "bf16_refine", "fp16_refine"]:
             if p == prec:
                 continue
             Gp = hier(p)

@@ -34,6 +34,7 @@
  *      NMG_FP64          f, u, every level vector: double
  *      NMG_FP32          f, u, every level vector: float
  *      NMG_BF16_REFINE,
+ *      NMG_BF16X3_REFINE,
  *      NMG_BF16FAST_REFINE,
  *      NMG_FP16_REFINE   f: float, u: double; level vectors of the inner
  *                        cycle (step entry points): float.  The smoother
@@ -72,25 +73,35 @@ enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };
  * an outer iterative refinement (residual in compensated fp32, update in
  * fp64) with the smoother's hidden layers on 16-bit tensor cores and fp32
  * accumulation:
- *   NMG_BF16_REFINE      every hidden-layer operand is a pair of bf16
- *                        values (hi + lo, 2^-16 relative), 2 MMAs per
- *                        product; per-cycle iterates agree with fp64 to
- *                        1e-4..1e-3 depending on how strongly the trained
- *                        smoother amplifies rounding.
+ *   NMG_BF16_REFINE      every hidden-layer operand (activation and
+ *                        weight) is a sum of three bf16 values (fp32-level,
+ *                        2^-24 relative); each product takes the six MMAs
+ *                        of its terms down to order 2^-16 (three MMA
+ *                        instructions, 6x the MMA work of one bf16
+ *                        product); per-cycle iterates agree with fp64 to
+ *                        about 1e-5 even for trained smoothers that amplify
+ *                        rounding strongly.
+ *   NMG_BF16X3_REFINE    every hidden-layer operand is a pair of bf16
+ *                        values (hi + lo, 2^-16 relative), three products
+ *                        a_hi*w_hi + a_hi*w_lo + a_lo*w_hi (2 MMA
+ *                        instructions, 3x the MMA work); per-cycle iterates
+ *                        agree with fp64 to 1e-4..2e-3 depending on how
+ *                        strongly the trained smoother amplifies rounding.
  *   NMG_BF16FAST_REFINE  one bf16 value per operand, 1 MMA per product;
  *                        the cycle converges at the same rate but single
  *                        cycles differ from fp64 by percents.
- *   NMG_FP16_REFINE      as NMG_BF16_REFINE with fp16 pairs (2^-22
+ *   NMG_FP16_REFINE      as NMG_BF16X3_REFINE with fp16 pairs (2^-22
  *                        relative) at the same cost; the network runs on
  *                        power-of-two-scaled values to stay inside fp16's
  *                        range (activations above 65504 are clamped).
- * All three take f: float, u: double, like NMG_BF16_REFINE above. */
+ * All four take f: float, u: double, like NMG_BF16_REFINE above. */
 typedef enum {
   NMG_FP64 = 0,
   NMG_FP32 = 1,
   NMG_BF16_REFINE = 2,
   NMG_BF16FAST_REFINE = 3,
-  NMG_FP16_REFINE = 4
+  NMG_FP16_REFINE = 4,
+  NMG_BF16X3_REFINE = 5
 } nmg_precision;
 
 /*
@@ -411,6 +422,24 @@ nmg_status nmg_hier_tuning(const nmg_hier* h, int level, int* res_tile, int* rst
  * rtol).  enable = 0 launches every kernel eagerly instead.  Profiling
  * (nmg_profile_enable) always launches eagerly.  Default: enabled. */
 nmg_status nmg_set_graphs(nmg_ctx* ctx, int enable);
+
+/* Bound of every device-side wait of the tensor-core kernels (mbarrier
+ * waits between their copy, MMA and epilogue roles), in nanoseconds; 2 s by
+ * default.  A launch whose wait runs out stops its roles, lets the copies
+ * and MMAs it already issued complete, releases its tensor memory and
+ * returns; the solve that ran it stops after that iteration and returns
+ * NMG_ERR_TIMEOUT (the context and hierarchy stay usable).  Read by the
+ * kernels at launch, so it also applies to already captured graphs.
+ * Synchronous.  NMG_ERR_ARG if ns <= 0. */
+nmg_status nmg_set_wait_limit(nmg_ctx* ctx, long long ns);
+
+/* Failure-injection hook for tests (the paper has no counterpart): while
+ * enable != 0, the MMA issuers of every warp-specialised tensor-core
+ * smoother launch on this context (levels of side >= 32 in the refinement
+ * precisions) first wait on a barrier that nothing arrives at, so each
+ * launch ends by the wait limit above and the solve reports NMG_ERR_TIMEOUT.
+ * No fault is raised on the device.  Synchronous. */
+nmg_status nmg_inject_stall(nmg_ctx* ctx, int enable);
 
 /* Wait for the context's stream. */
 nmg_status nmg_sync(nmg_ctx* ctx);

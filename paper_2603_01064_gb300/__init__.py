@@ -16,17 +16,18 @@ from typing import Sequence
 import numpy as np
 
 __all__ = [
-    "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "FP16_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
+    "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "FP16_REFINE", "BF16X3_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
     "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo", "solve_multi", "Server",
     "NOALLOC_SCRATCH_BYTES",
 ]
 
-FP64, FP32, BF16_REFINE, BF16FAST_REFINE, FP16_REFINE = 0, 1, 2, 3, 4
+FP64, FP32, BF16_REFINE, BF16FAST_REFINE, FP16_REFINE, BF16X3_REFINE = 0, 1, 2, 3, 4, 5
 # kernel classes of Context.profile_read (NMG_K_* in nmg.h)
 KERNEL_CLASSES = ["residual", "restrict", "cnn_first", "cnn_hidden", "cnn_last", "filter",
                   "coarse", "prolong", "refine_residual", "other", "cnn_fused"]
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE,
-              "bf16fast_refine": BF16FAST_REFINE, "fp16_refine": FP16_REFINE}
+              "bf16fast_refine": BF16FAST_REFINE, "fp16_refine": FP16_REFINE,
+              "bf16x3_refine": BF16X3_REFINE}
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 1 << 20  # NMG_NOALLOC_SCRATCH_BYTES in nmg.h
 
@@ -113,6 +114,8 @@ def lib():
         "nmg_launch_count": (ctypes.c_longlong, [P]),
         "nmg_profile_enable": (I, [P, I]),
         "nmg_set_graphs": (I, [P, I]),
+        "nmg_set_wait_limit": (I, [P, ctypes.c_longlong]),
+        "nmg_inject_stall": (I, [P, I]),
         "nmg_autotune": (I, [P, P, I, ctypes.c_char_p]),
         "nmg_hier_tuning": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                 ctypes.POINTER(I)]),
@@ -236,6 +239,15 @@ class Context:
     def set_graphs(self, enable: bool):
         """Replay captured CUDA graphs per outer iteration (default) or launch eagerly."""
         self.check(lib().nmg_set_graphs(self._h, 1 if enable else 0))
+
+    def set_wait_limit(self, ns: int):
+        """Bound of every device wait of the tensor-core kernels, in ns."""
+        self.check(lib().nmg_set_wait_limit(self._h, int(ns)))
+
+    def inject_stall(self, enable: bool):
+        """Test hook: tensor-core smoother launches give up on a wait that
+        nothing ends (after the wait limit), reporting NMG_ERR_TIMEOUT."""
+        self.check(lib().nmg_inject_stall(self._h, 1 if enable else 0))
 
     def profile(self, enable: bool):
         self.check(lib().nmg_profile_enable(self._h, 1 if enable else 0))

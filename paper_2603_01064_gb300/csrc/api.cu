@@ -27,7 +27,7 @@
 namespace nmg {
 void bf16_cnn_launch(int n, int B, int map_imgs, int layers, const void* pack, const float* b,
                      const double* s, float* act0, float* act1, float* h, const int* active,
-                     int* err, cudaStream_t st, LaunchLog& log);
+                     int* err, const long long* ctl, cudaStream_t st, LaunchLog& log);
 void bf16_cnn_forget(const void* pack);
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W, const std::vector<const double*>& bias,
                     int split);
@@ -55,6 +55,10 @@ struct nmg_ctx {
   std::vector<const void*> mkey;
   double mrtol = -1.0;
   long long mkernels = 0;
+  // device control words read by the tensor-core kernels at launch (so that
+  // captured graphs see later changes): [0] the bound of every device wait
+  // in nanoseconds, [1] the stall test hook (nmg_inject_stall)
+  long long* ctl = nullptr;
 };
 
 namespace {
@@ -166,9 +170,12 @@ nmg_status cuda_fail(nmg_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 size_t elem_size(int precision) { return precision == NMG_FP64 ? 8 : 4; }
+
+// default bound of every device wait of the tensor-core kernels
+constexpr long long kDefaultWaitNs = 2000000000LL;
 bool is_refine(int precision) {
   return precision == NMG_BF16_REFINE || precision == NMG_BF16FAST_REFINE ||
-         precision == NMG_FP16_REFINE;
+         precision == NMG_FP16_REFINE || precision == NMG_BF16X3_REFINE;
 }
 
 size_t plane(const nmg_hier* h, int l) {
@@ -251,11 +258,16 @@ nmg_status ensure_work(nmg_hier* h, int B) {
   AL(B * sizeof(int), w.cycles);
   AL(B * sizeof(int), w.active);
   AL(B * sizeof(int), w.ones);
-  AL(sizeof(int), w.nactive);
-  AL(sizeof(int), w.err);
+  // [0]: right-hand sides still active, [1]: the error word of bounded
+  // device waits (0 = ok); both copied to the host after every iteration
+  AL(2 * sizeof(int), w.nactive);
+  w.err = w.nactive + 1;
   if (h->dim == 2 && h->L > 1) {
     size_t n0 = plane(h, 0);
-    size_t actb = (size_t)h->width * n0 * B * (h->precision == NMG_FP64 ? 8 : 4);
+    // bytes per channel and grid point: fp64 / fp32 (SIMT forms), two 16-bit
+    // terms (pair forms, one in the fast form), three (three-term bf16 form)
+    size_t actb = (size_t)h->width * n0 * B *
+                  (h->precision == NMG_FP64 ? 8 : h->precision == NMG_BF16_REFINE ? 6 : 4);
     AL(actb, w.act0);
     AL(actb, w.act1);
     AL(n0 * B * 2 * es, w.cbuf);
@@ -270,7 +282,7 @@ nmg_status ensure_work(nmg_hier* h, int B) {
     AL(plane(h, 0) * B * sizeof(float), w.d32);
   }
   {
-    cudaError_t e = cudaMallocHost(&w.h_nactive, sizeof(int));
+    cudaError_t e = cudaMallocHost(&w.h_nactive, 2 * sizeof(int));
     if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "cudaMallocHost"); }
   }
   {
@@ -532,8 +544,9 @@ nmg_status run_outer(nmg_hier* h, int B, const void* f, const void* u, double rt
       test();
     }
     CK(cudaStreamSynchronize(st));
-    nactive = *w.h_nactive;
+    nactive = w.h_nactive[0];
     ctx->log.active_hint = nactive;
+    if (w.h_nactive[1]) break;  // a device wait gave up: reported below
   }
   CK(cudaGetLastError());
   {
@@ -583,9 +596,14 @@ nmg_status run_outer_multi(nmg_ctx* ctx, std::vector<OuterItem>& items, const st
   }
   for (auto& it : items) it.test();
   CK(cudaStreamSynchronize(st));
+  // right-hand sides still active over all items; 0 once a device wait of
+  // any item gave up (finish_item reports it)
   auto any_active = [&]() {
     int tot = 0;
-    for (auto& it : items) tot += *it.h->w.h_nactive;
+    for (auto& it : items) {
+      if (it.h->w.h_nactive[1]) return 0;
+      tot += it.h->w.h_nactive[0];
+    }
     return tot;
   };
   int nact = any_active();
@@ -677,7 +695,7 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     cudaMemsetAsync(w.nactive, 0, sizeof(int), ctx->stream);
     launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, ctx->stream,
                     ctx->log);
-    cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(w.h_nactive, w.nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   };
   auto step = [&]() {
     cycle_body<T>(h, B, f, u, u, b0, w.s[0], w.active);
@@ -701,7 +719,7 @@ nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rt
     cudaMemsetAsync(w.nactive, 0, sizeof(int), ctx->stream);
     launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, ctx->stream,
                     ctx->log);
-    cudaMemcpyAsync(w.h_nactive, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(w.h_nactive, w.nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   };
   auto step = [&]() {
     // inner bf16 cycle on (0, r): d = NMGF(0, r); u += d in fp64
@@ -762,7 +780,7 @@ OuterItem make_item(nmg_hier* h, int B, const void* f, void* u, double rtol,
       cudaMemsetAsync(w->nactive, 0, sizeof(int), c->stream);
       launch_converge(w->s[0], w->fn, rtol, B, w->active, w->relres, w->status, w->nactive,
                       c->stream, c->log);
-      cudaMemcpyAsync(w->h_nactive, w->nactive, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(w->h_nactive, w->nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     };
     it.step = [h, B, f, u, w, dbl]() {
       nmg_ctx* c = h->ctx;
@@ -785,7 +803,7 @@ OuterItem make_item(nmg_hier* h, int B, const void* f, void* u, double rtol,
       cudaMemsetAsync(w->nactive, 0, sizeof(int), c->stream);
       launch_converge(w->s[0], w->fn, rtol, B, w->active, w->relres, w->status, w->nactive,
                       c->stream, c->log);
-      cudaMemcpyAsync(w->h_nactive, w->nactive, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(w->h_nactive, w->nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     };
     it.step = [h, B, u, w]() {
       nmg_ctx* c = h->ctx;
@@ -839,7 +857,32 @@ nmg_status nmg_create(nmg_ctx** out, int device, void* stream) {
   }
   e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return NMG_ERR_CUDA;
+  {
+    const long long ctl0[2] = {kDefaultWaitNs, 0};
+    e = cudaMalloc(&ctx->ctl, sizeof(ctl0));
+    if (e != cudaSuccess) return NMG_ERR_OOM;
+    e = cudaMemcpy(ctx->ctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return NMG_ERR_CUDA;
+  }
   *out = ctx.release();
+  return NMG_OK;
+}
+
+nmg_status nmg_set_wait_limit(nmg_ctx* ctx, long long ns) {
+  if (!ctx) return NMG_ERR_ARG;
+  if (ns <= 0) return fail(ctx, NMG_ERR_ARG, "wait limit must be positive");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(ctx->ctl, &ns, sizeof(ns), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return NMG_OK;
+}
+
+nmg_status nmg_inject_stall(nmg_ctx* ctx, int enable) {
+  if (!ctx) return NMG_ERR_ARG;
+  const long long v = enable ? 1 : 0;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(ctx->ctl + 1, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return NMG_OK;
 }
 
@@ -853,6 +896,7 @@ void nmg_destroy(nmg_ctx* ctx) {
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->mexec) cudaGraphExecDestroy(ctx->mexec);
+  if (ctx->ctl) cudaFree(ctx->ctl);
   for (cudaStream_t sd : ctx->side) cudaStreamDestroy(sd);
   for (cudaEvent_t ev : ctx->fork_join) cudaEventDestroy(ev);
   delete ctx;
@@ -862,7 +906,7 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
                      nmg_hier** out) {
   if (!ctx || !op || !out) return fail(ctx, NMG_ERR_ARG, "null argument to nmg_setup");
   *out = nullptr;
-  if (op->precision < NMG_FP64 || op->precision > NMG_FP16_REFINE)
+  if (op->precision < NMG_FP64 || op->precision > NMG_BF16X3_REFINE)
     return fail(ctx, NMG_ERR_ARG, "unknown precision");
   if (is_refine(op->precision) && op->dim != 2)
     return fail(ctx, NMG_ERR_UNSUPPORTED, "the bf16 refinement form is 2D only");
@@ -1044,8 +1088,9 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
           bp.push_back(base + o);
           o += cout;
         }
-        const int split = h->precision == NMG_BF16_REFINE   ? 1
-                          : h->precision == NMG_FP16_REFINE ? 2
+        const int split = h->precision == NMG_BF16_REFINE     ? 3
+                          : h->precision == NMG_BF16X3_REFINE ? 1
+                          : h->precision == NMG_FP16_REFINE   ? 2
                                                             : 0;
         d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp, split);
         if (!d.bf16_pack) st = fail(ctx, NMG_ERR_UNSUPPORTED, "bf16 tensor-core smoother unavailable");
@@ -1995,8 +2040,8 @@ void launch_cnn2d_bf16_dispatch(nmg_hier* h, int l, int B, const float* b, const
                                 float* out, const int* active) {
   DevLevel& d = h->lv[l];
   bf16_cnn_launch(d.n, B, B, h->layers, d.bf16_pack, b, s, reinterpret_cast<float*>(h->w.act0),
-                  reinterpret_cast<float*>(h->w.act1), out, active, h->w.err, h->ctx->stream,
-                  h->ctx->log);
+                  reinterpret_cast<float*>(h->w.act1), out, active, h->w.err, h->ctx->ctl,
+                  h->ctx->stream, h->ctx->log);
 }
 
 void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const float* f,

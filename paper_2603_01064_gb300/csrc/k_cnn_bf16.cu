@@ -37,6 +37,17 @@
 // product is formed from bf16 MMAs a_hi*w_hi + a_hi*w_lo + a_lo*w_hi,
 // accumulated in fp32.  The SIMT layers compute in fp32.
 //
+// Three-term bf16 form (SPLIT = 3): every operand is a sum of three bf16
+// values, v = v1 + v2 + v3 (each the bf16 rounding of what the previous
+// terms leave, 2^-25 relative together: fp32-level), activations in chunks
+// 0-3 / 4-7 / 8-11, weights in three 32-column blocks of B.  Each product
+// is formed from the six MMAs whose terms are of order 2^-16 or larger,
+// a1*(w1 + w2 + w3) + a2*(w1 + w2) + a3*w1, accumulated in fp32; the dropped
+// products are below 2^-24 relative.  Trained smoothers with large,
+// cancelling weights amplify the pair forms' 2^-16 .. 2^-18 errors (of the
+// activations and of the weights alike) past a 1e-3 per-cycle error; this
+// form keeps a cycle within about 1e-5 of fp64.
+//
 // fp16 split form (SPLIT = 2): the same [hi | lo] pairs and MMAs with fp16
 // operands (11-bit significands: hi + lo carries 2^-22 instead of 2^-16).
 // fp16's range is narrow, so the network runs on sigma-scaled values: the
@@ -66,12 +77,28 @@ constexpr int RH = TILE + 2;            // staged input rows
 constexpr int CH_BYTES = RH * RW * 16;  // one 8-channel chunk of the staged tile
 constexpr int WIDTH = 32;
 constexpr int THREADS = 128;
-// MMA N: fast form 32 output channels; split form 64 = [w_hi | w_lo] so that
-// the hi A operand's MMA forms both a_hi*w_hi and a_hi*w_lo (summed in the
-// epilogue); the lo A operand's MMA uses N = 32 (w_hi only)
-template <int SPLIT> struct NB { static constexpr int value = SPLIT ? 64 : 32; };
-template <int SPLIT> struct TMC { static constexpr int value = SPLIT ? 256 : 128; };  // TMEM columns
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bound of every mbarrier wait
+// 16-bit terms per operand: 1 (fast form), 2 (pair forms), 3 (SPLIT = 3)
+template <int SPLIT> struct TERMS { static constexpr int value = SPLIT == 3 ? 3 : (SPLIT ? 2 : 1); };
+// MMA N of the hi A operand: one 32-column block per weight term.  Pair
+// forms: 64 = [w_hi | w_lo], so the hi A operand's MMA forms a_hi*w_hi and
+// a_hi*w_lo (summed in the epilogue) and the lo A operand's MMA uses N = 32
+// (w_hi only).  SPLIT = 3: 96 = [w_1 | w_2 | w_3]; the middle A term takes
+// N = 64 ([w_1 | w_2]) and the last N = 32 (w_1).
+template <int SPLIT> struct NB { static constexpr int value = 32 * TERMS<SPLIT>::value; };
+// TMEM columns allocated: two accumulators of NT x NB columns, rounded up to
+// a power of two
+template <int SPLIT> struct TMC { static constexpr int value = SPLIT == 3 ? 512 : (SPLIT ? 256 : 128); };
+// 8-channel chunk planes of one pixel's activations (4 per term)
+template <int SPLIT> struct ACHS { static constexpr int value = 4 * TERMS<SPLIT>::value; };
+// Every mbarrier wait is bounded by the context's wait limit (ctl[0], in
+// nanoseconds, set on the host; 2 s by default).  A block that gives up
+// records the error, stops its roles and then drains what it still has in
+// flight (its tensor-copy writes into shared memory, its MMAs into tensor
+// memory) before it releases tensor memory and exits; those drain waits are
+// bounded by kDrainNs, not by the settable limit.  ctl[1] != 0 is a test
+// hook: the MMA issuers of the warp-specialised kernel first wait on a
+// barrier nothing arrives at, so the launch gives up after the wait limit.
+constexpr unsigned long long kDrainNs = 1000000000ull;
 constexpr int B_HALF = 9 * 4 * WIDTH * 16;  // bf16 weights of a hidden layer for N = 32
 
 // per layer: hidden layers use bf16 weights in the MMA B layout
@@ -167,14 +194,23 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// wait for a phase of an mbarrier, giving up after kWaitLimitNs
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+// wait for a phase of an mbarrier, giving up after limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity,
+                                                  unsigned long long limit_ns) {
   if (mbar_try_wait(mbar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (unsigned it = 1;; ++it) {
     if (mbar_try_wait(mbar, parity)) return true;
-    if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    if ((it & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// commit every MMA this thread issued to `mbar` and wait (bounded by
+// kDrainNs) until they have completed: their tensor-memory writes are done
+__device__ __forceinline__ void drain_mmas(uint32_t mbar, int* err) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+  if (!mbar_wait_bounded(mbar, 0u, kDrainNs)) atomicExch(err, 2);
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
@@ -211,6 +247,30 @@ template <int SPLIT>
 __device__ __forceinline__ void store_pixel_planar(const float* a, __nv_bfloat16* px0,
                                                    size_t cstride) {
   if (!px0) return;
+  if (SPLIT == 3) {
+    // three bf16 terms: t1 = bf16(a), t2 = bf16(a - t1), t3 = bf16(a - t1 - t2)
+    // (both differences are exact in fp32)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t t1[4], t2[4], t3[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float a0 = a[8 * q + 2 * c], a1 = a[8 * q + 2 * c + 1];
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+        const float r0 = a0 - __low2float(h2), r1 = a1 - __high2float(h2);
+        const __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
+        const __nv_bfloat162 l2 =
+            __floats2bfloat162_rn(r0 - __low2float(m2), r1 - __high2float(m2));
+        t1[c] = *reinterpret_cast<const uint32_t*>(&h2);
+        t2[c] = *reinterpret_cast<const uint32_t*>(&m2);
+        t3[c] = *reinterpret_cast<const uint32_t*>(&l2);
+      }
+      *reinterpret_cast<uint4*>(px0 + q * cstride) = make_uint4(t1[0], t1[1], t1[2], t1[3]);
+      *reinterpret_cast<uint4*>(px0 + (4 + q) * cstride) = make_uint4(t2[0], t2[1], t2[2], t2[3]);
+      *reinterpret_cast<uint4*>(px0 + (8 + q) * cstride) = make_uint4(t3[0], t3[1], t3[2], t3[3]);
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     uint32_t hi[4], lo[4];
@@ -247,7 +307,7 @@ __global__ void __launch_bounds__(256)
 k_first_simt(int n, const float* __restrict__ bsrc, __nv_bfloat16* __restrict__ aout,
              const __grid_constant__ FirstW fw, const double* __restrict__ snorm,
              const int* __restrict__ active, int tiles_x) {
-  constexpr int ACHN = SPLIT ? 8 : 4;  // chunk planes per image
+  constexpr int ACHN = ACHS<SPLIT>::value;  // chunk planes per image
   const int b = blockIdx.y;
   if (!active[b]) return;
   // ||b|| = 0 (tested on the bits): h = 0 is written by the last layer.
@@ -313,8 +373,11 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
   constexpr int N = NB<SPLIT>::value;
   constexpr uint32_t idesc = make_idesc(128, N, SPLIT == 2);
   // lo A operand: N = 32 (w_hi only, the first 32 rows of B) accumulating
-  // into the hi columns; a_lo * w_lo (~2^-32 relative) is not formed
+  // into the hi columns; a_lo * w_lo (~2^-32 relative) is not formed.
+  // SPLIT = 3: the middle A term with N = 64 ([w_1 | w_2], the first 64
+  // rows of B) and the last with N = 32 (w_1)
   constexpr uint32_t idesc_lo = make_idesc(128, 32, SPLIT == 2);
+  constexpr uint32_t idesc_mid = make_idesc(128, 64, false);
   const uint64_t ad0 = make_desc(a_base, PITCH, RW * 16);
   const uint64_t bd0 = make_desc(b_base, N * 16, 128);
   // the M tiles' accumulation chains are interleaved (consecutive MMAs write
@@ -330,7 +393,15 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a_base, uint32_t b_base
         const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
         mma_bf16(d, ad0 + aoff, bd0 + boff, idesc, (tap | kh) ? 1u : 0u);
       }
-      if (SPLIT) {
+      if (SPLIT == 3) {
+#pragma unroll
+        for (int mt = MT0; mt < MT0 + MTN; ++mt) {
+          const uint32_t d = d0 + mt * N;
+          const uint32_t aoff = (2 * kh * PITCH + ((tap / 3) * RW + 8 * mt + (tap % 3)) * 16) >> 4;
+          mma_bf16(d, ad0 + aoff + ((4 * PITCH) >> 4), bd0 + boff, idesc_mid, 1u);
+          mma_bf16(d, ad0 + aoff + ((8 * PITCH) >> 4), bd0 + boff, idesc_lo, 1u);
+        }
+      } else if (SPLIT) {
 #pragma unroll
         for (int mt = MT0; mt < MT0 + MTN; ++mt) {
           const uint32_t d = d0 + mt * N;
@@ -356,7 +427,20 @@ __device__ __forceinline__ void finish_pixel(uint32_t taddr, const float* __rest
                                              bool store) {
   float v[32];
   tmem_ld32(taddr, v);
-  if (SPLIT) {
+  if (SPLIT == 3) {
+    // the w_2 and w_3 column blocks added in turn (one 32-column block of
+    // registers at a time)
+#pragma unroll
+    for (int blk = 1; blk < 3; ++blk) {
+      float w[32];
+      tmem_ld32(taddr + 32 * blk, w);
+#pragma unroll
+      for (int c = 0; c < 32; c += 2) {
+        unsigned long long* vp = reinterpret_cast<unsigned long long*>(&v[c]);
+        asm("add.rn.f32x2 %0, %0, %1;" : "+l"(*vp) : "l"(*reinterpret_cast<const unsigned long long*>(&w[c])));
+      }
+    }
+  } else if (SPLIT) {
     float w[32];
     tmem_ld32(taddr + 32, w);
 #pragma unroll
@@ -439,10 +523,10 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
             __nv_bfloat16* __restrict__ aout, float* __restrict__ gout, LayerPack lp,
             const float* __restrict__ w4, const __grid_constant__ OutW ow,
             const double* __restrict__ snorm, const int* __restrict__ active,
-            int* __restrict__ err, int nbuf) {
-  constexpr int ACH = SPLIT ? 8 : 4;  // 8-channel chunks per staged pixel
+            int* __restrict__ err, int nbuf, const long long* __restrict__ ctl) {
+  constexpr int ACH = ACHS<SPLIT>::value;  // 8-channel chunks per staged pixel
   constexpr int ABUF = ACH * CH_BYTES;
-  constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  constexpr int B_BYTES = TERMS<SPLIT>::value * B_HALF;
   constexpr int TMEM_COLS = TMC<SPLIT>::value;
   constexpr int NACC = NT * NB<SPLIT>::value;  // columns of one accumulator
   extern __shared__ __align__(16) unsigned char smem[];
@@ -450,6 +534,8 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   // staged ahead, and two CTAs fit on an SM), then the weights
   unsigned char* Bs = smem + nbuf * ABUF;
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t drain_bar;  // completion of all MMAs issued (abort path)
+  const unsigned long long wait_ns = (unsigned long long)ctl[0];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -473,6 +559,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&drain_bar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
   }
@@ -512,7 +599,7 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   auto wait_mma = [&](int buf, uint32_t parity) {
-    if (!mbar_wait_bounded(smem_u32(&mbar[buf]), parity)) {
+    if (!mbar_wait_bounded(smem_u32(&mbar[buf]), parity, wait_ns)) {
       atomicExch(err, 1);
       abort_flag = 1;
     }
@@ -577,6 +664,9 @@ k_hidden_tc(int n, int nimg, const __nv_bfloat16* __restrict__ ain,
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // after a timed-out wait, MMAs issued by thread 0 may still be writing
+  // tensor memory: wait for all of them before releasing it
+  if (abort_flag && tid == 0 && k > 0) drain_mmas(smem_u32(&drain_bar), err);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -640,13 +730,13 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
             const float* __restrict__ w4, const __grid_constant__ OutW ow,
             const double* __restrict__ snorm, const int* __restrict__ active,
             int* __restrict__ err, const float* __restrict__ bsrc,
-            const __grid_constant__ FirstW fw) {
+            const __grid_constant__ FirstW fw, const long long* __restrict__ ctl) {
   constexpr int NTHR = WST<SPLIT, FUSE, FIRST>::value;
   static_assert(!FIRST || (SPLIT && !FUSE), "the fused first layer serves the split forms' first hidden layer");
-  constexpr int ACH = SPLIT ? 8 : 4;
+  constexpr int ACH = ACHS<SPLIT>::value;
   constexpr int SBYTES = ACH * CH_PITCH;           // one stage
   constexpr uint32_t TX = ACH * RH * RW * 16;      // bytes the copies of one stage write
-  constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  constexpr int B_BYTES = TERMS<SPLIT>::value * B_HALF;
   constexpr int TMEM_COLS = TMC<SPLIT>::value;
   constexpr int NACC = NT * NB<SPLIT>::value;
   extern __shared__ __align__(16) unsigned char smem_raw_ws[];
@@ -654,6 +744,11 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
   unsigned char* smem = smem_raw_ws + ((1024u - (smem_u32(smem_raw_ws) & 1023u)) & 1023u);
   unsigned char* Bs = smem + STAGES * SBYTES;
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  // drain[i]: completion of MMA issuer i's MMAs (abort path); stall_bar:
+  // the barrier nothing arrives at (test hook ctl[1])
+  __shared__ __align__(8) uint64_t drain[NT], stall_bar;
+  const unsigned long long wait_ns = (unsigned long long)ctl[0];
+  const bool stall = ctl[1] != 0;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -697,6 +792,9 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
                    "r"(EPI<SPLIT, FUSE>::value));
     }
+    for (int i = 0; i < NT; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&drain[i])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&stall_bar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
   }
@@ -730,7 +828,7 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
     const uint64_t t0 = global_ns();
     for (unsigned it = 1;; ++it) {
       if (mbar_try_wait(smem_u32(bar), parity)) return true;
-      if ((it & 63u) == 0 && (*(volatile int*)&abort_flag || global_ns() - t0 > kWaitLimitNs)) {
+      if ((it & 63u) == 0 && (*(volatile int*)&abort_flag || global_ns() - t0 > wait_ns)) {
         atomicExch(err, 1);
         abort_flag = 1;
         return false;
@@ -840,13 +938,25 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         const uint32_t dst = smem_u32(smem + s * SBYTES);
         for (int c = 0; c < ACH; ++c) tma_load_5d(dst + c * CH_PITCH, &amap, 0, x0 - 1, y0 - 1, c, b, fb);
       }
+      if (*(volatile int*)&abort_flag) {
+        // copies issued for a stage land whether or not its tile was
+        // consumed: wait for the last one of every stage (the phase of tile
+        // j is (j / STAGES) & 1; a phase already completed returns at once)
+        for (int s = 0; s < STAGES && s < i; ++s) {
+          const int last = s + ((i - 1 - s) / STAGES) * STAGES;
+          if (!mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((last / STAGES) & 1), kDrainNs))
+            atomicExch(err, 2);
+        }
+      }
     }
   } else if (warp <= ISS<SPLIT>::value) {
     // ---- MMA issuer(s): all M tiles, or M tile warp - 1
     if (lane == 0) {
       const uint32_t b_base = smem_u32(Bs);
       int i = 0;
-      for (int t = first(); t < total; t = advance(t), ++i) {
+      // test hook: a wait that runs out before any MMA is issued
+      const bool go = !stall || wait(&stall_bar, 0u);
+      for (int t = go ? first() : total; t < total; t = advance(t), ++i) {
         const int s = i % STAGES, a = i & 1;
         if (!wait(&full[s], (uint32_t)((i / STAGES) & 1))) break;
         if (i >= 2 && !wait(&acc_empty[a], (uint32_t)((i / 2 - 1) & 1))) break;
@@ -861,6 +971,8 @@ k_hidden_ws(const __grid_constant__ CUtensorMap amap, int n, int nimg,
         mma_commit(smem_u32(&empty[s]));
         mma_commit(smem_u32(&acc_full[a]));
       }
+      // after an abort this issuer's MMAs may still be writing tensor memory
+      if (*(volatile int*)&abort_flag && i > 0) drain_mmas(smem_u32(&drain[warp - 1]), err);
     }
   } else {
     // ---- epilogue warps: lane quarter q = warp % 4 of tensor memory; group
@@ -1071,14 +1183,17 @@ int num_sms() {
 template <int SPLIT, int FUSE, int FIRST = 0>
 void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv_bfloat16* aout,
                    float* gout, const LayerPack& lp, const float* w4, const OutW& ow,
-                   const double* s, const int* active, int* err, cudaStream_t st,
-                   LaunchLog& log, const float* bsrc = nullptr, const FirstW* fw = nullptr) {
-  constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
+                   const double* s, const int* active, int* err, const long long* ctl,
+                   cudaStream_t st, LaunchLog& log, const float* bsrc = nullptr,
+                   const FirstW* fw = nullptr) {
+  constexpr int CWs = TERMS<SPLIT>::value * WIDTH;
   const CUtensorMap* map = n >= 32 ? act_map(ain, n, map_imgs, CWs) : nullptr;
   if (map) {
-    constexpr int STAGES = 3;
-    constexpr int ACHs = SPLIT ? 8 : 4;
-    constexpr int B_BYTESs = SPLIT ? 2 * B_HALF : B_HALF;
+    // three operand stages (two for the three-term form, whose stages are
+    // 1.5x larger)
+    constexpr int STAGES = SPLIT == 3 ? 2 : 3;
+    constexpr int ACHs = ACHS<SPLIT>::value;
+    constexpr int B_BYTESs = TERMS<SPLIT>::value * B_HALF;
     const size_t sm = (size_t)STAGES * ACHs * CH_PITCH + B_BYTESs + 1024;
     const int tiles_x = (n + TILE - 1) / TILE;
     long long total = (long long)nimg * tiles_x * tiles_x;
@@ -1089,13 +1204,13 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int pi_ = log.begin(K_CNN_HIDDEN, st);
     k_hidden_ws<SPLIT, STAGES, FUSE, FIRST><<<(int)grid, WST<SPLIT, FUSE, FIRST>::value, sm, st>>>(
-        *map, n, map_imgs, aout, gout, lp, w4, ow, s, active, err, bsrc, fw ? *fw : FirstW{});
+        *map, n, map_imgs, aout, gout, lp, w4, ow, s, active, err, bsrc, fw ? *fw : FirstW{}, ctl);
     log.end(pi_, st, (double)n * n * log.active_hint);
     return;
   }
   if (FIRST) return;  // not reached: run_layers takes FIRST only where a map exists
-  constexpr int ACH = SPLIT ? 8 : 4;
-  constexpr int B_BYTES = SPLIT ? 2 * B_HALF : B_HALF;
+  constexpr int ACH = ACHS<SPLIT>::value;
+  constexpr int B_BYTES = TERMS<SPLIT>::value * B_HALF;
   const int tiles_x = (n + TILE - 1) / TILE;
   long long total = (long long)nimg * tiles_x * tiles_x;
   long long grid = (long long)num_sms() * (SPLIT ? 1 : 3);
@@ -1109,18 +1224,18 @@ void launch_hidden(int n, int nimg, int map_imgs, const __nv_bfloat16* ain, __nv
   cudaFuncSetAttribute(k_hidden_tc<SPLIT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int pi_ = log.begin(K_CNN_HIDDEN, st);
   k_hidden_tc<SPLIT, FUSE><<<(int)grid, THREADS, sm, st>>>(n, nimg, ain, aout, gout, lp, w4, ow, s, active,
-                                                           err, nbuf);
+                                                           err, nbuf, ctl);
   log.end(pi_, st, (double)n * n * log.active_hint);
 }
 
 template <int SPLIT>
 void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const float* b, const double* s,
                 __nv_bfloat16* a0, __nv_bfloat16* a1, float* h, const int* active, int* err,
-                cudaStream_t st, LaunchLog& log) {
+                const long long* ctl, cudaStream_t st, LaunchLog& log) {
   const int tiles_x = (n + TILE - 1) / TILE;
   dim3 grid(tiles_x * tiles_x, B);
   const double units = (double)n * n * log.active_hint;
-  constexpr int CWs = SPLIT ? 2 * WIDTH : WIDTH;
+  constexpr int CWs = TERMS<SPLIT>::value * WIDTH;
   // split forms with a first hidden layer that is not the last one, on the
   // persistent path: the first layer runs inside that layer's kernel
   const bool fused_first = SPLIT && layers >= 4 && n >= 32 && act_map(a0, n, map_imgs, CWs);
@@ -1129,7 +1244,7 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   int li0 = 1;
   if (fused_first) {
     launch_hidden<SPLIT, 0, SPLIT ? 1 : 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[1], nullptr, P.last,
-                                          s, active, err, st, log, b, &P.first);
+                                          s, active, err, ctl, st, log, b, &P.first);
     cur = a1;
     nxt = a0;
     li0 = 2;
@@ -1144,13 +1259,13 @@ void run_layers(int n, int B, int map_imgs, int layers, const Bf16Pack& P, const
   for (int li = li0; li < layers - 1; ++li) {
     if (li < layers - 2) {
       launch_hidden<SPLIT, 0>(n, B, map_imgs, cur, nxt, nullptr, P.l[li], nullptr, P.last, s, active, err,
-                              st, log);
+                              ctl, st, log);
       __nv_bfloat16* t = cur;
       cur = nxt;
       nxt = t;
     } else {
       launch_hidden<SPLIT, 1>(n, B, map_imgs, cur, nxt, reinterpret_cast<float*>(nxt), P.l[li],
-                              L4.wf, P.last, s, active, err, st, log);
+                              L4.wf, P.last, s, active, err, ctl, st, log);
     }
   }
   float bias0 = 0.f;
@@ -1166,8 +1281,9 @@ std::vector<std::pair<const void*, Bf16Pack>> g_headers;
 }  // namespace
 
 // Build the device weight pack of one smoother level from PyTorch-layout
-// fp64 weights (width 32, 3x3, at least 3 layers).  split = 1: the split
-// bf16 form; 2: the split fp16 form; 0: plain bf16.  Returns one device allocation holding packed
+// fp64 weights (width 32, 3x3, at least 3 layers).  split = 1: the bf16
+// pair form; 2: the fp16 pair form; 3: the three-term bf16 form; 0: plain
+// bf16.  Returns one device allocation holding packed
 // weights and biases; the per-layer device pointers are kept in a host
 // table keyed by it.
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
@@ -1204,7 +1320,7 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
                     reinterpret_cast<const unsigned char*>(f.data() + f.size()));
       continue;
     }
-    const int N = split ? 2 * WIDTH : WIDTH;
+    const int N = (split == 3 ? 3 : (split ? 2 : 1)) * WIDTH;
     std::vector<uint16_t> p((size_t)9 * 4 * N * 8, 0);
     for (int co = 0; co < cout; ++co)
       for (int ci = 0; ci < cin; ++ci)
@@ -1222,7 +1338,21 @@ void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
           }
           const size_t row = ((size_t)tap * 4 + ci / 8) * N;
           p[(row + co) * 8 + ci % 8] = hb;
-          if (split) {
+          if (split == 3) {
+            // w = w1 + w2 + w3, each the bf16 rounding of the remainder
+            // (the remainders formed in fp64)
+            const double r1 = v - (double)hf;
+            const uint16_t b2 = bf16_bits((float)r1);
+            float f2;
+            {
+              const uint32_t u2 = (uint32_t)b2 << 16;
+              std::memcpy(&f2, &u2, 4);
+            }
+            const uint16_t b3 = bf16_bits((float)(r1 - (double)f2));
+            p[(row + WIDTH + co) * 8 + ci % 8] = b2;
+            p[(row + 2 * WIDTH + co) * 8 + ci % 8] = b3;
+            if ((b2 != 0 && b2 != 0x8000) || (b3 != 0 && b3 != 0x8000)) has_lo[li] = 1;
+          } else if (split) {
             const float rest = (float)(v - (double)hf);
             const uint16_t lb = split == 2 ? f16_bits(rest) : bf16_bits(rest);
             p[(row + WIDTH + co) * 8 + ci % 8] = lb;
@@ -1281,19 +1411,21 @@ void bf16_cnn_forget(const void* pack) {
 // serves every chunk; err: device error word of the bounded waits.
 void bf16_cnn_launch(int n, int B, int map_imgs, int layers, const void* pack, const float* b,
                      const double* s, float* act0, float* act1, float* h, const int* active,
-                     int* err, cudaStream_t st, LaunchLog& log) {
+                     int* err, const long long* ctl, cudaStream_t st, LaunchLog& log) {
   const Bf16Pack* P = nullptr;
   for (auto& e : g_headers)
     if (e.first == pack) P = &e.second;
   if (!P) return;
   __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(act0);
   __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(act1);
-  if (P->split == 2)
-    run_layers<2>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
+  if (P->split == 3)
+    run_layers<3>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, ctl, st, log);
+  else if (P->split == 2)
+    run_layers<2>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, ctl, st, log);
   else if (P->split)
-    run_layers<1>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
+    run_layers<1>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, ctl, st, log);
   else
-    run_layers<0>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, st, log);
+    run_layers<0>(n, B, map_imgs, layers, *P, b, s, a0, a1, h, active, err, ctl, st, log);
 }
 
 }  // namespace nmg

@@ -34,6 +34,15 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def test_noalloc_limit_matches_header():
+    """The binding's copy of NMG_NOALLOC_SCRATCH_BYTES equals the header's."""
+    import paper_2603_01064_gb300 as nmg
+    src = open(os.path.join(ROOT, "include", "nmg.h")).read()
+    m = re.search(r"#define\s+NMG_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", src)
+    assert m, "define not found"
+    assert int(m.group(1)) << int(m.group(2)) == nmg.NOALLOC_SCRATCH_BYTES
+
+
 def test_library_exports_every_declared_symbol(libpath):
     L = ctypes.CDLL(libpath)
     missing = [n for n in _declared() if not hasattr(L, n)]
