@@ -405,8 +405,9 @@ nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double*
 /* Autotuner: for every level of a 2D hierarchy, time the candidate launch
  * shapes (tile sides of the residual, the fused residual + restriction and
  * the compensated outer residual; output filter as three passes (mode 0),
- * one block-synchronous kernel (1) or one warp-level kernel for 64x64 and
- * 128x128 levels (2)) on the hierarchy's workspace with `batch`
+ * one block-synchronous kernel (1), one warp-level kernel for 64x64 and
+ * 128x128 levels (2), or three warp-level passes for 256x256 and 512x512
+ * levels (3)) on the hierarchy's workspace with `batch`
  * right-hand sides, and
  * keep the fastest for later solves.  cache_path (may be NULL): a text file
  * from which choices for the same operator shape, precision and batch are

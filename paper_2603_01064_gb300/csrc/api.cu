@@ -343,6 +343,21 @@ int op_residual_restrict(nmg_hier* h, int l, int B, const T* x, const T* y, T* y
   int nt = 0;
   nmg_ctx* c = h->ctx;
   if (h->dim == 2) {
+    if constexpr (std::is_same<T, float>::value) {
+      // wide PSF stencils: the strip residual into the level's temporary
+      // (free at this point of the cycle), then full weighting
+      const Band2D<float> op = band<float>(h, l);
+      if (wide_residual_applies(op, x, y) && restrict_fw_applies(op.n)) {
+        float* tmp = reinterpret_cast<float*>(h->w.t[l]);
+        int pi_ = c->log.begin(K_RESTRICT, c->stream);
+        launch_residual_wide(op, B, x, y, tmp, nullptr, active, c->stream);
+        c->log.end(pi_, c->stream, (double)op.n * op.n * c->log.active_hint);
+        pi_ = c->log.begin(K_RESTRICT, c->stream);
+        nt = launch_restrict_fw(op.n, B, tmp, yc, part, active, c->stream);
+        c->log.end(pi_, c->stream, 0.0);
+        return nt;
+      }
+    }
     launch_residual_restrict2d<T>(band<T>(h, l), B, x, y, yc, part, &nt, active, c->stream,
                                   c->log, h->lv[l].rst_tile);
   } else {
@@ -1489,7 +1504,8 @@ nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_
       d.rst_tile = keep;
       best = 1e30f;
       int keepm = -1;
-      for (int m : {0, 1, 2}) {
+      for (int m : {0, 1, 2, 3}) {
+        if (m == 3 && d.n != 256 && d.n != 512) continue;  // the same kernels as mode 0
         d.filt_mode = m;
         float ms = timeit([&]() {
           if (dbl) op_filter<double>(h, l, batch, (double*)w.x[l], (double*)w.h[l], (double*)w.x[l], w.active);
@@ -1503,7 +1519,7 @@ nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_
       // u is fp64 for the outer residual: reuse the complex filter scratch
       best = 1e30f;
       int keep = 0;
-      for (int t : {16, 32, 64}) {
+      for (int t : {0, 16, 32, 64}) {  // 0: the strip forms where they apply
         d.ref_tile = t;
         float ms = timeit([&]() {
           int nt = 0;

@@ -482,7 +482,11 @@ __device__ __forceinline__ void warp_dit_inv(Cx<T> (&v)[L / 32], const Cx<T>* tw
 }
 
 template <int L>
-__device__ __forceinline__ int brev_len(int s) { return __brev(s) >> (32 - (L == 32 ? 5 : L == 64 ? 6 : 7)); }
+__device__ __forceinline__ int brev_len(int s) {
+  constexpr int bits = L == 32 ? 5 : L == 64 ? 6 : L == 128 ? 7 : L == 256 ? 8 : 9;
+  static_assert(L == (1 << bits), "transform length: a power of two from 32 to 512");
+  return __brev(s) >> (32 - bits);
+}
 
 // threads of the warp-level filter: one warp per row / column pair at a
 // time; 16 warps for 128 x 128 (a block holds one image, so more warps
@@ -623,6 +627,215 @@ size_t filter_warp_smem() {
          (size_t)(N / 2) * (N + 1) * sizeof(Cx<T>);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-level form for levels too large for one block (n = 256, 512): the
+// same half-spectrum transforms as k_filter_warp, in three launches over the
+// row-pair layout buffer C ([B][n/2][n] complex, global memory, mostly
+// L2-resident between the passes):
+//   rows: one warp per row pair, h in, forward row FFT in registers, split,
+//         coalesced row write;
+//   cols: one block per kFcCols column pairs (even-row columns p and their
+//         odd-row partners), staged through shared memory so that every
+//         global access is a contiguous run; one warp per column pair does
+//         the forward column FFTs, the mask and the inverse FFTs;
+//   rows: one warp per row pair, join, inverse row FFT, x = x* + z / n^2.
+// ---------------------------------------------------------------------------
+constexpr int kFrWarps = 8;  // row pairs per block (row passes)
+constexpr int kFcCols = 8;   // column pairs per block (column pass), one warp each
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * kFrWarps)
+k_fwarp_rows_fwd(const T* __restrict__ h, Cx<T>* __restrict__ C, const Cx<T>* __restrict__ twg,
+                 const int* __restrict__ active) {
+  constexpr int HN = N / 2, MR = N / 32;
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  extern __shared__ __align__(16) unsigned char fr_smem[];
+  Cx<T>* tw = reinterpret_cast<Cx<T>*>(fr_smem);  // [HN], then one row per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < HN; k += blockDim.x) tw[k] = twg[k];
+  __syncthreads();
+  const int k = blockIdx.x * kFrWarps + warp;  // row pair (HN is a multiple of kFrWarps)
+  const size_t plane = (size_t)N * N;
+  const T* h0 = h + (size_t)b * plane + (size_t)(2 * k) * N;
+  Cx<T> v[MR];
+#pragma unroll
+  for (int m = 0; m < MR; ++m) v[m] = Cx<T>{h0[lane + 32 * m], h0[N + lane + 32 * m]};
+  warp_dif<T, N, N>(v, tw, lane);
+  Cx<T>* row = tw + HN + warp * N;
+#pragma unroll
+  for (int m = 0; m < MR; ++m) row[brev_len<N>(lane + 32 * m)] = v[m];
+  __syncwarp();
+  Cx<T>* Cr = C + (size_t)b * (plane / 2) + (size_t)k * N;
+  for (int t = lane; t < HN; t += 32) {
+    if (t == 0) {
+      const Cx<T> a = row[0], c = row[HN];
+      Cr[0] = Cx<T>{a.x, c.x};
+      Cr[HN] = Cx<T>{a.y, c.y};
+    } else {
+      const Cx<T> za = row[t], zb = row[N - t];
+      Cr[t] = Cx<T>{T(0.5) * (za.x + zb.x), T(0.5) * (za.y - zb.y)};
+      Cr[N - t] = Cx<T>{T(0.5) * (za.y + zb.y), T(0.5) * (zb.x - za.x)};
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * kFcCols)
+k_fwarp_cols(Cx<T>* __restrict__ C, const Cx<T>* __restrict__ twg,
+             const double* __restrict__ mtab, const int* __restrict__ active) {
+  constexpr int HN = N / 2, MC = HN / 32, PT = kFcCols + 1;  // odd tile pitch
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  extern __shared__ __align__(16) unsigned char fc_smem[];
+  Cx<T>* tw = reinterpret_cast<Cx<T>*>(fc_smem);
+  Cx<T>* q = tw + HN;                                  // packed pair scratch (N)
+  Cx<T>* E = q + N;                                    // [HN][PT]: even-row columns
+  Cx<T>* O = E + HN * PT;                              // [HN][PT]: odd-row partners
+  T* mt = reinterpret_cast<T*>(O + HN * PT);           // mask table, HN + 1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < HN; k += blockDim.x) tw[k] = twg[k];
+  for (int k = threadIdx.x; k <= HN; k += blockDim.x) mt[k] = (T)mtab[k];
+  const int p0 = blockIdx.x * kFcCols;
+  Cx<T>* Cb = C + (size_t)b * ((size_t)N * N / 2);
+  // stage: column p0 + s (even rows) and its partner (odd rows) of every row
+  for (int t = threadIdx.x; t < HN * kFcCols; t += blockDim.x) {
+    const int k = t / kFcCols, s2 = t % kFcCols;
+    const int p = p0 + s2;
+    const int co = p == 0 ? HN : N - p;
+    E[k * PT + s2] = Cb[(size_t)k * N + p];
+    O[k * PT + s2] = Cb[(size_t)k * N + co];
+  }
+  __syncthreads();
+  const int p = p0 + warp;
+  Cx<T> e[MC], o[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    e[m] = E[(lane + 32 * m) * PT + warp];
+    o[m] = O[(lane + 32 * m) * PT + warp];
+  }
+  warp_dif<T, HN, N>(e, tw, lane);
+  warp_dif<T, HN, N>(o, tw, lane);
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const int k1 = brev_len<HN>(lane + 32 * m);
+    const Cx<T> w = tw[k1], wo = cmul(o[m], w);
+    Cx<T> y0{e[m].x + wo.x, e[m].y + wo.y}, y1{e[m].x - wo.x, e[m].y - wo.y};
+    if (p == 0) {  // packed pair: separated below
+      q[k1] = y0;
+      q[k1 + HN] = y1;
+      continue;
+    }
+    const T m0 = mt[k1 > p ? k1 : p], m1 = mt[HN - k1 > p ? HN - k1 : p];
+    y0.x *= m0; y0.y *= m0;
+    y1.x *= m1; y1.y *= m1;
+    e[m] = Cx<T>{y0.x + y1.x, y0.y + y1.y};
+    o[m] = cmulc(Cx<T>{y0.x - y1.x, y0.y - y1.y}, w);
+  }
+  if (p == 0) {  // warp-uniform
+    __syncwarp();
+    const T mb = mt[HN];
+    for (int K = lane; K <= HN; K += 32) {
+      const int Kp = K == 0 ? 0 : N - K;
+      const T ma = mt[K], c1 = T(0.5) * (ma + mb), c2 = T(0.5) * (ma - mb);
+      const Cx<T> qa = q[K], qb = q[Kp];
+      q[K] = Cx<T>{c1 * qa.x + c2 * qb.x, c1 * qa.y - c2 * qb.y};
+      if (Kp != K) q[Kp] = Cx<T>{c1 * qb.x + c2 * qa.x, c1 * qb.y - c2 * qa.y};
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      const int k1 = brev_len<HN>(lane + 32 * m);
+      const Cx<T> y0 = q[k1], y1 = q[k1 + HN];
+      e[m] = Cx<T>{y0.x + y1.x, y0.y + y1.y};
+      o[m] = cmulc(Cx<T>{y0.x - y1.x, y0.y - y1.y}, tw[k1]);
+    }
+  }
+  warp_dit_inv<T, HN, N>(e, tw, lane);
+  warp_dit_inv<T, HN, N>(o, tw, lane);
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    E[(lane + 32 * m) * PT + warp] = e[m];
+    O[(lane + 32 * m) * PT + warp] = o[m];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < HN * kFcCols; t += blockDim.x) {
+    const int k = t / kFcCols, s2 = t % kFcCols;
+    const int pp = p0 + s2;
+    const int co = pp == 0 ? HN : N - pp;
+    Cb[(size_t)k * N + pp] = E[k * PT + s2];
+    Cb[(size_t)k * N + co] = O[k * PT + s2];
+  }
+}
+
+template <typename T, int N>
+size_t fwarp_cols_smem() {
+  return (size_t)(N / 2 + N + 2 * (N / 2) * (kFcCols + 1)) * sizeof(Cx<T>) +
+         (size_t)(N / 2 + 2) * sizeof(T);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * kFrWarps)
+k_fwarp_rows_inv(const Cx<T>* __restrict__ C, const T* xstar, T* x, const Cx<T>* __restrict__ twg,
+                 const int* __restrict__ active) {
+  constexpr int HN = N / 2, MR = N / 32;
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  extern __shared__ __align__(16) unsigned char fr_smem[];
+  Cx<T>* tw = reinterpret_cast<Cx<T>*>(fr_smem);  // [HN], then one row per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < HN; k += blockDim.x) tw[k] = twg[k];
+  __syncthreads();
+  const int k = blockIdx.x * kFrWarps + warp;
+  const size_t plane = (size_t)N * N;
+  const Cx<T>* Cr = C + (size_t)b * (plane / 2) + (size_t)k * N;
+  Cx<T>* row = tw + HN + warp * N;
+  for (int t = lane; t < HN; t += 32) {
+    if (t == 0) {
+      const Cx<T> a = Cr[0], c = Cr[HN];
+      row[0] = Cx<T>{a.x, c.x};
+      row[HN] = Cx<T>{a.y, c.y};
+    } else {
+      const Cx<T> xa = Cr[t], xb = Cr[N - t];
+      row[t] = Cx<T>{xa.x - xb.y, xa.y + xb.x};
+      row[N - t] = Cx<T>{xa.x + xb.y, xb.x - xa.y};
+    }
+  }
+  __syncwarp();
+  Cx<T> v[MR];
+#pragma unroll
+  for (int m = 0; m < MR; ++m) v[m] = row[brev_len<N>(lane + 32 * m)];
+  warp_dit_inv<T, N, N>(v, tw, lane);
+  const T scale = T(1.0 / ((double)N * (double)N));
+  const size_t g0 = (size_t)b * plane + (size_t)(2 * k) * N;
+#pragma unroll
+  for (int m = 0; m < MR; ++m) {
+    const size_t g = g0 + lane + 32 * m;
+    x[g] = (xstar ? xstar[g] : T(0)) + v[m].x * scale;
+    x[g + N] = (xstar ? xstar[g + N] : T(0)) + v[m].y * scale;
+  }
+}
+
+template <typename T, int N>
+void launch_fwarp3(int B, const T* xstar, const T* h, T* x, Cx<T>* C, const Cx<T>* tw,
+                   const double* mask_tab, const int* active, cudaStream_t st, LaunchLog& log,
+                   double units) {
+  const size_t smc = fwarp_cols_smem<T, N>();
+  const size_t smr = (size_t)(N / 2 + kFrWarps * N) * sizeof(Cx<T>);
+  cudaFuncSetAttribute(k_fwarp_cols<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  cudaFuncSetAttribute(k_fwarp_rows_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  cudaFuncSetAttribute(k_fwarp_rows_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  int pi_ = log.begin(K_FILTER, st);
+  k_fwarp_rows_fwd<T, N><<<dim3(N / 2 / kFrWarps, B), 32 * kFrWarps, smr, st>>>(h, C, tw, active);
+  log.end(pi_, st, units);
+  pi_ = log.begin(K_FILTER, st);
+  k_fwarp_cols<T, N><<<dim3(N / 2 / kFcCols, B), 32 * kFcCols, smc, st>>>(C, tw, mask_tab, active);
+  log.end(pi_, st, units);
+  pi_ = log.begin(K_FILTER, st);
+  k_fwarp_rows_inv<T, N><<<dim3(N / 2 / kFrWarps, B), 32 * kFrWarps, smr, st>>>(C, xstar, x, tw, active);
+  log.end(pi_, st, units);
+}
+
 // 1D: x[b][i] = x*[b][i] + sum_k c[(i - k) mod n] h[b][k]; one warp per output
 template <typename T>
 __global__ void k_filter1d(int n, const T* xs, const T* __restrict__ h, T* x, const double* __restrict__ circ,
@@ -669,8 +882,16 @@ void launch_filter2d(int n, int B, const T* xstar, const T* h, T* x, void* cbuf,
       return;
     }
   }
+  // warp-level three-pass form (default for 256 and 512; autotuner mode 3)
+  if ((n == 256 || n == 512) && (mode == 3 || mode < 0)) {
+    if (n == 256)
+      launch_fwarp3<T, 256>(B, xstar, h, x, C, tw, mask_tab, active, st, log, units);
+    else
+      launch_fwarp3<T, 512>(B, xstar, h, x, C, tw, mask_tab, active, st, log, units);
+    return;
+  }
   const size_t fused_sm = (size_t)(halfn + (size_t)n * halfn) * sizeof(Cx<T>);
-  if (fused_sm <= 160 * 1024 && mode != 0) {
+  if (fused_sm <= 160 * 1024 && mode != 0 && mode != 3) {
     cudaFuncSetAttribute(k_filter_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_sm);
     const int work = n * n / 4;
     const int threads = work < 32 ? 32 : (work > 512 ? 512 : work);

@@ -402,6 +402,14 @@ void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
   int tx = ceil_div(op.n, tile);
   int pi_ = log.begin(K_RESIDUAL, st);
   int nparts = tx * tx;
+  if constexpr (std::is_same<T, float>::value) {
+    if (wide_residual_applies(op, x, y)) {
+      nparts = launch_residual_wide(op, B, x, y, r, partials, active, st);
+      if (ntiles) *ntiles = nparts;
+      log.end(pi_, st, (double)op.n * op.n * log.active_hint);
+      return;
+    }
+  }
   if (!launch_stencil_residual<T, false>(op, B, x, y, r, partials, active, tile, tx, st, &nparts)) {
     nparts = tx * tx;
     size_t sm = residual_smem<T>(tile, tile, op.wK, op.wM, false);
@@ -419,7 +427,11 @@ void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
 template <typename T>
 int residual2d_tiles(const Band2D<T>& op, int tile_req) {
   const int tx = ceil_div(op.n, pick_tile<T>(op.n, op.wK, op.wM, false, tile_req));
-  const int strip = stencil_strip_parts<T>(op);
+  int strip = stencil_strip_parts<T>(op);
+  if (op.n % 128 == 0) {
+    const int wide = (op.n / 64) * (op.n / 128);  // the wide strip form's units
+    strip = wide > strip ? wide : strip;
+  }
   return tx * tx > strip ? tx * tx : strip;
 }
 

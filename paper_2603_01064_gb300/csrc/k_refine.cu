@@ -612,6 +612,197 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Strip form for wide stencils (half-width 9..32, n a multiple of 64 and of
+// the unit height): one warp computes kRwH consecutive output rows of a
+// 64-column strip, lane j owning columns 2j and 2j + 1 (two-lane packed
+// double-float operations).  Input rows stream through a warp-private
+// cp.async ring; each staged row is split into float pairs once; the row
+// pass reads the lane's window from that split row.  The double-float
+// row-pass outputs of the last 2 W + 1 rows live in a warp-private
+// shared-memory ring (each lane reads back only its own columns, so the
+// ring needs no barrier), and the column pass of output row i = a - W
+// gathers them from there.  f is staged with u for the output rows, and
+// g = f - alpha u of row a (double-float) is kept in a second ring of W + 1
+// rows until row a's column pass, so no global load waits inside the row
+// loop and no staged row has to outlive the prefetch window.
+// ---------------------------------------------------------------------------
+constexpr int kRwH = 128;  // output rows per warp unit
+constexpr int kRwPF = 4;   // staged rows ahead
+constexpr int kRwRing = kRwPF + 2;
+template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 6 : 3; };
+template <int W> struct RwGeom {
+  static constexpr int XW = kRsSW + 2 * W;                   // staged u row (doubles)
+  static constexpr int P = 2 * W + 1;                        // row-pass ring rows
+  static constexpr int Q = W + 1;                            // g ring rows
+  // per-warp shared memory in 4-byte words: t ring and g ring (float4 per
+  // lane and row), u ring, split row (hi, lo), f ring (64 per row)
+  static constexpr int words = (P + Q) * 128 + kRwRing * XW * 2 + 2 * XW + kRwRing * kRsSW;
+};
+
+template <int W>
+__global__ void __launch_bounds__(32 * RwWarps<W>::value, 1)
+k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
+              const float* __restrict__ f, float* __restrict__ r,
+              double* __restrict__ partials, const int* __restrict__ active) {
+  using G = RwGeom<W>;
+  constexpr int XW = G::XW, P = G::P, Q = G::Q;
+  extern __shared__ __align__(16) float rw_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* wbase = rw_smem + (size_t)wib * G::words;
+  float4* tring = reinterpret_cast<float4*>(wbase);                 // [P][32 lanes]
+  float4* gring = tring + P * 32;                                   // [Q][32 lanes]
+  double* uring = reinterpret_cast<double*>(gring + Q * 32);        // [ring][XW]
+  float* xh = reinterpret_cast<float*>(uring + kRwRing * XW);        // [XW]
+  float* xl = xh + XW;                                               // [XW]
+  float* fring = xl + XW;                                            // [ring][64]
+  const int n = op.n;
+  const int ns = n / kRsSW, upi = ns * (n / kRwH);
+  const int total = B * upi;
+  const size_t plane = (size_t)n * n;
+
+  for (int unit = blockIdx.x * RwWarps<W>::value + wib; unit < total;
+       unit += gridDim.x * RwWarps<W>::value) {
+    const int b = unit / upi;
+    if (!active[b]) continue;  // warp-uniform
+    const int rem = unit - b * upi;
+    const int c0 = (rem % ns) * kRsSW, i0 = (rem / ns) * kRwH;
+    const int alo = i0 - W, ahi = i0 + kRwH + W;  // input rows
+    const double* ub = u + (size_t)b * plane;
+    const float* fb = f + (size_t)b * plane;
+    auto stage = [&](int a) {
+      if (a < ahi) {
+        const int slot = (a - alo) % kRwRing;
+        const bool rin = a >= 0 && a < n;
+        double* ud = uring + slot * XW;
+        for (int ch = lane; ch < XW / 2; ch += 32) {
+          const int gc = c0 - W + 2 * ch;
+          const bool in = rin && gc >= 0 && gc < n;
+          cp_async_16r(ud + 2 * ch, in ? ub + (size_t)a * n + gc : ub, in);
+        }
+        if (a >= i0 && a < i0 + kRwH && lane < kRsSW / 4)
+          cp_async_16r(fring + slot * kRsSW + 4 * lane, fb + (size_t)a * n + c0 + 4 * lane, true);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int k = 0; k < kRwPF; ++k) stage(alo + k);
+    float ss = 0.f;
+#pragma unroll 1
+    for (int a = alo; a < ahi; ++a) {
+      asm volatile("cp.async.wait_group %0;" ::"n"(kRwPF - 1) : "memory");
+      __syncwarp();
+      stage(a + kRwPF);
+      // split the staged row once (the previous row's window reads are
+      // ordered before this by the barrier above)
+      const double* us = uring + ((a - alo) % kRwRing) * XW;
+      for (int k = lane; k < XW; k += 32) {
+        float h, l;
+        split_double(us[k], h, l);
+        xh[k] = h;
+        xl[k] = l;
+      }
+      __syncwarp();
+      // row pass: t[c] = sum_d K[d] u[a][c0 + 2 lane + c + d - W], the
+      // lane's window read as aligned pairs (odd taps take the halves of
+      // two neighbouring pairs)
+      float2 th = make_float2(0.f, 0.f), tl = make_float2(0.f, 0.f);
+      {
+        const float2* h2 = reinterpret_cast<const float2*>(xh) + lane;
+        const float2* l2 = reinterpret_cast<const float2*>(xl) + lane;
+        float2 ph = h2[0], pl = l2[0];
+        // W = 32: partial unrolling keeps the window loads from being all
+        // hoisted into registers (the kernel then spills)
+#pragma unroll(W > 16 ? 8 : W)
+        for (int k = 0; k < W; ++k) {
+          const float2 qh = h2[k + 1], ql = l2[k + 1];
+          df_fma2(th, tl, op.kh2[2 * k], op.nkh2[2 * k], op.kl2[2 * k], ph, pl);
+          df_fma2(th, tl, op.kh2[2 * k + 1], op.nkh2[2 * k + 1], op.kl2[2 * k + 1],
+                  make_float2(ph.y, qh.x), make_float2(pl.y, ql.x));
+          ph = qh;
+          pl = ql;
+        }
+        df_fma2(th, tl, op.kh2[2 * W], op.nkh2[2 * W], op.kl2[2 * W], ph, pl);
+      }
+      df_norm2(th, tl);
+      const int sa = (a - alo) % P;
+      tring[sa * 32 + lane] = make_float4(th.x, th.y, tl.x, tl.y);
+      if (a >= i0 && a < i0 + kRwH) {
+        // g = f - alpha u of this row (double-float), kept until its column
+        // pass W rows on; u's pairs are the split row's (index W + 2 lane)
+        const float2 uh = *reinterpret_cast<const float2*>(xh + W + 2 * lane);
+        const float2 ulp = *reinterpret_cast<const float2*>(xl + W + 2 * lane);
+        const float2 fv =
+            *reinterpret_cast<const float2*>(fring + ((a - alo) % kRwRing) * kRsSW + 2 * lane);
+        float gh[2], gl[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          DF au{0.f, 0.f};
+          df_fma(au, op.ah, op.al, c ? uh.y : uh.x, c ? ulp.y : ulp.x);
+          au = df_norm(au);
+          float s2, e;
+          two_sum(c ? fv.y : fv.x, -au.h, s2, e);
+          const DF g = df_norm(DF{s2, e - au.l});
+          gh[c] = g.h;
+          gl[c] = g.l;
+        }
+        gring[((a - i0) % Q) * 32 + lane] = make_float4(gh[0], gh[1], gl[0], gl[1]);
+      }
+      if (a >= i0 + W) {
+        // column pass for output row i = a - W over the rows a - 2W .. a
+        const int i = a - W;
+        int s0 = sa - 2 * W;
+        if (s0 < 0) s0 += P;
+        float2 zh2 = make_float2(0.f, 0.f), zl2 = make_float2(0.f, 0.f);
+#pragma unroll(W > 16 ? 5 : P)
+        for (int d = 0; d < P; ++d) {
+          int sl = s0 + d;
+          sl = sl >= P ? sl - P : sl;
+          const float4 t = tring[sl * 32 + lane];
+          df_fma2(zh2, zl2, op.kh2[d], op.nkh2[d], op.kl2[d], make_float2(t.x, t.y),
+                  make_float2(t.z, t.w));
+        }
+        df_norm2(zh2, zl2);
+        // r = g - z (double-float, rounded once)
+        const float4 g4 = gring[((i - i0) % Q) * 32 + lane];
+        const size_t g = (size_t)i * n + c0 + 2 * lane;
+        float rv[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float s2, e;
+          two_sum(c ? g4.y : g4.x, -(c ? zh2.y : zh2.x), s2, e);
+          rv[c] = s2 + (e + ((c ? g4.w : g4.z) - (c ? zl2.y : zl2.x)));
+          ss = fmaf(rv[c], rv[c], ss);
+        }
+        *reinterpret_cast<float2*>(r + (size_t)b * plane + g) = make_float2(rv[0], rv[1]);
+      }
+    }
+    __syncwarp();  // every lane is done with the rings before the next unit restages them
+    if (partials) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) partials[(size_t)b * upi + rem] = (double)ss;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int W>
+void launch_refine_wide(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
+                        const float* f, float* r, double* partials, const int* active,
+                        cudaStream_t st) {
+  constexpr int NW = RwWarps<W>::value;
+  const size_t sm = (size_t)NW * RwGeom<W>::words * 4;
+  auto kern = k_refine_wide<W>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const long long units = (long long)B * (n / kRsSW) * (n / kRwH);
+  long long grid = (units + NW - 1) / NW;
+  const long long cap = (long long)num_sms_refine();
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, 32 * NW, sm, st>>>(refine_args<W>(sd, alpha, n), B, u, f, r, partials, active);
+}
+
 template <int WK>
 void launch_refine_strip(const StencilHost<double>& sd, double alpha, int n, int B,
                          const double* u, const float* f, float* r, double* partials,
@@ -653,11 +844,12 @@ bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int 
 
 // the stencil kernels when the level qualifies (Toeplitz K, M = I, aligned
 // buffers, n a multiple of 4): the strip form for half-widths <= 8 and n a
-// multiple of 64, else the tiled pipeline; false otherwise.  *nparts:
+// multiple of 64, the wide strip form for half-widths <= 32 and n a
+// multiple of 128 (if wide_ok), else the tiled pipeline; false otherwise.  *nparts:
 // partial sums written per right-hand side.
 bool try_refine_pipe(const StencilHost<double>* sd, double alpha, int n, int B, const double* u,
                      const float* f, float* r, double* partials, const int* active, int tile,
-                     int tx, cudaStream_t st, int* nparts) {
+                     int tx, bool wide_ok, cudaStream_t st, int* nparts) {
   if (!sd || !sd->valid || sd->nbK != 0 || sd->wM != 0 || sd->sM[0] != 1.0 || n % 4 != 0 ||
       (reinterpret_cast<uintptr_t>(u) & 15) || (reinterpret_cast<uintptr_t>(f) & 15))
     return false;
@@ -667,6 +859,12 @@ bool try_refine_pipe(const StencilHost<double>* sd, double alpha, int n, int B, 
     else if (w <= 4) launch_refine_strip<4>(*sd, alpha, n, B, u, f, r, partials, active, st);
     else launch_refine_strip<8>(*sd, alpha, n, B, u, f, r, partials, active, st);
     *nparts = (n / kRsSW) * (n / kRsH);
+    return true;
+  }
+  if (wide_ok && w <= 32 && n % kRsSW == 0 && n % kRwH == 0) {
+    if (w <= 16) launch_refine_wide<16>(*sd, alpha, n, B, u, f, r, partials, active, st);
+    else launch_refine_wide<32>(*sd, alpha, n, B, u, f, r, partials, active, st);
+    *nparts = (n / kRsSW) * (n / kRwH);
     return true;
   }
   *nparts = tx * tx;
@@ -697,7 +895,9 @@ void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float*
   int tx = ceil_div(hi.n, tile);
   int pi_ = log.begin(K_REFINE_RESIDUAL, st);
   int nparts = tx * tx;
-  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, st, &nparts)) {
+  // tile_req <= 0 (the default): the wide strip kernel where it applies
+  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, tile_req <= 0,
+                       st, &nparts)) {
     nparts = tx * tx;
     size_t sm = smem(tile);
     cudaFuncSetAttribute(k_refine_residual2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

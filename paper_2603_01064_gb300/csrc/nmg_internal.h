@@ -159,6 +159,18 @@ bool launch_stencil_residual(const Band2D<T>& op, int B, const T* x, const T* y,
 template <typename T>
 int stencil_strip_parts(const Band2D<T>& op);
 
+// wide PSF stencils (k_wide.cu): the fp32 fine-level residual for Toeplitz K
+// of half-width 9..32 with M = I and n a multiple of 128 (16-byte aligned
+// vectors), as a strip kernel; returns the partial sums written per
+// right-hand side.  The full-weighting restriction of a fine residual r
+// into yc (n a multiple of 128), with the squared norms per unit.
+bool wide_residual_applies(const Band2D<float>& op, const float* x, const float* y);
+int launch_residual_wide(const Band2D<float>& op, int B, const float* x, const float* y, float* r,
+                         double* partials, const int* active, cudaStream_t st);
+bool restrict_fw_applies(int n);
+int launch_restrict_fw(int n, int B, const float* r, float* yc, double* partials, const int* active,
+                       cudaStream_t st);
+
 // r = y - A x on a 2D level (+ per-tile partial sums of r^2 if partials)
 // tile_req: requested tile side (0 = default), see pick_tile
 template <typename T>

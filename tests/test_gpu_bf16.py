@@ -174,6 +174,26 @@ def test_refine_step_matches_fp64_cycle(ctx, prec):
     assert rel(ud.cpu().numpy(), O.nmgf(H, W, 0, u0, f32)) < CYCLE_TOL[prec]
 
 
+@pytest.mark.parametrize("sigma", [4.0, 8.0])
+def test_refine_step_wide_stencils(ctx, sigma):
+    """The compensated outer residual's wide strip kernel (PSF half-width 16
+    for sigma 4 px, 32 for sigma 8 px) inside one refinement step from a
+    nonzero state on a 256 x 256 grid: the step's increment against the
+    oracle cycle's from the same state."""
+    n, L = 256, 4
+    H, G, W = make(ctx, "bf16_refine", n=n, levels=L, sigma=sigma, alpha=1e-2, seed=31)
+    rng = np.random.default_rng(int(sigma))
+    f = rng.standard_normal((3, n, n))
+    u0 = 0.2 * rng.standard_normal((3, n, n))
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    f32 = fd.double().cpu().numpy()
+    ud = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    G.cycle(fd, ud)
+    torch.cuda.synchronize()
+    ref = O.nmgf(H, W, 0, u0, f32)
+    assert rel(ud.cpu().numpy() - u0, ref - u0) < 1e-4
+
+
 @pytest.fixture(scope="module")
 def c2w():
     if not os.path.exists(C2W):

@@ -160,3 +160,29 @@ def test_512_full_batch_solve_sampled(ctx, c3f, alpha):
     assert np.all(st == 0) and np.all(rr <= 1e-6)
     rr_o = O.relres(H, fd[C3_SAMPLE].double().cpu().numpy(), ud[C3_SAMPLE].cpu().numpy())
     assert np.all(rr_o <= 1.01e-6), rr_o
+    # the compensated outer residual (w = 16 stencil) reports the residual
+    # the oracle's fp64 apply finds for the same iterate
+    assert np.max(np.abs(rr_o - rr[C3_SAMPLE]) / rr_o) < 1e-3
+
+
+def test_512_refinement_step_from_nonzero_state(ctx, c3f):
+    """One refinement step (compensated residual r = f - A u with the
+    half-width-16 stencil, inner cycle on r, fp64 update) from a nonzero u:
+    its increment against the oracle cycle's from the same state, at the
+    bf16 form's 1e-4."""
+    alpha = 1e-2
+    W = nmg.load_weights(os.path.join(WDIR, "c3_2d_n512_s4_a1e-2.npz"))
+    taps = I.gaussian_taps(4.0)
+    H = O.build_hierarchy_2d(taps, 512, alpha, 7)
+    G = nmg.Hierarchy(ctx, dim=2, n=512, levels=7, alpha=alpha, taps=taps,
+                      precision="bf16_refine", weights=W)
+    fd = torch.tensor(c3f[:8], dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(9)
+    u0 = 0.3 * rng.standard_normal((8, 512, 512))
+    ud = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    G.cycle(fd, ud)
+    torch.cuda.synchronize()
+    k = [0, 5]
+    ref = O.nmgf(H, W, 0, u0[k], fd[k].double().cpu().numpy())
+    # the step's increments (u0 itself would hide an error in them)
+    assert np.max(rel(ud[k].cpu().numpy() - u0[k], ref - u0[k])) < 1e-4

@@ -111,6 +111,42 @@ def test_residual_restrict(ctx, prec):
         assert relerr(host(yc), ref) < TOL_STEP[prec]
 
 
+@pytest.mark.parametrize("sigma,n", [(4.0, 256), (8.0, 256), (4.0, 512)])
+def test_wide_stencil_residual_and_restrict(ctx, sigma, n):
+    """fp32 fine level with a wide PSF stencil (half-width 16 or 32): the
+    strip residual r = y - A x with its norms, and the residual followed by
+    the separate full-weighting restriction, against the oracle's dense
+    factors; x, y with a zero right-hand side inside the batch."""
+    taps = I.gaussian_taps(sigma)
+    L = int(np.log2(n // 32)) + 1  # coarsest level 32 x 32
+    H = O.build_hierarchy_2d(taps, n, 1e-2, L)
+    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=1e-2, taps=taps, precision="fp32",
+                      weights=I.random_cnn_weights(2, L - 1, seed=8))
+    rng = np.random.default_rng(int(sigma) + n)
+    x = rng.standard_normal((3, n, n))
+    y = rng.standard_normal((3, n, n))
+    x[1] = 0.0
+    y[1] = 0.0
+    xd, yd = dev(x, "fp32"), dev(y, "fp32")
+    x32, y32 = host(xd), host(yd)
+    rd = torch.empty_like(xd)
+    norms = G.residual(0, xd, yd, rd, norms=True)
+    ref = y32 - O.apply_level(H, 0, x32)
+    keep = [0, 2]
+    got = host(rd)
+    assert np.all(got[1] == 0.0) and norms[1] == 0.0
+    assert relerr(got[keep], ref[keep]) < TOL_STEP["fp32"]
+    nref = np.linalg.norm(ref.reshape(3, -1), axis=1)[keep]
+    assert np.max(np.abs(norms[keep] - nref) / nref) < TOL_STEP["fp32"]
+    yc = torch.full((3, n // 2, n // 2), 7.0, dtype=torch.float32, device="cuda")
+    G.residual_restrict(0, xd, yd, yc)
+    refc = O.restrict(H, 0, ref)
+    gotc = host(yc)
+    assert np.all(gotc[1] == 0.0)
+    assert relerr(gotc[keep], refc[keep]) < TOL_STEP["fp32"]
+    G.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_smoother(ctx, prec):
     H, G, W = make2d(ctx, prec)
@@ -148,6 +184,33 @@ def test_filter_update(ctx, prec):
         out = torch.empty_like(xd)
         G.filter_update(l, None, dev(h, prec), out)
         assert relerr(host(out), O.spectral_filter(h, 2)) < TOL_STEP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [256, 512])
+def test_filter_update_large_levels(ctx, prec, n):
+    """The warp-level three-pass filter of 256 x 256 and 512 x 512 levels
+    (row pairs, column pairs through shared memory, rows), in place and from
+    a zero x*, with a zero image in the batch (its F'(h) is 0)."""
+    taps = I.gaussian_taps(2.0)
+    L = int(np.log2(n // 32)) + 1  # coarsest level 32 x 32
+    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=1e-2, taps=taps, precision=prec,
+                      weights=I.random_cnn_weights(2, L - 1, seed=7))
+    rng = np.random.default_rng(n)
+    h = rng.standard_normal((3, n, n))
+    h[1] = 0.0
+    xs = rng.standard_normal((3, n, n))
+    xd = dev(xs, prec)
+    G.filter_update(0, xd, dev(h, prec), xd)
+    ref = xs + O.spectral_filter(h, 2)
+    assert relerr(host(xd), ref) < TOL_STEP[prec]
+    out = torch.empty_like(xd)
+    G.filter_update(0, None, dev(h, prec), out)
+    got = host(out)
+    assert np.all(got[1] == 0.0)
+    keep = [0, 2]
+    assert relerr(got[keep], O.spectral_filter(h[keep], 2)) < TOL_STEP[prec]
+    G.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
