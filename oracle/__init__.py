@@ -5,3 +5,4 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 binding never import it, and the two share no code.
 """
 from .nmg_oracle import *  # noqa: F401,F403
+from .classical import *  # noqa: F401,F403,E402

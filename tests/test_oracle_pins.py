@@ -392,20 +392,8 @@ def test_cycle_with_initial_guess_is_defect_correction():
 # paper's printed closed forms (Section 2.2), golden fixture
 # ---------------------------------------------------------------------------
 
-def test_jacobi_symbol_golden():
-    """Section 2.2: for the periodic matrix tridiag(-1, 2+alpha, -1) and weighted
-    Jacobi with omega = 1/2, the extreme values of the error-propagation symbol
-    are 1 - (4+alpha)/(4+2alpha) and 1 - alpha/(4+2alpha)."""
-    with open(os.path.join(GOLDEN, "jacobi_symbol.json")) as fh:
-        g = json.load(fh)
-    n = 16
-    for case in g["cases"]:
-        alpha = case["alpha"]
-        A = (2 + alpha) * np.eye(n) - np.roll(np.eye(n), 1, 1) - np.roll(np.eye(n), -1, 1)
-        S = np.eye(n) - 0.5 / (2 + alpha) * A
-        ev = np.sort(np.linalg.eigvalsh(S))
-        assert abs(ev[0] - case["mu_min"]) < 1e-12
-        assert abs(ev[-1] - case["mu_max"]) < 1e-12
+# (the printed Jacobi symbol values pin the oracle's weighted Jacobi step in
+# test_oracle_classical.py)
 
 
 # ---------------------------------------------------------------------------
