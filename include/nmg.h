@@ -217,6 +217,32 @@ void nmg_destroy_hier(nmg_hier* h);
 nmg_status nmg_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u,
                      double rtol, int max_cycles, nmg_solve_info* info);
 
+/* ---- classical comparators (the paper's comparison columns) -----------
+ * Both run on a hierarchy of precision NMG_FP64 or NMG_FP32 (f and u in
+ * that type; NMG_ERR_UNSUPPORTED otherwise), with its operators, transfers
+ * and coarsest Cholesky solve, from the caller's u (zeros for x^0 = 0), and
+ * stop a right-hand side once ||f - A u|| / ||f|| <= rtol.  Synchronous;
+ * info as for nmg_solve (cycles = V-cycles or CG iterations).
+ *
+ * nmg_solve_mg_jacobi: x^tau = MG(x^{tau-1}, f) with the V-cycle of
+ * Algorithm 1 (nu1 pre- and nu2 post-smoothing steps per level; the paper's
+ * comparator is the backslash cycle nu1 = 5, nu2 = 0, Section 4.1) and the
+ * weighted Jacobi smoother of Section 2.2, x <- x + omega_l D_l^{-1}
+ * (y - A_l x).  The paper does not print omega for this comparator; each
+ * level uses omega_l = 1 / max_i (sum_j |A_l[i][j]|) / A_l[i][i], the
+ * reciprocal of a Gershgorin bound on the largest eigenvalue of
+ * D_l^{-1} A_l (a fixed omega = 1/2 diverges on blur operators, whose
+ * diagonal is small against their largest eigenvalue).  nu1 + nu2 <= 64.
+ *
+ * nmg_solve_cg: conjugate gradients on A_1 u = f (no preconditioner, as in
+ * Section 4.2); the stopping test uses the recurred residual r_k.
+ * max_iters bounds the iterations. */
+nmg_status nmg_solve_mg_jacobi(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u,
+                               double rtol, int max_cycles, int nu1, int nu2,
+                               nmg_solve_info* info);
+nmg_status nmg_solve_cg(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u, double rtol,
+                        int max_iters, nmg_solve_info* info);
+
 /* One batch of one hierarchy inside a multi-hierarchy solve. */
 typedef struct {
   nmg_hier* hier;        /* hierarchy of this item (each at most once per call) */

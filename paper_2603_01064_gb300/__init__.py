@@ -90,6 +90,8 @@ def lib():
         "nmg_solve_host": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
         "nmg_solve_host_zero": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
         "nmg_solve_multi": (I, [P, I, ctypes.POINTER(_SolveItem), D, I]),
+        "nmg_solve_mg_jacobi": (I, [P, P, I, P, P, D, I, I, I, ctypes.POINTER(SolveInfo)]),
+        "nmg_solve_cg": (I, [P, P, I, P, P, D, I, ctypes.POINTER(SolveInfo)]),
         "nmg_server_create": (I, [P, ctypes.c_size_t, D, I, ctypes.POINTER(P)]),
         "nmg_server_destroy": (V, [P]),
         "nmg_server_add_operator": (I, [P, P, I, ctypes.POINTER(I)]),
@@ -335,6 +337,26 @@ class Hierarchy:
         info = (SolveInfo * max(B, 1))()
         self.ctx.check(lib().nmg_solve(self.ctx._h, self._h, B, _ptr(f), _ptr(u), float(rtol),
                                        int(max_cycles), info))
+        return _unpack(info, B)
+
+    def solve_mg_jacobi(self, f, u, rtol=1e-6, max_cycles=5000, nu1=5, nu2=0):
+        """Classical comparator: V-cycles of Algorithm 1 with weighted Jacobi
+        smoothing (nu1 pre-, nu2 post-smoothing steps).  Returns (cycles,
+        status, relres)."""
+        B = f.shape[0]
+        info = (SolveInfo * max(B, 1))()
+        self.ctx.check(lib().nmg_solve_mg_jacobi(self.ctx._h, self._h, B, _ptr(f), _ptr(u),
+                                                 float(rtol), int(max_cycles), int(nu1), int(nu2),
+                                                 info))
+        return _unpack(info, B)
+
+    def solve_cg(self, f, u, rtol=1e-6, max_iters=10000):
+        """Classical comparator: conjugate gradients.  Returns (iterations,
+        status, relres)."""
+        B = f.shape[0]
+        info = (SolveInfo * max(B, 1))()
+        self.ctx.check(lib().nmg_solve_cg(self.ctx._h, self._h, B, _ptr(f), _ptr(u), float(rtol),
+                                          int(max_iters), info))
         return _unpack(info, B)
 
     def solve_host(self, f: np.ndarray, u: np.ndarray, rtol=1e-6, max_cycles=100,

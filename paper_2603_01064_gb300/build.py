@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "hierarchy.cpp", "k_ops.cu", "k_cnn.cu", "k_cnn_bf16.cu", "k_filter.cu",
-           "k_coarse.cu", "k_refine.cu", "k_stencil_f32.cu", "k_stencil_f64.cu", "k_fno.cu", "k_wide.cu"]
+           "k_coarse.cu", "k_refine.cu", "k_stencil_f32.cu", "k_stencil_f64.cu", "k_fno.cu", "k_wide.cu", "k_classic.cu"]
 
 
 def _nvcc():

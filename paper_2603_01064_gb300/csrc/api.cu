@@ -14,6 +14,8 @@
 // residual: r = f - A u with u in fp64 and r computed in compensated fp32,
 // d = NMGF(0, r), u += d in fp64.  Because NMGF(x*, y) = x* + NMGF(0, y - A x*)
 // (the cycle's first steps only see y - A x*), this is the same iteration.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -109,6 +111,7 @@ struct Work {
   void* cbuf = nullptr;
   void* fno_a = nullptr;  // FNO spectral scratch: [cap][width][n][m] complex
   void* fno_b = nullptr;  // 2 x [cap][width][2m][m] complex
+  double* cg = nullptr;   // conjugate gradients: (r, r), alpha, beta per right-hand side
   float* r32 = nullptr;   // refinement residual (inner rhs)
   float* d32 = nullptr;   // refinement correction
   void* fdev = nullptr;   // nmg_solve_host staging
@@ -123,6 +126,7 @@ struct Work {
   const void* gu = nullptr;
   double grtol = -1.0;
   long long gkernels = 0;
+  int gkind = -1;  // which iteration the graph holds (neural cycle, V-cycle, CG)
 };
 
 }  // namespace
@@ -253,6 +257,7 @@ nmg_status ensure_work(nmg_hier* h, int B) {
     AL(B * sizeof(double), w.s[l]);
   }
   AL(B * sizeof(double), w.fn);
+  AL(3 * B * sizeof(double), w.cg);
   AL(B * sizeof(double), w.relres);
   AL(B * sizeof(int), w.status);
   AL(B * sizeof(int), w.cycles);
@@ -499,7 +504,7 @@ void launch_refine_residual_dispatch(nmg_hier* h, int B, const double* u, const 
 // replayed on the context's stream (eager launches when profiling).
 template <typename Step, typename Test>
 nmg_status run_outer(nmg_hier* h, int B, const void* f, const void* u, double rtol,
-                     int max_cycles, nmg_solve_info* info, Step step, Test test) {
+                     int max_cycles, nmg_solve_info* info, Step step, Test test, int kind = 0) {
   nmg_ctx* ctx = h->ctx;
   Work& w = h->w;
   cudaStream_t st = ctx->stream;
@@ -517,7 +522,7 @@ nmg_status run_outer(nmg_hier* h, int B, const void* f, const void* u, double rt
   ctx->log.active_hint = nactive;
   cudaGraphExec_t exec = nullptr;
   if (ctx->graphs && !ctx->log.prof && nactive > 0 && max_cycles > 0) {
-    if (w.gexec && w.gB == B && w.gf == f && w.gu == u && w.grtol == rtol) {
+    if (w.gexec && w.gB == B && w.gf == f && w.gu == u && w.grtol == rtol && w.gkind == kind) {
       exec = w.gexec;
     } else {
       if (w.gexec) cudaGraphExecDestroy(w.gexec);
@@ -540,6 +545,7 @@ nmg_status run_outer(nmg_hier* h, int B, const void* f, const void* u, double rt
           w.gf = f;
           w.gu = u;
           w.grtol = rtol;
+          w.gkind = kind;
           w.gkernels = ctx->log.launches - l0;
           exec = w.gexec;
         } else {
@@ -717,6 +723,172 @@ nmg_status solve_plain(nmg_hier* h, int B, const T* f, T* u, double rtol, int ma
     launch_count_cycles(B, w.active, w.cycles, ctx->stream, ctx->log);
   };
   return run_outer(h, B, f, u, rtol, max_cycles, info, step, test);
+}
+
+// ---------------------------------------------------------------------------
+// classical comparators: the backslash V-cycle of Algorithm 1 with weighted
+// Jacobi smoothing (Section 2.2) and conjugate gradients, on the same
+// hierarchy (operators, transfers, coarsest solve) as the neural cycle
+// ---------------------------------------------------------------------------
+
+// omega_l = 1 / max over rows of (sum_j |A_l[i][j]|) / A_l[i][i] (a
+// Gershgorin bound on the largest eigenvalue of D^{-1} A_l, so the weighted
+// Jacobi step contracts and maps the top of the spectrum to about 1, as
+// omega = 1/2 does for the model problem of Section 2.2), from the level's
+// fp64 factors
+nmg_status jacobi_weights(nmg_hier* h, std::vector<double>& om) {
+  nmg_ctx* ctx = h->ctx;
+  om.assign(h->L, 0.0);
+  for (int l = 0; l + 1 < h->L; ++l) {
+    const DevLevel& d = h->lv[l];
+    const int n = d.n;
+    double rho = 0.0;
+    if (h->dim == 1) {
+      std::vector<double> A((size_t)n * n);
+      CK(cudaMemcpy(A.data(), d.A_d, A.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      for (int i = 0; i < n; ++i) {
+        double sr = 0.0;
+        for (int j = 0; j < n; ++j) sr += std::fabs(A[(size_t)i * n + j]);
+        rho = std::max(rho, sr / A[(size_t)i * n + i]);
+      }
+    } else {
+      const int nk = 2 * d.wK + 1, nm = 2 * d.wM + 1;
+      std::vector<double> K((size_t)n * nk), M((size_t)n * nm);
+      CK(cudaMemcpy(K.data(), d.Kd_d, K.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(M.data(), d.Md_d, M.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      std::vector<double> sk(n), sm(n), dk(n), dm(n);
+      for (int i = 0; i < n; ++i) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < nk; ++k) a += std::fabs(K[(size_t)i * nk + k]);
+        for (int k = 0; k < nm; ++k) b += std::fabs(M[(size_t)i * nm + k]);
+        sk[i] = a;
+        sm[i] = b;
+        dk[i] = K[(size_t)i * nk + d.wK];
+        dm[i] = M[(size_t)i * nm + d.wM];
+      }
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          rho = std::max(rho, (h->alpha * sm[i] * sm[j] + sk[i] * sk[j]) /
+                                  (h->alpha * dm[i] * dm[j] + dk[i] * dk[j]));
+    }
+    om[l] = 1.0 / rho;
+  }
+  return NMG_OK;
+}
+
+template <typename T>
+void op_jacobi(nmg_hier* h, int l, int B, T* x, const T* r, double omega, const int* active) {
+  nmg_ctx* c = h->ctx;
+  if (h->dim == 2)
+    launch_jacobi2d<T>(band<T>(h, l), B, x, r, omega, active, c->stream, c->log);
+  else
+    launch_jacobi1d<T>(h->lv[l].n, Ad<T>(h->lv[l]), B, x, r, omega, active, c->stream, c->log);
+}
+
+// one V-cycle MG(A, x*, y, nu1, nu2, 1, L) of Algorithm 1 on level 0's x0
+// (the current iterate, in place) with right-hand side f
+template <typename T>
+void mgj_body(nmg_hier* h, int B, const T* f, T* x0, int nu1, int nu2,
+              const std::vector<double>& om, const int* active) {
+  Work& w = h->w;
+  nmg_ctx* c = h->ctx;
+  const int L = h->L;
+  if (L == 1) {
+    op_coarse<T>(h, B, f, x0, active);
+    return;
+  }
+  auto X = [&](int l) { return l == 0 ? x0 : reinterpret_cast<T*>(w.x[l]); };
+  auto Y = [&](int l) { return l == 0 ? f : reinterpret_cast<const T*>(w.y[l]); };
+  auto smooth = [&](int l, int nu, bool zero_guess) {
+    T* r = reinterpret_cast<T*>(w.h[l]);
+    for (int k = 0; k < nu; ++k) {
+      if (k == 0 && zero_guess) {
+        op_jacobi<T>(h, l, B, X(l), Y(l), om[l], active);  // r = y for x = 0
+      } else {
+        op_residual<T>(h, l, B, X(l), Y(l), r, w.part[l], active);
+        op_jacobi<T>(h, l, B, X(l), r, om[l], active);
+      }
+    }
+  };
+  for (int l = 0; l < L - 1; ++l) {
+    if (l > 0) cudaMemsetAsync(X(l), 0, plane(h, l) * (size_t)B * sizeof(T), c->stream);
+    smooth(l, nu1, l > 0);
+    op_residual_restrict<T>(h, l, B, X(l), Y(l), reinterpret_cast<T*>(w.y[l + 1]), w.part[l + 1],
+                            active);
+  }
+  op_coarse<T>(h, B, Y(L - 1), X(L - 1), active);
+  for (int l = L - 2; l >= 0; --l) {
+    op_prolong<T>(h, l, B, X(l + 1), X(l), active);
+    smooth(l, nu2, false);
+  }
+}
+
+template <typename T>
+nmg_status solve_mgj(nmg_hier* h, int B, const T* f, T* u, double rtol, int max_cycles, int nu1,
+                     int nu2, nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  std::vector<double> om;
+  nmg_status s = jacobi_weights(h, om);
+  if (s != NMG_OK) return s;
+  int nt = 0;
+  ctx->log.active_hint = B;
+  launch_sumsq<T>(f, (long long)plane(h, 0), B, w.part[0], &nt, w.ones, ctx->stream, ctx->log);
+  launch_norms(w.part[0], nt, B, w.fn, w.ones, ctx->stream, ctx->log);
+  T* b0 = reinterpret_cast<T*>(w.t[0]);
+  auto test = [&]() {
+    int ntl = op_residual<T>(h, 0, B, u, f, b0, w.part[0], w.active);
+    launch_norms(w.part[0], ntl, B, w.s[0], w.active, ctx->stream, ctx->log);
+    cudaMemsetAsync(w.nactive, 0, sizeof(int), ctx->stream);
+    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, ctx->stream,
+                    ctx->log);
+    cudaMemcpyAsync(w.h_nactive, w.nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  };
+  auto step = [&]() {
+    mgj_body<T>(h, B, f, u, nu1, nu2, om, w.active);
+    launch_count_cycles(B, w.active, w.cycles, ctx->stream, ctx->log);
+  };
+  return run_outer(h, B, f, u, rtol, max_cycles, info, step, test, 1000 + 32 * nu1 + nu2);
+}
+
+// conjugate gradients on A_1 u = f: r = f - A u and p = r at the first
+// test; every step is one iteration (q = -A p by the residual kernel with a
+// zero right-hand side, then alpha, u, r, beta, p); the convergence test
+// reads the recurred residual's norm
+template <typename T>
+nmg_status solve_cg(nmg_hier* h, int B, const T* f, T* u, double rtol, int max_iters,
+                    nmg_solve_info* info) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  int nt = 0;
+  const long long len = (long long)plane(h, 0);
+  ctx->log.active_hint = B;
+  launch_sumsq<T>(f, len, B, w.part[0], &nt, w.ones, ctx->stream, ctx->log);
+  launch_norms(w.part[0], nt, B, w.fn, w.ones, ctx->stream, ctx->log);
+  T* r = reinterpret_cast<T*>(w.h[0]);
+  T* p = reinterpret_cast<T*>(w.x[0]);
+  T* q = reinterpret_cast<T*>(w.t[0]);
+  bool first = true;
+  auto test = [&]() {
+    if (first) {
+      first = false;
+      int ntl = op_residual<T>(h, 0, B, u, f, r, w.part[0], w.active);
+      launch_norms(w.part[0], ntl, B, w.s[0], w.active, ctx->stream, ctx->log);
+      launch_cg_init(B, w.s[0], w.cg, w.active, ctx->stream, ctx->log);
+      cudaMemcpyAsync(p, r, (size_t)len * B * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    cudaMemsetAsync(w.nactive, 0, sizeof(int), ctx->stream);
+    launch_converge(w.s[0], w.fn, rtol, B, w.active, w.relres, w.status, w.nactive, ctx->stream,
+                    ctx->log);
+    cudaMemcpyAsync(w.h_nactive, w.nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  };
+  auto step = [&]() {
+    op_residual<T>(h, 0, B, p, (const T*)nullptr, q, w.part[0], w.active);  // q = -A p
+    launch_cg_iteration<T>(len, B, u, r, p, q, w.cg, w.s[0], w.part[0], w.active, ctx->stream,
+                           ctx->log);
+    launch_count_cycles(B, w.active, w.cycles, ctx->stream, ctx->log);
+  };
+  return run_outer(h, B, f, u, rtol, max_iters, info, step, test, 2);
 }
 
 nmg_status solve_refine(nmg_hier* h, int B, const float* f, double* u, double rtol,
@@ -1190,6 +1362,41 @@ nmg_status nmg_solve(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* 
     default:
       return solve_refine(h, batch, (const float*)f, (double*)u, rtol, max_cycles, info);
   }
+}
+
+nmg_status nmg_solve_mg_jacobi(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u,
+                               double rtol, int max_cycles, int nu1, int nu2,
+                               nmg_solve_info* info) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!f || !u) return fail(ctx, NMG_ERR_ARG, "null f or u");
+  if (!(rtol >= 0.0) || max_cycles < 0 || nu1 < 0 || nu2 < 0 || nu1 + nu2 > 64)
+    return fail(ctx, NMG_ERR_ARG, "bad rtol, max_cycles or smoothing steps");
+  if (h->precision != NMG_FP64 && h->precision != NMG_FP32)
+    return fail(ctx, NMG_ERR_UNSUPPORTED, "the classical solvers run in the FP64 and FP32 forms");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  if (h->precision == NMG_FP64)
+    return solve_mgj<double>(h, batch, (const double*)f, (double*)u, rtol, max_cycles, nu1, nu2,
+                             info);
+  return solve_mgj<float>(h, batch, (const float*)f, (float*)u, rtol, max_cycles, nu1, nu2, info);
+}
+
+nmg_status nmg_solve_cg(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* u, double rtol,
+                        int max_iters, nmg_solve_info* info) {
+  nmg_status s = check_common(ctx, h, batch);
+  if (s != NMG_OK) return s;
+  if (batch == 0) return NMG_OK;
+  if (!f || !u) return fail(ctx, NMG_ERR_ARG, "null f or u");
+  if (!(rtol >= 0.0) || max_iters < 0) return fail(ctx, NMG_ERR_ARG, "bad rtol or max_iters");
+  if (h->precision != NMG_FP64 && h->precision != NMG_FP32)
+    return fail(ctx, NMG_ERR_UNSUPPORTED, "the classical solvers run in the FP64 and FP32 forms");
+  if ((s = set_device(ctx)) != NMG_OK) return s;
+  if ((s = ensure_work(h, batch)) != NMG_OK) return s;
+  if (h->precision == NMG_FP64)
+    return solve_cg<double>(h, batch, (const double*)f, (double*)u, rtol, max_iters, info);
+  return solve_cg<float>(h, batch, (const float*)f, (float*)u, rtol, max_iters, info);
 }
 
 nmg_status nmg_solve_multi(nmg_ctx* ctx, int nitems, const nmg_solve_item* items, double rtol,

@@ -168,6 +168,20 @@ bool wide_residual_applies(const Band2D<float>& op, const float* x, const float*
 int launch_residual_wide(const Band2D<float>& op, int B, const float* x, const float* y, float* r,
                          double* partials, const int* active, cudaStream_t st);
 bool restrict_fw_applies(int n);
+// classical comparators (k_classic.cu): x += omega r / diag(A_l), and one
+// conjugate-gradient iteration after q = -A p (scal: (r, r), alpha, beta)
+template <typename T>
+void launch_jacobi2d(const Band2D<T>& op, int B, T* x, const T* r, double omega, const int* active,
+                     cudaStream_t st, LaunchLog& log);
+template <typename T>
+void launch_jacobi1d(int n, const T* A, int B, T* x, const T* r, double omega, const int* active,
+                     cudaStream_t st, LaunchLog& log);
+template <typename T>
+void launch_cg_iteration(long long len, int B, T* u, T* r, T* p, const T* q, double* scal,
+                         double* s, double* partials, const int* active, cudaStream_t st,
+                         LaunchLog& log);
+void launch_cg_init(int B, const double* s, double* scal, const int* active, cudaStream_t st,
+                    LaunchLog& log);
 int launch_restrict_fw(int n, int B, const float* r, float* yc, double* partials, const int* active,
                        cudaStream_t st);
 
