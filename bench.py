@@ -506,6 +506,11 @@ def run_ours(args, wl, world, rank, local):
         Gs.close()
         compare["headline_vs_fp32_single_rhs"] = value / world / compare["fp32_single_rhs"]["value"]
 
+    # ---- the paper's classical comparators on the same operator and right-hand sides
+    classical = None
+    if not args.no_classical:
+        classical = classical_leg(ctx, wl, f, taps, stream, mean_cycles)
+
     # ---- alpha sweep of the workload's operator (its own trained smoothers per alpha)
     sweep = None
     if wl.get("sweep") and not args.no_sweep:
@@ -537,6 +542,10 @@ def run_ours(args, wl, world, rank, local):
     serving = None
     if not args.no_serving:
         serving = serving_leg(ctx, rank)
+    # ---- mixed batch: 24 operator classes in one multi-solve
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_leg(ctx, flush, stream, rank)
     fno = None
     if not args.no_fno:
         fno = fno_leg(ctx, WORKLOADS["c2"])
@@ -571,7 +580,8 @@ def run_ours(args, wl, world, rank, local):
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "converged": converged, "max_relres": max_relres, "mean_cycles": mean_cycles,
-                "compare": compare, "alpha_sweep": sweep, "roofline": roof,
+                "compare": compare, "classical": classical, "alpha_sweep": sweep,
+                "mixed_batch": mixed, "roofline": roof,
                 "kernels": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "secondary": secondary, "serving": serving, "fno_smoother": fno,
@@ -579,13 +589,54 @@ def run_ours(args, wl, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+CLASSICAL_RHS = 16  # right-hand sides of the workload the classical comparators solve
+
+
+def classical_leg(ctx, wl, f, taps, stream, neural_cycles):
+    """The comparators of the paper's tables on the workload's operator, fp32,
+    to the same 1e-6: the backslash V-cycle of Algorithm 1 with weighted
+    Jacobi smoothing (nu1 = 5, nu2 = 0) and conjugate gradients, on the
+    first CLASSICAL_RHS right-hand sides (one solve call each form, CUDA
+    events around it), beside the neural cycle's count."""
+    import torch
+    import paper_2603_01064_gb300 as nmg
+    B = min(CLASSICAL_RHS, f.shape[0])
+    G = nmg.Hierarchy(ctx, dim=2, n=wl["n"], levels=wl["levels"], alpha=wl["alpha"], taps=taps,
+                      precision="fp32", weights=nmg.load_weights(os.path.join(WEIGHTS, wl["weights"])))
+    fs = f[:B].contiguous()
+    out = {"rhs": B, "precision": "fp32", "neural_mean_cycles": neural_cycles}
+    for name, fn in [("mg_jacobi_nu1_5", lambda u: G.solve_mg_jacobi(fs, u, 1e-6, 20000, 5, 0)),
+                     ("cg", lambda u: G.solve_cg(fs, u, 1e-6, 20000))]:
+        u = torch.zeros_like(fs)
+        fn(u)  # warm-up (graph capture)
+        u.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cyc, st, rr = fn(u)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": B / (ms / 1e3), "unit": "RHS/s", "mean_cycles": float(np.mean(cyc)),
+                     "max_cycles": int(np.max(cyc)), "converged": int((st == 0).sum()),
+                     "max_relres": float(np.max(rr)), "ms": ms}
+    G.close()
+    return out
+
+
 SWEEP_ORACLE_SAMPLE = 1  # right-hand sides per alpha checked against the oracle's cycle
+
+
+# the CNN smoothers of the alpha = 1e-3 operator take about 170 cycles to
+# 1e-6 (their 3 x 3, four-layer receptive field is short for that level's
+# operator); the limit leaves them room and bounds the alpha = 1e-4 solve
+SWEEP_MAX_CYCLES = 250
 
 
 def sweep_leg(ctx, wl, f, taps, flush, stream, rank):
     """For each alpha of the workload's sweep, with that operator's trained
     CNN smoothers: a bf16 split refinement solve of the whole batch to 1e-6
-    (at most 100 cycles), its cycles and residuals, the final residual of
+    (at most SWEEP_MAX_CYCLES cycles), its cycles and residuals, the final residual of
     sampled right-hand sides recomputed by the FP64 oracle's own apply, and
     one cycle from zero of the whole batch against the oracle's cycle for a
     sampled right-hand side (the per-cycle parity bar of the bf16 form is
@@ -601,8 +652,9 @@ def sweep_leg(ctx, wl, f, taps, flush, stream, rank):
                           precision="bf16_refine", weights=Wa)
         G.autotune(B)
         u = torch.zeros(f.shape, dtype=torch.float64, device="cuda")
-        G.solve(f, u, rtol=1e-6, max_cycles=100)
-        tp, rp = timed_steps(lambda: (u.zero_(), G.solve(f, u, rtol=1e-6, max_cycles=100))[1],
+        G.solve(f, u, rtol=1e-6, max_cycles=SWEEP_MAX_CYCLES)
+        tp, rp = timed_steps(lambda: (u.zero_(), G.solve(f, u, rtol=1e-6,
+                                                         max_cycles=SWEEP_MAX_CYCLES))[1],
                              1, flush, stream)
         row = {"alpha": alpha, "weights": wname, **solve_summary(B, tp, rp)}
         if rank == 0:
@@ -665,10 +717,103 @@ def secondary_leg(ctx, wl, prec, flush, stream, rank):
     return out
 
 
-SERVING = dict(requests=800, rate=400.0, seed=4242,
-               ops=[  # (n, levels, sigma px, alpha, weights, slots)
-                   (128, 5, 2.0, 1e-2, "c2_2d_n128_s2_a1e-2.npz", 128),
-                   (512, 7, 4.0, 1e-2, "c3_2d_n512_s4_a1e-2.npz", 16)])
+def operator_weights(sigma, alpha, levels):
+    from paper_2603_01064_gb300.weights import operator_weights as ow
+    return ow(sigma, alpha, levels)
+
+
+# Mixed batch: 512 right-hand sides drawn uniformly (seeded) over 24
+# operator classes, grid sides {64, 128, 256, 512} x PSF sigma {1, 2, 4} px x
+# alpha {1e-3, 1e-2}, levels log2(n) - 2 (coarsest 8 x 8); one
+# nmg_solve_multi call: one captured graph per outer iteration with the
+# classes as parallel branches, launch shapes autotuned per class
+MIXED = dict(rhs=512, seed=777, sizes=[64, 128, 256, 512], sigmas=[1.0, 2.0, 4.0],
+             alphas=[1e-3, 1e-2], max_cycles=250, steps=2)
+
+
+def mixed_leg(ctx, flush, stream, rank):
+    """The mixed batch solved to 1e-6 in one multi-solve (CUDA events around
+    each of MIXED['steps'] solves after one untimed one), beside the same
+    classes solved one after another with nmg_solve; per class its cycles
+    and convergence; kernels launched per outer iteration."""
+    import torch
+    import paper_2603_01064_gb300 as nmg
+    classes = [(n, sg, al) for n in MIXED["sizes"] for sg in MIXED["sigmas"]
+               for al in MIXED["alphas"]]
+    rng = np.random.default_rng(MIXED["seed"] + 7919 * rank)
+    counts = np.bincount(rng.integers(0, len(classes), MIXED["rhs"]), minlength=len(classes))
+    items, meta = [], []
+    for k, ((n, sg, al), B) in enumerate(zip(classes, counts)):
+        if B == 0:
+            continue
+        L = int(np.log2(n)) - 2
+        G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=al, taps=I.gaussian_taps(sg),
+                          precision="bf16_refine", weights=operator_weights(sg, al, L))
+        G.autotune(int(B))
+        f, _ = I.rhs_2d_waves_rects(n, int(B), MIXED["seed"] + 31 * k + 7919 * rank, sg)
+        fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+        items.append((G, fd, torch.zeros(fd.shape, dtype=torch.float64, device="cuda")))
+        meta.append({"n": n, "sigma_px": sg, "alpha": al, "levels": L, "rhs": int(B)})
+
+    def multi():
+        for _, _, u in items:
+            u.zero_()
+        return nmg.solve_multi(ctx, items, rtol=1e-6, max_cycles=MIXED["max_cycles"])
+
+    multi()
+    torch.cuda.synchronize()
+    l0 = ctx.launches()
+    tp, rp = timed_steps(multi, MIXED["steps"], flush, stream)
+    kernels = (ctx.launches() - l0) / MIXED["steps"]
+    iters = max(int(r[0].max()) for r in rp[-1]) + 1
+
+    def sequential():
+        out = []
+        for G, f, u in items:
+            u.zero_()
+            out.append(G.solve(f, u, rtol=1e-6, max_cycles=MIXED["max_cycles"]))
+        return out
+
+    sequential()
+    ts, _ = timed_steps(sequential, 1, flush, stream)
+    total = int(sum(m["rhs"] for m in meta))
+    per_class = []
+    for m, r in zip(meta, rp[-1]):
+        per_class.append(dict(m, mean_cycles=float(r[0].mean()), max_cycles=int(r[0].max()),
+                              converged=int((r[1] == 0).sum()), max_relres=float(r[2].max())))
+    for G, _, _ in items:
+        G.close()
+    return {"rhs": total, "classes": len(meta), "precision": "bf16_refine",
+            "value": total * len(tp) / (sum(tp) / 1e3), "unit": "RHS/s",
+            "ms_per_solve": float(np.mean(tp)), "outer_iterations": iters,
+            "graph_launches_per_iteration": 1 if ctx.graphs else None,
+            "kernels_per_iteration": kernels / iters,
+            "converged": int(sum(c["converged"] for c in per_class)),
+            "sequential_value": total / (ts[0] / 1e3),
+            "note": "one nmg_solve_multi call; sequential_value: the same classes solved one "
+                    "nmg_solve call after another",
+            "per_class": per_class}
+
+
+# Serving: grid sides n = 2^e with e uniform in {6..11} (log-uniform 64^2 ..
+# 2048^2), levels e - 2 (coarsest 8 x 8), PSF sigma = max(1, 8 n / 2048) px,
+# alpha 1e-3 (the 2048^2 class: 9 levels, sigma 8 px).  Smoother sets per
+# sigma (trained level-wise for that sigma and alpha); a class with more
+# smoother levels than its set repeats the set's last (coarsest) net.
+SERVING = dict(requests=240, burst=60, load=0.8, seed=4242, alpha=1e-3, max_cycles=300,
+               exps=[6, 7, 8, 9, 10, 11],
+               slots={6: 64, 7: 64, 8: 32, 9: 16, 10: 8, 11: 4}, fp32_sample=12)
+
+
+def serving_classes():
+    """(n, levels, sigma, weights) of the serving size classes."""
+    out = []
+    for e in SERVING["exps"]:
+        n = 1 << e
+        sigma = max(1.0, 8.0 * n / 2048.0)
+        L = e - 2
+        out.append((n, L, sigma, operator_weights(sigma, SERVING["alpha"], L)))
+    return out
 
 
 FNO = dict(width=64, layers=4, modes=8, ksize=3, seed=0, reps=5)
@@ -771,28 +916,78 @@ def hbm_apply_leg(ctx, flush, stream):
 
 
 def serving_leg(ctx, rank):
-    """Requests drawn uniformly from two resident operators (128x128 sigma 2
-    px and 512x512 sigma 4 px, both alpha 1e-2, bf16 split refinement),
-    arriving as a seeded Poisson stream in real time; every request runs to
-    1e-6.  Latency = completion - submission (host clock)."""
+    """Continuous batching over the serving size classes (bf16 refinement
+    form, every request to 1e-6 or the cycle limit), all hierarchies
+    resident, pools admitted by free device memory:
+      1. saturation: SERVING['burst'] requests submitted at once; completed
+         requests per second = the saturated throughput X;
+      2. a seeded Poisson stream of SERVING['requests'] requests at rate
+         load x X in real time: throughput and p50 / p99 latency (completion
+         - submission, host clock);
+      3. the plain fp32 cycle one request at a time (no batching, no queue)
+         on a sample of the same requests: requests per second and the
+         per-request latencies."""
+    import torch
     import paper_2603_01064_gb300 as nmg
     from paper_2603_01064_gb300 import serve
-    ops = [serve.Operator(n, L, sig, a, nmg.load_weights(os.path.join(WEIGHTS, w)), "bf16_refine",
-                          slots) for (n, L, sig, a, w, slots) in SERVING["ops"]]
-    srv, hs, ids = serve.build_server(ctx, ops, budget_bytes=48 << 30)
-    for G in hs:
-        G.autotune(16)
-    reqs = serve.poisson_stream(ops, SERVING["requests"], SERVING["rate"],
-                                SERVING["seed"] + 7919 * rank, rhs_batch=8)
-    elapsed, done = serve.run_stream(srv, ids, reqs, time_limit_s=60.0)
+    cls = serving_classes()
+    ops = [serve.Operator(n, L, sg, SERVING["alpha"], W, "bf16_refine",
+                          SERVING["slots"][int(np.log2(n))]) for (n, L, sg, W) in cls]
+    srv, hs, ids = serve.build_server(ctx, ops, budget_bytes=0,
+                                      max_cycles=SERVING["max_cycles"])
+    seed = SERVING["seed"] + 7919 * rank
+    burst = serve.poisson_stream(ops, SERVING["burst"], 1e9, seed + 1, rhs_batch=4)
+    t_b, done_b = serve.run_stream(srv, ids, burst, time_limit_s=120.0)
+    sat = len(done_b) / t_b if t_b > 0 else None
+    rate = SERVING["load"] * sat if sat else 10.0
+    reqs = serve.poisson_stream(ops, SERVING["requests"], rate, seed, rhs_batch=4)
+    elapsed, done = serve.run_stream(srv, ids, reqs, time_limit_s=120.0)
     lat = serve.latency_stats(done)
-    out = {"requests": len(reqs), "completed": len(done), "rate_rps": SERVING["rate"],
-           "sizes": [o.n for o in ops], "slots": [o.slots for o in ops],
-           "precision": "bf16_refine", "wall_s": elapsed,
+    per_class = {}
+    for k, o in enumerate(ops):
+        dk = [r for r in done if r.op == k]
+        if dk:
+            per_class[str(o.n)] = {"requests": len(dk),
+                                   "mean_cycles": float(np.mean([r.info[0] for r in dk])),
+                                   "converged": int(sum(r.info[1] == 0 for r in dk)),
+                                   **serve.latency_stats(dk)}
+    out = {"requests": len(reqs), "completed": len(done), "wall_s": elapsed,
+           "saturated_rhs_s": sat, "rate_rps": rate, "load": SERVING["load"],
            "throughput_rhs_s": len(done) / elapsed if elapsed > 0 else None,
-           "converged": all(r.info and r.info[1] == 0 for r in done), **lat}
+           "converged": int(sum(r.info and r.info[1] == 0 for r in done)),
+           "sizes": [o.n for o in ops], "sigma_px": [o.sigma for o in ops], "alpha": SERVING["alpha"],
+           "max_slots": [o.slots for o in ops], "precision": "bf16_refine",
+           "admission": "free device memory (pools grow on demand)", **lat, "per_class": per_class}
     srv.close()
     for G in hs:
+        G.close()
+    # the plain fp32 cycle, one request at a time, on a sample of the stream
+    sample = reqs[:SERVING["fp32_sample"]]
+    hs32 = {}
+    lat32, cyc32, conv32 = [], [], 0
+    t0 = time.perf_counter()
+    for r in sample:
+        o = ops[r.op]
+        if r.op not in hs32:
+            hs32[r.op] = nmg.Hierarchy(ctx, dim=2, n=o.n, levels=o.levels, alpha=o.alpha,
+                                       taps=I.gaussian_taps(o.sigma), precision="fp32",
+                                       weights=o.weights)
+        G = hs32[r.op]
+        ts = time.perf_counter()
+        fd = torch.tensor(r.f[None], device="cuda")
+        ud = torch.zeros_like(fd)
+        cyc, st, rr = G.solve(fd, ud, rtol=1e-6, max_cycles=SERVING["max_cycles"])
+        ud.cpu()
+        lat32.append(time.perf_counter() - ts)
+        cyc32.append(int(cyc[0]))
+        conv32 += int(st[0] == 0)
+    t32 = time.perf_counter() - t0
+    out["fp32_one_at_a_time"] = {
+        "requests": len(sample), "value": len(sample) / t32, "unit": "RHS/s",
+        "p50_ms": 1e3 * float(np.percentile(lat32, 50)), "p99_ms": 1e3 * float(np.percentile(lat32, 99)),
+        "mean_cycles": float(np.mean(cyc32)), "converged": conv32,
+        "note": "solve time per request alone (setup of the hierarchies excluded)"}
+    for G in hs32.values():
         G.close()
     return out
 
@@ -812,8 +1007,12 @@ def main():
     ap.add_argument("--precision", default="bf16_refine", choices=sorted(PRECISION_TEXT))
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison forms")
     ap.add_argument("--no-sweep", action="store_true", help="skip the alpha sweep")
+    ap.add_argument("--no-classical", action="store_true",
+                    help="skip the classical comparators (Jacobi V-cycle, CG)")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 128x128 line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the 24-class mixed batch (one multi-solve)")
     ap.add_argument("--no-fno", action="store_true", help="skip the FNO smoother timing")
     ap.add_argument("--no-hbm-apply", action="store_true",
                     help="skip the out-of-L2 operator apply timing")

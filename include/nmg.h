@@ -158,6 +158,7 @@ typedef struct {
  * are neural operators, Section 3.1; here conv -> ReLU -> ... -> conv with
  * zero 'same' padding and a bias on every layer), or the FNO of Appendix A.
  *   layers   number of conv layers (>= 2); channels 1 -> width ->...-> 1
+ *            (every level, unless level_layers is given)
  *   width    hidden channels (2D: 32; 1D: 16 in this build)
  *   ksize    kernel size (2D: 3; 1D: 5 in this build)
  *   nlevels  smoother levels present in `weights`; must be >= levels-1.
@@ -166,6 +167,12 @@ typedef struct {
  *   weights  host doubles, copied at setup.  For each level, for each
  *            layer: W in PyTorch Conv layout [Cout][Cin][k] (1D) or
  *            [Cout][Cin][k][k] (2D), then bias [Cout].
+ *   level_layers  CNN only, optional: nlevels layer counts, one per smoother
+ *            level (2..16; 3..16 in the refinement precisions), read at
+ *            setup; NULL = `layers` on every level.  The paper sizes each
+ *            level's network separately (Appendix A, Table 6: more layers
+ *            and wider kernels on some grids); a deeper net widens the
+ *            receptive field where the level's operator needs it.
  *   nweights total number of doubles in `weights` (checked).
  *   arch     NMG_SMOOTHER_CNN (0, the above) or NMG_SMOOTHER_FNO (1).
  *   modes    FNO only: m, the retained modes per axis (the half spectrum of
@@ -189,6 +196,7 @@ typedef struct {
   size_t nweights;
   int arch;
   int modes;
+  const int* level_layers;
 } nmg_smoother_desc;
 
 typedef struct {
@@ -292,13 +300,20 @@ nmg_status nmg_cycle(nmg_ctx* ctx, nmg_hier* h, int batch, const void* f, void* 
  * computed independently: a request's result does not depend on the other
  * requests in flight.  The server does not own the hierarchies. */
 typedef struct nmg_server nmg_server;
-/* budget_bytes bounds the device memory of all slot pools. */
+/* budget_bytes bounds the device memory of all slot pools and their
+ * workspaces (0: no bound beyond the device's free memory). */
 nmg_status nmg_server_create(nmg_ctx* ctx, size_t budget_bytes, double rtol, int max_cycles,
                              nmg_server** out);
 void nmg_server_destroy(nmg_server* s);
-/* Make hierarchy h servable with `slots` concurrent requests; allocates its
- * workspace for that many right-hand sides plus slot buffers for f and u
- * (NMG_ERR_OOM if the budget would be exceeded).  op_id: returned handle. */
+/* Make hierarchy h servable with up to `slots` concurrent requests.  The
+ * pool (slot buffers for f and u and the hierarchy's workspace) starts with
+ * min(slots, 4) slots and grows by doubling, up to `slots`, when requests
+ * wait for it at a scheduler step -- each growth only if the device's free
+ * memory at that moment (cudaMemGetInfo, less a reserve of max(256 MiB,
+ * 1/64 of the device)) and the budget allow it; otherwise the requests stay
+ * queued until slots free up (admission bounded by free HBM).  Growth keeps
+ * the live requests in their slots.  NMG_ERR_OOM if not even the first
+ * slots fit.  op_id: returned handle. */
 nmg_status nmg_server_add_operator(nmg_server* s, nmg_hier* h, int slots, int* op_id);
 /* Queue one right-hand side (host, the operator's f type, copied now); u_host
  * (host, the operator's u type) receives the solution when the request is

@@ -53,7 +53,8 @@ class _OpDesc(ctypes.Structure):
 class _SmDesc(ctypes.Structure):
     _fields_ = [("layers", ctypes.c_int), ("width", ctypes.c_int), ("ksize", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("weights", ctypes.POINTER(ctypes.c_double)),
-                ("nweights", ctypes.c_size_t), ("arch", ctypes.c_int), ("modes", ctypes.c_int)]
+                ("nweights", ctypes.c_size_t), ("arch", ctypes.c_int), ("modes", ctypes.c_int),
+                ("level_layers", ctypes.POINTER(ctypes.c_int))]
 
 SMOOTHER_CNN, SMOOTHER_FNO = 0, 1
 
@@ -211,8 +212,8 @@ def load_weights(path: str):
                      layers=[(z[f"l{l}_k{i}_w"], z[f"l{l}_k{i}_b"],
                               z[f"l{l}_k{i}_rre"] + 1j * z[f"l{l}_k{i}_rim"]) for i in range(nk)],
                      proj=(z[f"l{l}_proj_w"], z[f"l{l}_proj_b"])) for l in range(nl)]
-    nlayers = len([k for k in z.files if k.startswith("l0_w")])
-    return [[(z[f"l{l}_w{i}"], z[f"l{l}_b{i}"]) for i in range(nlayers)] for l in range(nl)]
+    depth = [len([k for k in z.files if k.startswith(f"l{l}_w")]) for l in range(nl)]
+    return [[(z[f"l{l}_w{i}"], z[f"l{l}_b{i}"]) for i in range(depth[l])] for l in range(nl)]
 
 
 class Context:
@@ -226,6 +227,7 @@ class Context:
         if rc != 0:
             raise NMGError(rc, L.nmg_status_str(rc).decode())
         self.device = device
+        self.graphs = True
 
     def check(self, rc):
         if rc != 0:
@@ -241,6 +243,7 @@ class Context:
     def set_graphs(self, enable: bool):
         """Replay captured CUDA graphs per outer iteration (default) or launch eagerly."""
         self.check(lib().nmg_set_graphs(self._h, 1 if enable else 0))
+        self.graphs = bool(enable)
 
     def set_wait_limit(self, ns: int):
         """Bound of every device wait of the tensor-core kernels, in ns."""
@@ -314,9 +317,11 @@ class Hierarchy:
                 W0 = np.asarray(weights[0][0][0])  # first layer: [width, 1, k(, k)]
                 layers, width, ksize = len(weights[0]), W0.shape[0], W0.shape[-1]
             self._w = pack_weights(weights)
+            # per-level depths (levels may differ, Appendix A's Table 6)
+            self._depths = np.array([len(lv) for lv in weights], dtype=np.int32)
             sm = _SmDesc(layers, width, ksize, len(weights),
                          self._w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._w.size,
-                         SMOOTHER_CNN, 0)
+                         SMOOTHER_CNN, 0, self._depths.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
             smp = ctypes.byref(sm)
         self._h = ctypes.c_void_p()
         ctx.check(L.nmg_setup(ctx._h, ctypes.byref(op), smp, ctypes.byref(self._h)))

@@ -67,6 +67,7 @@ namespace {
 
 struct DevLevel {
   int n = 0, wK = 0, wM = 0;
+  int layers = 0;  // CNN smoother depth on this level
   double *Kd_d = nullptr, *Md_d = nullptr;
   float *Kd_f = nullptr, *Md_f = nullptr;
   float *Kd_lo = nullptr, *Md_lo = nullptr;  // fp32 residual of the fp64 coefficients
@@ -216,27 +217,13 @@ void free_work(Work& w) {
   w = Work();
 }
 
-nmg_status ensure_work(nmg_hier* h, int B) {
-  nmg_ctx* ctx = h->ctx;
-  Work& w = h->w;
-  if (B <= w.cap) return NMG_OK;
-  free_work(w);
+// Every device buffer of a workspace for B right-hand sides, in allocation
+// order: fn(bytes, slot) is called with the Work member that receives the
+// pointer; false from fn stops the walk.  ensure_work allocates along it and
+// work_bytes sums it, so the two cannot disagree.
+template <typename Fn>
+bool for_work_buffers(const nmg_hier* h, int B, Work& w, Fn fn) {
   const size_t es = elem_size(h->precision);
-  auto alloc = [&](size_t bytes, void** out) -> nmg_status {
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(out, bytes);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(workspace)");
-    w.all.push_back(*out);
-    w.bytes += bytes;
-    return NMG_OK;
-  };
-#define AL(bytes, ptr)                                                 \
-  do {                                                                 \
-    void* p_ = nullptr;                                                \
-    nmg_status s_ = alloc((bytes), &p_);                               \
-    if (s_ != NMG_OK) { free_work(w); return s_; }                     \
-    ptr = reinterpret_cast<decltype(ptr)>(p_);                         \
-  } while (0)
   const int L = h->L;
   w.x.assign(L, nullptr);
   w.y.assign(L, nullptr);
@@ -245,47 +232,86 @@ nmg_status ensure_work(nmg_hier* h, int B) {
   w.part.assign(L, nullptr);
   w.s.assign(L, nullptr);
   // partial-sum slots per level: generous upper bound on tiles per item
-  size_t maxparts = 4096;
+  const size_t maxparts = 4096;
   w.part_per_level = maxparts;
+#define WB(bytes, member) \
+  if (!fn((size_t)(bytes), reinterpret_cast<void**>(&(member)))) return false
   for (int l = 0; l < L; ++l) {
-    size_t pl = plane(h, l) * (size_t)B * es;
-    AL(pl, w.x[l]);
-    AL(pl, w.y[l]);
-    AL(pl, w.h[l]);
-    AL(pl, w.t[l]);
-    AL(maxparts * B * sizeof(double), w.part[l]);
-    AL(B * sizeof(double), w.s[l]);
+    const size_t pl = plane(h, l) * (size_t)B * es;
+    WB(pl, w.x[l]);
+    WB(pl, w.y[l]);
+    WB(pl, w.h[l]);
+    WB(pl, w.t[l]);
+    WB(maxparts * B * sizeof(double), w.part[l]);
+    WB(B * sizeof(double), w.s[l]);
   }
-  AL(B * sizeof(double), w.fn);
-  AL(3 * B * sizeof(double), w.cg);
-  AL(B * sizeof(double), w.relres);
-  AL(B * sizeof(int), w.status);
-  AL(B * sizeof(int), w.cycles);
-  AL(B * sizeof(int), w.active);
-  AL(B * sizeof(int), w.ones);
+  WB(B * sizeof(double), w.fn);
+  WB(3 * B * sizeof(double), w.cg);
+  WB(B * sizeof(double), w.relres);
+  WB(B * sizeof(int), w.status);
+  WB(B * sizeof(int), w.cycles);
+  WB(B * sizeof(int), w.active);
+  WB(B * sizeof(int), w.ones);
   // [0]: right-hand sides still active, [1]: the error word of bounded
   // device waits (0 = ok); both copied to the host after every iteration
-  AL(2 * sizeof(int), w.nactive);
-  w.err = w.nactive + 1;
+  WB(2 * sizeof(int), w.nactive);
   if (h->dim == 2 && h->L > 1) {
-    size_t n0 = plane(h, 0);
+    const size_t n0 = plane(h, 0);
     // bytes per channel and grid point: fp64 / fp32 (SIMT forms), two 16-bit
     // terms (pair forms, one in the fast form), three (three-term bf16 form)
-    size_t actb = (size_t)h->width * n0 * B *
-                  (h->precision == NMG_FP64 ? 8 : h->precision == NMG_BF16_REFINE ? 6 : 4);
-    AL(actb, w.act0);
-    AL(actb, w.act1);
-    AL(n0 * B * 2 * es, w.cbuf);
+    const size_t actb = (size_t)h->width * n0 * B *
+                        (h->precision == NMG_FP64 ? 8 : h->precision == NMG_BF16_REFINE ? 6 : 4);
+    WB(actb, w.act0);
+    WB(actb, w.act1);
+    WB(n0 * B * 2 * es, w.cbuf);
     if (h->arch == NMG_SMOOTHER_FNO) {
       const size_t m = (size_t)h->modes, c = (size_t)h->width;
-      AL((size_t)B * c * h->n * m * 2 * es, w.fno_a);
-      AL(2 * (size_t)B * c * 2 * m * m * 2 * es, w.fno_b);
+      WB((size_t)B * c * h->n * m * 2 * es, w.fno_a);
+      WB(2 * (size_t)B * c * 2 * m * m * 2 * es, w.fno_b);
     }
   }
   if (is_refine(h->precision)) {
-    AL(plane(h, 0) * B * sizeof(float), w.r32);
-    AL(plane(h, 0) * B * sizeof(float), w.d32);
+    WB(plane(h, 0) * B * sizeof(float), w.r32);
+    WB(plane(h, 0) * B * sizeof(float), w.d32);
   }
+#undef WB
+  return true;
+}
+
+// device bytes of a workspace for B right-hand sides (what ensure_work would
+// allocate)
+size_t work_bytes(const nmg_hier* h, int B) {
+  Work dummy;
+  size_t total = 0;
+  for_work_buffers(h, B, dummy, [&](size_t bytes, void**) {
+    total += bytes ? bytes : 16;
+    return true;
+  });
+  return total;
+}
+
+nmg_status ensure_work(nmg_hier* h, int B) {
+  nmg_ctx* ctx = h->ctx;
+  Work& w = h->w;
+  if (B <= w.cap) return NMG_OK;
+  free_work(w);
+  cudaError_t failed = cudaSuccess;
+  const bool ok = for_work_buffers(h, B, w, [&](size_t bytes, void** slot) {
+    if (bytes == 0) bytes = 16;
+    const cudaError_t e = cudaMalloc(slot, bytes);
+    if (e != cudaSuccess) {
+      failed = e;
+      return false;
+    }
+    w.all.push_back(*slot);
+    w.bytes += bytes;
+    return true;
+  });
+  if (!ok) {
+    free_work(w);
+    return cuda_fail(ctx, failed, "cudaMalloc(workspace)");
+  }
+  w.err = w.nactive + 1;
   {
     cudaError_t e = cudaMallocHost(&w.h_nactive, 2 * sizeof(int));
     if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "cudaMallocHost"); }
@@ -298,7 +324,6 @@ nmg_status ensure_work(nmg_hier* h, int B) {
   cudaError_t e = cudaMemcpy(w.ones, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "cudaMemcpy(ones)"); }
   w.cap = B;
-#undef AL
   return NMG_OK;
 }
 
@@ -393,13 +418,13 @@ void op_smooth<double>(nmg_hier* h, int l, int B, const double* b, const double*
     return;
   }
   if (h->dim == 2) {
-    std::vector<ConvW<double>> cw(h->layers);
-    for (int i = 0; i < h->layers; ++i) cw[i] = ConvW<double>{d.Wd[i], d.bd[i]};
-    launch_cnn2d_simt<double>(d.n, B, h->layers, h->width, cw.data(), b, s,
+    std::vector<ConvW<double>> cw(d.layers);
+    for (int i = 0; i < d.layers; ++i) cw[i] = ConvW<double>{d.Wd[i], d.bd[i]};
+    launch_cnn2d_simt<double>(d.n, B, d.layers, h->width, cw.data(), b, s,
                               reinterpret_cast<double*>(h->w.act0),
                               reinterpret_cast<double*>(h->w.act1), out, active, c->stream, c->log);
   } else {
-    launch_cnn1d<double>(d.n, B, h->layers, h->width, h->ksize, d.wp_d, b, s, out, active,
+    launch_cnn1d<double>(d.n, B, d.layers, h->width, h->ksize, d.wp_d, b, s, out, active,
                          c->stream, c->log);
   }
 }
@@ -421,13 +446,13 @@ void op_smooth<float>(nmg_hier* h, int l, int B, const float* b, const double* s
       launch_cnn2d_bf16_dispatch(h, l, B, b, s, out, active);
       return;
     }
-    std::vector<ConvW<float>> cw(h->layers);
-    for (int i = 0; i < h->layers; ++i) cw[i] = ConvW<float>{d.Wf[i], d.bf[i]};
-    launch_cnn2d_simt<float>(d.n, B, h->layers, h->width, cw.data(), b, s,
+    std::vector<ConvW<float>> cw(d.layers);
+    for (int i = 0; i < d.layers; ++i) cw[i] = ConvW<float>{d.Wf[i], d.bf[i]};
+    launch_cnn2d_simt<float>(d.n, B, d.layers, h->width, cw.data(), b, s,
                              reinterpret_cast<float*>(h->w.act0),
                              reinterpret_cast<float*>(h->w.act1), out, active, c->stream, c->log);
   } else {
-    launch_cnn1d<float>(d.n, B, h->layers, h->width, h->ksize, d.wp_f, b, s, out, active,
+    launch_cnn1d<float>(d.n, B, d.layers, h->width, h->ksize, d.wp_f, b, s, out, active,
                         c->stream, c->log);
   }
 }
@@ -1138,22 +1163,26 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
     h->width = sm->width;
     h->ksize = sm->ksize;
   } else if (L > 1) {
-    if (sm->layers < 2) return fail(ctx, NMG_ERR_WEIGHTS, "smoother needs at least 2 layers");
+    int maxd = 0;
+    for (int l = 0; l < sm->nlevels; ++l) {
+      const int dl = sm->level_layers ? sm->level_layers[l] : sm->layers;
+      if (dl < 2) return fail(ctx, NMG_ERR_WEIGHTS, "smoother needs at least 2 layers");
+      if (dl > kMaxCnnLayers) return fail(ctx, NMG_ERR_UNSUPPORTED, "more than 16 layers on a smoother level");
+      maxd = std::max(maxd, dl);
+    }
     if (op->dim == 2 && (sm->width != 32 || sm->ksize != 3))
       return fail(ctx, NMG_ERR_UNSUPPORTED, "2D smoother must be width 32, 3x3");
     if (op->dim == 1 && (sm->width < 1 || sm->width > 64 || sm->ksize < 1 || sm->ksize > 15 ||
                          (sm->ksize % 2) == 0))
       return fail(ctx, NMG_ERR_UNSUPPORTED, "1D smoother: width <= 64, odd ksize <= 15");
-    h->layers = sm->layers;
+    h->layers = maxd;
     h->width = sm->width;
     h->ksize = sm->ksize;
-    size_t kk = op->dim == 1 ? (size_t)sm->ksize : (size_t)sm->ksize * sm->ksize;
-    size_t per_level = 0;
-    for (int i = 0; i < sm->layers; ++i) {
-      size_t cin = i == 0 ? 1 : sm->width, cout = i == sm->layers - 1 ? 1 : sm->width;
-      per_level += cout * cin * kk + cout;
-    }
-    if (sm->nweights != per_level * (size_t)sm->nlevels)
+    size_t total = 0;
+    for (int l = 0; l < sm->nlevels; ++l)
+      total += cnn_weights_per_level(sm->level_layers ? sm->level_layers[l] : sm->layers,
+                                     sm->width, sm->ksize, op->dim);
+    if (sm->nweights != total)
       return fail(ctx, NMG_ERR_WEIGHTS, "nweights does not match layers/width/ksize/nlevels");
     for (size_t i = 0; i < sm->nweights; ++i)
       if (!std::isfinite(sm->weights[i])) return fail(ctx, NMG_ERR_WEIGHTS, "non-finite weight");
@@ -1233,24 +1262,21 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
       return st;
     }
   } else if (L > 1) {
-    size_t off = 0;
-    const size_t kk = op->dim == 1 ? (size_t)h->ksize : (size_t)h->ksize * h->ksize;
-    size_t per_level = 0;
-    for (int i = 0; i < h->layers; ++i) {
-      size_t cin = i == 0 ? 1 : h->width, cout = i == h->layers - 1 ? 1 : h->width;
-      per_level += cout * cin * kk + cout;
-    }
+    size_t off = 0, level_off = 0;
     for (int l = 0; l < L - 1; ++l) {
       DevLevel& d = h->lv[l];
-      const double* base = sm->weights + per_level * l;
+      d.layers = sm->level_layers ? sm->level_layers[l] : sm->layers;
+      const size_t per_level = cnn_weights_per_level(d.layers, h->width, h->ksize, op->dim);
+      const double* base = sm->weights + level_off;
+      level_off += per_level;
       if (op->dim == 1) {
         std::vector<double> v(base, base + per_level);
         d.wp_d = upload(ctx, h->allocs, v, &st);
         d.wp_f = upload(ctx, h->allocs, to_f(v), &st);
       } else {
         off = 0;
-        for (int i = 0; i < h->layers; ++i) {
-          int cin = i == 0 ? 1 : h->width, cout = i == h->layers - 1 ? 1 : h->width;
+        for (int i = 0; i < d.layers; ++i) {
+          int cin = i == 0 ? 1 : h->width, cout = i == d.layers - 1 ? 1 : h->width;
           std::vector<double> W((size_t)cin * 9 * cout), bb(cout);
           for (int co = 0; co < cout; ++co)
             for (int ci = 0; ci < cin; ++ci)
@@ -1268,8 +1294,8 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
       if (st == NMG_OK && is_refine(h->precision)) {
         std::vector<const double*> Wp, bp;
         size_t o = 0;
-        for (int i = 0; i < h->layers; ++i) {
-          int cin = i == 0 ? 1 : h->width, cout = i == h->layers - 1 ? 1 : h->width;
+        for (int i = 0; i < d.layers; ++i) {
+          int cin = i == 0 ? 1 : h->width, cout = i == d.layers - 1 ? 1 : h->width;
           Wp.push_back(base + o);
           o += (size_t)cout * cin * 9;
           bp.push_back(base + o);
@@ -1279,7 +1305,7 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
                           : h->precision == NMG_BF16X3_REFINE ? 1
                           : h->precision == NMG_FP16_REFINE   ? 2
                                                             : 0;
-        d.bf16_pack = bf16_cnn_pack(h->layers, Wp, bp, split);
+        d.bf16_pack = bf16_cnn_pack(d.layers, Wp, bp, split);
         if (!d.bf16_pack) st = fail(ctx, NMG_ERR_UNSUPPORTED, "bf16 tensor-core smoother unavailable");
         else h->allocs.push_back(d.bf16_pack);
       }
@@ -1903,8 +1929,10 @@ const char* nmg_last_error(const nmg_ctx* ctx) { return ctx ? ctx->err.c_str() :
 //   1. admits queued requests in arrival order into free slots of their
 //      operator (copies f in, zeroes u, computes ||f|| and the first
 //      residual test for the new slots only, then joins them to the active
-//      set) -- admission is bounded by the slots, whose memory was checked
-//      against the server's byte budget when the operator was added;
+//      set).  A pool starts small and grows (doubling, up to the operator's
+//      slot count) when requests wait for it, if the device's free memory at
+//      that moment (cudaMemGetInfo, less a reserve) and the optional byte
+//      budget allow: admission is bounded by free HBM;
 //   2. runs one outer iteration (one cycle + convergence test) for every
 //      live request of every operator: one captured graph per operator;
 //   3. retires requests that converged, diverged or used their cycles
@@ -1928,7 +1956,8 @@ struct SrvReq {
 
 struct SrvOp {
   nmg_hier* h = nullptr;
-  int cap = 0;
+  int cap = 0;        // slots allocated now
+  int max_slots = 0;  // the most the pool may grow to
   void* f = nullptr;  // device slot buffers
   void* u = nullptr;
   int* d_new = nullptr;
@@ -1946,7 +1975,8 @@ struct SrvOp {
 
 struct nmg_server {
   nmg_ctx* ctx = nullptr;
-  size_t budget = 0, used = 0;
+  size_t budget = 0, used = 0;  // budget 0: no bound beyond free device memory
+  long long grows = 0;          // pool growths so far
   double rtol = 1e-6;
   int max_cycles = 100;
   std::vector<SrvOp> ops;
@@ -1998,17 +2028,117 @@ void srv_step(SrvOp& o) {
   launch_count_cycles(o.cap, w.active, w.cycles, c->stream, c->log);
 }
 
+void free_host_arrays(SrvOp& o) {
+  if (o.h_new) cudaFreeHost(o.h_new);
+  if (o.h_status) cudaFreeHost(o.h_status);
+  if (o.h_cycles) cudaFreeHost(o.h_cycles);
+  if (o.h_relres) cudaFreeHost(o.h_relres);
+  o.h_new = nullptr;
+  o.h_status = o.h_cycles = nullptr;
+  o.h_relres = nullptr;
+}
+
 void free_op(SrvOp& o) {
   if (o.exec) cudaGraphExecDestroy(o.exec);
   if (o.f) cudaFree(o.f);
   if (o.u) cudaFree(o.u);
   if (o.d_new) cudaFree(o.d_new);
-  if (o.h_new) cudaFreeHost(o.h_new);
-  if (o.h_status) cudaFreeHost(o.h_status);
-  if (o.h_cycles) cudaFreeHost(o.h_cycles);
-  if (o.h_relres) cudaFreeHost(o.h_relres);
+  free_host_arrays(o);
   if (o.h_zero) cudaFreeHost(o.h_zero);
 }
+
+// Grow (or create, cap == 0) operator o's pool to `want` slots if the device
+// memory free right now, less a reserve, and the server's budget allow it;
+// *got = the new capacity (unchanged if it does not fit).  Live requests keep
+// their slots: f and u are copied into the new slot buffers, the workspace
+// (per-slot flags, norms, the last residual) is reallocated and rebuilt from
+// them (cycle counts restored, ||f|| and the residual test recomputed), and
+// the pool's captured graph is dropped.
+nmg_status grow_pool(nmg_server* s, SrvOp& o, int want, int* got) {
+  nmg_ctx* ctx = s->ctx;
+  nmg_hier* h = o.h;
+  cudaStream_t st = ctx->stream;
+  *got = o.cap;
+  if (want <= o.cap) return NMG_OK;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const size_t reserve = std::max<size_t>((size_t)256 << 20, total_b / 64);
+  const size_t ws_cur = h->w.bytes;
+  int newcap = want;
+  for (; newcap > o.cap; newcap = o.cap + (newcap - o.cap) / 2) {
+    const size_t ws_new = work_bytes(h, std::max(newcap, h->w.cap));
+    const size_t slots_new = o.pl * (size_t)newcap * (o.fes + o.ues);
+    const size_t peak = slots_new + (ws_new > ws_cur ? ws_new - ws_cur : 0);
+    const size_t used_new = s->used - o.bytes + slots_new + ws_new;
+    if (peak + reserve <= free_b && (s->budget == 0 || used_new <= s->budget)) break;
+  }
+  if (newcap <= o.cap) return NMG_OK;  // does not fit now: requests stay queued
+  CK(cudaStreamSynchronize(st));
+  const int old = o.cap;
+  std::vector<int> cyc(old > 0 ? old : 1, 0);
+  if (old > 0)
+    CK(cudaMemcpy(cyc.data(), h->w.cycles, old * sizeof(int), cudaMemcpyDeviceToHost));
+  void* nf = nullptr;
+  void* nu = nullptr;
+  int* nd = nullptr;
+  CK(cudaMalloc(&nf, o.pl * newcap * o.fes));
+  CK(cudaMalloc(&nu, o.pl * newcap * o.ues));
+  CK(cudaMalloc(&nd, newcap * sizeof(int)));
+  CK(cudaMemset(nf, 0, o.pl * newcap * o.fes));
+  CK(cudaMemset(nu, 0, o.pl * newcap * o.ues));
+  if (old > 0) {
+    CK(cudaMemcpy(nf, o.f, o.pl * old * o.fes, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(nu, o.u, o.pl * old * o.ues, cudaMemcpyDeviceToDevice));
+  }
+  if (o.f) cudaFree(o.f);
+  if (o.u) cudaFree(o.u);
+  if (o.d_new) cudaFree(o.d_new);
+  o.f = nf;
+  o.u = nu;
+  o.d_new = nd;
+  if (o.exec) cudaGraphExecDestroy(o.exec);
+  o.exec = nullptr;
+  nmg_status rs = ensure_work(h, newcap);
+  if (rs != NMG_OK) return rs;
+  std::vector<int> hn(newcap, 0), act(newcap, 0), stat(newcap, NMG_NOT_CONVERGED);
+  free_host_arrays(o);
+  CK(cudaMallocHost(&o.h_new, newcap * sizeof(int)));
+  CK(cudaMallocHost(&o.h_status, newcap * sizeof(int)));
+  CK(cudaMallocHost(&o.h_cycles, newcap * sizeof(int)));
+  CK(cudaMallocHost(&o.h_relres, newcap * sizeof(double)));
+  std::memset(o.h_new, 0, newcap * sizeof(int));
+  cyc.resize(newcap, 0);
+  o.slot.resize(newcap, -1);
+  for (int j = 0; j < newcap; ++j) act[j] = o.slot[j] >= 0 ? 1 : 0;
+  Work& w = h->w;
+  CK(cudaMemcpy(w.cycles, cyc.data(), newcap * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(w.status, stat.data(), newcap * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(w.active, act.data(), newcap * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(o.d_new, hn.data(), newcap * sizeof(int), cudaMemcpyHostToDevice));
+  s->used = s->used - o.bytes;
+  o.bytes = o.pl * (size_t)newcap * (o.fes + o.ues) + w.bytes;
+  s->used += o.bytes;
+  o.cap = newcap;
+  ++s->grows;
+  if (o.live > 0) {
+    // ||f|| and the residual test of the live slots, as at their admission
+    int nt = 0;
+    ctx->log.active_hint = o.live;
+    if (h->precision == NMG_FP64)
+      launch_sumsq<double>((const double*)o.f, (long long)o.pl, o.cap, w.part[0], &nt, w.active,
+                           st, ctx->log);
+    else
+      launch_sumsq<float>((const float*)o.f, (long long)o.pl, o.cap, w.part[0], &nt, w.active, st,
+                          ctx->log);
+    launch_norms(w.part[0], nt, o.cap, w.fn, w.active, st, ctx->log);
+    srv_test(o, s->rtol, w.active);
+    CK(cudaStreamSynchronize(st));
+  }
+  *got = newcap;
+  return NMG_OK;
+}
+
+constexpr int kInitialSlots = 4;  // a pool's first allocation
 
 }  // namespace
 
@@ -2045,32 +2175,22 @@ nmg_status nmg_server_add_operator(nmg_server* s, nmg_hier* h, int slots, int* o
   if (st != NMG_OK) return st;
   SrvOp o;
   o.h = h;
-  o.cap = slots;
+  o.max_slots = slots;
   o.pl = plane(h, 0);
   o.fes = h->precision == NMG_FP64 ? 8 : 4;
   o.ues = h->precision == NMG_FP32 ? 4 : 8;
-  const size_t before = h->w.bytes;
-  if ((st = ensure_work(h, slots)) != NMG_OK) return st;
-  o.bytes = (h->w.bytes > before ? h->w.bytes - before : 0) + o.pl * slots * (o.fes + o.ues);
-  if (s->used + o.bytes > s->budget)
-    return fail(ctx, NMG_ERR_OOM, "operator's slot pool exceeds the server's memory budget");
-  CK(cudaMalloc(&o.f, o.pl * slots * o.fes));
-  CK(cudaMalloc(&o.u, o.pl * slots * o.ues));
-  CK(cudaMalloc(&o.d_new, slots * sizeof(int)));
-  CK(cudaMallocHost(&o.h_new, slots * sizeof(int)));
-  CK(cudaMallocHost(&o.h_status, slots * sizeof(int)));
-  CK(cudaMallocHost(&o.h_cycles, slots * sizeof(int)));
-  CK(cudaMallocHost(&o.h_relres, slots * sizeof(double)));
   CK(cudaMallocHost(&o.h_zero, sizeof(int)));
   *o.h_zero = 0;
-  std::memset(o.h_new, 0, slots * sizeof(int));
-  CK(cudaMemsetAsync(h->w.active, 0, slots * sizeof(int), ctx->stream));
-  CK(cudaMemsetAsync(h->w.cycles, 0, slots * sizeof(int), ctx->stream));
-  CK(cudaMemsetAsync(o.f, 0, o.pl * slots * o.fes, ctx->stream));
-  CK(cudaMemsetAsync(o.u, 0, o.pl * slots * o.ues, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  o.slot.assign(slots, -1);
-  s->used += o.bytes;
+  int got = 0;
+  if ((st = grow_pool(s, o, std::min(slots, kInitialSlots), &got)) != NMG_OK) {
+    free_op(o);
+    return st;
+  }
+  if (got < 1) {
+    free_op(o);
+    return fail(ctx, NMG_ERR_OOM,
+                "operator's first slots exceed the free device memory or the server's budget");
+  }
   *op_id = (int)s->ops.size();
   s->ops.push_back(o);
   return NMG_OK;
@@ -2100,7 +2220,20 @@ nmg_status nmg_server_step(nmg_server* s, int* completed) {
   nmg_status rs = set_device(ctx);
   if (rs != NMG_OK) return rs;
   int done = 0;
-  // ---- 1. admission in arrival order into free slots
+  // ---- 1. admission in arrival order into free slots; pools with waiting
+  // requests grow first, as far as free device memory allows
+  {
+    std::vector<int> waiting(s->ops.size(), 0);
+    for (long long id : s->queue) ++waiting[s->reqs[id].op];
+    for (size_t k = 0; k < s->ops.size(); ++k) {
+      SrvOp& o = s->ops[k];
+      if (waiting[k] > o.cap - o.live && o.cap < o.max_slots) {
+        int want = std::min(o.max_slots, std::max(2 * o.cap, o.live + waiting[k]));
+        int got = 0;
+        if ((rs = grow_pool(s, o, want, &got)) != NMG_OK) return rs;
+      }
+    }
+  }
   std::vector<int> admitted(s->ops.size(), 0);
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     SrvReq& r = s->reqs[*it];
@@ -2262,7 +2395,7 @@ namespace {
 void launch_cnn2d_bf16_dispatch(nmg_hier* h, int l, int B, const float* b, const double* s,
                                 float* out, const int* active) {
   DevLevel& d = h->lv[l];
-  bf16_cnn_launch(d.n, B, B, h->layers, d.bf16_pack, b, s, reinterpret_cast<float*>(h->w.act0),
+  bf16_cnn_launch(d.n, B, B, d.layers, d.bf16_pack, b, s, reinterpret_cast<float*>(h->w.act0),
                   reinterpret_cast<float*>(h->w.act1), out, active, h->w.err, h->ctx->ctl,
                   h->ctx->stream, h->ctx->log);
 }

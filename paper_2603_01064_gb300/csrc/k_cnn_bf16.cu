@@ -130,7 +130,7 @@ struct OutW {
 struct Bf16Pack {
   int layers;
   int split;
-  LayerPack l[8];
+  LayerPack l[kMaxCnnLayers];
   FirstW first;  // host copy of layer 0
   OutW last;     // host copy of the output layer
 };
@@ -1288,7 +1288,7 @@ std::vector<std::pair<const void*, Bf16Pack>> g_headers;
 // table keyed by it.
 void* bf16_cnn_pack(int layers, const std::vector<const double*>& W,
                     const std::vector<const double*>& bias, int split) {
-  if (layers < 3 || layers > 8) return nullptr;
+  if (layers < 3 || layers > kMaxCnnLayers) return nullptr;
   std::vector<std::vector<unsigned char>> wl(layers), bl(layers);
   std::vector<int> has_lo(layers, 0);
   FirstW first{};

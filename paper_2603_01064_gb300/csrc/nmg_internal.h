@@ -236,6 +236,18 @@ struct FnoDims {
   int width, layers, ksize, modes;
 };
 size_t fno_weights_per_level(int c, int layers, int ks, int m);
+// CNN smoother: the most layers one level may have, and the doubles of one
+// level's weights (PyTorch layout, channels 1 -> width -> ... -> 1)
+constexpr int kMaxCnnLayers = 16;
+inline size_t cnn_weights_per_level(int layers, int width, int ksize, int dim) {
+  const size_t kk = dim == 1 ? (size_t)ksize : (size_t)ksize * ksize;
+  size_t n = 0;
+  for (int i = 0; i < layers; ++i) {
+    const size_t cin = i == 0 ? 1 : width, cout = i == layers - 1 ? 1 : width;
+    n += cout * cin * kk + cout;
+  }
+  return n;
+}
 // h = N_FNO(b / s) s on an n x n level; wts: the level's weights in the
 // nmg_smoother_desc layout (type T); tw: e^{-2 pi i j / n}, j < n, as (re, im)
 // pairs; z0, z1: [B][width][n][n]; cA: [B][width][n][modes] complex;

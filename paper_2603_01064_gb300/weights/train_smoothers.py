@@ -372,13 +372,22 @@ def fno_to_npz(nets, path, meta):
     np.savez(path, **arrs)
 
 
-def nets_from_npz(path, dim, layers, width, ksize, device="cpu", gains=None):
+def nets_from_npz(path, dim, layers, width, ksize, device="cpu", gains=None, depths=None):
+    """CNN smoothers from a stored file (gains as used in training).  A level
+    whose stored depth differs from depths[l] (when given) starts from a fresh
+    net of that depth instead."""
     z = np.load(path)
     nl = int(z["meta_smoother_levels"])
     nets = []
     for l in range(nl):
         g = 1.0 if gains is None else gains[l]
-        net = CNN(dim, layers, width, ksize, gain=g)
+        stored = len([k for k in z.files if k.startswith(f"l{l}_w")])
+        want = stored if depths is None else depths[l]
+        net = CNN(dim, want, width, ksize, gain=g)
+        if want != stored:
+            print(f"level {l}: stored depth {stored}, fresh net of depth {want}")
+            nets.append(net.to(device))
+            continue
         last = len(net.convs) - 1
         for i, c in enumerate(net.convs):
             s = 1.0 / g if i == last else 1.0
@@ -421,6 +430,16 @@ def main(argv=None):
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--eval-batch", type=int, default=8)
     ap.add_argument("--eval-every", type=int, default=100)
+    ap.add_argument("--eval-cycles", type=int, default=60,
+                    help="cycle limit of the evaluation solves")
+    ap.add_argument("--depths", default=None,
+                    help="comma list of CNN layers per smoother level (default: the preset's "
+                         "layers on every level)")
+    ap.add_argument("--train-levels", default=None,
+                    help="comma list of smoother levels to train (default: all); the others "
+                         "stay as initialised")
+    ap.add_argument("--clip", type=float, default=0.0,
+                    help="clip each trained level's gradient norm to this (0: off)")
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     if a.threads:
@@ -442,15 +461,25 @@ def main(argv=None):
         prob = Problem(2, cfg["n"], cfg["levels"], cfg["alpha"], taps=taps, device=a.device)
     gains = [prob.top_gain(l) for l in range(cfg["levels"] - 1)]
     print("output gains", ["%.3g" % g for g in gains])
+    nsm = cfg["levels"] - 1
+    depths = [cfg["layers"]] * nsm if a.depths is None else [int(v) for v in a.depths.split(",")]
+    if len(depths) != nsm or min(depths) < 2:
+        raise SystemExit(f"--depths needs {nsm} entries >= 2")
     if cfg.get("arch") == "fno":
         nets = [FNO(cfg["layers"], cfg["width"], cfg["ksize"], cfg["modes"], gain=g).to(a.device)
                 for g in gains]
     elif a.init:
-        nets = nets_from_npz(a.init, dim, cfg["layers"], cfg["width"], cfg["ksize"], a.device, gains)
+        nets = nets_from_npz(a.init, dim, cfg["layers"], cfg["width"], cfg["ksize"], a.device, gains,
+                             depths if a.depths is not None else None)
     else:
-        nets = [CNN(dim, cfg["layers"], cfg["width"], cfg["ksize"], gain=g).to(a.device)
-                for g in gains]
-    opts = [torch.optim.Adam(n_.parameters(), lr=a.lr) for n_ in nets]
+        nets = [CNN(dim, d, cfg["width"], cfg["ksize"], gain=g).to(a.device)
+                for d, g in zip(depths, gains)]
+    if cfg.get("arch") != "fno":
+        cfg["depths"] = [len(n_.convs) for n_ in nets]
+    train = list(range(nsm)) if a.train_levels is None else [int(v) for v in a.train_levels.split(",")]
+    for l, n_ in enumerate(nets):
+        n_.requires_grad_(l in train)
+    opts = [torch.optim.Adam(nets[l].parameters(), lr=a.lr) for l in train]
     scheds = [torch.optim.lr_scheduler.CosineAnnealingLR(o, a.epochs, eta_min=a.lr * 0.02) for o in opts]
     if dim == 1:
         f_eval, _ = nmg_inputs.rhs_1d_sines_steps(cfg["n"], a.eval_batch, 4242)
@@ -461,12 +490,21 @@ def main(argv=None):
     f_eval = torch.tensor(f_eval, dtype=torch.float32, device=a.device)
     t0 = time.time()
     best = float("inf")
+    if a.epochs == 0:
+        # evaluation only (the initial nets, e.g. a stored file given by --init)
+        cyc, hist = evaluate(prob, nets, f_eval, rtol=1e-6, max_cycles=a.eval_cycles)
+        print(f"   eval cycles to 1e-6 (fp32): {cyc.tolist()} relres every 10 cycles " +
+              " ".join(f"{v:.1e}" for v in hist[9::10]), flush=True)
+        return
     for ep in range(1, a.epochs + 1):
         x, y = data_generation(prob, nets, a.bs, a.K, gen)
         losses = levelwise_losses(prob, nets, x, y)
         for o in opts:
             o.zero_grad(set_to_none=True)
-        sum(losses).backward()
+        sum(losses[l] for l in train).backward()
+        if a.clip > 0:
+            for l in train:
+                torch.nn.utils.clip_grad_norm_(nets[l].parameters(), a.clip)
         for o, s in zip(opts, scheds):
             o.step()
             s.step()
@@ -474,8 +512,13 @@ def main(argv=None):
             print(f"ep {ep} t={time.time() - t0:.0f}s losses " +
                   " ".join(f"{v.item():.3e}" for v in losses), flush=True)
         if ep % a.eval_every == 0 or ep == a.epochs:
-            cyc, hist = evaluate(prob, nets, f_eval, rtol=1e-6, max_cycles=60)
+            cyc, hist = evaluate(prob, nets, f_eval, rtol=1e-6, max_cycles=a.eval_cycles)
+            # mean cycles to 1e-6; if some right-hand side did not get there,
+            # also the orders of magnitude left (so checkpoints that do not
+            # converge within the limit are still ranked by how far they got)
             score = float(cyc.double().mean())
+            if hist and hist[-1] > 1e-6:
+                score += 100.0 * math.log10(hist[-1] / 1e-6)
             print(f"   eval cycles to 1e-6 (fp32): {cyc.tolist()} last relres {hist[-1]:.2e}", flush=True)
             if score <= best:
                 # keep the checkpoint that solves the evaluation set in the fewest cycles

@@ -156,6 +156,56 @@ def test_split_smoother_depths_and_zero_rhs(ctx, prec, layers):
         assert rel(h[keep], O.smoother(W[l], b32[keep])) < SPLIT_TOL[prec], (l, layers)
 
 
+def _mixed_depth_weights(depths, seed):
+    """Seeded random CNN weights with a different depth on every level."""
+    return [I.random_cnn_weights(2, 1, seed=seed + l, layers=d)[0] for l, d in enumerate(depths)]
+
+
+@pytest.mark.parametrize("prec", ["bf16_refine", "fp16_refine", "fp32", "fp64"])
+def test_per_level_depths(ctx, prec):
+    """Smoother levels of different depth (4, 12, 3 layers; the deep one is
+    the receptive field a transition level needs, Appendix A sizes every
+    level's net separately): each level's smoother and one whole cycle
+    against the FP64 oracle with the same weights."""
+    W = _mixed_depth_weights([4, 12, 3], seed=70)
+    H, G, W = make(ctx, prec, n=64, levels=4, weights=W)
+    rng = np.random.default_rng(71)
+    tol = {"fp64": 1e-12, "fp32": 2e-5}.get(prec, SPLIT_TOL.get(prec))
+    for l in range(3):
+        m = H.size(l)
+        b = rng.standard_normal((3, m, m)) * np.array([1.0, 1e-3, 20.0])[:, None, None]
+        if prec == "fp64":
+            bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+            hd = torch.zeros_like(bd)
+            G.smooth(l, bd, hd)
+            torch.cuda.synchronize()
+            assert rel(hd.cpu().numpy(), O.smoother(W[l], b)) < tol, l
+        else:
+            b32, h = smooth_gpu(G, l, b)
+            assert rel(h, O.smoother(W[l], b32)) < tol, (l, prec)
+    f = rng.standard_normal((3, 64, 64))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    fd = torch.tensor(f, dtype=dt, device="cuda")
+    f_in = fd.double().cpu().numpy()
+    udt = torch.float64 if prec in ("fp64", "bf16_refine", "fp16_refine") else torch.float32
+    ud = torch.zeros(fd.shape, dtype=udt, device="cuda")
+    G.cycle(fd, ud)
+    torch.cuda.synchronize()
+    ctol = {"fp64": 1e-10, "fp32": 1e-5}.get(prec, CYCLE_TOL.get(prec))
+    assert rel(ud.double().cpu().numpy(), O.nmgf(H, W, 0, None, f_in)) < ctol
+
+
+def test_per_level_depth_limits(ctx):
+    """More than 16 layers on a level, or fewer than 3 in a tensor-core
+    form, is refused at setup with a status, not at the first launch."""
+    with pytest.raises(nmg.NMGError) as e:
+        make(ctx, "fp32", n=64, levels=3, weights=_mixed_depth_weights([4, 17], seed=80))
+    assert e.value.code == -7  # NMG_ERR_UNSUPPORTED
+    with pytest.raises(nmg.NMGError):
+        make(ctx, "bf16_refine", n=64, levels=3, weights=_mixed_depth_weights([4, 2], seed=81))
+    make(ctx, "fp32", n=64, levels=3, weights=_mixed_depth_weights([4, 2], seed=81))
+
+
 CYCLE_TOL = {"bf16_refine": 1e-4, "bf16x3_refine": 1e-3, "fp16_refine": 1e-4}
 
 

@@ -12,7 +12,7 @@ sides are checked against the FP64 oracle one by one.
   {1e-1, 1e-2, 1e-3, 1e-4}: one cycle of the whole batch (autotuned launch
   shapes) in the bf16 and fp16 split refinement forms against the oracle
   for sampled items; full solves for the alphas whose trained CNN smoothers
-  converge (1e-1, 1e-2).
+  converge (1e-1, 1e-2, and 1e-3 in about 170 cycles).
 """
 import os
 
@@ -145,10 +145,11 @@ def test_512_full_batch_one_cycle_sampled(ctx, c3f, alpha, prec, tol):
     assert np.max(rel(u, ref)) < tol
 
 
-@pytest.mark.parametrize("alpha", [1e-1, 1e-2])
-def test_512_full_batch_solve_sampled(ctx, c3f, alpha):
+@pytest.mark.parametrize("alpha,max_cycles", [(1e-1, 100), (1e-2, 100), (1e-3, 250)])
+def test_512_full_batch_solve_sampled(ctx, c3f, alpha, max_cycles):
     """The alphas whose sigma-4 CNN smoothers converge reach 1e-6 on the
-    whole 64-RHS batch (checked with the oracle's own apply)."""
+    whole 64-RHS batch (checked with the oracle's own apply); at alpha 1e-3
+    the smoothers' short receptive field makes that about 170 cycles."""
     W = nmg.load_weights(os.path.join(WDIR, f"c3_2d_n512_s4_a{alpha:.0e}".replace("e-0", "e-") + ".npz"))
     taps = I.gaussian_taps(4.0)
     H = O.build_hierarchy_2d(taps, 512, alpha, 7)
@@ -156,7 +157,7 @@ def test_512_full_batch_solve_sampled(ctx, c3f, alpha):
                       precision="bf16_refine", weights=W)
     fd = torch.tensor(c3f, dtype=torch.float32, device="cuda")
     ud = torch.zeros((64, 512, 512), dtype=torch.float64, device="cuda")
-    cyc, st, rr = G.solve(fd, ud, rtol=1e-6, max_cycles=100)
+    cyc, st, rr = G.solve(fd, ud, rtol=1e-6, max_cycles=max_cycles)
     assert np.all(st == 0) and np.all(rr <= 1e-6)
     rr_o = O.relres(H, fd[C3_SAMPLE].double().cpu().numpy(), ud[C3_SAMPLE].cpu().numpy())
     assert np.all(rr_o <= 1.01e-6), rr_o
