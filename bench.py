@@ -84,9 +84,10 @@ FLOPS_PER_PX = {"cnn_hidden": 2 * 9 * 32 * 32, "cnn_first": 2 * 9 * 32, "cnn_las
 # tensor-core MMA flops per pixel actually issued by the hidden layers, per bf16 form
 # (the roofline's "achieved" uses the algorithmic flops above)
 # DRAM bytes per output pixel of the hidden convs, mean of the two hidden
-# layers, from one ncu capture of this kernel version (128x128, 64 RHS,
-# level 0; summarised under profiles/); None where no capture exists
-HIDDEN_DRAM_B_PER_UNIT = {("bf16_refine", 128): 109.9}
+# layers, from one ncu capture of the level-0 launches of the current kernel
+# version (summarised under profiles/: the three-term form at 512x512 with
+# 16 RHS, the pair form at 128x128 with 64 RHS); None where no capture exists
+HIDDEN_DRAM_B_PER_UNIT = {("bf16_refine", 512): 203.5, ("bf16x3_refine", 128): 109.9}
 MMA_FLOPS_PER_PX = {
     # three-term form per tap and K half: a1 x N = 96 ([w1 | w2 | w3]), a2 x N = 64, a3 x N = 32
     "bf16_refine": {"cnn_hidden": 2 * 9 * 32 * (96 + 64 + 32)},

@@ -231,8 +231,8 @@ bool for_work_buffers(const nmg_hier* h, int B, Work& w, Fn fn) {
   w.t.assign(L, nullptr);
   w.part.assign(L, nullptr);
   w.s.assign(L, nullptr);
-  // partial-sum slots per level: generous upper bound on tiles per item
-  const size_t maxparts = 4096;
+  // partial-sum slots per level: upper bound on tiles / strip units per item
+  const size_t maxparts = kMaxPartsPerItem;
   w.part_per_level = maxparts;
 #define WB(bytes, member) \
   if (!fn((size_t)(bytes), reinterpret_cast<void**>(&(member)))) return false
@@ -376,11 +376,14 @@ int op_residual_restrict(nmg_hier* h, int l, int B, const T* x, const T* y, T* y
     if constexpr (std::is_same<T, float>::value) {
       // wide PSF stencils: the strip residual into the level's temporary
       // (free at this point of the cycle), then full weighting
+      // (rst_tile <= 0: the strip kernel with -rst_tile chunks per strip,
+      // 0 its own choice; > 0: the tiled pipeline with that coarse tile)
       const Band2D<float> op = band<float>(h, l);
-      if (wide_residual_applies(op, x, y) && restrict_fw_applies(op.n)) {
+      const int rq = h->lv[l].rst_tile;
+      if (rq <= 0 && wide_residual_applies(op, x, y) && restrict_fw_applies(op.n)) {
         float* tmp = reinterpret_cast<float*>(h->w.t[l]);
         int pi_ = c->log.begin(K_RESTRICT, c->stream);
-        launch_residual_wide(op, B, x, y, tmp, nullptr, active, c->stream);
+        launch_residual_wide(op, B, x, y, tmp, nullptr, active, -rq, c->stream);
         c->log.end(pi_, c->stream, (double)op.n * op.n * c->log.active_hint);
         pi_ = c->log.begin(K_RESTRICT, c->stream);
         nt = launch_restrict_fw(op.n, B, tmp, yc, part, active, c->stream);
@@ -1721,12 +1724,22 @@ nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_
     return ms;
   };
   const bool dbl = h->precision == NMG_FP64;
+  // levels whose fp32 residual can take the wide-stencil strip kernel: its
+  // chunk counts (-k; 0 = its own choice) compete with the tiled pipeline
+  auto wide_level = [&](int l) {
+    return !dbl && h->dim == 2 &&
+           wide_residual_applies(band<float>(h, l), (const float*)w.x[l], (const float*)w.y[l]);
+  };
+  const std::vector<int> wide_cands = {0, -1, -2, -4, -8};
   for (int l = 0; l < h->L; ++l) {
     DevLevel& d = h->lv[l];
     float best = 1e30f;
     if (l < h->L - 1) {
       int keep = 0;
-      for (int t : {8, 16, 32}) {
+      std::vector<int> cands = {8, 16, 32};
+      if (wide_level(l) && restrict_fw_applies(d.n))
+        cands.insert(cands.begin(), wide_cands.begin(), wide_cands.end());
+      for (int t : cands) {
         d.rst_tile = t;
         float ms = timeit([&]() {
           if (dbl) op_residual_restrict<double>(h, l, batch, (double*)w.x[l], (double*)w.y[l], (double*)w.y[l + 1], w.part[l + 1], w.active);
@@ -1752,7 +1765,9 @@ nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_
       // u is fp64 for the outer residual: reuse the complex filter scratch
       best = 1e30f;
       int keep = 0;
-      for (int t : {0, 16, 32, 64}) {  // 0: the strip forms where they apply
+      // <= 0: the strip forms where they apply (-k: k chunks per strip of
+      // the wide-stencil form, 0: its own choice)
+      for (int t : {0, -1, -2, -4, -8, 16, 32, 64}) {
         d.ref_tile = t;
         float ms = timeit([&]() {
           int nt = 0;
@@ -1767,7 +1782,9 @@ nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_
     DevLevel& d = h->lv[l];
     float best = 1e30f;
     int keep = 0;
-    for (int t : {16, 32, 64}) {
+    std::vector<int> cands = {16, 32, 64};
+    if (wide_level(l)) cands.insert(cands.begin(), wide_cands.begin(), wide_cands.end());
+    for (int t : cands) {
       d.res_tile = t;
       float ms = timeit([&]() {
         if (dbl) op_residual<double>(h, l, batch, (double*)w.x[l], (double*)w.y[l], (double*)w.t[l], w.part[l], w.active);

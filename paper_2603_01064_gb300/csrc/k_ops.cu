@@ -398,13 +398,15 @@ template <typename T>
 void launch_residual2d(const Band2D<T>& op, int B, const T* x, const T* y, T* r,
                        double* partials, int* ntiles, const int* active, cudaStream_t st,
                        LaunchLog& log, int tile_req) {
-  int tile = pick_tile<T>(op.n, op.wK, op.wM, false, tile_req);
+  // tile_req <= 0 on a wide-stencil level: the strip kernel with -tile_req
+  // chunks per strip (0: its own choice); > 0: the tiled pipeline
+  int tile = pick_tile<T>(op.n, op.wK, op.wM, false, tile_req > 0 ? tile_req : 0);
   int tx = ceil_div(op.n, tile);
   int pi_ = log.begin(K_RESIDUAL, st);
   int nparts = tx * tx;
   if constexpr (std::is_same<T, float>::value) {
-    if (wide_residual_applies(op, x, y)) {
-      nparts = launch_residual_wide(op, B, x, y, r, partials, active, st);
+    if (tile_req <= 0 && wide_residual_applies(op, x, y)) {
+      nparts = launch_residual_wide(op, B, x, y, r, partials, active, -tile_req, st);
       if (ntiles) *ntiles = nparts;
       log.end(pi_, st, (double)op.n * op.n * log.active_hint);
       return;
@@ -428,8 +430,8 @@ template <typename T>
 int residual2d_tiles(const Band2D<T>& op, int tile_req) {
   const int tx = ceil_div(op.n, pick_tile<T>(op.n, op.wK, op.wM, false, tile_req));
   int strip = stencil_strip_parts<T>(op);
-  if (op.n % 128 == 0) {
-    const int wide = (op.n / 64) * (op.n / 128);  // the wide strip form's units
+  if (op.n % 64 == 0) {
+    const int wide = (op.n / 64) * wide_chunks_max(op.n);  // the wide strip form's units
     strip = wide > strip ? wide : strip;
   }
   return tx * tx > strip ? tx * tx : strip;

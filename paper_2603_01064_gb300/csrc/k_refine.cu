@@ -613,9 +613,10 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
 }
 
 // ---------------------------------------------------------------------------
-// Strip form for wide stencils (half-width 9..32, n a multiple of 64 and of
-// the unit height): one warp computes kRwH consecutive output rows of a
-// 64-column strip, lane j owning columns 2j and 2j + 1 (two-lane packed
+// Strip form for wide stencils (half-width 9..32, n a multiple of 64): one
+// warp computes a chunk of consecutive output rows of a 64-column strip (the
+// launch cuts every strip into kch chunks so that the units spread evenly
+// over the SMs), lane j owning columns 2j and 2j + 1 (two-lane packed
 // double-float operations).  Input rows stream through a warp-private
 // cp.async ring; each staged row is split into float pairs once; the row
 // pass reads the lane's window from that split row.  The double-float
@@ -627,7 +628,6 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
 // rows until row a's column pass, so no global load waits inside the row
 // loop and no staged row has to outlive the prefetch window.
 // ---------------------------------------------------------------------------
-constexpr int kRwH = 128;  // output rows per warp unit
 constexpr int kRwPF = 4;   // staged rows ahead
 constexpr int kRwRing = kRwPF + 2;
 template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 6 : 3; };
@@ -644,7 +644,7 @@ template <int W>
 __global__ void __launch_bounds__(32 * RwWarps<W>::value, 1)
 k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
               const float* __restrict__ f, float* __restrict__ r,
-              double* __restrict__ partials, const int* __restrict__ active) {
+              double* __restrict__ partials, const int* __restrict__ active, int kch) {
   using G = RwGeom<W>;
   constexpr int XW = G::XW, P = G::P, Q = G::Q;
   extern __shared__ __align__(16) float rw_smem[];
@@ -657,17 +657,20 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
   float* xl = xh + XW;                                               // [XW]
   float* fring = xl + XW;                                            // [ring][64]
   const int n = op.n;
-  const int ns = n / kRsSW, upi = ns * (n / kRwH);
+  const int ns = n / kRsSW, upi = ns * kch, hu = (n + kch - 1) / kch;
   const int total = B * upi;
   const size_t plane = (size_t)n * n;
 
-  for (int unit = blockIdx.x * RwWarps<W>::value + wib; unit < total;
-       unit += gridDim.x * RwWarps<W>::value) {
+  // units dealt block-cyclically: every SM gets the same number to within one
+  for (int j = wib;; j += RwWarps<W>::value) {
+    const int unit = j * gridDim.x + blockIdx.x;
+    if (unit >= total) break;
     const int b = unit / upi;
     if (!active[b]) continue;  // warp-uniform
     const int rem = unit - b * upi;
-    const int c0 = (rem % ns) * kRsSW, i0 = (rem / ns) * kRwH;
-    const int alo = i0 - W, ahi = i0 + kRwH + W;  // input rows
+    const int c0 = (rem % ns) * kRsSW, i0 = (rem / ns) * hu;
+    const int H = min(hu, n - i0);                  // output rows of this unit
+    const int alo = i0 - W, ahi = i0 + H + W;  // input rows
     const double* ub = u + (size_t)b * plane;
     const float* fb = f + (size_t)b * plane;
     auto stage = [&](int a) {
@@ -680,7 +683,7 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
           const bool in = rin && gc >= 0 && gc < n;
           cp_async_16r(ud + 2 * ch, in ? ub + (size_t)a * n + gc : ub, in);
         }
-        if (a >= i0 && a < i0 + kRwH && lane < kRsSW / 4)
+        if (a >= i0 && a < i0 + H && lane < kRsSW / 4)
           cp_async_16r(fring + slot * kRsSW + 4 * lane, fb + (size_t)a * n + c0 + 4 * lane, true);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
@@ -727,7 +730,7 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
       df_norm2(th, tl);
       const int sa = (a - alo) % P;
       tring[sa * 32 + lane] = make_float4(th.x, th.y, tl.x, tl.y);
-      if (a >= i0 && a < i0 + kRwH) {
+      if (a >= i0 && a < i0 + H) {
         // g = f - alpha u of this row (double-float), kept until its column
         // pass W rows on; u's pairs are the split row's (index W + 2 lane)
         const float2 uh = *reinterpret_cast<const float2*>(xh + W + 2 * lane);
@@ -788,19 +791,23 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
 }
 
 template <int W>
-void launch_refine_wide(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
-                        const float* f, float* r, double* partials, const int* active,
-                        cudaStream_t st) {
+int launch_refine_wide(const StencilHost<double>& sd, double alpha, int n, int B, const double* u,
+                       const float* f, float* r, double* partials, const int* active, int kch,
+                       cudaStream_t st) {
   constexpr int NW = RwWarps<W>::value;
   const size_t sm = (size_t)NW * RwGeom<W>::words * 4;
   auto kern = k_refine_wide<W>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const long long units = (long long)B * (n / kRsSW) * (n / kRwH);
-  long long grid = (units + NW - 1) / NW;
+  if (kch > wide_chunks_max(n)) kch = wide_chunks_max(n);
+  if (kch <= 0) kch = wide_chunks(n, W, (long long)B * (n / kRsSW), num_sms_refine(), NW);
+  const long long units = (long long)B * (n / kRsSW) * kch;
+  long long grid = units;  // one block per SM while there are units for every SM
   const long long cap = (long long)num_sms_refine();
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  kern<<<(int)grid, 32 * NW, sm, st>>>(refine_args<W>(sd, alpha, n), B, u, f, r, partials, active);
+  kern<<<(int)grid, 32 * NW, sm, st>>>(refine_args<W>(sd, alpha, n), B, u, f, r, partials, active,
+                                       kch);
+  return (n / kRsSW) * kch;
 }
 
 template <int WK>
@@ -845,11 +852,12 @@ bool launch_refine_pipe(const StencilHost<double>& sd, double alpha, int n, int 
 // the stencil kernels when the level qualifies (Toeplitz K, M = I, aligned
 // buffers, n a multiple of 4): the strip form for half-widths <= 8 and n a
 // multiple of 64, the wide strip form for half-widths <= 32 and n a
-// multiple of 128 (if wide_ok), else the tiled pipeline; false otherwise.  *nparts:
+// multiple of 64 (if wide_req <= 0: -wide_req chunks per strip, 0 its own
+// choice), else the tiled pipeline; false otherwise.  *nparts:
 // partial sums written per right-hand side.
 bool try_refine_pipe(const StencilHost<double>* sd, double alpha, int n, int B, const double* u,
                      const float* f, float* r, double* partials, const int* active, int tile,
-                     int tx, bool wide_ok, cudaStream_t st, int* nparts) {
+                     int tx, int wide_req, cudaStream_t st, int* nparts) {
   if (!sd || !sd->valid || sd->nbK != 0 || sd->wM != 0 || sd->sM[0] != 1.0 || n % 4 != 0 ||
       (reinterpret_cast<uintptr_t>(u) & 15) || (reinterpret_cast<uintptr_t>(f) & 15))
     return false;
@@ -861,10 +869,11 @@ bool try_refine_pipe(const StencilHost<double>* sd, double alpha, int n, int B, 
     *nparts = (n / kRsSW) * (n / kRsH);
     return true;
   }
-  if (wide_ok && w <= 32 && n % kRsSW == 0 && n % kRwH == 0) {
-    if (w <= 16) launch_refine_wide<16>(*sd, alpha, n, B, u, f, r, partials, active, st);
-    else launch_refine_wide<32>(*sd, alpha, n, B, u, f, r, partials, active, st);
-    *nparts = (n / kRsSW) * (n / kRwH);
+  if (wide_req <= 0 && w <= 32 && n % kRsSW == 0 && n >= 2 * kRsSW) {
+    *nparts = w <= 16 ? launch_refine_wide<16>(*sd, alpha, n, B, u, f, r, partials, active,
+                                               -wide_req, st)
+                      : launch_refine_wide<32>(*sd, alpha, n, B, u, f, r, partials, active,
+                                               -wide_req, st);
     return true;
   }
   *nparts = tx * tx;
@@ -895,8 +904,9 @@ void refine_residual2d(const Band2D<float>& hi, const float* Kd_lo, const float*
   int tx = ceil_div(hi.n, tile);
   int pi_ = log.begin(K_REFINE_RESIDUAL, st);
   int nparts = tx * tx;
-  // tile_req <= 0 (the default): the wide strip kernel where it applies
-  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, tile_req <= 0,
+  // tile_req <= 0 (the default): the wide strip kernel where it applies,
+  // with -tile_req chunks per strip (0: its own choice)
+  if (!try_refine_pipe(stencil, alpha, hi.n, B, u, f, r, partials, active, tile, tx, tile_req,
                        st, &nparts)) {
     nparts = tx * tx;
     size_t sm = smem(tile);

@@ -4,8 +4,9 @@
 // and the full-weighting restriction y_{l+1} = R r (R = (P (x) P)^T / 4, the
 // [1 2 1] / 4 stencil per axis) of such a residual.
 //
-// Strip form: one warp computes kWideH consecutive output rows of a
-// 64-column strip of one right-hand side, lane j owning columns 2j and
+// Strip form: one warp computes a chunk of consecutive output rows of a
+// 64-column strip of one right-hand side (the launch cuts every strip into
+// kch chunks, so that the units spread evenly over the SMs), lane j owning columns 2j and
 // 2j + 1 (the two columns' multiply-adds are one packed fma.rn.f32x2).
 // Input rows of x stream through a warp-private cp.async ring; the row pass
 // of input row a reads the lane's window from the staged row; its outputs t
@@ -28,7 +29,6 @@ namespace nmg {
 namespace {
 
 constexpr int kWideSW = 64;   // columns per strip
-constexpr int kWideH = 128;   // output rows per warp unit
 constexpr int kWidePF = 4;    // rows staged ahead
 constexpr int kWideRing = kWidePF + 2;
 
@@ -87,7 +87,7 @@ template <int W>
 __global__ void __launch_bounds__(32 * WideWarps<W>::value, 1)
 k_res_wide(WideArgs<W> op, int B, const float* __restrict__ x, const float* __restrict__ y,
            float* __restrict__ r, double* __restrict__ partials,
-           const int* __restrict__ active) {
+           const int* __restrict__ active, int kch) {
   using G = WideGeom<W>;
   constexpr int XW = G::XW, P = G::P, Q = G::Q;
   extern __shared__ __align__(16) float wide_smem[];
@@ -99,7 +99,7 @@ k_res_wide(WideArgs<W> op, int B, const float* __restrict__ x, const float* __re
   float* yring = xring + kWideRing * XW;                    // [ring][64]
   float* xodd = yring + kWideRing * kWideSW;                // [XW]: staged row from column + 1
   const int n = op.n;
-  const int ns = n / kWideSW, upi = ns * (n / kWideH);
+  const int ns = n / kWideSW, upi = ns * kch, hu = (n + kch - 1) / kch;
   const int total = B * upi;
   const size_t plane = (size_t)n * n;
   const float alpha = op.alpha;
@@ -112,13 +112,18 @@ k_res_wide(WideArgs<W> op, int B, const float* __restrict__ x, const float* __re
   for (int d = 0; d < KR; ++d) kr[d] = op.k2[d];
   auto K = [&](int d) -> float2 { return W <= 16 ? kr[d < KR ? d : 0] : op.k2[d]; };
 
-  for (int unit = blockIdx.x * WideWarps<W>::value + wib; unit < total;
-       unit += gridDim.x * WideWarps<W>::value) {
+  // units dealt block-cyclically (block blockIdx.x takes units blockIdx.x,
+  // + gridDim.x, ...; its warps take those in turn), so every SM gets the
+  // same number of units to within one
+  for (int j = wib;; j += WideWarps<W>::value) {
+    const int unit = j * gridDim.x + blockIdx.x;
+    if (unit >= total) break;
     const int b = unit / upi;
     if (!active[b]) continue;  // warp-uniform
     const int rem = unit - b * upi;
-    const int c0 = (rem % ns) * kWideSW, i0 = (rem / ns) * kWideH;
-    const int alo = i0 - W, ahi = i0 + kWideH + W;  // input rows
+    const int c0 = (rem % ns) * kWideSW, i0 = (rem / ns) * hu;
+    const int H = min(hu, n - i0);                  // output rows of this unit
+    const int alo = i0 - W, ahi = i0 + H + W;  // input rows
     const float* xb = x + (size_t)b * plane;
     const float* yb = y ? y + (size_t)b * plane : nullptr;
     float* rb = r + (size_t)b * plane;
@@ -133,7 +138,7 @@ k_res_wide(WideArgs<W> op, int B, const float* __restrict__ x, const float* __re
           const bool in = rin && gc >= 0 && gc < n;
           cp_async16(xd + 4 * ch, in ? xb + (size_t)a * n + gc : xb, in);
         }
-        if (yb && a >= i0 && a < i0 + kWideH && lane < kWideSW / 4)
+        if (yb && a >= i0 && a < i0 + H && lane < kWideSW / 4)
           cp_async16(yring + slot * kWideSW + 4 * lane, yb + (size_t)a * n + c0 + 4 * lane, true);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
@@ -185,7 +190,7 @@ k_res_wide(WideArgs<W> op, int B, const float* __restrict__ x, const float* __re
       const float2 t = add2(add2(t0, t1), add2(t2, t3));
       tring[sa * 32 + lane] = t;
       tring[(sa + P) * 32 + lane] = t;
-      if (a >= i0 && a < i0 + kWideH) {
+      if (a >= i0 && a < i0 + H) {
         // g = y - alpha x of this row, kept until its column pass W rows on
         const float2 xv = xe[W / 2];  // columns c0 + 2 lane, + 1 (staged index W + 2 lane)
         const float2 yv = yb ? *reinterpret_cast<const float2*>(yring + slot * kWideSW + 2 * lane)
@@ -221,7 +226,8 @@ k_res_wide(WideArgs<W> op, int B, const float* __restrict__ x, const float* __re
 // row as one 16-byte load (the column left of them from the left lane, or
 // from memory for lane 0), the horizontal sums of a fine row are reused by
 // the two coarse rows it serves, and each fine row is read once.
-constexpr int kRsBand = 32;  // coarse rows per unit
+constexpr int kRsBand = 8;   // coarse rows per unit (many short units: the loads of
+                             // enough warps in flight to cover the memory latency)
 constexpr int kRsWarps = 8;
 
 __global__ void __launch_bounds__(32 * kRsWarps)
@@ -272,7 +278,7 @@ k_restrict_fw(int n, int B, const float* __restrict__ r, float* __restrict__ yc,
 
 template <int W>
 int launch_wide(const Band2D<float>& op, int B, const float* x, const float* y, float* r,
-                double* partials, const int* active, cudaStream_t st) {
+                double* partials, const int* active, int kch, cudaStream_t st) {
   WideArgs<W> a{};
   a.n = op.n;
   a.alpha = op.alpha;
@@ -285,12 +291,13 @@ int launch_wide(const Band2D<float>& op, int B, const float* x, const float* y, 
   const size_t sm = (size_t)NW * WideGeom<W>::words * sizeof(float);
   auto kern = k_res_wide<W>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const long long units = (long long)B * (op.n / kWideSW) * (op.n / kWideH);
-  long long grid = (units + NW - 1) / NW;
+  if (kch <= 0) kch = wide_chunks(op.n, W, (long long)B * (op.n / kWideSW), sms(), NW);
+  const long long units = (long long)B * (op.n / kWideSW) * kch;
+  long long grid = units;  // one block per SM while there are units for every SM
   if (grid > sms()) grid = sms();
   if (grid < 1) grid = 1;
-  kern<<<(int)grid, 32 * NW, sm, st>>>(a, B, x, y, r, partials, active);
-  return (op.n / kWideSW) * (op.n / kWideH);
+  kern<<<(int)grid, 32 * NW, sm, st>>>(a, B, x, y, r, partials, active, kch);
+  return (op.n / kWideSW) * kch;
 }
 
 }  // namespace
@@ -299,23 +306,27 @@ bool wide_residual_applies(const Band2D<float>& op, const float* x, const float*
   if (!op.st || !op.st->valid) return false;
   const StencilHost<float>& h = *op.st;
   if (h.wM != 0 || h.nbM != 0 || h.nbK != 0 || h.sM[0] != 1.f) return false;
-  if (h.wK <= 8 || h.wK > 32 || op.n % kWideH != 0 || op.n < kWideH) return false;
+  if (h.wK <= 8 || h.wK > 32 || op.n % kWideSW != 0 || op.n < 2 * kWideSW) return false;
   return !((reinterpret_cast<uintptr_t>(x) & 15) || (y && (reinterpret_cast<uintptr_t>(y) & 15)));
 }
 
 int launch_residual_wide(const Band2D<float>& op, int B, const float* x, const float* y, float* r,
-                         double* partials, const int* active, cudaStream_t st) {
-  return op.st->wK <= 16 ? launch_wide<16>(op, B, x, y, r, partials, active, st)
-                         : launch_wide<32>(op, B, x, y, r, partials, active, st);
+                         double* partials, const int* active, int kch, cudaStream_t st) {
+  if (kch > wide_chunks_max(op.n)) kch = wide_chunks_max(op.n);
+  return op.st->wK <= 16 ? launch_wide<16>(op, B, x, y, r, partials, active, kch, st)
+                         : launch_wide<32>(op, B, x, y, r, partials, active, kch, st);
 }
 
-bool restrict_fw_applies(int n) { return n % 128 == 0 && (n / 2) % kRsBand == 0; }
+bool restrict_fw_applies(int n) {
+  return n % 128 == 0 && (n / 2) % kRsBand == 0 &&
+         (long long)(n / 128) * ((n / 2) / kRsBand) <= kMaxPartsPerItem;
+}
 
 int launch_restrict_fw(int n, int B, const float* r, float* yc, double* partials, const int* active,
                        cudaStream_t st) {
   const long long units = (long long)B * (n / 128) * ((n / 2) / kRsBand);
   long long grid = (units + kRsWarps - 1) / kRsWarps;
-  const long long cap = 4LL * sms();
+  const long long cap = 16LL * sms();
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   k_restrict_fw<<<(int)grid, 32 * kRsWarps, 0, st>>>(n, B, r, yc, partials, active);

@@ -165,8 +165,10 @@ int stencil_strip_parts(const Band2D<T>& op);
 // right-hand side.  The full-weighting restriction of a fine residual r
 // into yc (n a multiple of 128), with the squared norms per unit.
 bool wide_residual_applies(const Band2D<float>& op, const float* x, const float* y);
+// kch: chunks per 64-column strip (<= 0: wide_chunks' choice); returns the
+// partial sums written per right-hand side
 int launch_residual_wide(const Band2D<float>& op, int B, const float* x, const float* y, float* r,
-                         double* partials, const int* active, cudaStream_t st);
+                         double* partials, const int* active, int kch, cudaStream_t st);
 bool restrict_fw_applies(int n);
 // classical comparators (k_classic.cu): x += omega r / diag(A_l), and one
 // conjugate-gradient iteration after q = -A p (scal: (r, r), alpha, beta)
@@ -236,6 +238,43 @@ struct FnoDims {
   int width, layers, ksize, modes;
 };
 size_t fno_weights_per_level(int c, int layers, int ks, int m);
+// Strip kernels of wide stencils (half-width W): a strip of n rows is cut
+// into kch chunks of ceil(n / kch) rows, each one warp's unit, at the cost
+// of 2W halo rows per chunk.  The launch puts min(units, sms) blocks of nw
+// warps on the GPU (one block per SM: the warps' rings fill its shared
+// memory) and deals the units to them block-cyclically.  The warps are
+// latency-bound (measured: a row step takes about as long with 4 warps on
+// the SM as with 9), so one SM's time is (waves of nw units) x (rows per
+// unit): wide_chunks picks the chunk count (chunks of at least
+// kWideChunkMinH rows) that minimises ceil(ceil(units / sms) / nw) x
+// (ceil(n / k) + 2W), the larger count on ties.
+constexpr int kWideChunkMinH = 32;
+// partial-sum slots of one right-hand side in a hierarchy's workspace
+constexpr int kMaxPartsPerItem = 4096;
+// the largest chunk count a launch may use: chunks of >= kWideChunkMinH
+// rows and at most kMaxPartsPerItem units (partial sums) per right-hand side
+inline int wide_chunks_max(int n) {
+  int k = n / kWideChunkMinH;
+  const int cap = kMaxPartsPerItem / (n / 64 > 0 ? n / 64 : 1);
+  if (k > cap) k = cap;
+  return k < 1 ? 1 : k;
+}
+inline int wide_chunks(int n, int W, long long strips, int sms, int nw) {
+  int best_k = 1;
+  long long best = -1;
+  for (int k = 1; k <= wide_chunks_max(n); ++k) {
+    const long long units = strips * k;
+    const long long u = (units + sms - 1) / sms;
+    const long long waves = (u + nw - 1) / nw;
+    const long long cost = waves * ((n + k - 1) / k + 2 * W);
+    if (best < 0 || cost <= best) {
+      best = cost;
+      best_k = k;
+    }
+  }
+  return best_k;
+}
+
 // CNN smoother: the most layers one level may have, and the doubles of one
 // level's weights (PyTorch layout, channels 1 -> width -> ... -> 1)
 constexpr int kMaxCnnLayers = 16;

@@ -244,6 +244,29 @@ def test_refine_step_wide_stencils(ctx, sigma):
     assert rel(ud.cpu().numpy() - u0, ref - u0) < 1e-4
 
 
+@pytest.mark.parametrize("kch", [1, 3, 5, 16])
+def test_refine_wide_chunk_counts(ctx, tmp_path, kch):
+    """The compensated outer residual's wide strip kernel with kch chunks
+    per strip (forced through the tuner's cache; 3 and 5 leave a shorter
+    last chunk) inside one refinement step on a 512 x 512 grid (PSF
+    half-width 16): the step's increment against the oracle cycle's."""
+    from tuning_util import force_tuning
+    n, L = 512, 5
+    H, G, W = make(ctx, "bf16_refine", n=n, levels=L, sigma=4.0, alpha=1e-2, seed=33)
+    force_tuning(G, 2, tmp_path / "tune.txt", {0: dict(ref=-kch)})
+    assert G.tuning(0)["ref_tile"] == -kch
+    rng = np.random.default_rng(40 + kch)
+    f = rng.standard_normal((2, n, n))
+    u0 = 0.2 * rng.standard_normal((2, n, n))
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    f32 = fd.double().cpu().numpy()
+    ud = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    G.cycle(fd, ud)
+    torch.cuda.synchronize()
+    ref = O.nmgf(H, W, 0, u0, f32)
+    assert rel(ud.cpu().numpy() - u0, ref - u0) < 1e-4
+
+
 @pytest.fixture(scope="module")
 def c2w():
     if not os.path.exists(C2W):

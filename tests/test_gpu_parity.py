@@ -147,6 +147,38 @@ def test_wide_stencil_residual_and_restrict(ctx, sigma, n):
     G.close()
 
 
+@pytest.mark.parametrize("kch", [1, 3, 5, 16])
+def test_wide_stencil_chunk_counts(ctx, tmp_path, kch):
+    """The wide strip kernels cut every 64-column strip into kch chunks
+    (512 rows: 3 and 5 leave a shorter last chunk), dealt block-cyclically
+    over the SMs: residual with norms and residual + restriction at each
+    chunk count, forced through the tuner's cache, against the oracle."""
+    from tuning_util import force_tuning
+    n, sigma, L = 512, 4.0, 5
+    taps = I.gaussian_taps(sigma)
+    H = O.build_hierarchy_2d(taps, n, 1e-2, L)
+    G = nmg.Hierarchy(ctx, dim=2, n=n, levels=L, alpha=1e-2, taps=taps, precision="fp32",
+                      weights=I.random_cnn_weights(2, L - 1, seed=9))
+    force_tuning(G, 3, tmp_path / "tune.txt", {0: dict(res=-kch, rst=-kch)})
+    t = G.tuning(0)
+    assert t["res_tile"] == -kch and t["rst_tile"] == -kch
+    rng = np.random.default_rng(kch)
+    x = rng.standard_normal((3, n, n))
+    y = rng.standard_normal((3, n, n))
+    xd, yd = dev(x, "fp32"), dev(y, "fp32")
+    x32, y32 = host(xd), host(yd)
+    rd = torch.empty_like(xd)
+    norms = G.residual(0, xd, yd, rd, norms=True)
+    ref = y32 - O.apply_level(H, 0, x32)
+    assert relerr(host(rd), ref) < TOL_STEP["fp32"]
+    nref = np.linalg.norm(ref.reshape(3, -1), axis=1)
+    assert np.max(np.abs(norms - nref) / nref) < TOL_STEP["fp32"]
+    yc = torch.full((3, n // 2, n // 2), 7.0, dtype=torch.float32, device="cuda")
+    G.residual_restrict(0, xd, yd, yc)
+    assert relerr(host(yc), O.restrict(H, 0, ref)) < TOL_STEP["fp32"]
+    G.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_smoother(ctx, prec):
     H, G, W = make2d(ctx, prec)
