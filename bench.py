@@ -62,6 +62,10 @@ WORKLOADS = {
                weights="c2_2d_n128_s2_a1e-2.npz", fno_weights="c2f_2d_n128_s2_a1e-2_fno.npz"),
 }
 PRECISION_TEXT = {
+    "bf16top_refine": "bf16 tensor-core smoother with three bf16 terms per operand (six products) "
+                      "on the finest level and bf16 pairs (three products) on the coarser levels, "
+                      "fp32 accumulation, fp32 cycle vectors, compensated-fp32 outer residual, "
+                      "fp64 update and coarse solve",
     "bf16_refine": "bf16 tensor-core smoother, every operand three bf16 terms (six products per "
                    "product, fp32 accumulation), fp32 cycle vectors, compensated-fp32 outer "
                    "residual, fp64 update and coarse solve",
@@ -76,6 +80,7 @@ PRECISION_TEXT = {
     "fp32": "fp32 throughout (SIMT smoother), fp64 coarse solve",
 }
 DTYPE = {"bf16_refine": "bf16x3+f32+f64", "bf16x3_refine": "bf16x2+f32+f64",
+         "bf16top_refine": "bf16x3/bf16x2+f32+f64",
          "bf16fast_refine": "bf16+f32+f64",
          "fp16_refine": "f16x2+f32+f64", "fp32": "f32"}
 
@@ -328,7 +333,19 @@ def solve_summary(B, tp, rp):
             "max_relres": float(max(r[2].max() for r in rp))}
 
 
-def roofline_of(kern, prec, n, peaks, peak_src):
+def mma_flops_per_px(prec, dom, n, levels):
+    """Issued MMA flops per output pixel of a kernel class; for the form with
+    three terms on the finest level and pairs below, the pixel-weighted mean
+    over the smoother levels."""
+    if prec == "bf16top_refine":
+        px = [(n >> l) ** 2 for l in range(levels - 1)]
+        f0 = px[0] / sum(px)
+        return (f0 * MMA_FLOPS_PER_PX["bf16_refine"][dom] +
+                (1 - f0) * MMA_FLOPS_PER_PX["bf16x3_refine"][dom])
+    return MMA_FLOPS_PER_PX[prec][dom]
+
+
+def roofline_of(kern, prec, n, levels, peaks, peak_src):
     """Roofline of the dominant kernel class: algorithmic work per unit x
     units / the class's summed CUDA-event time."""
     dom = max(kern, key=lambda k: kern[k]["ms"])
@@ -337,7 +354,8 @@ def roofline_of(kern, prec, n, peaks, peak_src):
     if dom in FLOPS_PER_PX and refine:
         fl = FLOPS_PER_PX[dom]
         achieved = fl * d["units"] / (d["ms"] / 1e3) / 1e12
-        issued = MMA_FLOPS_PER_PX[prec][dom] * d["units"] / (d["ms"] / 1e3) / 1e12
+        mpx = mma_flops_per_px(prec, dom, n, levels)
+        issued = mpx * d["units"] / (d["ms"] / 1e3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
         bpu = HIDDEN_DRAM_B_PER_UNIT.get((prec, n)) if dom == "cnn_hidden" else None
         traffic = bpu * d["units"] / d["launches"] if bpu else None
@@ -349,7 +367,7 @@ def roofline_of(kern, prec, n, peaks, peak_src):
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flop_per_unit": fl, "unit_def": "output pixel x active right-hand side",
                 "mma_issued_tflops": issued,
-                "mma_issued_flop_per_unit": MMA_FLOPS_PER_PX[prec][dom],
+                "mma_issued_flop_per_unit": mpx,
                 "launch_ms": d["ms"] / d["launches"]}
     if dom in FLOPS_PER_PX:
         achieved = FLOPS_PER_PX[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
@@ -465,13 +483,14 @@ def run_ours(args, wl, world, rank, local):
         if c:
             kern[name] = {"launches": c, "ms": ms, "units": units}
     peaks, peak_src = load_peaks()
-    roof = roofline_of(kern, prec, wl["n"], peaks, peak_src)
+    roof = roofline_of(kern, prec, wl["n"], wl["levels"], peaks, peak_src)
     breakdown = kernel_breakdown(kern, prec, ksteps, peaks)
 
     # ---- the comparison forms on the same GPU and right-hand sides
     compare = {}
     if not args.no_compare:
-        for p in ["fp32", "bf16fast_refine", "bf16x3_refine", "bf16_refine", "fp16_refine"]:
+        for p in ["fp32", "bf16fast_refine", "bf16x3_refine", "bf16_refine", "bf16top_refine",
+                  "fp16_refine"]:
             if p == prec:
                 continue
             Gp = hier(p)

@@ -34,6 +34,7 @@
  *      NMG_FP64          f, u, every level vector: double
  *      NMG_FP32          f, u, every level vector: float
  *      NMG_BF16_REFINE,
+ *      NMG_BF16TOP_REFINE,
  *      NMG_BF16X3_REFINE,
  *      NMG_BF16FAST_REFINE,
  *      NMG_FP16_REFINE   f: float, u: double; level vectors of the inner
@@ -81,6 +82,19 @@ enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };
  *                        product); per-cycle iterates agree with fp64 to
  *                        about 1e-5 even for trained smoothers that amplify
  *                        rounding strongly.
+ *   NMG_BF16TOP_REFINE   the three-term form of NMG_BF16_REFINE on the
+ *                        finest level's smoother, the pair form of
+ *                        NMG_BF16X3_REFINE on every coarser level.  The
+ *                        rounding of the finest smoother reaches the
+ *                        cycle's result undamped; a coarser level's
+ *                        output reaches it only through the filter,
+ *                        prolongation and the finer levels, and for the
+ *                        trained smoothers of the 512x512 operators the
+ *                        pairs there leave the cycle's error at the
+ *                        three-term level (a product emulation shows
+ *                        the same error as three terms everywhere).
+ *                        Saves about half the MMA work of the coarser
+ *                        levels (a quarter of the pixels).
  *   NMG_BF16X3_REFINE    every hidden-layer operand is a pair of bf16
  *                        values (hi + lo, 2^-16 relative), three products
  *                        a_hi*w_hi + a_hi*w_lo + a_lo*w_hi (2 MMA
@@ -94,14 +108,15 @@ enum { NMG_CONVERGED = 0, NMG_NOT_CONVERGED = 1, NMG_DIVERGED = 2 };
  *                        relative) at the same cost; the network runs on
  *                        power-of-two-scaled values to stay inside fp16's
  *                        range (activations above 65504 are clamped).
- * All four take f: float, u: double, like NMG_BF16_REFINE above. */
+ * All of them take f: float, u: double, like NMG_BF16_REFINE above. */
 typedef enum {
   NMG_FP64 = 0,
   NMG_FP32 = 1,
   NMG_BF16_REFINE = 2,
   NMG_BF16FAST_REFINE = 3,
   NMG_FP16_REFINE = 4,
-  NMG_BF16X3_REFINE = 5
+  NMG_BF16X3_REFINE = 5,
+  NMG_BF16TOP_REFINE = 6
 } nmg_precision;
 
 /*

@@ -16,18 +16,20 @@ from typing import Sequence
 import numpy as np
 
 __all__ = [
-    "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "FP16_REFINE", "BF16X3_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
+    "FP64", "FP32", "BF16_REFINE", "BF16FAST_REFINE", "FP16_REFINE", "BF16X3_REFINE",
+    "BF16TOP_REFINE", "PRECISIONS", "NMGError", "Context", "Hierarchy",
     "lib", "lib_path", "pack_weights", "load_weights", "SolveInfo", "solve_multi", "Server",
     "NOALLOC_SCRATCH_BYTES",
 ]
 
-FP64, FP32, BF16_REFINE, BF16FAST_REFINE, FP16_REFINE, BF16X3_REFINE = 0, 1, 2, 3, 4, 5
+FP64, FP32, BF16_REFINE, BF16FAST_REFINE, FP16_REFINE, BF16X3_REFINE, BF16TOP_REFINE = \
+    0, 1, 2, 3, 4, 5, 6
 # kernel classes of Context.profile_read (NMG_K_* in nmg.h)
 KERNEL_CLASSES = ["residual", "restrict", "cnn_first", "cnn_hidden", "cnn_last", "filter",
                   "coarse", "prolong", "refine_residual", "other", "cnn_fused"]
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16_refine": BF16_REFINE,
               "bf16fast_refine": BF16FAST_REFINE, "fp16_refine": FP16_REFINE,
-              "bf16x3_refine": BF16X3_REFINE}
+              "bf16x3_refine": BF16X3_REFINE, "bf16top_refine": BF16TOP_REFINE}
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 1 << 20  # NMG_NOALLOC_SCRATCH_BYTES in nmg.h
 

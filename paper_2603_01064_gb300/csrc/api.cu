@@ -180,7 +180,8 @@ size_t elem_size(int precision) { return precision == NMG_FP64 ? 8 : 4; }
 constexpr long long kDefaultWaitNs = 2000000000LL;
 bool is_refine(int precision) {
   return precision == NMG_BF16_REFINE || precision == NMG_BF16FAST_REFINE ||
-         precision == NMG_FP16_REFINE || precision == NMG_BF16X3_REFINE;
+         precision == NMG_FP16_REFINE || precision == NMG_BF16X3_REFINE ||
+         precision == NMG_BF16TOP_REFINE;
 }
 
 size_t plane(const nmg_hier* h, int l) {
@@ -260,7 +261,9 @@ bool for_work_buffers(const nmg_hier* h, int B, Work& w, Fn fn) {
     // bytes per channel and grid point: fp64 / fp32 (SIMT forms), two 16-bit
     // terms (pair forms, one in the fast form), three (three-term bf16 form)
     const size_t actb = (size_t)h->width * n0 * B *
-                        (h->precision == NMG_FP64 ? 8 : h->precision == NMG_BF16_REFINE ? 6 : 4);
+                        (h->precision == NMG_FP64                                           ? 8
+                         : h->precision == NMG_BF16_REFINE || h->precision == NMG_BF16TOP_REFINE ? 6
+                                                                                               : 4);
     WB(actb, w.act0);
     WB(actb, w.act1);
     WB(n0 * B * 2 * es, w.cbuf);
@@ -1121,7 +1124,7 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
                      nmg_hier** out) {
   if (!ctx || !op || !out) return fail(ctx, NMG_ERR_ARG, "null argument to nmg_setup");
   *out = nullptr;
-  if (op->precision < NMG_FP64 || op->precision > NMG_BF16X3_REFINE)
+  if (op->precision < NMG_FP64 || op->precision > NMG_BF16TOP_REFINE)
     return fail(ctx, NMG_ERR_ARG, "unknown precision");
   if (is_refine(op->precision) && op->dim != 2)
     return fail(ctx, NMG_ERR_UNSUPPORTED, "the bf16 refinement form is 2D only");
@@ -1304,10 +1307,12 @@ nmg_status nmg_setup(nmg_ctx* ctx, const nmg_operator_desc* op, const nmg_smooth
           bp.push_back(base + o);
           o += cout;
         }
-        const int split = h->precision == NMG_BF16_REFINE     ? 3
-                          : h->precision == NMG_BF16X3_REFINE ? 1
-                          : h->precision == NMG_FP16_REFINE   ? 2
-                                                            : 0;
+        // split: 3 three bf16 terms, 1 bf16 pairs, 2 fp16 pairs, 0 one bf16
+        const int split = h->precision == NMG_BF16_REFINE      ? 3
+                          : h->precision == NMG_BF16TOP_REFINE ? (l == 0 ? 3 : 1)
+                          : h->precision == NMG_BF16X3_REFINE  ? 1
+                          : h->precision == NMG_FP16_REFINE    ? 2
+                                                               : 0;
         d.bf16_pack = bf16_cnn_pack(d.layers, Wp, bp, split);
         if (!d.bf16_pack) st = fail(ctx, NMG_ERR_UNSUPPORTED, "bf16 tensor-core smoother unavailable");
         else h->allocs.push_back(d.bf16_pack);

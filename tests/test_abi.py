@@ -43,6 +43,17 @@ def test_noalloc_limit_matches_header():
     assert int(m.group(1)) << int(m.group(2)) == nmg.NOALLOC_SCRATCH_BYTES
 
 
+def test_precision_constants_match_header():
+    """The binding's precision numbers equal the header's nmg_precision."""
+    import paper_2603_01064_gb300 as nmg
+    src = open(os.path.join(ROOT, "include", "nmg.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} nmg_precision;", src).group(1)
+    hdr = {k: int(v) for k, v in re.findall(r"NMG_([A-Z0-9_]+)\s*=\s*(\d+)", body)}
+    assert hdr and set(hdr) == {k.upper() for k in nmg.PRECISIONS}
+    for name, val in nmg.PRECISIONS.items():
+        assert hdr[name.upper()] == val, name
+
+
 def test_library_exports_every_declared_symbol(libpath):
     L = ctypes.CDLL(libpath)
     missing = [n for n in _declared() if not hasattr(L, n)]

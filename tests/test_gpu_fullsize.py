@@ -127,7 +127,9 @@ def c3f():
                                             (1e-3, "bf16_refine", 1e-3), (1e-4, "bf16_refine", 1e-3),
                                             (1e-1, "bf16x3_refine", 1e-3), (1e-2, "fp32", 1e-4),
                                             (1e-1, "fp16_refine", 1e-3), (1e-2, "fp16_refine", 1e-3),
-                                            (1e-3, "fp16_refine", 1e-3), (1e-4, "fp16_refine", 1e-3)])
+                                            (1e-3, "fp16_refine", 1e-3), (1e-4, "fp16_refine", 1e-3),
+                                            (1e-1, "bf16top_refine", 1e-3), (1e-2, "bf16top_refine", 1e-3),
+                                            (1e-3, "bf16top_refine", 1e-3), (1e-4, "bf16top_refine", 1e-3)])
 def test_512_full_batch_one_cycle_sampled(ctx, c3f, alpha, prec, tol):
     W = nmg.load_weights(os.path.join(WDIR, f"c3_2d_n512_s4_a{alpha:.0e}".replace("e-0", "e-") + ".npz"))
     taps = I.gaussian_taps(4.0)
