@@ -647,9 +647,9 @@ def classical_leg(ctx, wl, f, taps, stream, neural_cycles):
 SWEEP_ORACLE_SAMPLE = 1  # right-hand sides per alpha checked against the oracle's cycle
 
 
-# the CNN smoothers of the alpha = 1e-3 operator take about 170 cycles to
-# 1e-6 (their 3 x 3, four-layer receptive field is short for that level's
-# operator); the limit leaves them room and bounds the alpha = 1e-4 solve
+# the CNN smoothers of the alpha = 1e-3 operator take about 50 cycles to
+# 1e-6; the limit leaves them room and bounds the alpha = 1e-4 solve, whose
+# smoothers do not converge
 SWEEP_MAX_CYCLES = 250
 
 
