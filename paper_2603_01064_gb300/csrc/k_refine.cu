@@ -628,9 +628,13 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
 // rows until row a's column pass, so no global load waits inside the row
 // loop and no staged row has to outlive the prefetch window.
 // ---------------------------------------------------------------------------
-constexpr int kRwPF = 4;   // staged rows ahead
+// staged rows ahead.  The warps are latency-bound, so warps per SM matter
+// more than prefetch depth: two rows ahead leave room for 7 warps at
+// half-width 16 (measured 0.73 ms per 64-RHS 512x512 launch, against
+// 0.93 ms with 4 rows ahead and 6 warps)
+constexpr int kRwPF = 2;
 constexpr int kRwRing = kRwPF + 2;
-template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 6 : 3; };
+template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 7 : 3; };
 template <int W> struct RwGeom {
   static constexpr int XW = kRsSW + 2 * W;                   // staged u row (doubles)
   static constexpr int P = 2 * W + 1;                        // row-pass ring rows
