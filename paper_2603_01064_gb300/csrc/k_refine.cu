@@ -629,19 +629,21 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
 // loop and no staged row has to outlive the prefetch window.
 // ---------------------------------------------------------------------------
 // staged rows ahead.  The warps are latency-bound, so warps per SM matter
-// more than prefetch depth: two rows ahead leave room for 7 warps at
-// half-width 16 (measured 0.73 ms per 64-RHS 512x512 launch, against
-// 0.93 ms with 4 rows ahead and 6 warps)
+// more than prefetch depth: two rows ahead, the split row written over its
+// own staged doubles and f read straight from global memory leave room for
+// 8 warps at half-width 16 (7 warps: 0.73 ms per 64-RHS 512x512 launch;
+// 6 warps with 4 rows ahead: 0.93 ms)
 constexpr int kRwPF = 2;
 constexpr int kRwRing = kRwPF + 2;
-template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 7 : 3; };
+template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 8 : 4; };
 template <int W> struct RwGeom {
   static constexpr int XW = kRsSW + 2 * W;                   // staged u row (doubles)
   static constexpr int P = 2 * W + 1;                        // row-pass ring rows
   static constexpr int Q = W + 1;                            // g ring rows
   // per-warp shared memory in 4-byte words: t ring and g ring (float4 per
-  // lane and row), u ring, split row (hi, lo), f ring (64 per row)
-  static constexpr int words = (P + Q) * 128 + kRwRing * XW * 2 + 2 * XW + kRwRing * kRsSW;
+  // lane and row), u ring (a slot's XW doubles are replaced by its split
+  // row, XW hi floats then XW lo floats, once the row is current)
+  static constexpr int words = (P + Q) * 128 + kRwRing * XW * 2;
 };
 
 template <int W>
@@ -657,9 +659,6 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
   float4* tring = reinterpret_cast<float4*>(wbase);                 // [P][32 lanes]
   float4* gring = tring + P * 32;                                   // [Q][32 lanes]
   double* uring = reinterpret_cast<double*>(gring + Q * 32);        // [ring][XW]
-  float* xh = reinterpret_cast<float*>(uring + kRwRing * XW);        // [XW]
-  float* xl = xh + XW;                                               // [XW]
-  float* fring = xl + XW;                                            // [ring][64]
   const int n = op.n;
   const int ns = n / kRsSW, upi = ns * kch, hu = (n + kch - 1) / kch;
   const int total = B * upi;
@@ -687,8 +686,6 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
           const bool in = rin && gc >= 0 && gc < n;
           cp_async_16r(ud + 2 * ch, in ? ub + (size_t)a * n + gc : ub, in);
         }
-        if (a >= i0 && a < i0 + H && lane < kRsSW / 4)
-          cp_async_16r(fring + slot * kRsSW + 4 * lane, fb + (size_t)a * n + c0 + 4 * lane, true);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
@@ -700,15 +697,29 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
       asm volatile("cp.async.wait_group %0;" ::"n"(kRwPF - 1) : "memory");
       __syncwarp();
       stage(a + kRwPF);
-      // split the staged row once (the previous row's window reads are
-      // ordered before this by the barrier above)
-      const double* us = uring + ((a - alo) % kRwRing) * XW;
-      for (int k = lane; k < XW; k += 32) {
-        float h, l;
-        split_double(us[k], h, l);
-        xh[k] = h;
-        xl[k] = l;
-      }
+      // f of this row's two columns, read now and used after the row pass
+      const bool grow = a >= i0 && a < i0 + H;  // warp-uniform
+      float2 fv = make_float2(0.f, 0.f);
+      if (grow) fv = __ldg(reinterpret_cast<const float2*>(fb + (size_t)a * n + c0 + 2 * lane));
+      // split the staged row once, over its own slot: every lane reads its
+      // doubles first, then the slot holds XW hi floats and XW lo floats
+      // (the slot is restaged only kRwPF rows on, after this row is done)
+      double* us = uring + ((a - alo) % kRwRing) * XW;
+      constexpr int PER = (XW + 31) / 32;
+      double uv[PER];
+#pragma unroll
+      for (int j = 0; j < PER; ++j) uv[j] = lane + 32 * j < XW ? us[lane + 32 * j] : 0.0;
+      __syncwarp();
+      float* xh = reinterpret_cast<float*>(us);
+      float* xl = xh + XW;
+#pragma unroll
+      for (int j = 0; j < PER; ++j)
+        if (lane + 32 * j < XW) {
+          float h, l;
+          split_double(uv[j], h, l);
+          xh[lane + 32 * j] = h;
+          xl[lane + 32 * j] = l;
+        }
       __syncwarp();
       // row pass: t[c] = sum_d K[d] u[a][c0 + 2 lane + c + d - W], the
       // lane's window read as aligned pairs (odd taps take the halves of
@@ -734,13 +745,11 @@ k_refine_wide(RefineArgs<W> op, int B, const double* __restrict__ u,
       df_norm2(th, tl);
       const int sa = (a - alo) % P;
       tring[sa * 32 + lane] = make_float4(th.x, th.y, tl.x, tl.y);
-      if (a >= i0 && a < i0 + H) {
+      if (grow) {
         // g = f - alpha u of this row (double-float), kept until its column
         // pass W rows on; u's pairs are the split row's (index W + 2 lane)
         const float2 uh = *reinterpret_cast<const float2*>(xh + W + 2 * lane);
         const float2 ulp = *reinterpret_cast<const float2*>(xl + W + 2 * lane);
-        const float2 fv =
-            *reinterpret_cast<const float2*>(fring + ((a - alo) % kRwRing) * kRsSW + 2 * lane);
         float gh[2], gl[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
