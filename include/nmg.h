@@ -460,7 +460,9 @@ nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double*
                             double* units);
 /* Autotuner: for every level of a 2D hierarchy, time the candidate launch
  * shapes (tile sides of the residual, the fused residual + restriction and
- * the compensated outer residual; output filter as three passes (mode 0),
+ * the compensated outer residual, and on levels with a wide Toeplitz
+ * stencil the strip kernels with k row chunks per 64-column strip; output
+ * filter as three passes (mode 0),
  * one block-synchronous kernel (1), one warp-level kernel for 64x64 and
  * 128x128 levels (2), or three warp-level passes for 256x256 and 512x512
  * levels (3)) on the hierarchy's workspace with `batch`
@@ -470,7 +472,10 @@ nmg_status nmg_profile_read(nmg_ctx* ctx, int kind, long long* launches, double*
  * read instead of timed, and to which new choices are appended.  No effect
  * on results beyond fp rounding order. */
 nmg_status nmg_autotune(nmg_ctx* ctx, nmg_hier* h, int batch, const char* cache_path);
-/* The launch choices of one level (0 / -1: built-in defaults). */
+/* The launch choices of one level (0 / -1: built-in defaults).  A tile
+ * choice t > 0 is a tile side; t <= 0 selects the strip kernel where the
+ * level has one, with -t row chunks per strip (0: the kernel's own choice
+ * from its occupancy model). */
 nmg_status nmg_hier_tuning(const nmg_hier* h, int level, int* res_tile, int* rst_tile,
                            int* ref_tile, int* filt_mode);
 
