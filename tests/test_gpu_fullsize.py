@@ -10,8 +10,9 @@ sides are checked against the FP64 oracle one by one.
   of the batch whose sampled results meet 1e-6 under the oracle's own apply.
 * 2D BTTB 512x512, sigma 4 px, 7 levels, 64 right-hand sides, alpha in
   {1e-1, 1e-2, 1e-3, 1e-4}: one cycle of the whole batch (autotuned launch
-  shapes) in the bf16 and fp16 split refinement forms against the oracle
-  for sampled items; full solves for the alphas whose trained CNN smoothers
+  shapes) in the bf16 three-term form, the form with three terms on the
+  finest level only and the fp16 pair form against the oracle for four
+  sampled items; full solves for the alphas whose trained CNN smoothers
   converge (1e-1, 1e-2 and 1e-3).
 """
 import os
@@ -108,7 +109,7 @@ def test_2d_full_batch_solve_sampled(ctx, c2, prec):
 # 2D BTTB 512x512, sigma 4 px, 7 levels, 64 right-hand sides, alpha sweep
 # ---------------------------------------------------------------------------
 
-C3_SAMPLE = [0, 63]
+C3_SAMPLE = [0, 21, 42, 63]
 
 
 @pytest.fixture(scope="module")
