@@ -1086,9 +1086,6 @@ k_last_gather(int n, int nimg, const float* __restrict__ g, float* __restrict__ 
   // every lane of a warp takes part in the shuffles: the loop runs to a
   // multiple of the warp size
   const int span = (quads + 31) / 32 * 32;
-  // two quads per trip in flight: the loads of the next quad issue before
-  // the current one's sums (the kernel waits on DRAM latency)
-#pragma unroll 2
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q - (int)(threadIdx.x & 31) < span;
        q += gridDim.x * blockDim.x) {
     const bool live = q < quads;
