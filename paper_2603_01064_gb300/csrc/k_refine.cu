@@ -631,8 +631,8 @@ k_refine_strip(RefineArgs<WK> op, int B, const double* __restrict__ u,
 // staged rows ahead.  The warps are latency-bound, so warps per SM matter
 // more than prefetch depth: two rows ahead, the split row written over its
 // own staged doubles and f read straight from global memory leave room for
-// 8 warps at half-width 16 (7 warps: 0.73 ms per 64-RHS 512x512 launch;
-// 6 warps with 4 rows ahead: 0.93 ms)
+// 8 warps at half-width 16 (measured per 64-RHS 512x512 launch: 0.69 ms;
+// 7 warps: 0.73 ms; 6 warps with 4 rows ahead: 0.93 ms)
 constexpr int kRwPF = 2;
 constexpr int kRwRing = kRwPF + 2;
 template <int W> struct RwWarps { static constexpr int value = W <= 16 ? 8 : 4; };
