@@ -12,8 +12,7 @@ sides are checked against the FP64 oracle one by one.
   {1e-1, 1e-2, 1e-3, 1e-4}: one cycle of the whole batch (autotuned launch
   shapes) in the bf16 three-term form, the form with three terms on the
   finest level only and the fp16 pair form against the oracle for four
-  sampled items; full solves for the alphas whose trained CNN smoothers
-  converge (1e-1, 1e-2 and 1e-3).
+  sampled items; full solves at every alpha.
 """
 import os
 
@@ -148,11 +147,11 @@ def test_512_full_batch_one_cycle_sampled(ctx, c3f, alpha, prec, tol):
     assert np.max(rel(u, ref)) < tol
 
 
-@pytest.mark.parametrize("alpha,max_cycles", [(1e-1, 100), (1e-2, 100), (1e-3, 250)])
+@pytest.mark.parametrize("alpha,max_cycles", [(1e-1, 100), (1e-2, 100), (1e-3, 250), (1e-4, 400)])
 def test_512_full_batch_solve_sampled(ctx, c3f, alpha, max_cycles):
-    """The alphas whose sigma-4 CNN smoothers converge reach 1e-6 on the
-    whole 64-RHS batch (checked with the oracle's own apply); about 50 cycles
-    at alpha 1e-3."""
+    """Every alpha of the sweep reaches 1e-6 on the whole 64-RHS batch
+    (checked with the oracle's own apply); about 50 cycles at alpha 1e-3 and
+    300 at alpha 1e-4."""
     W = nmg.load_weights(os.path.join(WDIR, f"c3_2d_n512_s4_a{alpha:.0e}".replace("e-0", "e-") + ".npz"))
     taps = I.gaussian_taps(4.0)
     H = O.build_hierarchy_2d(taps, 512, alpha, 7)
