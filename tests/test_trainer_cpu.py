@@ -61,6 +61,25 @@ def test_trainer_cycle_equals_oracle_cycle(zero_out_bias):
     assert np.max(np.abs(xt - xo)) <= 1e-11 * np.max(np.abs(xo))
 
 
+def test_evaluation_is_the_refined_outer_iteration():
+    """The trainer's evaluation runs x^t = NMGF(x^{t-1}, f) with the residual
+    and update in fp64 around its fp32 cycle: its residual history over
+    three cycles equals the FP64 oracle's iteration to fp32 rounding."""
+    nets = _nets(0)
+    W = _weights(nets, False)
+    nets32 = [n.float() for n in nets]
+    prob = T.Problem(2, N, L, ALPHA, taps=I.gaussian_taps(SIGMA), dtype=torch.float32)
+    f = np.random.default_rng(5).standard_normal((2, N, N)).astype(np.float32)
+    cyc, hist = T.evaluate(prob, nets32, torch.tensor(f), rtol=0.0, max_cycles=3)
+    H = O.build_hierarchy_2d(I.gaussian_taps(SIGMA), N, ALPHA, L)
+    f64 = f.astype(np.float64)
+    u = np.zeros_like(f64)
+    for t in range(3):
+        u = O.nmgf(H, W, 0, u, f64)
+        rr = np.max(O.relres(H, f64, u))
+        assert abs(hist[t] - rr) <= 1e-4 * rr, (t, hist[t], rr)
+
+
 def test_data_generation_pairs():
     nets = _nets(1)
     prob = _problem()
