@@ -37,3 +37,32 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_every_bench_operator_class_has_a_smoother_set():
+    """The mixed-batch and serving legs draw their smoother sets from the
+    package's operator table: every class they use has a stored file, cut or
+    extended to the class's levels."""
+    from paper_2603_01064_gb300.weights import operator_weights
+    for n in bench.MIXED["sizes"]:
+        for sg in bench.MIXED["sigmas"]:
+            for al in bench.MIXED["alphas"]:
+                L = n.bit_length() - 3  # log2(n) - 2
+                assert len(operator_weights(sg, al, L)) == L - 1
+    for n, L, sg, W in bench.serving_classes():
+        assert len(W) == L - 1 and L == n.bit_length() - 3
+
+
+def test_issued_mma_work_per_pixel():
+    """Issued MMA flops per output pixel of the hidden convs: 6 products for
+    three bf16 terms, 3 for the pair forms, 1 for one bf16; the form with
+    three terms on the finest level only weights the two by pixels."""
+    alg = bench.FLOPS_PER_PX["cnn_hidden"]
+    assert bench.mma_flops_per_px("bf16_refine", "cnn_hidden", 512, 7) == 6 * alg
+    assert bench.mma_flops_per_px("bf16x3_refine", "cnn_hidden", 512, 7) == 3 * alg
+    assert bench.mma_flops_per_px("fp16_refine", "cnn_hidden", 512, 7) == 3 * alg
+    assert bench.mma_flops_per_px("bf16fast_refine", "cnn_hidden", 512, 7) == alg
+    px = [(512 >> l) ** 2 for l in range(6)]
+    f0 = px[0] / sum(px)
+    top = bench.mma_flops_per_px("bf16top_refine", "cnn_hidden", 512, 7)
+    assert abs(top - (6 * f0 + 3 * (1 - f0)) * alg) < 1e-6 * alg
